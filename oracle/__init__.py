@@ -1,0 +1,215 @@
+"""FP64 CPU oracle for the time-domain Helmholtz preconditioner (test infrastructure).
+
+This package is the checker, not the product.  Only the test suite, the smoke
+check and the benchmark's CPU-baseline / reference leg may import it.  It wraps
+``htd_oracle.c`` (plain C, double precision) with ctypes and shares no code with
+the CUDA library.
+
+Functions take a ``workloads.Problem`` (grid, c per cell, R per node, physical
+omega, T, rho) and a stencil name ("q1mix" or "fd5").
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "htd_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+
+STENCILS = {"q1mix": 0, "fd5": 1}
+MODES = {"table1": 0, "exact": 1}
+PRECONDS = {"identity": 0, "table1": 1, "exact": 2, "direct": 3}
+KRYLOV = {"fgmres": 0, "left": 1}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/liboracle.so`` (gcc, -O2, no fast-math)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
+                               "-fno-fast-math", "-ffp-contract=off",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_longlong * 3), ("h", ctypes.c_double),
+                ("stencil", ctypes.c_int), ("c_cell", ctypes.c_void_p),
+                ("R_node", ctypes.c_void_p), ("omega_phys", ctypes.c_double)]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("k_min", ctypes.c_double), ("k_max", ctypes.c_double),
+                ("omega", ctypes.c_double), ("lam_max_reH", ctypes.c_double),
+                ("lam_max_A", ctypes.c_double), ("nP", ctypes.c_int),
+                ("dt", ctypes.c_double), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
+                ("T", ctypes.c_int), ("rho", ctypes.c_double), ("nsteps", ctypes.c_longlong)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int),
+                ("precond_applies", ctypes.c_int), ("converged", ctypes.c_int),
+                ("rel_res_true", ctypes.c_double), ("rel_res_est", ctypes.c_double),
+                ("hist_len", ctypes.c_int), ("hist", ctypes.c_double * 4096)]
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        P = ctypes.POINTER(_Problem)
+        Q = ctypes.POINTER(_Params)
+        vp = ctypes.c_void_p
+        lib.ora_tables.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp]
+        lib.ora_setup.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_int, Q]
+        lib.ora_apply_reH.argtypes = [P, vp, ctypes.c_longlong, vp]
+        lib.ora_apply_H.argtypes = [P, vp, vp]
+        lib.ora_assemble_H.argtypes = [P, ctypes.c_longlong, vp, vp, vp, vp]
+        lib.ora_assemble_H.restype = ctypes.c_longlong
+        lib.ora_window.argtypes = [ctypes.c_double, ctypes.c_double]
+        lib.ora_window.restype = ctypes.c_double
+        lib.ora_acd_step.argtypes = [P, Q, vp, vp, vp, vp]
+        lib.ora_precond.argtypes = [P, Q, ctypes.c_int, vp, vp]
+        lib.ora_direct_solve.argtypes = [P, vp, vp]
+        lib.ora_gmres.argtypes = [P, Q, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_double,
+                                  ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                  ctypes.POINTER(_Info)]
+        _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+class Oracle:
+    """One problem bound to the C oracle.  Keeps its input arrays alive."""
+
+    def __init__(self, prob, stencil: str = "q1mix", nP: int = 0, T: int | None = None,
+                 rho: float | None = None):
+        self.lib = _load()
+        self.prob = prob
+        self.ndim = prob.ndim
+        self.n = tuple(int(m) for m in prob.n)
+        self.N = int(np.prod(self.n))
+        self.c = np.ascontiguousarray(prob.c_cell, dtype=np.float64)
+        self.R = np.ascontiguousarray(prob.R_node, dtype=np.float64)
+        assert self.c.size == int(np.prod([m + 1 for m in self.n]))
+        assert self.R.size == self.N
+        p = _Problem()
+        p.ndim = prob.ndim
+        for a in range(3):
+            p.n[a] = self.n[a] if a < prob.ndim else 1
+        p.h = prob.h
+        p.stencil = STENCILS[stencil]
+        p.c_cell = _ptr(self.c)
+        p.R_node = _ptr(self.R)
+        p.omega_phys = prob.omega
+        self._p = p
+        self.params = _Params()
+        rc = self.lib.ora_setup(ctypes.byref(p), int(prob.T if T is None else T),
+                                float(prob.rho if rho is None else rho), int(nP),
+                                ctypes.byref(self.params))
+        if rc != 0:
+            raise ValueError(f"oracle setup failed (rc={rc})")
+
+    # ---- parameters -------------------------------------------------------
+    def param_dict(self) -> dict:
+        q = self.params
+        return {f: getattr(q, f) for f, _ in _Params._fields_}
+
+    # ---- operator ---------------------------------------------------------
+    def _c(self, x) -> np.ndarray:
+        x = np.ascontiguousarray(np.asarray(x, dtype=np.complex128).reshape(-1))
+        assert x.size == self.N
+        return x
+
+    def apply_H(self, U) -> np.ndarray:
+        U = self._c(U)
+        out = np.empty_like(U)
+        self.lib.ora_apply_H(ctypes.byref(self._p), _ptr(U), _ptr(out))
+        return out.reshape(self.n)
+
+    def apply_reH(self, u) -> np.ndarray:
+        u = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(-1))
+        out = np.empty_like(u)
+        self.lib.ora_apply_reH(ctypes.byref(self._p), _ptr(u), 1, _ptr(out))
+        return out.reshape(self.n)
+
+    def assemble_H(self):
+        """(rows, cols, values) triplets of H; duplicates are to be summed."""
+        cnt = self.lib.ora_assemble_H(ctypes.byref(self._p), 0, None, None, None, None)
+        rows = np.empty(cnt, np.int64)
+        cols = np.empty(cnt, np.int64)
+        re = np.empty(cnt)
+        im = np.empty(cnt)
+        self.lib.ora_assemble_H(ctypes.byref(self._p), cnt, _ptr(rows), _ptr(cols),
+                                _ptr(re), _ptr(im))
+        return rows, cols, re + 1j * im
+
+    def H_sparse(self):
+        import scipy.sparse as sp
+        r, c, v = self.assemble_H()
+        return sp.csr_matrix((v, (r, c)), shape=(self.N, self.N))
+
+    # ---- method -----------------------------------------------------------
+    def window(self, s: float, rho: float | None = None) -> float:
+        return self.lib.ora_window(float(s), float(self.params.rho if rho is None else rho))
+
+    def acd_step(self, un, unm1, fn) -> np.ndarray:
+        un, unm1, fn = self._c(un), self._c(unm1), self._c(fn)
+        out = np.empty_like(un)
+        self.lib.ora_acd_step(ctypes.byref(self._p), ctypes.byref(self.params),
+                              _ptr(un), _ptr(unm1), _ptr(fn), _ptr(out))
+        return out.reshape(self.n)
+
+    def precond(self, F, mode: str = "table1") -> np.ndarray:
+        F = self._c(F)
+        out = np.empty_like(F)
+        rc = self.lib.ora_precond(ctypes.byref(self._p), ctypes.byref(self.params),
+                                  MODES[mode], _ptr(F), _ptr(out))
+        if rc:
+            raise ValueError("bad mode")
+        return out.reshape(self.n)
+
+    def direct_solve(self, F) -> np.ndarray:
+        F = self._c(F)
+        out = np.empty_like(F)
+        if self.lib.ora_direct_solve(ctypes.byref(self._p), _ptr(F), _ptr(out)):
+            raise ArithmeticError("singular H")
+        return out.reshape(self.n)
+
+    def gmres(self, F, krylov: str = "fgmres", precond: str = "table1", tol: float = 1e-6,
+              restart: int = 20, maxit: int = 200, fixed: bool = False, U0=None):
+        F = self._c(F)
+        U = np.zeros_like(F) if U0 is None else self._c(U0).copy()
+        info = _Info()
+        rc = self.lib.ora_gmres(ctypes.byref(self._p), ctypes.byref(self.params),
+                                KRYLOV[krylov], PRECONDS[precond], _ptr(F), _ptr(U),
+                                float(tol), int(restart), int(maxit), int(bool(fixed)),
+                                ctypes.byref(info))
+        if rc:
+            raise ValueError("gmres failed")
+        d = {f: getattr(info, f) for f, _ in _Info._fields_ if f != "hist"}
+        d["hist"] = list(info.hist[: info.hist_len])
+        return U.reshape(self.n), d
+
+
+def tables(ndim: int, stencil: str = "q1mix"):
+    """(S, M) Hamming-distance tables used by the oracle (length ndim + 1)."""
+    lib = _load()
+    S = np.zeros(4)
+    M = np.zeros(4)
+    if lib.ora_tables(ndim, STENCILS[stencil], _ptr(S), _ptr(M)):
+        raise ValueError("bad stencil")
+    return S[: ndim + 1].copy(), M[: ndim + 1].copy()

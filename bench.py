@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Benchmark of the time-domain preconditioned FGMRES solver on one GB300.
+
+One step = one complete solve of H U = F to a true relative residual of 1e-6
+(preconditioner split, T n_P recurrence steps per application, snapshot /
+join, true-operator residual, FP64 Arnoldi and Givens, solution update) on the
+2-D 1001 x 1001 heterogeneous workload: h = 1/1000, c a seeded smooth Gaussian
+random field (correlation length 0.05, clipped to [1.5, 4.5]), omega for 8
+points per wavelength at min c, 40-cell absorbing layer, one centre point
+source, T = 125 periods, n_P = 12 (1500 steps per application), FGMRES(20),
+FP32 recurrence with FP64 Krylov ("mixed").
+
+Printed (one JSON line on rank 0):
+  value       recurrence grid-point updates per second over the whole solve,
+              all ranks (Gupd/s), device time (CUDA events on the solve stream),
+              L2 flushed (256 MiB write) between timed steps;
+  roofline    the step kernel: algorithmic bytes per launch / average launch
+              time, measured live (events around every preconditioner
+              application), against the measured HBM copy bandwidth;
+  e2e         the same metric through htd_gmres_solve_host with pinned host
+              buffers, host<->device copies inside the timed region;
+  time_to_tol_ms / fp64_time_to_tol_ms / speedup_vs_fp64
+              the solve time in mixed and in plain FP64 mode on the same GPU;
+  cpu_baseline the FP64 CPU oracle on a bounded sample of the same workload.
+
+--impl reference times the oracle (the CPU reference of this build) on the
+same workload and metric.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "recurrence Gpt-updates/s & %HBM peak; GMRES time-to-1e-6 vs FP64 plain"
+UNIT = "Gupd/s"
+TOL = 1e-6
+BYTES_PER_UPDATE = {"f32": 28, "f64": 56}   # u_j, u_{j-1}, q*kappa, d, Re F, Im F read; u_{j+1} written
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="2d_grf_1001", choices=["2d_grf_1001", "3d_layered_256",
+                                                                   "2d_const_101"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--cpu-sample-s", type=float, default=10.0)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    return ap.parse_args()
+
+
+def make_workload(name, rank=0):
+    from paper_2006_16861_gb300 import workloads as W
+    if name == "2d_grf_1001":
+        p = W.config_2d_heterogeneous(1001)
+        desc = ("2-D 1001x1001 heterogeneous (GRF c in [1.5,4.5], corr 0.05), h=1/1000, "
+                "8 ppw at min c, 40-cell layer R0=2w, point source, T=125, rho=0.25")
+    elif name == "3d_layered_256":
+        p = W.config_3d_layered(256)
+        desc = ("3-D 256^3 4-layer c [1.5..4.5] x (1+0.1 GRF), h=1/255, 8 ppw at min c, "
+                "24-cell layer R0=2w, point source, T=32, rho=0.25")
+    else:
+        p = W.config_2d_constant(101)
+        desc = "2-D 101x101 constant c=1, h=0.01, 10 ppw, 20-cell layer, point source, T=10"
+    if rank:
+        # weak scaling: every rank solves its own independent instance (source moved)
+        pos = tuple((m - 1) // 2 + (rank * 7) % max(1, m // 4) for m in p.n)
+        p.F = W.point_source(p.ndim, p.n, p.h, pos=pos)
+    return p, desc
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:  # noqa: BLE001 - fall back to the recipe's figure
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:  # noqa: BLE001 - no nvidia-smi: no clock record
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:  # noqa: BLE001
+            self.proc.kill()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [x for x in sm if x >= 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax),
+                "power_w_max": max(power), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_baseline(p, budget_s):
+    """The FP64 oracle (single thread) on a bounded sample: one Table 1 application
+    with T_sample periods on the same grid.  Returns (Gupd/s, description)."""
+    import oracle
+    o1 = oracle.Oracle(p, T=1)
+    t0 = time.perf_counter()
+    o1.precond(p.F)
+    t1 = time.perf_counter() - t0
+    T_sample = int(max(1, min(p.T, math.floor(budget_s / max(t1, 1e-3)))))
+    o = oracle.Oracle(p, T=T_sample)
+    t0 = time.perf_counter()
+    o.precond(p.F)
+    dt = time.perf_counter() - t0
+    ups = math.prod(p.n) * o.params.nsteps
+    return ups / dt / 1e9, (f"oracle Table-1 preconditioner, {T_sample} periods "
+                            f"({o.params.nsteps} steps) on the full grid, {dt:.1f} s")
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    p, desc = make_workload(args.workload)
+    # each step: a bounded sample (2 periods of the recurrence) of the workload
+    o = oracle.Oracle(p, T=2)
+    ups = math.prod(p.n) * o.params.nsteps
+    for _ in range(args.warmup):
+        o.precond(p.F)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        o.precond(p.F)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = ups * len(times) / total / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": args.workload, "description": desc,
+                                        "sample": "2 periods of the recurrence per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"oracle Table-1 preconditioner, 2 periods "
+                                   f"({o.params.nsteps} steps) per step, full grid"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2006_16861_gb300 import htd
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def allmax(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def allsum(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    p, desc = make_workload(args.workload, rank)
+    N = math.prod(p.n)
+    stream = torch.cuda.current_stream()
+    F = torch.from_numpy(np.ascontiguousarray(p.F)).cuda()
+    U = torch.zeros_like(F)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    solver = htd.Solver(p, precision="mixed", mode="table1", krylov="fgmres", restart=20)
+    prm = solver.params
+
+    def solve_once():
+        U.zero_()
+        return htd.htd_gmres_solve(solver.handle, F, U, TOL, 400, stream)
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        solve_once()
+    torch.cuda.synchronize()
+
+    props = torch.cuda.get_device_properties(local)
+    gpu_id = f"GPU-{props.uuid}" if hasattr(props, "uuid") else str(local)
+    clocks = ClockSampler(gpu_id)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ms_steps, ups, launches, ms_prec, steps_run, its, rels = [], 0, 0, 0.0, 0, [], []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        flush.fill_(2)                       # evict L2 between timed steps
+        e0.record(stream)
+        info = solve_once()
+        e1.record(stream)
+        e1.synchronize()
+        ms_steps.append(e0.elapsed_time(e1))
+        ups += N * info["steps"]
+        launches += info["launches"]
+        ms_prec += info["ms_precond"]
+        steps_run += info["steps"]
+        its.append(info["iterations"])
+        rels.append(info["rel_res_true"])
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    total_ms = allmax(sum(ms_steps))
+    all_ups = allsum(ups)
+    value = all_ups / (total_ms * 1e-3) / 1e9
+
+    # roofline of the step kernel: algorithmic bytes per launch / average launch time
+    avg_launch_s = ms_prec * 1e-3 / max(1, steps_run)
+    bytes_per_launch = N * BYTES_PER_UPDATE["f32"]
+    achieved = bytes_per_launch / avg_launch_s / 1e9
+    peak, peak_kind = peaks()
+    l2_resident = bytes_per_launch < 96 * (1 << 20)
+
+    # e2e: host buffers through the C ABI (copies inside the timed region)
+    e2e = None
+    if args.e2e_steps > 0:
+        Fh = torch.from_numpy(np.ascontiguousarray(p.F)).pin_memory()
+        Uh = torch.zeros_like(Fh).pin_memory()
+        Fn, Un = Fh.numpy(), Uh.numpy()
+        Un[...] = 0
+        htd.htd_gmres_solve_host(solver.handle, Fn, Un, TOL, 400, stream)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        e_ups = 0
+        for _ in range(args.e2e_steps):
+            Un[...] = 0
+            info = htd.htd_gmres_solve_host(solver.handle, Fn, Un, TOL, 400, stream)
+            e_ups += N * info["steps"]
+        torch.cuda.synchronize()
+        wall = allmax(time.perf_counter() - t0)
+        e2e = {"value": allsum(e_ups) / wall / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": 2 * Fn.nbytes, "d2h_bytes_per_step": Un.nbytes,
+               "ms_per_step": 1e3 * wall / args.e2e_steps}
+    solver.close()
+
+    # plain FP64 GPU form on the same workload: time to 1e-6
+    fp64_ms = None
+    fp64_info = None
+    if args.fp64_steps > 0:
+        s64 = htd.Solver(p, precision="fp64", mode="table1", krylov="fgmres", restart=20)
+        U.zero_()
+        htd.htd_gmres_solve(s64.handle, F, U, TOL, 400, stream)
+        t = []
+        for _ in range(args.fp64_steps):
+            flush.fill_(3)
+            U.zero_()
+            e0.record(stream)
+            fp64_info = htd.htd_gmres_solve(s64.handle, F, U, TOL, 400, stream)
+            e1.record(stream)
+            e1.synchronize()
+            t.append(e0.elapsed_time(e1))
+        fp64_ms = allmax(statistics.mean(t))
+        s64.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and args.cpu_sample_s > 0:
+        import oracle
+        oracle.build()
+        v, sample = cpu_baseline(p, args.cpu_sample_s)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+    ms_per_step = total_ms / args.steps
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "dtype_detail": "recurrence f32; Arnoldi, Givens, true residual f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc, "n": list(p.n),
+                       "T": prm["T"], "nP": prm["nP"], "steps_per_apply": prm["steps"],
+                       "krylov": "FGMRES(20)", "tol": TOL, "mode": "table1",
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "parallelism": f"independent instance per GPU x{world}"},
+            "time_to_tol_ms": ms_per_step,
+            "fp64_time_to_tol_ms": fp64_ms,
+            "speedup_vs_fp64": (fp64_ms / ms_per_step) if fp64_ms else None,
+            "iterations": its[-1], "rel_res_true": max(rels),
+            "fp64_iterations": fp64_info["iterations"] if fp64_info else None,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "step2d_kernel<float>" if p.ndim == 2 else "step3d_kernel<float>",
+                         "bytes_per_launch": bytes_per_launch,
+                         "avg_launch_us": avg_launch_s * 1e6,
+                         "peak_kind": f"{peak_kind} HBM copy bandwidth",
+                         "l2_resident": l2_resident},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,207 @@
+/*
+ * htd.h -- C ABI of the GB300 time-domain Helmholtz preconditioner library
+ * (libhtd.so).  Method: C. C. Stolk, "A time-domain preconditioner for the
+ * Helmholtz equation" (arXiv 2006.16861).
+ *
+ * The library solves H U = F for the damped Helmholtz operator of Sec. 1,
+ *     -Delta U - (omega/c)^2 U + i omega R U = F,   zero Dirichlet data,
+ * discretised on a regular grid by the compact-stencil cell form of App. A
+ * (9 points in 2-D, 27 in 3-D).  The preconditioner is Table 1
+ * (TimeDomainPreconditioner): T n_P steps of the frequency-adapted leapfrog
+ * recurrence I_acd (Def. of I_acd) driven by the windowed time-harmonic
+ * forcing (Def. approx_solver), used inside restarted GMRES (Sec. 2.4).
+ *
+ * Conventions (all entry points):
+ *  - Plain C types only.  Pointers named *_dev are CUDA device pointers on the
+ *    handle's device; pointers named *_host are host pointers.
+ *  - Grid: n[a] unknown nodes per axis at x_i = i h (a < ndim), zero ghost
+ *    ring at i = -1 and i = n[a].  Node arrays have prod(n[a]) entries,
+ *    row-major with the last axis fastest.  Cell arrays have prod(n[a] + 1)
+ *    entries; cell a (lower-corner node index a = -1 .. n-1 per axis) is stored
+ *    at a + 1, its wave speed applies on [a h, (a+1) h].
+ *  - Complex vectors are complex128, interleaved (re, im), node layout.
+ *  - The caller owns every buffer it passes; the handle owns its internal
+ *    device workspaces (allocated by htd_create, freed by htd_destroy).
+ *  - Every call returns an htd_status.  No exception or abort crosses the ABI.
+ *    On error, outputs are unspecified; the handle stays usable except after
+ *    HTD_ERR_CUDA.
+ *  - A handle is not thread-safe.  Work is enqueued on the given CUDA stream
+ *    (NULL = the legacy default stream); calls that return host values
+ *    (htd_gmres_solve, htd_residual_norm) synchronise that stream.
+ */
+#ifndef HTD_H
+#define HTD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct htd_ctx *htd_handle;
+
+typedef enum {
+    HTD_OK = 0,
+    HTD_ERR_ARG = 1,            /* invalid argument (null pointer, bad size or option) */
+    HTD_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+    HTD_ERR_OOM = 3,            /* device allocation failed */
+    HTD_ERR_UNSTABLE = 4,       /* requested n_P violates the CFL bound, or not a multiple of 4 */
+    HTD_ERR_NONFINITE = 5,      /* NaN/Inf in an input or a residual norm */
+    HTD_ERR_NOT_CONVERGED = 6,  /* iteration cap reached before the tolerance */
+    HTD_ERR_TIMEOUT = 7         /* a bounded device-side wait gave up */
+} htd_status;
+
+enum { HTD_FP64 = 0, HTD_MIXED = 1 };            /* recurrence precision */
+enum { HTD_MODE_TABLE1 = 0, HTD_MODE_EXACT = 1 }; /* preconditioner form */
+enum { HTD_FGMRES = 0, HTD_LEFT_GMRES = 1 };     /* Krylov method */
+enum { HTD_STENCIL_Q1MIX = 0, HTD_STENCIL_FD5 = 1 };
+enum { HTD_BC_DIRICHLET = 0 };
+
+typedef struct {
+    int ndim;          /* 2 or 3 */
+    int64_t n[3];      /* unknown nodes per axis, n[a] >= 1 for a < ndim */
+    double h;          /* grid spacing > 0 */
+} htd_grid;
+
+typedef struct {
+    int precision;     /* HTD_FP64: recurrence in double; HTD_MIXED: recurrence in
+                          float, Krylov, residual and Givens in double */
+    int mode;          /* HTD_MODE_TABLE1: Table 1, one real run, U = u_{T n_P} +
+                          i u_{(T-1/4) n_P}.  HTD_MODE_EXACT: S_T^acd F of
+                          Def. approx_solver, two real runs (forcings F and -iF) */
+    int krylov;        /* HTD_FGMRES (flexible right preconditioning, default) or
+                          HTD_LEFT_GMRES (left preconditioning, Sec. 2.4) */
+    int T;             /* periods per preconditioner application, >= 1 */
+    double rho;        /* window parameter in [0, 1]; 0 means a ramp over one
+                          period (rho = 1/T), as in Sec. 5.1 */
+    int nP;            /* time steps per period; 0 = smallest stable multiple of 4 */
+    int stencil;       /* HTD_STENCIL_Q1MIX or HTD_STENCIL_FD5 */
+    int restart;       /* Krylov restart length m for htd_gmres_solve, 1..64 */
+} htd_options;
+
+typedef struct {
+    int iterations;           /* Arnoldi steps taken */
+    int restarts;             /* Krylov cycles started */
+    int precond_applies;      /* preconditioner applications */
+    int converged;            /* 1 if the true relative residual <= tol */
+    long long steps;          /* recurrence steps run (all applications) */
+    double rel_res_true;      /* ||F - H U|| / ||F|| at exit (FP64) */
+    double rel_res_est;       /* last Arnoldi residual estimate */
+    double ms_total;          /* wall time of the call, host clock */
+    double ms_precond;        /* device time inside preconditioner applications,
+                                 CUDA events on the call's stream */
+    long long launches;       /* kernels launched by the call (graph nodes counted) */
+    int hist_len;
+    double hist[256];         /* Arnoldi estimate after each step (first 256) */
+} htd_solve_info;
+
+/* Fill *opt with the defaults: FP64, TABLE1, FGMRES, T = 10, rho = 0.25,
+ * nP = 0 (automatic), Q1MIX stencil, restart 20. */
+void htd_default_options(htd_options *opt);
+
+/*
+ * Create a solver for one problem on the current CUDA device.
+ *   grid        grid description (see conventions).
+ *   c_cell_host wave speed per cell, prod(n+1) doubles > 0, host memory.
+ *   R_node_host damping per node, prod(n) doubles >= 0, host memory
+ *               ((Im H)_ii = omega_phys * R_i, Sec. 1 damped Helmholtz eq.).
+ *   omega_phys  physical angular frequency > 0.
+ *   bc          HTD_BC_DIRICHLET (the only boundary condition).
+ *   opt         options (NULL = defaults).
+ * Parameter selection (Sec. 2.2 with the bounds of App. A): omega = k_max =
+ * max omega_phys / c; lambda_max(Re H) bounded by the constant-coefficient
+ * symbol at k_min; n_P the smallest multiple of 4 with
+ * sin^2(pi / n_P) < omega^2 / lambda_max(A) (Eq. define_Deltat_ImH_diagonal);
+ * dt = 2 pi / (omega n_P); alpha, beta of Eq. define_alpha_beta.
+ * Errors: HTD_ERR_ARG, HTD_ERR_UNSTABLE (bad requested nP), HTD_ERR_NONFINITE,
+ * HTD_ERR_OOM, HTD_ERR_CUDA.  *out is set only on success.
+ */
+htd_status htd_create(const htd_grid *grid, const double *c_cell_host,
+                      const double *R_node_host, double omega_phys, int bc,
+                      const htd_options *opt, htd_handle *out);
+
+/* Release the handle and its device memory.  NULL is accepted. */
+htd_status htd_destroy(htd_handle h);
+
+/* Parameters selected for a problem (see htd_plan). */
+typedef struct {
+    double k_min, k_max;     /* min / max of omega_phys / c over cells */
+    double omega_c;          /* computational omega (= k_max, App. A bound) */
+    double lam_max_reH;      /* upper bound for lambda_max(Re H) */
+    double lam_max_A;        /* lam_max_reH + omega_c^2 */
+    double dt, alpha, beta;  /* time step, Eq. define_alpha_beta */
+    double rho;              /* window parameter used (1/T when 0 was asked) */
+    int nP;                  /* time steps per period */
+    int T;                   /* periods */
+    long long steps;         /* recurrence steps per real run: T * nP */
+} htd_params;
+
+/*
+ * Host-only parameter selection (no CUDA call, no allocation): validates the
+ * arguments exactly as htd_create does and fills *out.  Same arguments as
+ * htd_create; errors HTD_ERR_ARG, HTD_ERR_UNSTABLE, HTD_ERR_NONFINITE.
+ */
+htd_status htd_plan(const htd_grid *grid, const double *c_cell_host, const double *R_node_host,
+                    double omega_phys, int bc, const htd_options *opt, htd_params *out);
+
+/* Parameters chosen by htd_create. */
+htd_status htd_get_params(htd_handle h, htd_params *out);
+
+/*
+ * U = P F: one application of the preconditioner (Table 1 or the exact S_T,
+ * per the handle's mode), in the handle's recurrence precision.
+ *   F_dev, U_dev  complex128[N] device vectors; they may not overlap.
+ *   stream        cudaStream_t (as void*), NULL = default stream.
+ * Asynchronous: returns after enqueueing.
+ */
+htd_status htd_apply_precond(htd_handle h, const void *F_dev, void *U_dev, void *stream);
+
+/*
+ * Y = H X, the true operator in complex128 (App. A cell form plus
+ * i omega_phys R on the diagonal).  X_dev, Y_dev complex128[N], no overlap.
+ * Asynchronous.
+ */
+htd_status htd_apply_H(htd_handle h, const void *X_dev, void *Y_dev, void *stream);
+
+/*
+ * r = F - H U (complex128) and *rel = ||r|| / ||F|| (host double; 0 if F = 0).
+ * r_dev may be NULL (the residual is then kept in handle workspace).
+ * Synchronises the stream.  HTD_ERR_NONFINITE if the norm is not finite.
+ */
+htd_status htd_residual_norm(htd_handle h, const void *F_dev, const void *U_dev,
+                             void *r_dev, double *rel, void *stream);
+
+/*
+ * Solve H U = F with restarted GMRES(m), m = opt.restart (Sec. 2.4): flexible
+ * right preconditioning (default) or left preconditioning, preconditioner P of
+ * the handle, Arnoldi by classical Gram-Schmidt with one reorthogonalisation
+ * in FP64, Givens least squares on the host.
+ *   F_dev      complex128[N] right-hand side (device).
+ *   U_dev      complex128[N] (device): initial guess on entry, solution on exit.
+ *   tol        stop when the Arnoldi estimate and the true relative residual
+ *              ||F - H U|| / ||F|| are <= tol.  tol <= 0: run exactly
+ *              max_iters Arnoldi steps with no early exit (returns HTD_OK).
+ *   max_iters  cap on Arnoldi steps (>= 0).
+ *   info       optional statistics (NULL allowed).
+ * Synchronises the stream.  HTD_ERR_NOT_CONVERGED if the cap is reached
+ * first (U holds the last iterate), HTD_ERR_NONFINITE on NaN/Inf.
+ */
+htd_status htd_gmres_solve(htd_handle h, const void *F_dev, void *U_dev, double tol,
+                           int max_iters, void *stream, htd_solve_info *info);
+
+/*
+ * Same as htd_gmres_solve with host buffers: copies F_host (complex128[N],
+ * pinned memory recommended) and the initial guess U_host to handle-owned
+ * device buffers, solves, and copies the solution back to U_host.
+ */
+htd_status htd_gmres_solve_host(htd_handle h, const void *F_host, void *U_host, double tol,
+                                int max_iters, void *stream, htd_solve_info *info);
+
+/* Static string for a status code. */
+const char *htd_status_string(htd_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HTD_H */

@@ -302,28 +302,26 @@ void ora_apply_reH(const ora_problem *p, const double *u, long long stride, doub
     for (a3[2] = (d == 3 ? lo[2] : 0); a3[2] <= (d == 3 ? hi[2] : 0); ++a3[2]) {
         double k = p->omega_phys / p->c_cell[cell_lin(p, a3)];
         double kap = (p->h * k) * (p->h * k);
+        /* the cell's corners: node index, or -1 for a ghost node (u = 0 there) */
+        long long corner[8];
         for (int b = 0; b < ncorner; ++b) {
             long long ib[3];
-            int inside_b = 1;
+            int inside = 1;
             for (int t = 0; t < d; ++t) {
                 ib[t] = a3[t] + ((b >> (d - 1 - t)) & 1);
-                if (ib[t] < 0 || ib[t] >= p->n[t]) inside_b = 0;
+                if (ib[t] < 0 || ib[t] >= p->n[t]) inside = 0;
             }
-            if (!inside_b) continue;
-            long long lb = node_lin(p, ib);
+            corner[b] = inside ? node_lin(p, ib) : -1;
+        }
+        for (int b = 0; b < ncorner; ++b) {
+            if (corner[b] < 0) continue;
             double acc = 0.0;
             for (int g = 0; g < ncorner; ++g) {
-                long long ig[3];
-                int inside_g = 1;
-                for (int t = 0; t < d; ++t) {
-                    ig[t] = a3[t] + ((g >> (d - 1 - t)) & 1);
-                    if (ig[t] < 0 || ig[t] >= p->n[t]) inside_g = 0;
-                }
-                if (!inside_g) continue;
+                if (corner[g] < 0) continue;
                 int s = popcount_small((unsigned)(b ^ g));
-                acc += (S[s] - kap * M[s]) * u[node_lin(p, ig) * stride];
+                acc += (S[s] - kap * M[s]) * u[corner[g] * stride];
             }
-            out[lb * stride] += ih2 * acc;
+            out[corner[b] * stride] += ih2 * acc;
         }
     }
 }

@@ -1,0 +1,798 @@
+// C ABI of libhtd (declared in include/htd.h): problem set-up, parameter
+// selection, the preconditioner driver and the restarted (F)GMRES driver.
+// Method: C. C. Stolk, "A time-domain preconditioner for the Helmholtz
+// equation" (arXiv 2006.16861).
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "htd.h"
+#include "htd_internal.h"
+
+using htd::Layout;
+using htd::OutSlot;
+using htd::StepCoef;
+typedef std::complex<double> zc;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kMaxRestart = 64;
+
+// ---------------------------------------------------------------------------
+// stencil weights per Hamming distance (App. A cell form, h = 1)
+// ---------------------------------------------------------------------------
+
+// Q1 elements factor into 1-D element matrices per axis: stiffness
+// k1 = [[1,-1],[-1,1]], consistent mass m1 = [[1/3,1/6],[1/6,1/3]].  For two
+// corners differing on s axes the d-D entries are
+//   stiffness: sum over axes of k1 on that axis times m1 on the others,
+//   consistent mass: prod of m1.
+// Q1MIX mass = half consistent + half lumped (2^-d on the diagonal).
+// FD5: each grid edge shared by 2^{d-1} cells carries weight w = 2^{1-d}, so a
+// corner has stiffness d w and its edge neighbours -w; lumped mass 2^-d.
+bool cell_weights(int d, int stencil, double S[4], double M[4])
+{
+    for (int s = 0; s < 4; ++s) { S[s] = 0.0; M[s] = 0.0; }
+    const double m_same = 1.0 / 3.0, m_diff = 1.0 / 6.0;
+    if (stencil == HTD_STENCIL_Q1MIX) {
+        for (int s = 0; s <= d; ++s) {
+            // axes that differ contribute k1 = -1 (and m1 = 1/6 when not differentiated)
+            double st = 0.0;
+            st += s * (-1.0) * std::pow(m_diff, s - 1) * std::pow(m_same, d - s);
+            st += (d - s) * (1.0) * std::pow(m_diff, s) * std::pow(m_same, d - s - 1);
+            S[s] = st;
+            double cons = std::pow(m_diff, s) * std::pow(m_same, d - s);
+            double lump = (s == 0) ? std::ldexp(1.0, -d) : 0.0;
+            M[s] = 0.5 * cons + 0.5 * lump;
+        }
+        return true;
+    }
+    if (stencil == HTD_STENCIL_FD5) {
+        double w = std::ldexp(1.0, 1 - d);
+        S[0] = d * w;
+        S[1] = -w;
+        M[0] = std::ldexp(1.0, -d);
+        return true;
+    }
+    return false;
+}
+
+double binom(int n, int k)
+{
+    if (k < 0 || k > n) return 0.0;
+    double r = 1.0;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return r;
+}
+
+// Eigenvalue of a Hamming-distance kernel f_s on {0,1}^d for Walsh functions
+// of weight w: sum_s f_s K_s(w), K_s the Krawtchouk polynomial.  2^d times it
+// is the constant-coefficient symbol at the vertex of [0,pi]^d with w
+// coordinates equal to pi.
+double walsh_eigen(int d, const double f[4], int w)
+{
+    double mu = 0.0;
+    for (int s = 0; s <= d; ++s) {
+        double K = 0.0;
+        for (int j = 0; j <= s; ++j) K += ((j & 1) ? -1.0 : 1.0) * binom(w, j) * binom(d - w, s - j);
+        mu += f[s] * K;
+    }
+    return mu;
+}
+
+// sine-squared window of the paper (Sec. 2.3), even, 1 on |s| <= 1 - rho
+double window_chi(double s, double rho)
+{
+    s = std::fabs(s);
+    if (s >= 1.0) return 0.0;
+    if (s <= 1.0 - rho) return 1.0;
+    const double v = std::sin(0.5 * kPi * (1.0 - s) / rho);
+    return v * v;
+}
+
+Layout make_layout(int d, const int64_t n[3], size_t esz)
+{
+    Layout L;
+    L.d = d;
+    L.nx = n[d - 1];
+    L.ny = n[d - 2];
+    L.nz = (d == 3) ? n[0] : 1;
+    const int64_t line = 128 / (int64_t)esz;       // elements per 128 bytes
+    L.xl = line;
+    L.pitch = ((L.xl + L.nx + 1 + line - 1) / line) * line;
+    L.plane = L.pitch * (L.ny + 2);
+    L.total = (d == 3) ? L.plane * (L.nz + 2) : L.plane;
+    L.N = L.nx * L.ny * L.nz;
+    return L;
+}
+
+}  // namespace
+
+struct htd_ctx {
+    int device = 0;
+    htd_options opt{};
+    int d = 0;
+    int64_t n[3] = {1, 1, 1};
+    double h = 0, omega_phys = 0;
+    // parameters
+    double kmin = 0, kmax = 0, omega = 0, lam_reH = 0, lam_A = 0, dt = 0, alpha = 0, beta = 0, rho = 0;
+    int nP = 0, T = 0;
+    long long nsteps = 0;
+    double S[4] = {0}, M[4] = {0};
+    Layout Lr{}, L64{};
+    size_t esz = 8;
+    // recurrence arrays (element type float or double)
+    void *kap = nullptr, *dco = nullptr, *fre = nullptr, *fim = nullptr, *u0 = nullptr, *u1 = nullptr;
+    std::vector<double> atab, btab;
+    StepCoef<double> C{};
+    // FP64 operator data
+    double *kap64 = nullptr, *imH = nullptr;
+    // Krylov workspace
+    int m = 20;
+    double2 *V = nullptr, *Z = nullptr, *w = nullptr, *t = nullptr, *r = nullptr;
+    double2 *partial = nullptr, *hdev = nullptr, *hhost = nullptr;
+    int nb = 1;
+    OutSlot *slot = nullptr;
+    double2 *Fh = nullptr, *Uh = nullptr;
+    // captured step sequence
+    cudaGraphExec_t exec = nullptr;
+    bool graph_tried = false;
+    long long steps_run = 0;
+    int applies = 0;
+    // device time of preconditioner applications (CUDA events on the call's stream)
+    cudaEvent_t pev[2] = {nullptr, nullptr};
+    bool pev_pending = false;
+    double ms_precond = 0.0;
+};
+
+namespace {
+
+#define HTD_CUDA(x)                                          \
+    do {                                                     \
+        cudaError_t e_ = (x);                                \
+        if (e_ != cudaSuccess) {                             \
+            (void)cudaGetLastError();                        \
+            return (e_ == cudaErrorMemoryAllocation) ? HTD_ERR_OOM : HTD_ERR_CUDA; \
+        }                                                    \
+    } while (0)
+
+template <typename T>
+StepCoef<T> cast_coef(const StepCoef<double> &c)
+{
+    StepCoef<T> o;
+    o.c0 = (T)c.c0;
+    for (int k = 0; k < 4; ++k) { o.cs[k] = (T)c.cs[k]; o.mt[k] = (T)c.mt[k]; }
+    return o;
+}
+
+void free_ctx(htd_ctx *c)
+{
+    if (!c) return;
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    for (cudaEvent_t e : c->pev)
+        if (e) cudaEventDestroy(e);
+    void *dev[] = {c->kap, c->dco, c->fre, c->fim, c->u0, c->u1, c->kap64, c->imH, c->V, c->Z,
+                   c->w, c->t, c->r, c->partial, c->hdev, c->slot, c->Fh, c->Uh};
+    for (void *p : dev)
+        if (p) cudaFree(p);
+    if (c->hhost) cudaFreeHost(c->hhost);
+    delete c;
+}
+
+// one preconditioner run of T n_P steps; the forcing planes are already filled
+template <typename T>
+htd_status run_steps_direct(htd_ctx *c, cudaStream_t s)
+{
+    const Layout &L = c->Lr;
+    const StepCoef<T> C = cast_coef<T>(c->C);
+    T *A = (T *)c->u0, *B = (T *)c->u1;
+    HTD_CUDA(cudaMemsetAsync(A, 0, sizeof(T) * L.total, s));
+    HTD_CUDA(cudaMemsetAsync(B, 0, sizeof(T) * L.total, s));
+    const long long jim = c->nsteps - c->nP / 4;
+    for (long long j = 0; j < c->nsteps; ++j) {
+        T *cur = (j & 1) ? B : A;
+        T *oth = (j & 1) ? A : B;
+        int flags = 0;
+        if (j + 1 == jim) flags |= 1;
+        if (j + 1 == c->nsteps) flags |= 2;
+        htd::launch_step<T>(L, cur, oth, (const T *)c->kap, (const T *)c->dco, (const T *)c->fre,
+                            (const T *)c->fim, C, (T)c->atab[j], (T)c->btab[j], c->slot, flags, s);
+    }
+    HTD_CUDA(cudaGetLastError());
+    return HTD_OK;
+}
+
+template <typename T>
+htd_status run_steps(htd_ctx *c, cudaStream_t s)
+{
+    static const bool no_graph = std::getenv("HTD_NO_GRAPH") != nullptr;
+    if (!no_graph && !c->graph_tried) {
+        c->graph_tried = true;
+        cudaStream_t cs;
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess) {
+            cudaGraph_t g = nullptr;
+            bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                const long long before = htd::g_launches;
+                htd_status st = run_steps_direct<T>(c, cs);
+                ok = cudaStreamEndCapture(cs, &g) == cudaSuccess && st == HTD_OK;
+                htd::g_launches = before;        // captured, not launched
+            }
+            if (ok && cudaGraphInstantiate(&c->exec, g, 0) != cudaSuccess) {
+                c->exec = nullptr;
+                ok = false;
+            }
+            if (g) cudaGraphDestroy(g);
+            cudaStreamDestroy(cs);
+            (void)cudaGetLastError();
+            if (!ok) c->exec = nullptr;
+        }
+    }
+    if (c->exec) {
+        HTD_CUDA(cudaGraphLaunch(c->exec, s));
+        htd::g_launches += c->nsteps;            // one step kernel per graph node
+        return HTD_OK;
+    }
+    return run_steps_direct<T>(c, s);
+}
+
+// add the elapsed time of the last timed preconditioner application
+htd_status collect_precond_time(htd_ctx *c)
+{
+    if (!c->pev_pending) return HTD_OK;
+    HTD_CUDA(cudaEventSynchronize(c->pev[1]));
+    float ms = 0.f;
+    HTD_CUDA(cudaEventElapsedTime(&ms, c->pev[0], c->pev[1]));
+    c->ms_precond += ms;
+    c->pev_pending = false;
+    return HTD_OK;
+}
+
+// U = P F (F, U compact complex128 on the device)
+htd_status precond(htd_ctx *c, const double2 *F, double2 *U, cudaStream_t s)
+{
+    const bool mixed = c->opt.precision == HTD_MIXED;
+    htd_status cst = collect_precond_time(c);
+    if (cst != HTD_OK) return cst;
+    HTD_CUDA(cudaEventRecord(c->pev[0], s));
+    double *Ure = reinterpret_cast<double *>(U);
+    const int runs = (c->opt.mode == HTD_MODE_EXACT) ? 2 : 1;
+    for (int run = 0; run < runs; ++run) {
+        // TABLE1: final state -> Re U, quarter-period-earlier snapshot -> Im U.
+        // EXACT: run 0 forcing F gives Re S_T F; run 1 forcing -iF gives Im S_T F.
+        if (mixed)
+            htd::launch_split<float>(c->Lr, F, (float *)c->fre, (float *)c->fim, run, s);
+        else
+            htd::launch_split<double>(c->Lr, F, (double *)c->fre, (double *)c->fim, run, s);
+        double *fin = Ure + run;
+        double *snap = (runs == 1) ? Ure + 1 : nullptr;
+        htd::launch_set_slot(c->slot, fin, snap, s);
+        HTD_CUDA(cudaGetLastError());
+        htd_status st = mixed ? run_steps<float>(c, s) : run_steps<double>(c, s);
+        if (st != HTD_OK) return st;
+        c->steps_run += c->nsteps;
+    }
+    HTD_CUDA(cudaEventRecord(c->pev[1], s));
+    c->pev_pending = true;
+    c->applies++;
+    return HTD_OK;
+}
+
+void apply_H(htd_ctx *c, const double2 *X, const double2 *F, double2 *Y, cudaStream_t s)
+{
+    double S2[4];
+    for (int k = 0; k < 4; ++k) S2[k] = std::ldexp(c->S[k], c->d - k);
+    htd::launch_apply_H(c->L64, c->kap64, c->imH, S2, c->M, 1.0 / (c->h * c->h), X, F, Y, s);
+}
+
+// dots of w with V_0..V_{k-1} into hdev + off (device); does not synchronise
+void dots_to(htd_ctx *c, const double2 *V, int k, const double2 *w, int off, cudaStream_t s)
+{
+    const int64_t N = c->Lr.N;
+    htd::launch_dots(V, N, k, w, N, c->partial, c->nb, s);
+    htd::launch_reduce(c->partial, c->nb, k, c->hdev + off, s);
+}
+
+// ||x|| (synchronises)
+htd_status norm(htd_ctx *c, const double2 *x, double *out, cudaStream_t s)
+{
+    dots_to(c, x, 1, x, 0, s);
+    HTD_CUDA(cudaMemcpyAsync(c->hhost, c->hdev, sizeof(double2), cudaMemcpyDeviceToHost, s));
+    HTD_CUDA(cudaStreamSynchronize(s));
+    const double v = c->hhost[0].x;
+    if (!std::isfinite(v)) return HTD_ERR_NONFINITE;
+    *out = std::sqrt(v > 0 ? v : 0.0);
+    return HTD_OK;
+}
+
+htd_status gmres(htd_ctx *c, const double2 *F, double2 *U, double tol, int maxit, cudaStream_t s,
+                 htd_solve_info *info)
+{
+    const auto t0 = std::chrono::steady_clock::now();
+    const int64_t N = c->Lr.N;
+    const int m = c->m;
+    const bool left = c->opt.krylov == HTD_LEFT_GMRES;
+    const bool fixed = !(tol > 0.0);
+    htd_solve_info loc;
+    std::memset(&loc, 0, sizeof(loc));
+    const int applies0 = c->applies;
+    const long long steps0 = c->steps_run;
+    const long long launches0 = htd::g_launches;
+    if (collect_precond_time(c) != HTD_OK) return HTD_ERR_CUDA;
+    const double msp0 = c->ms_precond;
+    htd_status st = HTD_OK;
+    double fnorm = 0.0, bnorm = 0.0;
+    std::vector<zc> Hm((size_t)(m + 1) * m), cs(m), g(m + 1), y(m);
+    std::vector<double> sn(m);
+    int its = 0;
+
+    if ((st = norm(c, F, &fnorm, s)) != HTD_OK) goto out;
+    if (fnorm == 0.0) {
+        HTD_CUDA(cudaMemsetAsync(U, 0, sizeof(double2) * N, s));
+        HTD_CUDA(cudaStreamSynchronize(s));
+        loc.converged = 1;
+        goto out;
+    }
+    bnorm = fnorm;
+    if (left) {
+        if ((st = precond(c, F, c->t, s)) != HTD_OK) goto out;
+        if ((st = norm(c, c->t, &bnorm, s)) != HTD_OK) goto out;
+        if (bnorm == 0.0) { st = HTD_ERR_NONFINITE; goto out; }
+    }
+    for (;;) {
+        // true residual r = F - H U
+        apply_H(c, U, F, c->r, s);
+        double rn;
+        if ((st = norm(c, c->r, &rn, s)) != HTD_OK) goto out;
+        loc.rel_res_true = rn / fnorm;
+        if (!fixed && loc.rel_res_true <= tol) { loc.converged = 1; break; }
+        if (its >= maxit) break;
+        const double2 *r0 = c->r;
+        if (left) {
+            if ((st = precond(c, c->r, c->w, s)) != HTD_OK) goto out;
+            r0 = c->w;
+        }
+        double beta;
+        if ((st = norm(c, r0, &beta, s)) != HTD_OK) goto out;
+        if (beta == 0.0) break;
+        loc.restarts++;
+        htd::launch_scale(r0, 1.0 / beta, c->V, N, s);
+        for (int k = 0; k <= m; ++k) g[k] = 0.0;
+        g[0] = beta;
+        int j = 0;
+        while (j < m && its < maxit) {
+            double2 *vj = c->V + (int64_t)j * N;
+            if (!left) {
+                double2 *zj = c->Z + (int64_t)j * N;
+                if ((st = precond(c, vj, zj, s)) != HTD_OK) goto out;
+                apply_H(c, zj, nullptr, c->w, s);
+            } else {
+                apply_H(c, vj, nullptr, c->t, s);
+                if ((st = precond(c, c->t, c->w, s)) != HTD_OK) goto out;
+            }
+            // classical Gram-Schmidt with one reorthogonalisation, FP64
+            const int k = j + 1;
+            dots_to(c, c->V, k, c->w, 0, s);
+            htd::launch_sub_combination(c->V, N, k, c->hdev, c->w, N, s);
+            dots_to(c, c->V, k, c->w, 72, s);
+            htd::launch_sub_combination(c->V, N, k, c->hdev + 72, c->w, N, s);
+            dots_to(c, c->w, 1, c->w, 144, s);
+            HTD_CUDA(cudaMemcpyAsync(c->hhost, c->hdev, sizeof(double2) * 145,
+                                     cudaMemcpyDeviceToHost, s));
+            HTD_CUDA(cudaStreamSynchronize(s));
+            HTD_CUDA(cudaGetLastError());
+            zc *col = &Hm[(size_t)j * (m + 1)];
+            for (int i = 0; i < k; ++i)
+                col[i] = zc(c->hhost[i].x + c->hhost[72 + i].x, c->hhost[i].y + c->hhost[72 + i].y);
+            const double hn2 = c->hhost[144].x;
+            if (!std::isfinite(hn2)) { st = HTD_ERR_NONFINITE; goto out; }
+            const double hn = std::sqrt(hn2 > 0 ? hn2 : 0.0);
+            col[j + 1] = hn;
+            if (hn > 0.0) htd::launch_scale(c->w, 1.0 / hn, c->V + (int64_t)(j + 1) * N, N, s);
+            // previous rotations, then a new one zeroing col[j+1]
+            for (int i = 0; i < j; ++i) {
+                const zc a = col[i], b = col[i + 1];
+                col[i] = std::conj(cs[i]) * a + sn[i] * b;
+                col[i + 1] = -sn[i] * a + cs[i] * b;
+            }
+            {
+                const zc a = col[j];
+                const double b = col[j + 1].real();
+                const double rr = std::sqrt(std::norm(a) + b * b);
+                if (rr == 0.0) { cs[j] = 1.0; sn[j] = 0.0; }
+                else { cs[j] = a / rr; sn[j] = b / rr; }
+                col[j] = std::conj(cs[j]) * a + sn[j] * b;
+                col[j + 1] = 0.0;
+                const zc gj = g[j];
+                g[j] = std::conj(cs[j]) * gj;
+                g[j + 1] = -sn[j] * gj;
+            }
+            ++its;
+            ++j;
+            const double est = std::abs(g[j]) / bnorm;
+            loc.rel_res_est = est;
+            if (loc.hist_len < 256) loc.hist[loc.hist_len++] = est;
+            if (!std::isfinite(est)) { st = HTD_ERR_NONFINITE; goto out; }
+            if (!fixed && est <= tol) break;
+            if (hn == 0.0) break;
+        }
+        // y = R^{-1} g; U += basis y
+        for (int i = j - 1; i >= 0; --i) {
+            zc acc = g[i];
+            for (int k2 = i + 1; k2 < j; ++k2) acc -= Hm[(size_t)k2 * (m + 1) + i] * y[k2];
+            y[i] = acc / Hm[(size_t)i * (m + 1) + i];
+        }
+        for (int i = 0; i < j; ++i) c->hhost[i] = make_double2(y[i].real(), y[i].imag());
+        HTD_CUDA(cudaMemcpyAsync(c->hdev, c->hhost, sizeof(double2) * j, cudaMemcpyHostToDevice, s));
+        htd::launch_add_combination(left ? c->V : c->Z, N, j, c->hdev, U, N, s);
+        // the host staging buffer is reused: wait for the copy before the next write
+        HTD_CUDA(cudaStreamSynchronize(s));
+    }
+    if (!fixed && !loc.converged) st = HTD_ERR_NOT_CONVERGED;
+    if (!std::isfinite(loc.rel_res_true)) st = HTD_ERR_NONFINITE;
+out:
+    if (collect_precond_time(c) != HTD_OK && st == HTD_OK) st = HTD_ERR_CUDA;
+    loc.ms_precond = c->ms_precond - msp0;
+    loc.launches = htd::g_launches - launches0;
+    loc.iterations = its;
+    loc.precond_applies = c->applies - applies0;
+    loc.steps = c->steps_run - steps0;
+    loc.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (info) *info = loc;
+    return st;
+}
+
+template <typename T>
+htd_status upload_recurrence(htd_ctx *c, const std::vector<double> &qkap, const std::vector<double> &dcoef)
+{
+    const Layout &L = c->Lr;
+    std::vector<T> a(L.total, (T)0), b(L.total, (T)0);
+    for (size_t i = 0; i < (size_t)L.total; ++i) { a[i] = (T)qkap[i]; b[i] = (T)dcoef[i]; }
+    HTD_CUDA(cudaMemcpy(c->kap, a.data(), sizeof(T) * L.total, cudaMemcpyHostToDevice));
+    HTD_CUDA(cudaMemcpy(c->dco, b.data(), sizeof(T) * L.total, cudaMemcpyHostToDevice));
+    return HTD_OK;
+}
+
+// Host-only validation and parameter selection (Sec. 2.2, App. A).
+struct Plan {
+    htd_options opt;
+    int d = 0;
+    int64_t n[3] = {1, 1, 1};
+    int64_t N = 1, Nc = 1;
+    double S[4], M[4];
+    htd_params p;
+};
+
+htd_status plan_impl(const htd_grid *grid, const double *c_cell, const double *R_node,
+                     double omega_phys, int bc, const htd_options *optp, Plan *pl)
+{
+    htd_options opt;
+    if (optp) opt = *optp; else htd_default_options(&opt);
+    if (!grid || !c_cell || !R_node) return HTD_ERR_ARG;
+    if (grid->ndim != 2 && grid->ndim != 3) return HTD_ERR_ARG;
+    if (!(grid->h > 0.0) || !std::isfinite(grid->h)) return HTD_ERR_ARG;
+    if (!(omega_phys > 0.0) || !std::isfinite(omega_phys)) return HTD_ERR_ARG;
+    if (bc != HTD_BC_DIRICHLET) return HTD_ERR_ARG;
+    if (opt.precision != HTD_FP64 && opt.precision != HTD_MIXED) return HTD_ERR_ARG;
+    if (opt.mode != HTD_MODE_TABLE1 && opt.mode != HTD_MODE_EXACT) return HTD_ERR_ARG;
+    if (opt.krylov != HTD_FGMRES && opt.krylov != HTD_LEFT_GMRES) return HTD_ERR_ARG;
+    if (opt.T < 1 || !(opt.rho >= 0.0 && opt.rho <= 1.0) || opt.nP < 0) return HTD_ERR_ARG;
+    if (opt.restart < 1 || opt.restart > kMaxRestart) return HTD_ERR_ARG;
+    const int d = grid->ndim;
+    pl->d = d;
+    pl->N = 1;
+    pl->Nc = 1;
+    for (int a = 0; a < 3; ++a) pl->n[a] = 1;
+    for (int a = 0; a < d; ++a) {
+        if (grid->n[a] < 1 || grid->n[a] > ((int64_t)1 << 24)) return HTD_ERR_ARG;
+        pl->n[a] = grid->n[a];
+        pl->N *= grid->n[a];
+        pl->Nc *= grid->n[a] + 1;
+    }
+    if (pl->N > ((int64_t)1 << 34)) return HTD_ERR_ARG;
+    if (!cell_weights(d, opt.stencil, pl->S, pl->M)) return HTD_ERR_ARG;
+    pl->opt = opt;
+
+    double kmin = INFINITY, kmax = 0.0;
+    for (int64_t i = 0; i < pl->Nc; ++i) {
+        const double cv = c_cell[i];
+        if (!std::isfinite(cv)) return HTD_ERR_NONFINITE;
+        if (!(cv > 0.0)) return HTD_ERR_ARG;
+        const double k = omega_phys / cv;
+        kmin = std::fmin(kmin, k);
+        kmax = std::fmax(kmax, k);
+    }
+    for (int64_t i = 0; i < pl->N; ++i) {
+        if (!std::isfinite(R_node[i])) return HTD_ERR_NONFINITE;
+        if (R_node[i] < 0.0) return HTD_ERR_ARG;
+    }
+    htd_params &P = pl->p;
+    P.k_min = kmin;
+    P.k_max = kmax;
+    P.omega_c = kmax;                              // omega = sqrt(-lambda_min) >= k_max bound
+    const double kap_min = (grid->h * kmin) * (grid->h * kmin);
+    double f[4];
+    for (int s = 0; s < 4; ++s) f[s] = pl->S[s] - kap_min * pl->M[s];
+    double lmax = -INFINITY;
+    for (int w = 0; w <= d; ++w) lmax = std::fmax(lmax, std::ldexp(walsh_eigen(d, f, w), d));
+    P.lam_max_reH = lmax / (grid->h * grid->h);
+    P.lam_max_A = P.lam_max_reH + P.omega_c * P.omega_c;
+    const double ratio = P.omega_c * P.omega_c / P.lam_max_A;
+    int nP = 0;
+    if (opt.nP > 0) {
+        const double sv = std::sin(kPi / opt.nP);
+        if (opt.nP % 4 != 0 || !(sv * sv < ratio)) return HTD_ERR_UNSTABLE;
+        nP = opt.nP;
+    } else {
+        for (int q = 4; q < (1 << 20) && !nP; q += 4) {
+            const double sv = std::sin(kPi / q);
+            if (sv * sv < ratio) nP = q;
+        }
+        if (!nP) return HTD_ERR_UNSTABLE;
+    }
+    P.nP = nP;
+    P.T = opt.T;
+    P.steps = (long long)opt.T * nP;
+    P.dt = 2.0 * kPi / (P.omega_c * nP);
+    const double x = P.omega_c * P.dt;
+    P.alpha = x * x / (2.0 - 2.0 * std::cos(x));
+    P.beta = x / std::sin(x);
+    P.rho = (opt.rho > 0.0) ? opt.rho : 1.0 / opt.T;
+    return HTD_OK;
+}
+
+htd_status create_impl(const htd_grid *grid, const double *c_cell, const double *R_node,
+                       double omega_phys, int bc, const htd_options *optp, htd_ctx *c)
+{
+    Plan pl;
+    htd_status pst = plan_impl(grid, c_cell, R_node, omega_phys, bc, optp, &pl);
+    if (pst != HTD_OK) return pst;
+    const htd_options opt = pl.opt;
+    const int d = pl.d;
+    const int64_t N = pl.N;
+    c->d = d;
+    for (int a = 0; a < 3; ++a) c->n[a] = pl.n[a];
+    for (int s = 0; s < 4; ++s) { c->S[s] = pl.S[s]; c->M[s] = pl.M[s]; }
+    c->opt = opt;
+    c->h = grid->h;
+    c->omega_phys = omega_phys;
+    c->m = opt.restart;
+    c->kmin = pl.p.k_min;
+    c->kmax = pl.p.k_max;
+    c->omega = pl.p.omega_c;
+    c->lam_reH = pl.p.lam_max_reH;
+    c->lam_A = pl.p.lam_max_A;
+    c->nP = pl.p.nP;
+    c->T = pl.p.T;
+    c->nsteps = pl.p.steps;
+    c->dt = pl.p.dt;
+    c->alpha = pl.p.alpha;
+    c->beta = pl.p.beta;
+    c->rho = pl.p.rho;
+    const int nP = c->nP;
+    HTD_CUDA(cudaGetDevice(&c->device));
+
+    // ---- recurrence coefficients ------------------------------------------
+    const double cK = c->dt * c->dt / c->alpha;          // dt^2 / alpha
+    const double q = cK / (grid->h * grid->h);
+    const double p = cK * c->omega * c->omega;
+    c->C.c0 = 2.0 - p - q * std::ldexp(c->S[0], d);
+    c->C.cs[0] = 0.0;
+    for (int s = 1; s < 4; ++s) c->C.cs[s] = (s <= d) ? q * std::ldexp(c->S[s], d - s) : 0.0;
+    for (int s = 0; s < 4; ++s) c->C.mt[s] = c->M[s];
+    c->atab.resize(c->nsteps);
+    c->btab.resize(c->nsteps);
+    for (long long j = 0; j < c->nsteps; ++j) {
+        const double chi = window_chi(1.0 - (double)j / (double)c->nsteps, c->rho);
+        const double ph = 2.0 * kPi * (double)(j % nP) / nP;
+        c->atab[j] = cK * chi * std::cos(ph);
+        c->btab[j] = cK * chi * std::sin(ph);
+    }
+
+    // ---- layouts and device memory ----------------------------------------
+    const bool mixed = opt.precision == HTD_MIXED;
+    c->esz = mixed ? sizeof(float) : sizeof(double);
+    c->Lr = make_layout(d, c->n, c->esz);
+    c->L64 = make_layout(d, c->n, sizeof(double));
+    const Layout &L = c->Lr;
+    const size_t bytes = c->esz * (size_t)L.total;
+    void **arrs[] = {&c->kap, &c->dco, &c->fre, &c->fim, &c->u0, &c->u1};
+    for (void **pp : arrs) {
+        HTD_CUDA(cudaMalloc(pp, bytes));
+        HTD_CUDA(cudaMemset(*pp, 0, bytes));
+    }
+    HTD_CUDA(cudaMalloc((void **)&c->kap64, sizeof(double) * c->L64.total));
+    HTD_CUDA(cudaMalloc((void **)&c->imH, sizeof(double) * N));
+
+    // per-cell kappa = (h omega_phys / c)^2 at the cell's stored position;
+    // per-node d = 1 / (1 + L_ii / 2), L = (beta dt / alpha) Im H / omega
+    std::vector<double> qk(L.total, 0.0), dc(L.total, 0.0), k64(c->L64.total, 0.0), imh(N);
+    const int64_t nx = c->n[d - 1], ny = c->n[d - 2], nz = (d == 3) ? c->n[0] : 1;
+    for (int64_t az = (d == 3 ? -1 : 0); az < (d == 3 ? nz : 1); ++az)
+        for (int64_t ay = -1; ay < ny; ++ay)
+            for (int64_t ax = -1; ax < nx; ++ax) {
+                const int64_t ci = (d == 3) ? ((az + 1) * (ny + 1) + (ay + 1)) * (nx + 1) + (ax + 1)
+                                            : (ay + 1) * (nx + 1) + (ax + 1);
+                const double k = omega_phys / c_cell[ci];
+                const double kap = (grid->h * k) * (grid->h * k);
+                qk[L.node(ax, ay, az)] = q * kap;
+                k64[c->L64.node(ax, ay, az)] = kap;
+            }
+    const double lcoef = c->beta * c->dt / c->alpha / c->omega;
+    for (int64_t iz = 0; iz < nz; ++iz)
+        for (int64_t iy = 0; iy < ny; ++iy)
+            for (int64_t ix = 0; ix < nx; ++ix) {
+                const int64_t ci = (iz * ny + iy) * nx + ix;
+                const double ih = omega_phys * R_node[ci];
+                imh[ci] = ih;
+                dc[L.node(ix, iy, iz)] = 1.0 / (1.0 + 0.5 * lcoef * ih);
+            }
+    htd_status st = mixed ? upload_recurrence<float>(c, qk, dc) : upload_recurrence<double>(c, qk, dc);
+    if (st != HTD_OK) return st;
+    HTD_CUDA(cudaMemcpy(c->kap64, k64.data(), sizeof(double) * c->L64.total, cudaMemcpyHostToDevice));
+    HTD_CUDA(cudaMemcpy(c->imH, imh.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+
+    // Krylov workspace
+    const size_t vb = sizeof(double2) * (size_t)N;
+    HTD_CUDA(cudaMalloc((void **)&c->V, vb * (c->m + 1)));
+    if (opt.krylov == HTD_FGMRES) HTD_CUDA(cudaMalloc((void **)&c->Z, vb * c->m));
+    HTD_CUDA(cudaMalloc((void **)&c->w, vb));
+    HTD_CUDA(cudaMalloc((void **)&c->t, vb));
+    HTD_CUDA(cudaMalloc((void **)&c->r, vb));
+    c->nb = htd::dots_blocks(N);
+    HTD_CUDA(cudaMalloc((void **)&c->partial, sizeof(double2) * (size_t)c->nb * (kMaxRestart + 1)));
+    HTD_CUDA(cudaMalloc((void **)&c->hdev, sizeof(double2) * 3 * 72));
+    HTD_CUDA(cudaMallocHost((void **)&c->hhost, sizeof(double2) * 3 * 72));
+    HTD_CUDA(cudaEventCreate(&c->pev[0]));
+    HTD_CUDA(cudaEventCreate(&c->pev[1]));
+    HTD_CUDA(cudaMalloc((void **)&c->slot, sizeof(OutSlot)));
+    HTD_CUDA(cudaMemset(c->slot, 0, sizeof(OutSlot)));
+    HTD_CUDA(cudaDeviceSynchronize());
+    return HTD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void htd_default_options(htd_options *opt)
+{
+    if (!opt) return;
+    opt->precision = HTD_FP64;
+    opt->mode = HTD_MODE_TABLE1;
+    opt->krylov = HTD_FGMRES;
+    opt->T = 10;
+    opt->rho = 0.25;
+    opt->nP = 0;
+    opt->stencil = HTD_STENCIL_Q1MIX;
+    opt->restart = 20;
+}
+
+htd_status htd_create(const htd_grid *grid, const double *c_cell_host, const double *R_node_host,
+                      double omega_phys, int bc, const htd_options *opt, htd_handle *out)
+{
+    if (!out) return HTD_ERR_ARG;
+    htd_ctx *c = new (std::nothrow) htd_ctx();
+    if (!c) return HTD_ERR_OOM;
+    htd_status st = create_impl(grid, c_cell_host, R_node_host, omega_phys, bc, opt, c);
+    if (st != HTD_OK) {
+        free_ctx(c);
+        return st;
+    }
+    *out = c;
+    return HTD_OK;
+}
+
+htd_status htd_destroy(htd_handle h)
+{
+    if (!h) return HTD_OK;
+    cudaDeviceSynchronize();
+    free_ctx(h);
+    return HTD_OK;
+}
+
+htd_status htd_plan(const htd_grid *grid, const double *c_cell_host, const double *R_node_host,
+                    double omega_phys, int bc, const htd_options *opt, htd_params *out)
+{
+    if (!out) return HTD_ERR_ARG;
+    Plan pl;
+    htd_status st = plan_impl(grid, c_cell_host, R_node_host, omega_phys, bc, opt, &pl);
+    if (st == HTD_OK) *out = pl.p;
+    return st;
+}
+
+htd_status htd_get_params(htd_handle h, htd_params *out)
+{
+    if (!h || !out) return HTD_ERR_ARG;
+    htd_params &P = *out;
+    P.k_min = h->kmin;
+    P.k_max = h->kmax;
+    P.omega_c = h->omega;
+    P.lam_max_reH = h->lam_reH;
+    P.lam_max_A = h->lam_A;
+    P.dt = h->dt;
+    P.alpha = h->alpha;
+    P.beta = h->beta;
+    P.rho = h->rho;
+    P.nP = h->nP;
+    P.T = h->T;
+    P.steps = h->nsteps;
+    return HTD_OK;
+}
+
+htd_status htd_apply_precond(htd_handle h, const void *F_dev, void *U_dev, void *stream)
+{
+    if (!h || !F_dev || !U_dev || F_dev == U_dev) return HTD_ERR_ARG;
+    return precond(h, (const double2 *)F_dev, (double2 *)U_dev, (cudaStream_t)stream);
+}
+
+htd_status htd_apply_H(htd_handle h, const void *X_dev, void *Y_dev, void *stream)
+{
+    if (!h || !X_dev || !Y_dev || X_dev == Y_dev) return HTD_ERR_ARG;
+    apply_H(h, (const double2 *)X_dev, nullptr, (double2 *)Y_dev, (cudaStream_t)stream);
+    HTD_CUDA(cudaGetLastError());
+    return HTD_OK;
+}
+
+htd_status htd_residual_norm(htd_handle h, const void *F_dev, const void *U_dev, void *r_dev,
+                             double *rel, void *stream)
+{
+    if (!h || !F_dev || !U_dev || !rel) return HTD_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    double2 *r = r_dev ? (double2 *)r_dev : h->r;
+    apply_H(h, (const double2 *)U_dev, (const double2 *)F_dev, r, s);
+    double rn, fn;
+    htd_status st = norm(h, r, &rn, s);
+    if (st != HTD_OK) return st;
+    if ((st = norm(h, (const double2 *)F_dev, &fn, s)) != HTD_OK) return st;
+    *rel = (fn > 0.0) ? rn / fn : 0.0;
+    return HTD_OK;
+}
+
+htd_status htd_gmres_solve(htd_handle h, const void *F_dev, void *U_dev, double tol, int max_iters,
+                           void *stream, htd_solve_info *info)
+{
+    if (!h || !F_dev || !U_dev || F_dev == U_dev || max_iters < 0) return HTD_ERR_ARG;
+    return gmres(h, (const double2 *)F_dev, (double2 *)U_dev, tol, max_iters, (cudaStream_t)stream, info);
+}
+
+htd_status htd_gmres_solve_host(htd_handle h, const void *F_host, void *U_host, double tol,
+                                int max_iters, void *stream, htd_solve_info *info)
+{
+    if (!h || !F_host || !U_host || max_iters < 0) return HTD_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t vb = sizeof(double2) * (size_t)h->Lr.N;
+    if (!h->Fh) HTD_CUDA(cudaMalloc((void **)&h->Fh, vb));
+    if (!h->Uh) HTD_CUDA(cudaMalloc((void **)&h->Uh, vb));
+    HTD_CUDA(cudaMemcpyAsync(h->Fh, F_host, vb, cudaMemcpyHostToDevice, s));
+    HTD_CUDA(cudaMemcpyAsync(h->Uh, U_host, vb, cudaMemcpyHostToDevice, s));
+    htd_status st = gmres(h, h->Fh, h->Uh, tol, max_iters, s, info);
+    if (st != HTD_OK && st != HTD_ERR_NOT_CONVERGED) return st;
+    HTD_CUDA(cudaMemcpyAsync(U_host, h->Uh, vb, cudaMemcpyDeviceToHost, s));
+    HTD_CUDA(cudaStreamSynchronize(s));
+    return st;
+}
+
+const char *htd_status_string(htd_status s)
+{
+    switch (s) {
+    case HTD_OK: return "ok";
+    case HTD_ERR_ARG: return "invalid argument";
+    case HTD_ERR_CUDA: return "CUDA runtime error";
+    case HTD_ERR_OOM: return "device out of memory";
+    case HTD_ERR_UNSTABLE: return "n_P violates the CFL bound or is not a multiple of 4";
+    case HTD_ERR_NONFINITE: return "non-finite value";
+    case HTD_ERR_NOT_CONVERGED: return "not converged within the iteration cap";
+    case HTD_ERR_TIMEOUT: return "device-side wait timed out";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

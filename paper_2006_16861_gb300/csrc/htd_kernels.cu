@@ -1,0 +1,447 @@
+// CUDA kernels of the time-domain Helmholtz preconditioner (sm_103a).
+//
+//  step2d / step3d   one step of the frequency-adapted leapfrog recurrence
+//                    I_acd (Def. of I_acd) with the windowed forcing of
+//                    Table 1 fused in, in place over u_{j-1}, and the
+//                    snapshot / final-state write of Table 1 fused in.
+//  split             complex128 right-hand side -> Re/Im planes (Table 1 uses
+//                    Re F and Im F every step).
+//  apply_H           true operator H X (or F - H X), complex128, FP64.
+//  dots / reduce     block dot products conj(V_k) . w with warp shuffles,
+//                    two-pass fixed-order reduction (deterministic).
+//  sub/add_combination, scale   Krylov vector updates.
+//
+// Operator (App. A cell form, h^2-scaled): for node beta and offset
+// o in {-1,0,1}^d with Hamming weight s = |o|,
+//   h^2 (Re H u)_beta = sum_o u_{beta+o} [ 2^{d-s} S_s - M_s * sum of kappa over
+//                       the 2^{d-s} cells that contain both beta and beta+o ],
+// kappa = (h k_cell)^2, S_s / M_s the stiffness / mass weights of the cell
+// kernel at Hamming distance s.  One step of I_acd with
+// K = (dt^2/alpha)(Re H + omega^2), L/2 = ell, d = 1/(1+ell):
+//   u_{j+1} = d ((2 - K) u_j + g_j - 2 u_{j-1}) + u_{j-1},
+//   g_j = a_j Re F - b_j Im F,
+// where (2 - K) u_j = c0 u - sum_{o != 0} cs_s u_{beta+o}
+//                     + sum_o M_s (sum of q kappa over the cells) u_{beta+o},
+// q = dt^2 / (alpha h^2), c0 = 2 - (dt^2/alpha) omega^2 - q 2^d S_0,
+// cs_s = q 2^{d-s} S_s; the stored per-cell coefficient is q * kappa.
+#include <cuda_runtime.h>
+
+#include "htd_internal.h"
+
+namespace htd {
+
+long long g_launches = 0;
+
+// ---------------------------------------------------------------------------
+// recurrence step
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+step2d_kernel(const T *__restrict__ u, T *__restrict__ um, const T *__restrict__ kap,
+              const T *__restrict__ dco, const T *__restrict__ fre, const T *__restrict__ fim,
+              Layout L, StepCoef<T> C, T a, T b, const OutSlot *__restrict__ slot, int flags)
+{
+    const int64_t ix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t iy = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
+    if (ix >= L.nx || iy >= L.ny) return;
+    const int64_t P = L.pitch;
+    const int64_t i = (iy + 1) * P + L.xl + ix;
+    // u_j on the 3x3 neighbourhood; first index = y offset, second = x offset
+    const T umm = u[i - P - 1], um0 = u[i - P], ump = u[i - P + 1];
+    const T u0m = u[i - 1], u00 = u[i], u0p = u[i + 1];
+    const T upm = u[i + P - 1], up0 = u[i + P], upp = u[i + P + 1];
+    // q*kappa of the four cells around the node, k<ay><ax>: cell at row y-1+ay, column x-1+ax
+    const T k00 = kap[i - P - 1], k01 = kap[i - P], k10 = kap[i - 1], k11 = kap[i];
+    T acc = (C.c0 + C.mt[0] * ((k00 + k01) + (k10 + k11))) * u00;
+    acc -= C.cs[1] * ((um0 + up0) + (u0m + u0p));
+    acc -= C.cs[2] * ((umm + ump) + (upm + upp));
+    acc += C.mt[1] * ((k00 + k01) * um0 + (k10 + k11) * up0 + (k00 + k10) * u0m + (k01 + k11) * u0p);
+    acc += C.mt[2] * (k00 * umm + k01 * ump + k10 * upm + k11 * upp);
+    const T g = a * fre[i] - b * fim[i];
+    const T d = dco[i];
+    const T uprev = um[i];
+    const T unew = d * (acc + g - T(2) * uprev) + uprev;
+    um[i] = unew;
+    if (flags) {
+        const int64_t c = iy * L.nx + ix;
+        if ((flags & 1) && slot->snap_part) slot->snap_part[2 * c] = (double)unew;
+        if ((flags & 2) && slot->final_part) slot->final_part[2 * c] = (double)unew;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+step3d_kernel(const T *__restrict__ u, T *__restrict__ um, const T *__restrict__ kap,
+              const T *__restrict__ dco, const T *__restrict__ fre, const T *__restrict__ fim,
+              Layout L, StepCoef<T> C, T a, T b, const OutSlot *__restrict__ slot, int flags)
+{
+    const int64_t ix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t iy = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
+    const int64_t iz = blockIdx.z;
+    if (ix >= L.nx || iy >= L.ny) return;
+    const int64_t P = L.pitch, Q = L.plane;
+    const int64_t i = (iz + 1) * Q + (iy + 1) * P + L.xl + ix;
+    // q*kappa of the 8 cells around the node: k[az][ay][ax] at plane z-1+az, row y-1+ay, column x-1+ax
+    T k[2][2][2];
+#pragma unroll
+    for (int az = 0; az < 2; ++az)
+#pragma unroll
+        for (int ay = 0; ay < 2; ++ay)
+#pragma unroll
+            for (int ax = 0; ax < 2; ++ax)
+                k[az][ay][ax] = kap[i - (1 - az) * Q - (1 - ay) * P - (1 - ax)];
+    // sums of kappa over the cells shared by the node and its neighbour at offset
+    // o - 1 (o in 0..2 per axis): offset -1 keeps the lower cell, +1 the upper, 0 both
+    T kx[2][2][3];
+#pragma unroll
+    for (int az = 0; az < 2; ++az)
+#pragma unroll
+        for (int ay = 0; ay < 2; ++ay) {
+            kx[az][ay][0] = k[az][ay][0];
+            kx[az][ay][1] = k[az][ay][0] + k[az][ay][1];
+            kx[az][ay][2] = k[az][ay][1];
+        }
+    T kxy[2][3][3];
+#pragma unroll
+    for (int az = 0; az < 2; ++az)
+#pragma unroll
+        for (int ox = 0; ox < 3; ++ox) {
+            kxy[az][0][ox] = kx[az][0][ox];
+            kxy[az][1][ox] = kx[az][0][ox] + kx[az][1][ox];
+            kxy[az][2][ox] = kx[az][1][ox];
+        }
+    T acc = T(0);
+#pragma unroll
+    for (int oz = 0; oz < 3; ++oz)
+#pragma unroll
+        for (int oy = 0; oy < 3; ++oy)
+#pragma unroll
+            for (int ox = 0; ox < 3; ++ox) {
+                const int s = (oz != 1) + (oy != 1) + (ox != 1);
+                const T ks = (oz == 0) ? kxy[0][oy][ox]
+                           : (oz == 2) ? kxy[1][oy][ox] : kxy[0][oy][ox] + kxy[1][oy][ox];
+                const T uv = u[i + (oz - 1) * Q + (oy - 1) * P + (ox - 1)];
+                const T coef = (s == 0) ? C.c0 + C.mt[0] * ks : C.mt[s] * ks - C.cs[s];
+                acc += coef * uv;
+            }
+    const T g = a * fre[i] - b * fim[i];
+    const T d = dco[i];
+    const T uprev = um[i];
+    const T unew = d * (acc + g - T(2) * uprev) + uprev;
+    um[i] = unew;
+    if (flags) {
+        const int64_t c = (iz * L.ny + iy) * L.nx + ix;
+        if ((flags & 1) && slot->snap_part) slot->snap_part[2 * c] = (double)unew;
+        if ((flags & 2) && slot->final_part) slot->final_part[2 * c] = (double)unew;
+    }
+}
+
+template <typename T>
+void launch_step(const Layout &L, const T *u, T *um, const T *kap, const T *dco,
+                 const T *fre, const T *fim, const StepCoef<T> &C, T a, T b,
+                 const OutSlot *slot, int flags, cudaStream_t s)
+{
+    if (L.d == 2) {
+        dim3 blk(32, 8);
+        dim3 grd((unsigned)((L.nx + 31) / 32), (unsigned)((L.ny + 7) / 8));
+        step2d_kernel<T><<<grd, blk, 0, s>>>(u, um, kap, dco, fre, fim, L, C, a, b, slot, flags);
+        ++g_launches;
+    } else {
+        dim3 blk(32, 4);
+        dim3 grd((unsigned)((L.nx + 31) / 32), (unsigned)((L.ny + 3) / 4), (unsigned)L.nz);
+        step3d_kernel<T><<<grd, blk, 0, s>>>(u, um, kap, dco, fre, fim, L, C, a, b, slot, flags);
+        ++g_launches;
+    }
+}
+
+template void launch_step<float>(const Layout &, const float *, float *, const float *,
+                                 const float *, const float *, const float *,
+                                 const StepCoef<float> &, float, float, const OutSlot *, int,
+                                 cudaStream_t);
+template void launch_step<double>(const Layout &, const double *, double *, const double *,
+                                  const double *, const double *, const double *,
+                                  const StepCoef<double> &, double, double, const OutSlot *,
+                                  int, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// split / output slot
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void split_kernel(Layout L, const double2 *__restrict__ F, T *__restrict__ fre,
+                             T *__restrict__ fim, int flip)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= L.N) return;
+    const int64_t ix = c % L.nx;
+    const int64_t r = c / L.nx;
+    const int64_t iy = r % L.ny;
+    const int64_t iz = r / L.ny;
+    const int64_t i = L.node(ix, iy, iz);
+    const double2 f = F[c];
+    // flip: forcing -i F, whose real part is Im F and imaginary part is -Re F
+    fre[i] = (T)(flip ? f.y : f.x);
+    fim[i] = (T)(flip ? -f.x : f.y);
+}
+
+template <typename T>
+void launch_split(const Layout &L, const double2 *F, T *fre, T *fim, int flip, cudaStream_t s)
+{
+    const int bs = 256;
+    split_kernel<T><<<(unsigned)((L.N + bs - 1) / bs), bs, 0, s>>>(L, F, fre, fim, flip);
+    ++g_launches;
+}
+template void launch_split<float>(const Layout &, const double2 *, float *, float *, int, cudaStream_t);
+template void launch_split<double>(const Layout &, const double2 *, double *, double *, int, cudaStream_t);
+
+__global__ void set_slot_kernel(OutSlot *slot, double *final_part, double *snap_part)
+{
+    slot->final_part = final_part;
+    slot->snap_part = snap_part;
+}
+
+void launch_set_slot(OutSlot *slot, double *final_part, double *snap_part, cudaStream_t s)
+{
+    set_slot_kernel<<<1, 1, 0, s>>>(slot, final_part, snap_part);
+    ++g_launches;
+}
+
+// ---------------------------------------------------------------------------
+// true operator, complex128
+// ---------------------------------------------------------------------------
+
+struct HCoef {
+    double S2[4];   // 2^{d-s} S_s
+    double M[4];
+    double ih2;
+};
+
+__global__ void __launch_bounds__(256)
+apply_H_kernel(Layout L, const double *__restrict__ kap64, const double *__restrict__ imH,
+               HCoef C, const double2 *__restrict__ X, const double2 *__restrict__ F,
+               double2 *__restrict__ Y)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= L.N) return;
+    const int64_t ix = c % L.nx;
+    const int64_t r = c / L.nx;
+    const int64_t iy = r % L.ny;
+    const int64_t iz = r / L.ny;
+    const int64_t i = L.node(ix, iy, iz);   // position in the padded cell array
+    const int64_t P = L.pitch, Q = L.plane;
+    const int zlo = (L.d == 3) ? -1 : 0, zhi = (L.d == 3) ? 1 : 0;
+    double re = 0.0, im = 0.0;
+    for (int oz = zlo; oz <= zhi; ++oz) {
+        const int64_t jz = iz + oz;
+        if (jz < 0 || jz >= L.nz) continue;
+        for (int oy = -1; oy <= 1; ++oy) {
+            const int64_t jy = iy + oy;
+            if (jy < 0 || jy >= L.ny) continue;
+            for (int ox = -1; ox <= 1; ++ox) {
+                const int64_t jx = ix + ox;
+                if (jx < 0 || jx >= L.nx) continue;
+                const int s = (oz != 0) + (oy != 0) + (ox != 0);
+                // cells shared by the node and its neighbour: lower (offset -1),
+                // upper (+1) or both (0) per axis
+                double ks = 0.0;
+                for (int az = (L.d == 3 ? 0 : 1); az < 2; ++az) {
+                    if (L.d == 3 && ((oz < 0 && az == 1) || (oz > 0 && az == 0))) continue;
+                    for (int ay = 0; ay < 2; ++ay) {
+                        if ((oy < 0 && ay == 1) || (oy > 0 && ay == 0)) continue;
+                        for (int ax = 0; ax < 2; ++ax) {
+                            if ((ox < 0 && ax == 1) || (ox > 0 && ax == 0)) continue;
+                            ks += kap64[i - (L.d == 3 ? (1 - az) * Q : 0) - (1 - ay) * P - (1 - ax)];
+                        }
+                    }
+                }
+                const double w = C.S2[s] - C.M[s] * ks;
+                const double2 x = X[(jz * L.ny + jy) * L.nx + jx];
+                re += w * x.x;
+                im += w * x.y;
+            }
+        }
+    }
+    const double2 xc = X[c];
+    const double damp = imH[c];
+    double2 y;
+    y.x = C.ih2 * re - damp * xc.y;
+    y.y = C.ih2 * im + damp * xc.x;
+    if (F) {
+        const double2 f = F[c];
+        y.x = f.x - y.x;
+        y.y = f.y - y.y;
+    }
+    Y[c] = y;
+}
+
+void launch_apply_H(const Layout &L, const double *kap64, const double *imH, const double S2[4],
+                    const double M[4], double ih2, const double2 *X, const double2 *F,
+                    double2 *Y, cudaStream_t s)
+{
+    HCoef C;
+    for (int k = 0; k < 4; ++k) { C.S2[k] = S2[k]; C.M[k] = M[k]; }
+    C.ih2 = ih2;
+    const int bs = 256;
+    apply_H_kernel<<<(unsigned)((L.N + bs - 1) / bs), bs, 0, s>>>(L, kap64, imH, C, X, F, Y);
+    ++g_launches;
+}
+
+// ---------------------------------------------------------------------------
+// Krylov vector operations (complex128)
+// ---------------------------------------------------------------------------
+
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// block-wide sum of (re, im); result valid in thread 0
+__device__ __forceinline__ double2 block_sum(double re, double im)
+{
+    __shared__ double sre[kRedThreads / 32], sim[kRedThreads / 32];
+    re = warp_sum(re);
+    im = warp_sum(im);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { sre[warp] = re; sim[warp] = im; }
+    __syncthreads();
+    double2 out = make_double2(0.0, 0.0);
+    if (warp == 0) {
+        re = lane < kRedThreads / 32 ? sre[lane] : 0.0;
+        im = lane < kRedThreads / 32 ? sim[lane] : 0.0;
+        re = warp_sum(re);
+        im = warp_sum(im);
+        out = make_double2(re, im);
+    }
+    return out;
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+dots_kernel(const double2 *__restrict__ V, int64_t ldv, const double2 *__restrict__ w,
+            int64_t N, double2 *__restrict__ partial, int nb)
+{
+    const int k = blockIdx.y;
+    const double2 *v = V + (int64_t)k * ldv;
+    double re = 0.0, im = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; i < N;
+         i += (int64_t)nb * kRedThreads) {
+        const double2 a = v[i], b = w[i];
+        // conj(a) * b
+        re += a.x * b.x + a.y * b.y;
+        im += a.x * b.y - a.y * b.x;
+    }
+    const double2 t = block_sum(re, im);
+    if (threadIdx.x == 0) partial[(int64_t)k * nb + blockIdx.x] = t;
+}
+
+int dots_blocks(int64_t N)
+{
+    int64_t nb = (N + 4 * kRedThreads - 1) / (4 * kRedThreads);
+    if (nb > 1216) nb = 1216;   // 8 blocks per SM on 152 SMs
+    if (nb < 1) nb = 1;
+    return (int)nb;
+}
+
+void launch_dots(const double2 *V, int64_t ldv, int kcount, const double2 *w, int64_t N,
+                 double2 *partial, int nb, cudaStream_t s)
+{
+    dim3 grd((unsigned)nb, (unsigned)kcount);
+    dots_kernel<<<grd, kRedThreads, 0, s>>>(V, ldv, w, N, partial, nb);
+    ++g_launches;
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+reduce_kernel(const double2 *__restrict__ partial, int nb, double2 *__restrict__ out)
+{
+    const int k = blockIdx.x;
+    double re = 0.0, im = 0.0;
+    for (int b = threadIdx.x; b < nb; b += kRedThreads) {
+        const double2 p = partial[(int64_t)k * nb + b];
+        re += p.x;
+        im += p.y;
+    }
+    const double2 t = block_sum(re, im);
+    if (threadIdx.x == 0) out[k] = t;
+}
+
+void launch_reduce(const double2 *partial, int nb, int kcount, double2 *out, cudaStream_t s)
+{
+    reduce_kernel<<<kcount, kRedThreads, 0, s>>>(partial, nb, out);
+    ++g_launches;
+}
+
+__global__ void __launch_bounds__(256)
+sub_combination_kernel(const double2 *__restrict__ V, int64_t ldv, int kcount,
+                       const double2 *__restrict__ h, double2 *__restrict__ w, int64_t N)
+{
+    __shared__ double2 sh[72];
+    for (int k = threadIdx.x; k < kcount; k += blockDim.x) sh[k] = h[k];
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double2 acc = w[i];
+    for (int k = 0; k < kcount; ++k) {
+        const double2 v = V[(int64_t)k * ldv + i];
+        const double2 c = sh[k];
+        acc.x -= c.x * v.x - c.y * v.y;
+        acc.y -= c.x * v.y + c.y * v.x;
+    }
+    w[i] = acc;
+}
+
+void launch_sub_combination(const double2 *V, int64_t ldv, int kcount, const double2 *h,
+                            double2 *w, int64_t N, cudaStream_t s)
+{
+    const int bs = 256;
+    sub_combination_kernel<<<(unsigned)((N + bs - 1) / bs), bs, 0, s>>>(V, ldv, kcount, h, w, N);
+    ++g_launches;
+}
+
+__global__ void __launch_bounds__(256)
+add_combination_kernel(const double2 *__restrict__ Z, int64_t ldz, int kcount,
+                       const double2 *__restrict__ y, double2 *__restrict__ U, int64_t N)
+{
+    __shared__ double2 sy[72];
+    for (int k = threadIdx.x; k < kcount; k += blockDim.x) sy[k] = y[k];
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double2 acc = U[i];
+    for (int k = 0; k < kcount; ++k) {
+        const double2 z = Z[(int64_t)k * ldz + i];
+        const double2 c = sy[k];
+        acc.x += c.x * z.x - c.y * z.y;
+        acc.y += c.x * z.y + c.y * z.x;
+    }
+    U[i] = acc;
+}
+
+void launch_add_combination(const double2 *Z, int64_t ldz, int kcount, const double2 *y,
+                            double2 *U, int64_t N, cudaStream_t s)
+{
+    const int bs = 256;
+    add_combination_kernel<<<(unsigned)((N + bs - 1) / bs), bs, 0, s>>>(Z, ldz, kcount, y, U, N);
+    ++g_launches;
+}
+
+__global__ void scale_kernel(const double2 *__restrict__ w, double scale, double2 *__restrict__ v,
+                             int64_t N)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double2 a = w[i];
+    v[i] = make_double2(a.x * scale, a.y * scale);
+}
+
+void launch_scale(const double2 *w, double scale, double2 *v, int64_t N, cudaStream_t s)
+{
+    const int bs = 256;
+    scale_kernel<<<(unsigned)((N + bs - 1) / bs), bs, 0, s>>>(w, scale, v, N);
+    ++g_launches;
+}
+
+}  // namespace htd

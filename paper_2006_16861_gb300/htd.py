@@ -1,0 +1,317 @@
+"""Thin ctypes binding of libhtd (include/htd.h) -- argument marshalling only.
+
+The functions carry the C names (``htd_create``, ``htd_apply_precond``,
+``htd_gmres_solve`` ...).  Device buffers are torch CUDA tensors (complex128,
+contiguous); streams are torch streams.  Every step of the computation runs in
+libhtd's CUDA kernels; there is no CPU fallback: if the library is missing or
+no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _native
+
+HTD_OK = 0
+STATUS = {0: "HTD_OK", 1: "HTD_ERR_ARG", 2: "HTD_ERR_CUDA", 3: "HTD_ERR_OOM",
+          4: "HTD_ERR_UNSTABLE", 5: "HTD_ERR_NONFINITE", 6: "HTD_ERR_NOT_CONVERGED",
+          7: "HTD_ERR_TIMEOUT"}
+FP64, MIXED = 0, 1
+MODE_TABLE1, MODE_EXACT = 0, 1
+FGMRES, LEFT_GMRES = 0, 1
+STENCIL_Q1MIX, STENCIL_FD5 = 0, 1
+BC_DIRICHLET = 0
+
+#: every function include/htd.h declares (checked by the ABI test)
+EXPORTS = ("htd_default_options", "htd_create", "htd_destroy", "htd_plan", "htd_get_params",
+           "htd_apply_precond", "htd_apply_H", "htd_residual_norm", "htd_gmres_solve",
+           "htd_gmres_solve_host", "htd_status_string")
+
+
+class HtdError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({_msg(status)})")
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_int64 * 3), ("h", ctypes.c_double)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("mode", ctypes.c_int), ("krylov", ctypes.c_int),
+                ("T", ctypes.c_int), ("rho", ctypes.c_double), ("nP", ctypes.c_int),
+                ("stencil", ctypes.c_int), ("restart", ctypes.c_int)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("k_min", ctypes.c_double), ("k_max", ctypes.c_double),
+                ("omega_c", ctypes.c_double), ("lam_max_reH", ctypes.c_double),
+                ("lam_max_A", ctypes.c_double), ("dt", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("rho", ctypes.c_double),
+                ("nP", ctypes.c_int), ("T", ctypes.c_int), ("steps", ctypes.c_longlong)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int),
+                ("precond_applies", ctypes.c_int), ("converged", ctypes.c_int),
+                ("steps", ctypes.c_longlong), ("rel_res_true", ctypes.c_double),
+                ("rel_res_est", ctypes.c_double), ("ms_total", ctypes.c_double),
+                ("ms_precond", ctypes.c_double), ("launches", ctypes.c_longlong),
+                ("hist_len", ctypes.c_int), ("hist", ctypes.c_double * 256)]
+
+    def as_dict(self) -> dict:
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "hist"}
+        d["hist"] = list(self.hist[: self.hist_len])
+        return d
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _native.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libhtd.so (building it first if needed).  Raises if it cannot be loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _native.build() if build_if_missing else _native.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libhtd.so not found at {path}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.htd_default_options.argtypes = [ctypes.POINTER(Options)]
+    lib.htd_default_options.restype = None
+    lib.htd_create.argtypes = [ctypes.POINTER(Grid), vp, vp, d, i, ctypes.POINTER(Options),
+                               ctypes.POINTER(vp)]
+    lib.htd_destroy.argtypes = [vp]
+    lib.htd_plan.argtypes = [ctypes.POINTER(Grid), vp, vp, d, i, ctypes.POINTER(Options),
+                             ctypes.POINTER(Params)]
+    lib.htd_get_params.argtypes = [vp, ctypes.POINTER(Params)]
+    lib.htd_apply_precond.argtypes = [vp, vp, vp, vp]
+    lib.htd_apply_H.argtypes = [vp, vp, vp, vp]
+    lib.htd_residual_norm.argtypes = [vp, vp, vp, vp, ctypes.POINTER(d), vp]
+    lib.htd_gmres_solve.argtypes = [vp, vp, vp, d, i, vp, ctypes.POINTER(SolveInfo)]
+    lib.htd_gmres_solve_host.argtypes = [vp, vp, vp, d, i, vp, ctypes.POINTER(SolveInfo)]
+    lib.htd_status_string.argtypes = [i]
+    lib.htd_status_string.restype = ctypes.c_char_p
+    for f in EXPORTS:
+        if f not in ("htd_default_options", "htd_status_string"):
+            getattr(lib, f).restype = i
+    _lib = lib
+    return lib
+
+
+def _msg(status: int) -> str:
+    try:
+        return load(False).htd_status_string(status).decode()
+    except Exception:  # noqa: BLE001 - only used to format an error message
+        return "?"
+
+
+def _check(st: int, where: str, allow=(HTD_OK,)) -> int:
+    if st not in allow:
+        raise HtdError(st, where)
+    return st
+
+
+def _dev_ptr(t) -> int:
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.complex128
+            and t.is_contiguous()):
+        raise TypeError("expected a contiguous complex128 CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _host_ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+# ---- the C entry points with the same names ---------------------------------
+
+def htd_default_options() -> Options:
+    o = Options()
+    load().htd_default_options(ctypes.byref(o))
+    return o
+
+
+def _grid(ndim: int, n, h: float) -> Grid:
+    g = Grid()
+    g.ndim = ndim
+    for a in range(3):
+        g.n[a] = int(n[a]) if a < min(ndim, len(n)) else 1
+    g.h = h
+    return g
+
+
+def htd_plan(ndim: int, n, h: float, c_cell: np.ndarray, R_node: np.ndarray,
+             omega_phys: float, bc: int = BC_DIRICHLET, options: Options | None = None) -> dict:
+    """Host-only parameter selection (no GPU needed)."""
+    c = np.ascontiguousarray(c_cell, dtype=np.float64)
+    R = np.ascontiguousarray(R_node, dtype=np.float64)
+    out = Params()
+    st = load().htd_plan(ctypes.byref(_grid(ndim, n, h)), _host_ptr(c), _host_ptr(R),
+                         float(omega_phys), int(bc),
+                         ctypes.byref(options) if options is not None else None, ctypes.byref(out))
+    _check(st, "htd_plan")
+    return out.as_dict()
+
+
+def htd_create(ndim: int, n, h: float, c_cell: np.ndarray, R_node: np.ndarray,
+               omega_phys: float, bc: int = BC_DIRICHLET, options: Options | None = None) -> int:
+    lib = load()
+    c = np.ascontiguousarray(c_cell, dtype=np.float64)
+    R = np.ascontiguousarray(R_node, dtype=np.float64)
+    handle = ctypes.c_void_p()
+    st = lib.htd_create(ctypes.byref(_grid(ndim, n, h)), _host_ptr(c), _host_ptr(R),
+                        float(omega_phys), int(bc),
+                        ctypes.byref(options) if options is not None else None,
+                        ctypes.byref(handle))
+    _check(st, "htd_create")
+    return handle.value
+
+
+def htd_destroy(handle: int) -> None:
+    _check(load().htd_destroy(handle), "htd_destroy")
+
+
+def htd_get_params(handle: int) -> dict:
+    out = Params()
+    _check(load().htd_get_params(handle, ctypes.byref(out)), "htd_get_params")
+    return out.as_dict()
+
+
+def htd_apply_precond(handle: int, F, U, stream=None) -> None:
+    _check(load().htd_apply_precond(handle, _dev_ptr(F), _dev_ptr(U), _stream_ptr(stream)),
+           "htd_apply_precond")
+
+
+def htd_apply_H(handle: int, X, Y, stream=None) -> None:
+    _check(load().htd_apply_H(handle, _dev_ptr(X), _dev_ptr(Y), _stream_ptr(stream)),
+           "htd_apply_H")
+
+
+def htd_residual_norm(handle: int, F, U, r=None, stream=None) -> float:
+    rel = ctypes.c_double()
+    _check(load().htd_residual_norm(handle, _dev_ptr(F), _dev_ptr(U),
+                                    None if r is None else _dev_ptr(r), ctypes.byref(rel),
+                                    _stream_ptr(stream)), "htd_residual_norm")
+    return rel.value
+
+
+def htd_gmres_solve(handle: int, F, U, tol: float, max_iters: int, stream=None,
+                    allow_not_converged: bool = False) -> dict:
+    info = SolveInfo()
+    allow = (HTD_OK, 6) if allow_not_converged else (HTD_OK,)
+    st = load().htd_gmres_solve(handle, _dev_ptr(F), _dev_ptr(U), float(tol), int(max_iters),
+                                _stream_ptr(stream), ctypes.byref(info))
+    _check(st, "htd_gmres_solve", allow)
+    d = info.as_dict()
+    d["status"] = STATUS[st]
+    return d
+
+
+def htd_gmres_solve_host(handle: int, F_host: np.ndarray, U_host: np.ndarray, tol: float,
+                         max_iters: int, stream=None, allow_not_converged: bool = False) -> dict:
+    if F_host.dtype != np.complex128 or U_host.dtype != np.complex128:
+        raise TypeError("host vectors must be complex128")
+    if not (F_host.flags.c_contiguous and U_host.flags.c_contiguous):
+        raise TypeError("host vectors must be C-contiguous")
+    info = SolveInfo()
+    allow = (HTD_OK, 6) if allow_not_converged else (HTD_OK,)
+    st = load().htd_gmres_solve_host(handle, F_host.ctypes.data, U_host.ctypes.data, float(tol),
+                                     int(max_iters), _stream_ptr(stream), ctypes.byref(info))
+    _check(st, "htd_gmres_solve_host", allow)
+    d = info.as_dict()
+    d["status"] = STATUS[st]
+    return d
+
+
+def htd_status_string(status: int) -> str:
+    return load().htd_status_string(int(status)).decode()
+
+
+# ---- convenience object ------------------------------------------------------
+
+def make_options(prob=None, precision: str = "fp64", mode: str = "table1",
+                 krylov: str = "fgmres", stencil: str = "q1mix", restart: int = 20,
+                 nP: int = 0, T: int | None = None, rho: float | None = None) -> Options:
+    """htd_options from names; T and rho default to the problem's."""
+    o = htd_default_options()
+    o.precision = {"fp64": FP64, "mixed": MIXED}[precision]
+    o.mode = {"table1": MODE_TABLE1, "exact": MODE_EXACT}[mode]
+    o.krylov = {"fgmres": FGMRES, "left": LEFT_GMRES}[krylov]
+    o.stencil = {"q1mix": STENCIL_Q1MIX, "fd5": STENCIL_FD5}[stencil]
+    o.restart = restart
+    o.nP = nP
+    if T is not None or prob is not None:
+        o.T = int(prob.T if T is None else T)
+    if rho is not None or prob is not None:
+        o.rho = float(prob.rho if rho is None else rho)
+    return o
+
+
+def plan(prob, **kw) -> dict:
+    """htd_plan for a workloads.Problem (host only)."""
+    return htd_plan(prob.ndim, prob.n, prob.h, prob.c_cell, prob.R_node, prob.omega,
+                    BC_DIRICHLET, make_options(prob, **kw))
+
+
+class Solver:
+    """One problem on the current CUDA device; owns an htd handle."""
+
+    def __init__(self, prob, precision: str = "fp64", mode: str = "table1",
+                 krylov: str = "fgmres", stencil: str = "q1mix", restart: int = 20,
+                 nP: int = 0, T: int | None = None, rho: float | None = None):
+        o = make_options(prob, precision, mode, krylov, stencil, restart, nP, T, rho)
+        self.prob = prob
+        self.n = tuple(prob.n)
+        self.handle = htd_create(prob.ndim, prob.n, prob.h, prob.c_cell, prob.R_node, prob.omega,
+                                 BC_DIRICHLET, o)
+        self.params = htd_get_params(self.handle)
+
+    def close(self):
+        if self.handle:
+            htd_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+    def zeros(self):
+        import torch
+        return torch.zeros(self.n, dtype=torch.complex128, device="cuda")
+
+    def precond(self, F, U=None, stream=None):
+        U = self.zeros() if U is None else U
+        htd_apply_precond(self.handle, F, U, stream)
+        return U
+
+    def apply_H(self, X, Y=None, stream=None):
+        Y = self.zeros() if Y is None else Y
+        htd_apply_H(self.handle, X, Y, stream)
+        return Y
+
+    def solve(self, F, U=None, tol=1e-6, max_iters=400, stream=None, allow_not_converged=False):
+        U = self.zeros() if U is None else U
+        info = htd_gmres_solve(self.handle, F, U, tol, max_iters, stream, allow_not_converged)
+        return U, info

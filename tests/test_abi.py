@@ -1,0 +1,123 @@
+"""Host-side checks of the C ABI: the library builds, loads and exports every
+function include/htd.h declares; the ctypes structs match the C layout; the
+host-only parameter selection (htd_plan) agrees with the oracle and rejects bad
+input.  No CUDA compute call is made here."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2006_16861_gb300 import htd
+from paper_2006_16861_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "htd.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(htd_[A-Za-z_0-9]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_function():
+    lib = htd.load()
+    names = declared_functions()
+    assert set(names) == set(htd.EXPORTS)
+    for name in names:
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", htd.library_path()],
+                         capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r" T (htd_\w+)", out))
+    assert set(names) <= exported
+
+
+def test_struct_layouts_match_header(tmp_path):
+    src = tmp_path / "sz.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "htd.h"\n'
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(htd_grid),"
+        " sizeof(htd_options), sizeof(htd_params), sizeof(htd_solve_info),"
+        " offsetof(htd_solve_info, hist), offsetof(htd_params, nP), offsetof(htd_options, restart));"
+        "return 0;}\n")
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    want = [ctypes.sizeof(htd.Grid), ctypes.sizeof(htd.Options), ctypes.sizeof(htd.Params),
+            ctypes.sizeof(htd.SolveInfo), htd.SolveInfo.hist.offset, htd.Params.nP.offset,
+            htd.Options.restart.offset]
+    assert got == want
+
+
+def test_default_options():
+    o = htd.htd_default_options()
+    assert (o.precision, o.mode, o.krylov, o.T, o.rho, o.nP, o.stencil, o.restart) == \
+        (htd.FP64, htd.MODE_TABLE1, htd.FGMRES, 10, 0.25, 0, htd.STENCIL_Q1MIX, 20)
+
+
+PROBLEMS = [
+    lambda: W.config_2d_constant(101),
+    lambda: W.config_2d_constant(57, ppw=6.0, layer=8, T=3),
+    lambda: W.config_2d_heterogeneous(201, layer=10, T=5),
+    lambda: W.config_3d_layered(20, layer=4, T=2),
+]
+
+
+@pytest.mark.parametrize("mk", PROBLEMS)
+@pytest.mark.parametrize("stencil", ["q1mix", "fd5"])
+def test_plan_matches_oracle_parameters(mk, stencil):
+    p = mk()
+    mine = htd.plan(p, stencil=stencil)
+    ref = oracle.Oracle(p, stencil).param_dict()
+    assert mine["nP"] == ref["nP"]
+    assert mine["T"] == ref["T"] and mine["steps"] == ref["nsteps"]
+    for a, b in [("omega_c", "omega"), ("k_min", "k_min"), ("k_max", "k_max"),
+                 ("lam_max_reH", "lam_max_reH"), ("lam_max_A", "lam_max_A"), ("dt", "dt"),
+                 ("alpha", "alpha"), ("beta", "beta"), ("rho", "rho")]:
+        assert mine[a] == pytest.approx(ref[b], rel=1e-12), a
+
+
+def test_plan_rejects_bad_input():
+    p = W.config_2d_constant(31, T=2)
+    ok = htd.plan(p)
+    with pytest.raises(htd.HtdError) as e:
+        htd.plan(p, nP=ok["nP"] - 4)               # violates the CFL bound
+    assert e.value.status == 4
+    with pytest.raises(htd.HtdError) as e:
+        htd.plan(p, nP=ok["nP"] + 2)               # not a multiple of 4
+    assert e.value.status == 4
+    c = p.c_cell.copy()
+    c[3, 4] = np.nan
+    with pytest.raises(htd.HtdError) as e:
+        htd.htd_plan(2, p.n, p.h, c, p.R_node, p.omega, 0, htd.make_options(p))
+    assert e.value.status == 5
+    c[3, 4] = -1.0
+    with pytest.raises(htd.HtdError) as e:
+        htd.htd_plan(2, p.n, p.h, c, p.R_node, p.omega, 0, htd.make_options(p))
+    assert e.value.status == 1
+    R = p.R_node.copy()
+    R[0, 0] = -1
+    with pytest.raises(htd.HtdError) as e:
+        htd.htd_plan(2, p.n, p.h, p.c_cell, R, p.omega, 0, htd.make_options(p))
+    assert e.value.status == 1
+    for kw in ({"restart": 0}, {"restart": 65}, {"T": 0}, {"rho": 1.5}):
+        with pytest.raises(htd.HtdError) as e:
+            htd.plan(p, **kw)
+        assert e.value.status == 1
+    with pytest.raises(htd.HtdError):
+        htd.htd_plan(2, p.n, -1.0, p.c_cell, p.R_node, p.omega, 0, htd.make_options(p))
+    with pytest.raises(htd.HtdError):
+        htd.htd_plan(4, p.n, p.h, p.c_cell, p.R_node, p.omega, 0, htd.make_options(p))
+    with pytest.raises(htd.HtdError):
+        htd.htd_plan(2, p.n, p.h, p.c_cell, p.R_node, p.omega, 1, htd.make_options(p))
+
+
+def test_status_strings():
+    for s in range(8):
+        assert htd.htd_status_string(s)

@@ -58,6 +58,7 @@ def parse_args():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--cpu-sample-s", type=float, default=10.0)
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--restart", type=int, default=20)
     return ap.parse_args()
 
 
@@ -236,7 +237,8 @@ def run_ours(args):
     U = torch.zeros_like(F)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
-    solver = htd.Solver(p, precision="mixed", mode="table1", krylov="fgmres", restart=20)
+    solver = htd.Solver(p, precision="mixed", mode="table1", krylov="fgmres",
+                        restart=args.restart)
     prm = solver.params
 
     def solve_once():
@@ -312,7 +314,8 @@ def run_ours(args):
     fp64_ms = None
     fp64_info = None
     if args.fp64_steps > 0:
-        s64 = htd.Solver(p, precision="fp64", mode="table1", krylov="fgmres", restart=20)
+        s64 = htd.Solver(p, precision="fp64", mode="table1", krylov="fgmres",
+                         restart=args.restart)
         U.zero_()
         htd.htd_gmres_solve(s64.handle, F, U, TOL, 400, stream)
         t = []
@@ -344,7 +347,7 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": args.workload, "description": desc, "n": list(p.n),
                        "T": prm["T"], "nP": prm["nP"], "steps_per_apply": prm["steps"],
-                       "krylov": "FGMRES(20)", "tol": TOL, "mode": "table1",
+                       "krylov": f"FGMRES({args.restart})", "tol": TOL, "mode": "table1",
                        "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": f"independent instance per GPU x{world}"},
             "time_to_tol_ms": ms_per_step,

@@ -48,7 +48,8 @@ typedef enum {
     HTD_ERR_UNSTABLE = 4,       /* requested n_P violates the CFL bound, or not a multiple of 4 */
     HTD_ERR_NONFINITE = 5,      /* NaN/Inf in an input or a residual norm */
     HTD_ERR_NOT_CONVERGED = 6,  /* iteration cap reached before the tolerance */
-    HTD_ERR_TIMEOUT = 7         /* a bounded device-side wait gave up */
+    HTD_ERR_TIMEOUT = 7,        /* a bounded device-side wait gave up */
+    HTD_ERR_SIZE = 8            /* problem larger than a fixed-size buffer allows */
 } htd_status;
 
 enum { HTD_FP64 = 0, HTD_MIXED = 1 };            /* recurrence precision */
@@ -170,6 +171,35 @@ htd_status htd_apply_H(htd_handle h, const void *X_dev, void *Y_dev, void *strea
  */
 htd_status htd_residual_norm(htd_handle h, const void *F_dev, const void *U_dev,
                              void *r_dev, double *rel, void *stream);
+
+/*
+ * Allocation-free variant of htd_residual_norm: *rel = ||F - H U|| / ||F||
+ * (0 if F = 0), with the residual vector and the reduction partial sums kept
+ * in a fixed buffer inside the library instead of the handle's workspace.
+ * The paper has no counterpart; this exists for callers that must not
+ * allocate device memory at call time -- code that runs while a CUDA stream
+ * capture is active (cudaMalloc is not permitted during a global-mode
+ * capture), or an application whose device memory belongs to its own pool
+ * and which forbids libraries to call cudaMalloc/cudaFree in its solve loop.
+ * The call makes no cudaMalloc, cudaFree or other allocating call.
+ *   Limit: N = prod(n) <= HTD_NOALLOC_MAX_NODES; larger problems return
+ *   HTD_ERR_SIZE and compute nothing.
+ *   The buffer is a static __device__ array of HTD_NOALLOC_MAX_NODES complex128
+ *   values plus 2 * 1216 + 2 partial sums (about 4.04 MiB); every GPU that
+ *   loads the library holds it until the process exits.
+ *   All calls on a device share the one buffer and it keeps the last call's
+ *   contents; every value a call reads is written by that call first, so no
+ *   clearing is needed.  Calls whose GPU work overlaps (several streams or
+ *   host threads at once) race on the buffer: serialise them.
+ *   The first call on each device looks up the buffer's device address
+ *   (cudaGetSymbolAddress, which may load the module); make that first call
+ *   before any stream capture.  The handle's device must be current.
+ * Synchronises the stream.  Errors: HTD_ERR_ARG, HTD_ERR_SIZE,
+ * HTD_ERR_NONFINITE, HTD_ERR_CUDA.
+ */
+#define HTD_NOALLOC_MAX_NODES 262144
+htd_status htd_residual_norm_noalloc(htd_handle h, const void *F_dev, const void *U_dev,
+                                     double *rel, void *stream);
 
 /*
  * Solve H U = F with restarted GMRES(m), m = opt.restart (Sec. 2.4): flexible

@@ -660,6 +660,23 @@ htd_status create_impl(const htd_grid *grid, const double *c_cell, const double 
 
 }  // namespace
 
+namespace htd {
+
+void operator_view(const htd_ctx *c, OperatorView *out)
+{
+    out->L64 = c->L64;
+    out->kap64 = c->kap64;
+    out->imH = c->imH;
+    for (int k = 0; k < 4; ++k) {
+        out->S2[k] = std::ldexp(c->S[k], c->d - k);
+        out->M[k] = c->M[k];
+    }
+    out->ih2 = 1.0 / (c->h * c->h);
+    out->device = c->device;
+}
+
+}  // namespace htd
+
 extern "C" {
 
 void htd_default_options(htd_options *opt)
@@ -791,6 +808,7 @@ const char *htd_status_string(htd_status s)
     case HTD_ERR_NONFINITE: return "non-finite value";
     case HTD_ERR_NOT_CONVERGED: return "not converged within the iteration cap";
     case HTD_ERR_TIMEOUT: return "device-side wait timed out";
+    case HTD_ERR_SIZE: return "problem larger than the fixed-size buffer of this call allows";
     }
     return "unknown status";
 }

@@ -84,4 +84,14 @@ void launch_add_combination(const double2 *Z, int64_t ldz, int kcount, const dou
 // v = w * scale
 void launch_scale(const double2 *w, double scale, double2 *v, int64_t N, cudaStream_t s);
 
+// Read-only view of a handle's FP64 operator data (defined in htd_capi.cu).
+struct OperatorView {
+    Layout L64;             // layout of kap64 (compact N = L64.N)
+    const double *kap64;    // (h k)^2 per cell
+    const double *imH;      // omega_phys R per node
+    double S2[4], M[4], ih2;
+    int device;
+};
+void operator_view(const htd_ctx *c, OperatorView *out);
+
 }  // namespace htd

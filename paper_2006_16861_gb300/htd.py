@@ -18,7 +18,8 @@ from . import _native
 HTD_OK = 0
 STATUS = {0: "HTD_OK", 1: "HTD_ERR_ARG", 2: "HTD_ERR_CUDA", 3: "HTD_ERR_OOM",
           4: "HTD_ERR_UNSTABLE", 5: "HTD_ERR_NONFINITE", 6: "HTD_ERR_NOT_CONVERGED",
-          7: "HTD_ERR_TIMEOUT"}
+          7: "HTD_ERR_TIMEOUT", 8: "HTD_ERR_SIZE"}
+HTD_NOALLOC_MAX_NODES = 262144
 FP64, MIXED = 0, 1
 MODE_TABLE1, MODE_EXACT = 0, 1
 FGMRES, LEFT_GMRES = 0, 1
@@ -27,7 +28,8 @@ BC_DIRICHLET = 0
 
 #: every function include/htd.h declares (checked by the ABI test)
 EXPORTS = ("htd_default_options", "htd_create", "htd_destroy", "htd_plan", "htd_get_params",
-           "htd_apply_precond", "htd_apply_H", "htd_residual_norm", "htd_gmres_solve",
+           "htd_apply_precond", "htd_apply_H", "htd_residual_norm", "htd_residual_norm_noalloc",
+           "htd_gmres_solve",
            "htd_gmres_solve_host", "htd_status_string")
 
 
@@ -100,6 +102,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.htd_apply_precond.argtypes = [vp, vp, vp, vp]
     lib.htd_apply_H.argtypes = [vp, vp, vp, vp]
     lib.htd_residual_norm.argtypes = [vp, vp, vp, vp, ctypes.POINTER(d), vp]
+    lib.htd_residual_norm_noalloc.argtypes = [vp, vp, vp, ctypes.POINTER(d), vp]
     lib.htd_gmres_solve.argtypes = [vp, vp, vp, d, i, vp, ctypes.POINTER(SolveInfo)]
     lib.htd_gmres_solve_host.argtypes = [vp, vp, vp, d, i, vp, ctypes.POINTER(SolveInfo)]
     lib.htd_status_string.argtypes = [i]
@@ -212,6 +215,18 @@ def htd_residual_norm(handle: int, F, U, r=None, stream=None) -> float:
     _check(load().htd_residual_norm(handle, _dev_ptr(F), _dev_ptr(U),
                                     None if r is None else _dev_ptr(r), ctypes.byref(rel),
                                     _stream_ptr(stream)), "htd_residual_norm")
+    return rel.value
+
+
+def htd_residual_norm_noalloc(handle: int, F, U, stream=None) -> float:
+    """||F - H U|| / ||F|| without any device allocation by the call: the residual
+    and the partial sums live in a fixed buffer inside the library (problems up
+    to HTD_NOALLOC_MAX_NODES nodes).  For callers that must not allocate while
+    they run, e.g. under CUDA stream capture or with an application-owned
+    memory pool.  Calls whose GPU work overlaps race on that buffer."""
+    rel = ctypes.c_double()
+    _check(load().htd_residual_norm_noalloc(handle, _dev_ptr(F), _dev_ptr(U), ctypes.byref(rel),
+                                            _stream_ptr(stream)), "htd_residual_norm_noalloc")
     return rel.value
 
 

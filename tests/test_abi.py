@@ -119,5 +119,5 @@ def test_plan_rejects_bad_input():
 
 
 def test_status_strings():
-    for s in range(8):
+    for s in range(9):
         assert htd.htd_status_string(s)

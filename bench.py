@@ -44,7 +44,11 @@ import numpy as np  # noqa: E402
 METRIC = "recurrence Gpt-updates/s & %HBM peak; GMRES time-to-1e-6 vs FP64 plain"
 UNIT = "Gupd/s"
 TOL = 1e-6
-BYTES_PER_UPDATE = {"f32": 28, "f64": 56}   # u_j, u_{j-1}, q*kappa, d, Re F, Im F read; u_{j+1} written
+# algorithmic bytes per node of one step-kernel launch (FP32): a one-step launch
+# reads u_j, u_{j-1}, q*kappa, d, Re F, Im F and writes u_{j+1} (7 words); a
+# B-step temporally blocked launch reads the same 6 planes once and writes the
+# last two states (8 words)
+WORDS_ONE_STEP, WORDS_BLOCKED = 7, 8
 
 
 def parse_args():
@@ -281,8 +285,11 @@ def run_ours(args):
     value = all_ups / (total_ms * 1e-3) / 1e9
 
     # roofline of the step kernel: algorithmic bytes per launch / average launch time
-    avg_launch_s = ms_prec * 1e-3 / max(1, steps_run)
-    bytes_per_launch = N * BYTES_PER_UPDATE["f32"]
+    spl = max(1, int(prm.get("steps_per_launch", 1) or 1))
+    runs = steps_run // prm["steps"]
+    step_launches = runs * (-(-prm["steps"] // spl))
+    avg_launch_s = ms_prec * 1e-3 / max(1, step_launches)
+    bytes_per_launch = N * 4 * (WORDS_ONE_STEP if spl == 1 else WORDS_BLOCKED)
     achieved = bytes_per_launch / avg_launch_s / 1e9
     peak, peak_kind = peaks()
     l2_resident = bytes_per_launch < 96 * (1 << 20)
@@ -357,7 +364,10 @@ def run_ours(args):
             "fp64_iterations": fp64_info["iterations"] if fp64_info else None,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "step2d_kernel<float>" if p.ndim == 2 else "step3d_kernel<float>",
+                         "kernel": {1: f"tb2d_kernel<float,{spl}>", 2: "stream3d_kernel"}.get(
+                             prm.get("step_kernel"),
+                             "step2d_kernel<float>" if p.ndim == 2 else "step3d_kernel<float>"),
+                         "steps_per_launch": spl,
                          "bytes_per_launch": bytes_per_launch,
                          "avg_launch_us": avg_launch_s * 1e6,
                          "peak_kind": f"{peak_kind} HBM copy bandwidth",

@@ -135,6 +135,15 @@ typedef struct {
     int nP;                  /* time steps per period */
     int T;                   /* periods */
     long long steps;         /* recurrence steps per real run: T * nP */
+    int steps_per_launch;    /* recurrence steps per kernel launch (temporal
+                                blocking; 1 = one step per launch; 0 in htd_plan,
+                                which does not look at the device) */
+    int tile[3];             /* owned tile (x, y, z) of the blocked step kernel, 0 if unused */
+    int ctas_per_sm;         /* resident CTAs per SM of the blocked step kernel */
+    int waves;               /* waves of CTAs per blocked launch */
+    int step_kernel;         /* recurrence kernel in use: 0 one step per launch
+                                (gather / z-march), 1 temporally blocked 2-D
+                                (TMA tiles), 2 TMA-streamed 3-D; -1 in htd_plan */
 } htd_params;
 
 /*

@@ -4,12 +4,14 @@
 // equation" (arXiv 2006.16861).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <complex>
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "htd.h"
@@ -141,6 +143,17 @@ struct htd_ctx {
     int nb = 1;
     OutSlot *slot = nullptr;
     double2 *Fh = nullptr, *Uh = nullptr;
+    // temporally blocked path (2-D, FP32): second pair of state planes
+    void *u2 = nullptr, *u3 = nullptr;
+    htd::TbPlan tb{};
+    htd::TbMaps tbmaps{};
+    bool use_tb = false;
+    // TMA-streamed 3-D step (FP32)
+    htd::Stream3Maps s3maps{};
+    bool use_s3 = false;
+    int s3_zchunk = 0;
+    int *err_dev = nullptr;     // set by a kernel whose bounded device wait gave up
+    float step_us = 0.f;        // autotuned time per recurrence step (microseconds)
     // captured step sequence
     cudaGraphExec_t exec = nullptr;
     bool graph_tried = false;
@@ -179,7 +192,8 @@ void free_ctx(htd_ctx *c)
     for (cudaEvent_t e : c->pev)
         if (e) cudaEventDestroy(e);
     void *dev[] = {c->kap, c->dco, c->fre, c->fim, c->u0, c->u1, c->kap64, c->imH, c->V, c->Z,
-                   c->w, c->t, c->r, c->partial, c->hdev, c->slot, c->Fh, c->Uh};
+                   c->w, c->t, c->r, c->partial, c->hdev, c->slot, c->Fh, c->Uh, c->u2, c->u3,
+                   c->err_dev};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (c->hhost) cudaFreeHost(c->hhost);
@@ -196,6 +210,47 @@ htd_status run_steps_direct(htd_ctx *c, cudaStream_t s)
     HTD_CUDA(cudaMemsetAsync(A, 0, sizeof(T) * L.total, s));
     HTD_CUDA(cudaMemsetAsync(B, 0, sizeof(T) * L.total, s));
     const long long jim = c->nsteps - c->nP / 4;
+    if constexpr (std::is_same<T, float>::value) {
+      if (c->use_tb) {
+        // B steps per launch; the state pair alternates between (u0,u1) and (u2,u3)
+        T *pairs[2][2] = {{A, B}, {(T *)c->u2, (T *)c->u3}};
+        const int map_of[2][2] = {{0, 1}, {2, 3}};
+        int from = 0;
+        for (long long j0 = 0; j0 < c->nsteps; j0 += c->tb.B) {
+            htd::TbSteps<T> S;
+            S.nsub = (int)std::min<long long>(c->tb.B, c->nsteps - j0);
+            for (int q = 0; q < htd::kTbMaxSteps; ++q) {
+                const long long j = j0 + q;
+                S.a[q] = (q < S.nsub) ? (T)c->atab[j] : T(0);
+                S.b[q] = (q < S.nsub) ? (T)c->btab[j] : T(0);
+                int flags = 0;
+                if (q < S.nsub && j + 1 == jim) flags |= 1;
+                if (q < S.nsub && j + 1 == c->nsteps) flags |= 2;
+                S.flags[q] = flags;
+            }
+            htd::launch_tb2d<T>(c->tb, c->tbmaps, map_of[from][0], map_of[from][1], L,
+                                pairs[1 - from][0], pairs[1 - from][1], (const T *)c->dco,
+                                (const T *)c->fre, (const T *)c->fim, C, S, c->slot,
+                                c->err_dev, s);
+            from = 1 - from;
+        }
+        HTD_CUDA(cudaGetLastError());
+        return HTD_OK;
+      }
+    }
+    if constexpr (std::is_same<T, float>::value) {
+        if (c->use_s3) {
+            for (long long j = 0; j < c->nsteps; ++j) {
+                int flags = 0;
+                if (j + 1 == jim) flags |= 1;
+                if (j + 1 == c->nsteps) flags |= 2;
+                htd::launch_stream3d(c->s3maps, (int)(j & 1), L, (j & 1) ? A : B, C, (T)c->atab[j],
+                                     (T)c->btab[j], c->slot, flags, c->s3_zchunk, c->err_dev, s);
+            }
+            HTD_CUDA(cudaGetLastError());
+            return HTD_OK;
+        }
+    }
     for (long long j = 0; j < c->nsteps; ++j) {
         T *cur = (j & 1) ? B : A;
         T *oth = (j & 1) ? A : B;
@@ -439,6 +494,17 @@ htd_status gmres(htd_ctx *c, const double2 *F, double2 *U, double tol, int maxit
     if (!std::isfinite(loc.rel_res_true)) st = HTD_ERR_NONFINITE;
 out:
     if (collect_precond_time(c) != HTD_OK && st == HTD_OK) st = HTD_ERR_CUDA;
+    {
+        // a bounded device-side wait that gave up makes the whole result invalid
+        int flag = 0;
+        if (cudaMemcpy(&flag, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            (void)cudaGetLastError();
+            if (st == HTD_OK) st = HTD_ERR_CUDA;
+        } else if (flag) {
+            cudaMemset(c->err_dev, 0, sizeof(int));
+            st = HTD_ERR_TIMEOUT;
+        }
+    }
     loc.ms_precond = c->ms_precond - msp0;
     loc.launches = htd::g_launches - launches0;
     loc.iterations = its;
@@ -457,6 +523,90 @@ htd_status upload_recurrence(htd_ctx *c, const std::vector<double> &qkap, const 
     for (size_t i = 0; i < (size_t)L.total; ++i) { a[i] = (T)qkap[i]; b[i] = (T)dcoef[i]; }
     HTD_CUDA(cudaMemcpy(c->kap, a.data(), sizeof(T) * L.total, cudaMemcpyHostToDevice));
     HTD_CUDA(cudaMemcpy(c->dco, b.data(), sizeof(T) * L.total, cudaMemcpyHostToDevice));
+    return HTD_OK;
+}
+
+// Time the one-step kernel and every blocked configuration on the handle's own
+// (zeroed) planes and keep the fastest per step.  No output is written: the
+// step flags are zero during tuning.
+htd_status autotune_tb2d(htd_ctx *c, int want_B, int want_RPT)
+{
+    const Layout &L = c->Lr;
+    std::vector<htd::TbPlan> all = htd::tb2d_candidates<float>(L, want_B);
+    std::vector<htd::TbPlan> cands;
+    for (const htd::TbPlan &p : all)
+        if (want_RPT == 0 || p.RPT == want_RPT) cands.push_back(p);
+    if (cands.empty()) return HTD_OK;
+    const size_t bytes = sizeof(float) * (size_t)L.total;
+    HTD_CUDA(cudaMalloc(&c->u2, bytes));
+    HTD_CUDA(cudaMemset(c->u2, 0, bytes));
+    HTD_CUDA(cudaMalloc(&c->u3, bytes));
+    HTD_CUDA(cudaMemset(c->u3, 0, bytes));
+    cudaStream_t s;
+    HTD_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    cudaEvent_t e0, e1;
+    HTD_CUDA(cudaEventCreate(&e0));
+    HTD_CUDA(cudaEventCreate(&e1));
+    const StepCoef<float> C = cast_coef<float>(c->C);
+    float *planes[5] = {(float *)c->u0, (float *)c->u1, (float *)c->u2, (float *)c->u3,
+                        (float *)c->kap};
+    const int reps = 4;
+    // the one-step kernel
+    float best_us = INFINITY;
+    {
+        for (int r = 0; r < 2 + reps * 4; ++r) {
+            if (r == 2) HTD_CUDA(cudaEventRecord(e0, s));
+            htd::launch_step<float>(L, (const float *)c->u0, (float *)c->u1, (const float *)c->kap,
+                                    (const float *)c->dco, (const float *)c->fre,
+                                    (const float *)c->fim, C, 0.f, 0.f, c->slot, 0, s);
+        }
+        HTD_CUDA(cudaEventRecord(e1, s));
+        HTD_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        HTD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        best_us = 1e3f * ms / (reps * 4);
+    }
+    const float one_step_us = best_us;
+    if (want_B > 0) best_us = INFINITY;     // a requested block depth is always used
+    int best = -1;
+    htd::TbMaps best_maps{};
+    for (size_t k = 0; k < cands.size(); ++k) {
+        htd::TbMaps maps;
+        if (!htd::make_tb2d_maps<float>(L, cands[k], planes, &maps)) continue;
+        htd::TbSteps<float> S;
+        S.nsub = cands[k].B;
+        for (int q = 0; q < htd::kTbMaxSteps; ++q) { S.a[q] = 0.f; S.b[q] = 0.f; S.flags[q] = 0; }
+        for (int r = 0; r < 2 + reps; ++r) {
+            if (r == 2) HTD_CUDA(cudaEventRecord(e0, s));
+            htd::launch_tb2d<float>(cands[k], maps, 0, 1, L, (float *)c->u2, (float *)c->u3,
+                                    (const float *)c->dco, (const float *)c->fre,
+                                    (const float *)c->fim, C, S, c->slot, c->err_dev, s);
+        }
+        HTD_CUDA(cudaEventRecord(e1, s));
+        HTD_CUDA(cudaEventSynchronize(e1));
+        HTD_CUDA(cudaGetLastError());
+        float ms = 0.f;
+        HTD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        const float us = 1e3f * ms / (reps * cands[k].B);
+        cands[k].us_per_step = us;
+        if (us < best_us) {
+            best_us = us;
+            best = (int)k;
+            best_maps = maps;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    int flag = 0;
+    HTD_CUDA(cudaMemcpy(&flag, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) return HTD_ERR_TIMEOUT;
+    c->step_us = (best >= 0) ? best_us : one_step_us;
+    if (best >= 0) {
+        c->use_tb = true;
+        c->tb = cands[best];
+        c->tbmaps = best_maps;
+    }
     return HTD_OK;
 }
 
@@ -545,6 +695,11 @@ htd_status plan_impl(const htd_grid *grid, const double *c_cell, const double *R
     P.alpha = x * x / (2.0 - 2.0 * std::cos(x));
     P.beta = x / std::sin(x);
     P.rho = (opt.rho > 0.0) ? opt.rho : 1.0 / opt.T;
+    P.steps_per_launch = 0;
+    P.tile[0] = P.tile[1] = P.tile[2] = 0;
+    P.ctas_per_sm = 0;
+    P.waves = 0;
+    P.step_kernel = -1;
     return HTD_OK;
 }
 
@@ -608,6 +763,10 @@ htd_status create_impl(const htd_grid *grid, const double *c_cell, const double 
         HTD_CUDA(cudaMalloc(pp, bytes));
         HTD_CUDA(cudaMemset(*pp, 0, bytes));
     }
+    HTD_CUDA(cudaMalloc((void **)&c->err_dev, sizeof(int)));
+    HTD_CUDA(cudaMemset(c->err_dev, 0, sizeof(int)));
+    HTD_CUDA(cudaMalloc((void **)&c->slot, sizeof(OutSlot)));
+    HTD_CUDA(cudaMemset(c->slot, 0, sizeof(OutSlot)));
     HTD_CUDA(cudaMalloc((void **)&c->kap64, sizeof(double) * c->L64.total));
     HTD_CUDA(cudaMalloc((void **)&c->imH, sizeof(double) * N));
 
@@ -639,6 +798,32 @@ htd_status create_impl(const htd_grid *grid, const double *c_cell, const double 
     HTD_CUDA(cudaMemcpy(c->kap64, k64.data(), sizeof(double) * c->L64.total, cudaMemcpyHostToDevice));
     HTD_CUDA(cudaMemcpy(c->imH, imh.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
 
+    // temporal blocking for the 2-D FP32 recurrence, picked by timing against the
+    // one-step kernel.  HTD_TB=0 disables it; HTD_TB=4/8 (and HTD_TB_RPT=8/12/16/20)
+    // force a blocked configuration of that depth (and rows per thread).
+    {
+        const char *env = std::getenv("HTD_TB");
+        const char *env_r = std::getenv("HTD_TB_RPT");
+        const int want = env ? std::atoi(env) : 0;
+        const int want_r = env_r ? std::atoi(env_r) : 0;
+        if (d == 2 && mixed && !(env && want == 0)) {
+            htd_status ts = autotune_tb2d(c, want, want_r);
+            if (ts != HTD_OK) return ts;
+        }
+    }
+
+    // TMA-streamed 3-D FP32 step (HTD_S3=0 keeps the register z-march kernel)
+    {
+        const char *env = std::getenv("HTD_S3");
+        if (d == 3 && mixed && !(env && std::atoi(env) == 0)) {
+            float *planes[6] = {(float *)c->u0, (float *)c->u1, (float *)c->kap, (float *)c->dco,
+                                (float *)c->fre, (float *)c->fim};
+            c->use_s3 = htd::make_stream3d_maps(L, planes, &c->s3maps);
+            if (c->use_s3) c->s3_zchunk = htd::stream3d_zchunk(L);
+            (void)cudaGetLastError();
+        }
+    }
+
     // Krylov workspace
     const size_t vb = sizeof(double2) * (size_t)N;
     HTD_CUDA(cudaMalloc((void **)&c->V, vb * (c->m + 1)));
@@ -652,8 +837,6 @@ htd_status create_impl(const htd_grid *grid, const double *c_cell, const double 
     HTD_CUDA(cudaMallocHost((void **)&c->hhost, sizeof(double2) * 3 * 72));
     HTD_CUDA(cudaEventCreate(&c->pev[0]));
     HTD_CUDA(cudaEventCreate(&c->pev[1]));
-    HTD_CUDA(cudaMalloc((void **)&c->slot, sizeof(OutSlot)));
-    HTD_CUDA(cudaMemset(c->slot, 0, sizeof(OutSlot)));
     HTD_CUDA(cudaDeviceSynchronize());
     return HTD_OK;
 }
@@ -741,6 +924,13 @@ htd_status htd_get_params(htd_handle h, htd_params *out)
     P.nP = h->nP;
     P.T = h->T;
     P.steps = h->nsteps;
+    P.steps_per_launch = h->use_tb ? h->tb.B : 1;
+    P.tile[0] = h->use_tb ? h->tb.TX : 0;
+    P.tile[1] = h->use_tb ? h->tb.TY : 0;
+    P.tile[2] = 0;
+    P.ctas_per_sm = h->use_tb ? h->tb.occ : 0;
+    P.waves = h->use_tb ? h->tb.waves : 0;
+    P.step_kernel = h->use_tb ? 1 : (h->use_s3 ? 2 : 0);
     return HTD_OK;
 }
 

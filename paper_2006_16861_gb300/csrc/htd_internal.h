@@ -2,8 +2,10 @@
 // Not part of the public ABI (include/htd.h is).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <vector>
 
 #include "htd.h"
 
@@ -41,6 +43,26 @@ struct StepCoef {
     T mt[4];    // M_s (mass weights per Hamming distance)
 };
 
+// (2 - K) u at one node of the 2-D cell-form operator (App. A), h^2-scaled
+// coefficients as in StepCoef.  u<r><c>: u_j at row offset r, column offset c
+// (m = -1, 0, p = +1); k<ay><ax>: q*kappa of the node's four cells; pm, p0, pp:
+// u_{-1,-1} + u_{-1,+1}, u_{0,-1} + u_{0,+1}, u_{+1,-1} + u_{+1,+1}; hk0 = k00 + k01,
+// hk1 = k10 + k11.  Written as a shallow tree of independent partial sums so
+// that the one-step and the temporally blocked kernels (which share it) give
+// identical results and have short dependency chains.
+template <typename T>
+__device__ __forceinline__ T stencil2d(const StepCoef<T> &C, T umm, T um0, T ump, T u0m, T u00,
+                                       T u0p, T upm, T up0, T upp, T k00, T k01, T k10, T k11,
+                                       T pm, T p0, T pp, T hk0, T hk1)
+{
+    const T center = C.c0 + C.mt[0] * (hk0 + hk1);
+    const T edge = (um0 + up0) + p0;
+    const T corner = pm + pp;
+    const T m1 = (hk0 * um0 + hk1 * up0) + ((k00 + k10) * u0m + (k01 + k11) * u0p);
+    const T m2 = (k00 * umm + k01 * ump) + (k10 * upm + k11 * upp);
+    return (center * u00 - C.cs[1] * edge) + (C.mt[1] * m1 + (C.mt[2] * m2 - C.cs[2] * corner));
+}
+
 // Output targets of a preconditioner run, read by the step kernels from device
 // memory so that a captured graph can be replayed for any output vector.
 struct OutSlot {
@@ -64,6 +86,53 @@ void launch_split(const Layout &L, const double2 *F, T *fre, T *fim, int flip, c
 
 void launch_set_slot(OutSlot *slot, double *final_part, double *snap_part, cudaStream_t s);
 
+// ---- temporally blocked 2-D recurrence (htd_tblock.cu) ------------------------
+
+constexpr int kTbMaxSteps = 8;
+
+// per-launch step data: forcing coefficients a_j, b_j of the nsub steps and
+// their output flags (bit 0: snapshot, bit 1: final state)
+template <typename T>
+struct TbSteps {
+    T a[kTbMaxSteps];
+    T b[kTbMaxSteps];
+    int flags[kTbMaxSteps];
+    int nsub;
+};
+
+struct TbPlan {
+    int B = 0;          // steps per launch (halo width)
+    int RPT = 0;        // rows per thread
+    int RG = 0;         // row groups: threads = 64 * RG, tile rows H = RG * RPT
+    int TX = 0, TY = 0; // owned tile
+    int H = 0;          // tile rows including the halo
+    size_t smem = 0;    // dynamic shared memory per CTA
+    int grid_x = 0, grid_y = 0;
+    int occ = 0;        // resident CTAs per SM
+    int waves = 0;      // ceil(tiles / (SMs * occ))
+    float us_per_step = 0.f;   // measured by the autotuner
+};
+
+// TMA descriptors of the planes u0, u1, u2, u3 and q*kappa.
+struct TbMaps {
+    CUtensorMap m[5];
+};
+
+// The blocked-kernel configurations (B = 4 or 8 steps per launch, want_B = 0:
+// both; rows per thread 8..20) that fit the device, for a 2-D grid.
+template <typename T>
+std::vector<TbPlan> tb2d_candidates(const Layout &L, int want_B);
+
+template <typename T>
+bool make_tb2d_maps(const Layout &L, const TbPlan &p, T *const planes[5], TbMaps *maps);
+
+// nsub <= B steps from the state pair (maps in0, in1) into the planes uC, uD;
+// a timed-out TMA wait sets *err = 1.
+template <typename T>
+void launch_tb2d(const TbPlan &p, const TbMaps &maps, int in0, int in1, const Layout &L, T *uC,
+                 T *uD, const T *dco, const T *fre, const T *fim, const StepCoef<T> &C,
+                 const TbSteps<T> &S, const OutSlot *slot, int *err, cudaStream_t s);
+
 // Y = H X (F == null) or Y = F - H X, complex128 compact vectors.
 void launch_apply_H(const Layout &L, const double *kap64, const double *imH,
                     const double S2[4], const double M[4], double ih2,
@@ -83,6 +152,21 @@ void launch_add_combination(const double2 *Z, int64_t ldz, int kcount, const dou
                             double2 *U, int64_t N, cudaStream_t s);
 // v = w * scale
 void launch_scale(const double2 *w, double scale, double2 *v, int64_t N, cudaStream_t s);
+
+// ---- TMA-streamed 3-D step, FP32 (htd_stream3d.cu) -----------------------------
+
+// TMA descriptors: u0, u1 and q*kappa with the x-y halo; d, Re F, Im F, u0, u1
+// as exact node boxes.
+struct Stream3Maps {
+    CUtensorMap m[8];
+};
+size_t stream3d_smem_bytes();
+bool make_stream3d_maps(const Layout &L, float *const planes[6], Stream3Maps *maps);
+int stream3d_zchunk(const Layout &L);
+// one step; from = 0: u_j in u0 and u_{j-1} (overwritten) in u1, from = 1 swapped
+void launch_stream3d(const Stream3Maps &maps, int from, const Layout &L, float *um,
+                     const StepCoef<float> &C, float a, float b, const OutSlot *slot, int flags,
+                     int zchunk, int *err, cudaStream_t s);
 
 // Read-only view of a handle's FP64 operator data (defined in htd_capi.cu).
 struct OperatorView {

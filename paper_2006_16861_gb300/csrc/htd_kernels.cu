@@ -53,11 +53,11 @@ step2d_kernel(const T *__restrict__ u, T *__restrict__ um, const T *__restrict__
     const T upm = u[i + P - 1], up0 = u[i + P], upp = u[i + P + 1];
     // q*kappa of the four cells around the node, k<ay><ax>: cell at row y-1+ay, column x-1+ax
     const T k00 = kap[i - P - 1], k01 = kap[i - P], k10 = kap[i - 1], k11 = kap[i];
-    T acc = (C.c0 + C.mt[0] * ((k00 + k01) + (k10 + k11))) * u00;
-    acc -= C.cs[1] * ((um0 + up0) + (u0m + u0p));
-    acc -= C.cs[2] * ((umm + ump) + (upm + upp));
-    acc += C.mt[1] * ((k00 + k01) * um0 + (k10 + k11) * up0 + (k00 + k10) * u0m + (k01 + k11) * u0p);
-    acc += C.mt[2] * (k00 * umm + k01 * ump + k10 * upm + k11 * upp);
+    // pair sums shared with the temporally blocked kernel (same order, same result)
+    const T pm = umm + ump, p0 = u0m + u0p, pp = upm + upp;
+    const T hk0 = k00 + k01, hk1 = k10 + k11;
+    const T acc = stencil2d(C, umm, um0, ump, u0m, u00, u0p, upm, up0, upp, k00, k01, k10, k11,
+                            pm, p0, pp, hk0, hk1);
     const T g = a * fre[i] - b * fim[i];
     const T d = dco[i];
     const T uprev = um[i];
@@ -70,6 +70,12 @@ step2d_kernel(const T *__restrict__ u, T *__restrict__ um, const T *__restrict__
     }
 }
 
+// Each thread walks a column of kZChunk planes in z with a 3x3x3 register
+// window of u_j (planes z-1, z, z+1) and a 2x2x2 window of cells, so a node
+// costs 9 new loads of u_j and 4 of q*kappa (neighbours in x and y come from
+// L1, the plane below and the node's own plane from registers).
+constexpr int kZChunk = 16;
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 step3d_kernel(const T *__restrict__ u, T *__restrict__ um, const T *__restrict__ kap,
@@ -78,62 +84,93 @@ step3d_kernel(const T *__restrict__ u, T *__restrict__ um, const T *__restrict__
 {
     const int64_t ix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t iy = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
-    const int64_t iz = blockIdx.z;
+    const int64_t z0 = (int64_t)blockIdx.z * kZChunk;
+    const int64_t z1 = min((int64_t)L.nz, z0 + kZChunk);
     if (ix >= L.nx || iy >= L.ny) return;
     const int64_t P = L.pitch, Q = L.plane;
-    const int64_t i = (iz + 1) * Q + (iy + 1) * P + L.xl + ix;
-    // q*kappa of the 8 cells around the node: k[az][ay][ax] at plane z-1+az, row y-1+ay, column x-1+ax
+    const int64_t col = (iy + 1) * P + L.xl + ix;     // (y, x) offset of the node in any plane
+    // w[p][oy][ox]: u_j at stored plane (iz + p), row offset oy-1, column offset ox-1
+    T w[3][3][3];
+    // k[az][ay][ax]: q*kappa of the cell at stored plane (iz + az), row y-1+ay, column x-1+ax
     T k[2][2][2];
 #pragma unroll
-    for (int az = 0; az < 2; ++az)
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int oy = 0; oy < 3; ++oy)
+#pragma unroll
+            for (int ox = 0; ox < 3; ++ox)
+                w[p][oy][ox] = u[(z0 + p) * Q + col + (oy - 1) * P + (ox - 1)];
+#pragma unroll
+    for (int ay = 0; ay < 2; ++ay)
+#pragma unroll
+        for (int ax = 0; ax < 2; ++ax)
+            k[0][ay][ax] = kap[z0 * Q + col - (1 - ay) * P - (1 - ax)];
+    for (int64_t iz = z0; iz < z1; ++iz) {
+#pragma unroll
+        for (int oy = 0; oy < 3; ++oy)
+#pragma unroll
+            for (int ox = 0; ox < 3; ++ox)
+                w[2][oy][ox] = u[(iz + 2) * Q + col + (oy - 1) * P + (ox - 1)];
 #pragma unroll
         for (int ay = 0; ay < 2; ++ay)
 #pragma unroll
             for (int ax = 0; ax < 2; ++ax)
-                k[az][ay][ax] = kap[i - (1 - az) * Q - (1 - ay) * P - (1 - ax)];
-    // sums of kappa over the cells shared by the node and its neighbour at offset
-    // o - 1 (o in 0..2 per axis): offset -1 keeps the lower cell, +1 the upper, 0 both
-    T kx[2][2][3];
+                k[1][ay][ax] = kap[(iz + 1) * Q + col - (1 - ay) * P - (1 - ax)];
+        // sums of kappa over the cells shared by the node and its neighbour at
+        // offset o - 1 (o in 0..2 per axis): -1 keeps the lower cell, +1 the upper, 0 both
+        T kx[2][2][3];
 #pragma unroll
-    for (int az = 0; az < 2; ++az)
+        for (int az = 0; az < 2; ++az)
 #pragma unroll
-        for (int ay = 0; ay < 2; ++ay) {
-            kx[az][ay][0] = k[az][ay][0];
-            kx[az][ay][1] = k[az][ay][0] + k[az][ay][1];
-            kx[az][ay][2] = k[az][ay][1];
+            for (int ay = 0; ay < 2; ++ay) {
+                kx[az][ay][0] = k[az][ay][0];
+                kx[az][ay][1] = k[az][ay][0] + k[az][ay][1];
+                kx[az][ay][2] = k[az][ay][1];
+            }
+        T kxy[2][3][3];
+#pragma unroll
+        for (int az = 0; az < 2; ++az)
+#pragma unroll
+            for (int ox = 0; ox < 3; ++ox) {
+                kxy[az][0][ox] = kx[az][0][ox];
+                kxy[az][1][ox] = kx[az][0][ox] + kx[az][1][ox];
+                kxy[az][2][ox] = kx[az][1][ox];
+            }
+        T acc = T(0);
+#pragma unroll
+        for (int oz = 0; oz < 3; ++oz)
+#pragma unroll
+            for (int oy = 0; oy < 3; ++oy)
+#pragma unroll
+                for (int ox = 0; ox < 3; ++ox) {
+                    const int s = (oz != 1) + (oy != 1) + (ox != 1);
+                    const T ks = (oz == 0) ? kxy[0][oy][ox]
+                               : (oz == 2) ? kxy[1][oy][ox] : kxy[0][oy][ox] + kxy[1][oy][ox];
+                    const T coef = (s == 0) ? C.c0 + C.mt[0] * ks : C.mt[s] * ks - C.cs[s];
+                    acc += coef * w[oz][oy][ox];
+                }
+        const int64_t i = (iz + 1) * Q + col;
+        const T g = a * fre[i] - b * fim[i];
+        const T d = dco[i];
+        const T uprev = um[i];
+        const T unew = d * (acc + g - T(2) * uprev) + uprev;
+        um[i] = unew;
+        if (flags) {
+            const int64_t c = (iz * L.ny + iy) * L.nx + ix;
+            if ((flags & 1) && slot->snap_part) slot->snap_part[2 * c] = (double)unew;
+            if ((flags & 2) && slot->final_part) slot->final_part[2 * c] = (double)unew;
         }
-    T kxy[2][3][3];
-#pragma unroll
-    for (int az = 0; az < 2; ++az)
-#pragma unroll
-        for (int ox = 0; ox < 3; ++ox) {
-            kxy[az][0][ox] = kx[az][0][ox];
-            kxy[az][1][ox] = kx[az][0][ox] + kx[az][1][ox];
-            kxy[az][2][ox] = kx[az][1][ox];
-        }
-    T acc = T(0);
-#pragma unroll
-    for (int oz = 0; oz < 3; ++oz)
 #pragma unroll
         for (int oy = 0; oy < 3; ++oy)
 #pragma unroll
             for (int ox = 0; ox < 3; ++ox) {
-                const int s = (oz != 1) + (oy != 1) + (ox != 1);
-                const T ks = (oz == 0) ? kxy[0][oy][ox]
-                           : (oz == 2) ? kxy[1][oy][ox] : kxy[0][oy][ox] + kxy[1][oy][ox];
-                const T uv = u[i + (oz - 1) * Q + (oy - 1) * P + (ox - 1)];
-                const T coef = (s == 0) ? C.c0 + C.mt[0] * ks : C.mt[s] * ks - C.cs[s];
-                acc += coef * uv;
+                w[0][oy][ox] = w[1][oy][ox];
+                w[1][oy][ox] = w[2][oy][ox];
             }
-    const T g = a * fre[i] - b * fim[i];
-    const T d = dco[i];
-    const T uprev = um[i];
-    const T unew = d * (acc + g - T(2) * uprev) + uprev;
-    um[i] = unew;
-    if (flags) {
-        const int64_t c = (iz * L.ny + iy) * L.nx + ix;
-        if ((flags & 1) && slot->snap_part) slot->snap_part[2 * c] = (double)unew;
-        if ((flags & 2) && slot->final_part) slot->final_part[2 * c] = (double)unew;
+#pragma unroll
+        for (int ay = 0; ay < 2; ++ay)
+#pragma unroll
+            for (int ax = 0; ax < 2; ++ax) k[0][ay][ax] = k[1][ay][ax];
     }
 }
 
@@ -148,8 +185,9 @@ void launch_step(const Layout &L, const T *u, T *um, const T *kap, const T *dco,
         step2d_kernel<T><<<grd, blk, 0, s>>>(u, um, kap, dco, fre, fim, L, C, a, b, slot, flags);
         ++g_launches;
     } else {
-        dim3 blk(32, 4);
-        dim3 grd((unsigned)((L.nx + 31) / 32), (unsigned)((L.ny + 3) / 4), (unsigned)L.nz);
+        dim3 blk(32, 8);
+        dim3 grd((unsigned)((L.nx + 31) / 32), (unsigned)((L.ny + 7) / 8),
+                 (unsigned)((L.nz + kZChunk - 1) / kZChunk));
         step3d_kernel<T><<<grd, blk, 0, s>>>(u, um, kap, dco, fre, fim, L, C, a, b, slot, flags);
         ++g_launches;
     }

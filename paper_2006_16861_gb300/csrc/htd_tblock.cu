@@ -1,0 +1,381 @@
+// Temporally blocked 2-D recurrence: B steps of I_acd (Def. of I_acd, with
+// Table 1's windowed forcing) per launch from shared memory, tiles moved by TMA.
+//
+// Each CTA owns a TX x TY tile of nodes (TX = 64 - 2B) and needs it with a halo
+// of B nodes (64 columns, H = TY + 2B rows), plus one more ring for the
+// neighbour reads, the q*kappa of the cells touching those nodes, the per-node
+// d and the two forcing planes.  All six come from the padded device layout,
+// where a cell sits at the position of its lower-corner node, so one TMA box
+// of kBoxW x (H + 2) elements per array covers everything: one thread issues
+// six cp.async.bulk.tensor.2d copies (zero fill outside the array) that
+// complete on one mbarrier; the box starts at a 16-byte aligned column.
+//
+// Step s (s = 0 .. nsub-1) updates the nodes of the ring-shrunk region
+// [s+1, 63-s) x [s+1, H-s-1); after nsub <= B steps the owned core
+// [B, B+TX) x [B, B+TY) holds u_{j+nsub} and u_{j+nsub-1}, which are stored to
+// the other pair of global state planes (so that neighbouring CTAs never read
+// a half-updated halo).  Per node the arithmetic is exactly that of
+// step2d_kernel (same expression, same order).
+//
+// Threads: 256 = 64 columns x 4 row groups; a thread walks down its rows with
+// a 3x3 register window of u_j and a 2x2 window of cells.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "htd_internal.h"
+
+namespace htd {
+
+namespace {
+
+constexpr int kW = 64;           // tile width including the halo
+constexpr int kBoxW = 72;        // TMA box width: 64 + 2 pad columns + up to 3 for alignment, rounded
+// threads = 64 columns x RG row groups (RG = 8 or 16)
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;   // 1 s bound on the mbarrier wait
+
+__host__ __device__ inline size_t round128(size_t b) { return (b + 127) & ~(size_t)127; }
+
+template <typename T>
+__host__ __device__ inline size_t tb2d_array_bytes(int H)
+{
+    return round128((size_t)(H + 2) * kBoxW * sizeof(T));
+}
+
+template <typename T>
+size_t tb2d_smem_bytes(int H)
+{
+    return 3 * tb2d_array_bytes<T>(H) + 16 + 128;   // three boxes, the mbarrier, alignment slack
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait on phase 0 of the mbarrier; false if the time limit ran out
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar)
+{
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, 0)) {
+        if (global_ns() - t0 > kWaitLimitNs) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+template <typename T, int B, int RPT, int RG>
+__global__ void __launch_bounds__(kW * RG, 1)
+tb2d_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, T *__restrict__ uC,
+            T *__restrict__ uD, const T *__restrict__ dco, const T *__restrict__ fre,
+            const T *__restrict__ fim, Layout L, StepCoef<T> C, TbSteps<T> S,
+            const OutSlot *__restrict__ slot, int *__restrict__ err)
+{
+    constexpr int W = kW, TX = W - 2 * B, BW = kBoxW;
+    constexpr int H = RG * RPT, TY = H - 2 * B;
+    constexpr int kAlign = 16 / (int)sizeof(T);          // TMA column alignment in elements
+    extern __shared__ unsigned char smem_raw[];
+    const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127;
+    const size_t ab = tb2d_array_bytes<T>(H);
+    T *su0 = reinterpret_cast<T *>(base);                 // u_j   (box row r = stored row y0 + r)
+    T *su1 = reinterpret_cast<T *>(base + ab);            // u_{j-1}
+    T *sk = reinterpret_cast<T *>(base + 2 * ab);         // q*kappa per cell
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base + 3 * ab);
+
+    const int tid = threadIdx.x;
+    const int64_t x0 = (int64_t)blockIdx.x * TX - B;      // global x of local column 0
+    const int64_t y0 = (int64_t)blockIdx.y * TY - B;      // global y of local row 0
+    // box origin: stored row y0 (local pad row 0 = global row y0 - 1), stored
+    // column of local pad column 0 rounded down to the TMA alignment
+    const int64_t c0 = L.xl + x0 - 1;
+    const int xs = (int)(c0 - (c0 % kAlign));
+    const int off = (int)(c0 - xs);                        // 0 .. kAlign-1
+
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        mbar_expect_tx(bar, (unsigned)(3 * (size_t)(H + 2) * BW * sizeof(T)));
+        const int ys = (int)y0;
+        tma_load_2d(su0, &maps.m[in0], xs, ys, bar);
+        tma_load_2d(su1, &maps.m[in1], xs, ys, bar);
+        tma_load_2d(sk, &maps.m[4], xs, ys, bar);
+    }
+
+    // this thread's nodes: column lx, rows row0 .. row0 + RPT - 1; their d and
+    // forcing stay in registers for all the launch's steps
+    const int lx = tid & (W - 1);
+    const int row0 = (tid / W) * RPT;
+    const int64_t gx = x0 + lx;
+    const bool col_in_domain = gx >= 0 && gx < L.nx;
+    T rd[RPT], rfr[RPT], rfi[RPT];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+        const int64_t gy = y0 + row0 + i;
+        const bool in = col_in_domain && gy >= 0 && gy < L.ny;
+        const int64_t g = in ? (gy + 1) * L.pitch + L.xl + gx : 0;
+        rd[i] = in ? dco[g] : T(0);
+        rfr[i] = in ? fre[g] : T(0);
+        rfi[i] = in ? fim[g] : T(0);
+    }
+
+    __syncthreads();                                      // barrier initialised before anyone waits
+    const bool ok = mbar_wait_bounded(bar);
+    if (__syncthreads_or(!ok)) {
+        // give up: record it, wait (bounded) once more for the copies in flight, return
+        if (tid == 0) {
+            atomicExch(err, 1);
+            mbar_wait_bounded(bar);
+        }
+        __syncthreads();
+        return;
+    }
+
+    // smem positions: node (ly, lx) at row ly + 1, column lx + 1 + off; its
+    // cells (ly + ay, lx + ax) at row ly + ay, column lx + ax + off
+    const bool col_owned = lx >= B && lx < B + TX;
+    const int cc = lx + off;                               // smem column of (lx - 1)
+    // rows of this tile inside the domain: y0 + ly in [0, ny)
+    const int dom_lo = (int)max((int64_t)0, -y0);
+    const int dom_hi = (int)min((int64_t)H, (int64_t)L.ny - y0);
+
+    // per-step forcing coefficients and flags, staged in shared memory so that
+    // the step loop does not index the parameter block dynamically
+    __shared__ T s_a[kTbMaxSteps], s_b[kTbMaxSteps];
+    __shared__ int s_flags[kTbMaxSteps];
+    if (tid == 0) {
+#pragma unroll
+        for (int q = 0; q < kTbMaxSteps; ++q) {
+            s_a[q] = S.a[q];
+            s_b[q] = S.b[q];
+            s_flags[q] = S.flags[q];
+        }
+    }
+    __syncthreads();
+
+    for (int s = 0; s < S.nsub; ++s) {
+        const T *__restrict__ cur = (s & 1) ? su1 : su0;   // u_{j+s}
+        T *__restrict__ prv = (s & 1) ? su0 : su1;         // u_{j+s-1}, overwritten by u_{j+s+1}
+        const T a = s_a[s], b = s_b[s];
+        const int flags = s_flags[s];
+        const bool col_ok = col_in_domain && lx >= s + 1 && lx < W - s - 1;
+        // rows updated in this step: ring-shrunk region and the domain
+        const int lo = max(s + 1, dom_lo), hi = min(H - s - 1, dom_hi);
+        // window: rows row0 - 1 (m) and row0 (0); outer-pair sums of u rows and
+        // horizontal sums of cell rows carried from row to row
+        const T *cp = cur + row0 * BW + cc;
+        T umm = cp[0], um0 = cp[1], ump = cp[2];
+        T u0m = cp[BW], u00 = cp[BW + 1], u0p = cp[BW + 2];
+        T pm = umm + ump, p0 = u0m + u0p;
+        T k00 = sk[row0 * BW + cc], k01 = sk[row0 * BW + cc + 1];
+        T hk0 = k00 + k01;
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+            const int ly = row0 + i;
+            const T *np = cur + (ly + 2) * BW + cc;
+            const T upm = np[0], up0 = np[1], upp = np[2];
+            const T k10 = sk[(ly + 1) * BW + cc], k11 = sk[(ly + 1) * BW + cc + 1];
+            const T pp = upm + upp;
+            const T hk1 = k10 + k11;
+            const T acc = stencil2d(C, umm, um0, ump, u0m, u00, u0p, upm, up0, upp, k00, k01, k10,
+                                    k11, pm, p0, pp, hk0, hk1);
+            if (col_ok && ly >= lo && ly < hi) {
+                const int ni = (ly + 1) * BW + cc + 1;
+                const T g = a * rfr[i] - b * rfi[i];
+                const T uprev = prv[ni];
+                const T unew = rd[i] * (acc + g - T(2) * uprev) + uprev;
+                prv[ni] = unew;
+                if (flags && col_owned && ly >= B && ly < B + TY) {
+                    const int64_t c = (y0 + ly) * L.nx + gx;
+                    if ((flags & 1) && slot->snap_part) slot->snap_part[2 * c] = (double)unew;
+                    if ((flags & 2) && slot->final_part) slot->final_part[2 * c] = (double)unew;
+                }
+            }
+            umm = u0m; um0 = u00; ump = u0p; pm = p0;
+            u0m = upm; u00 = up0; u0p = upp; p0 = pp;
+            k00 = k10; k01 = k11; hk0 = hk1;
+        }
+        __syncthreads();
+    }
+
+    // ---- store the owned core of the last two states ----------------------
+    const T *last = (S.nsub & 1) ? su1 : su0;               // u_{j+nsub}
+    const T *prev = (S.nsub & 1) ? su0 : su1;               // u_{j+nsub-1}
+    if (lx >= B && lx < B + TX && col_in_domain) {
+        for (int ly = max(row0, B); ly < min(row0 + RPT, B + TY); ++ly) {
+            const int64_t gy = y0 + ly;
+            if (gy >= L.ny) break;
+            const int64_t g = (gy + 1) * L.pitch + L.xl + gx;
+            const int si = (ly + 1) * BW + cc + 1;
+            uC[g] = last[si];
+            uD[g] = prev[si];
+        }
+    }
+}
+
+template <typename T, int B, int RPT, int RG>
+void add_candidate(const Layout &L, std::vector<TbPlan> &out)
+{
+    constexpr int H = RG * RPT, TY = H - 2 * B, TX = kW - 2 * B, kThreads = kW * RG;
+    const size_t smem = tb2d_smem_bytes<T>(H);
+    if (H + 2 > 256 || smem > 220 * 1024) return;
+    if (cudaFuncSetAttribute(tb2d_kernel<T, B, RPT, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return;
+    }
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tb2d_kernel<T, B, RPT, RG>, kThreads, smem) !=
+            cudaSuccess || occ < 1) {
+        (void)cudaGetLastError();
+        return;
+    }
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    TbPlan p;
+    p.B = B;
+    p.RPT = RPT;
+    p.RG = RG;
+    p.TX = TX;
+    p.TY = TY;
+    p.H = H;
+    p.smem = smem;
+    p.grid_x = (int)((L.nx + TX - 1) / TX);
+    p.grid_y = (int)((L.ny + TY - 1) / TY);
+    p.occ = occ;
+    const int64_t slots = (int64_t)nsm * occ;
+    p.waves = (int)(((int64_t)p.grid_x * p.grid_y + slots - 1) / slots);
+    out.push_back(p);
+}
+
+}  // namespace
+
+template <typename T>
+std::vector<TbPlan> tb2d_candidates(const Layout &L, int want_B)
+{
+    std::vector<TbPlan> v;
+    if (L.d != 2) return v;
+    if (want_B == 0 || want_B == 4) {
+        add_candidate<T, 4, 12, 8>(L, v);
+        add_candidate<T, 4, 20, 8>(L, v);
+        add_candidate<T, 4, 6, 16>(L, v);
+        add_candidate<T, 4, 10, 16>(L, v);
+    }
+    if (want_B == 0 || want_B == 8) {
+        add_candidate<T, 8, 12, 8>(L, v);
+        add_candidate<T, 8, 20, 8>(L, v);
+        add_candidate<T, 8, 6, 16>(L, v);
+        add_candidate<T, 8, 10, 16>(L, v);
+    }
+    return v;
+}
+
+// Tensor maps of the planes u0, u1, u2, u3 and q*kappa as 2-D arrays
+// (pitch x rows) with a kBoxW x (H + 2) box.
+template <typename T>
+bool make_tb2d_maps(const Layout &L, const TbPlan &p, T *const planes[5], TbMaps *maps)
+{
+    typedef CUresult (*EncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                 const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                 const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    EncodeFn encode = reinterpret_cast<EncodeFn>(fn);
+    const cuuint64_t dims[2] = {(cuuint64_t)L.pitch, (cuuint64_t)(L.ny + 2)};
+    const cuuint64_t strides[1] = {(cuuint64_t)(L.pitch * sizeof(T))};
+    const cuuint32_t box[2] = {(cuuint32_t)kBoxW, (cuuint32_t)(p.H + 2)};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUtensorMapDataType dt =
+        sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    for (int i = 0; i < 5; ++i) {
+        if (encode(&maps->m[i], dt, 2, (void *)planes[i], dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+            CUDA_SUCCESS)
+            return false;
+    }
+    return true;
+}
+
+template <typename T>
+void launch_tb2d(const TbPlan &p, const TbMaps &maps, int in0, int in1, const Layout &L, T *uC,
+                 T *uD, const T *dco, const T *fre, const T *fim, const StepCoef<T> &C,
+                 const TbSteps<T> &S, const OutSlot *slot, int *err, cudaStream_t s)
+{
+    dim3 grd((unsigned)p.grid_x, (unsigned)p.grid_y);
+#define HTD_TB2D_CASE(BB, RR, GG)                                                              \
+    if (p.B == BB && p.RPT == RR && p.RG == GG) {                                              \
+        tb2d_kernel<T, BB, RR, GG><<<grd, kW * GG, p.smem, s>>>(maps, in0, in1, uC, uD, dco,   \
+                                                               fre, fim, L, C, S, slot, err);  \
+        ++g_launches;                                                                          \
+        return;                                                                                \
+    }
+    HTD_TB2D_CASE(4, 12, 8)
+    HTD_TB2D_CASE(4, 20, 8)
+    HTD_TB2D_CASE(4, 6, 16)
+    HTD_TB2D_CASE(4, 10, 16)
+    HTD_TB2D_CASE(8, 12, 8)
+    HTD_TB2D_CASE(8, 20, 8)
+    HTD_TB2D_CASE(8, 6, 16)
+    HTD_TB2D_CASE(8, 10, 16)
+#undef HTD_TB2D_CASE
+}
+
+template std::vector<TbPlan> tb2d_candidates<float>(const Layout &, int);
+template bool make_tb2d_maps<float>(const Layout &, const TbPlan &, float *const[5], TbMaps *);
+template void launch_tb2d<float>(const TbPlan &, const TbMaps &, int, int, const Layout &, float *,
+                                 float *, const float *, const float *, const float *,
+                                 const StepCoef<float> &, const TbSteps<float> &, const OutSlot *,
+                                 int *, cudaStream_t);
+
+}  // namespace htd

@@ -54,10 +54,16 @@ class Params(ctypes.Structure):
                 ("omega_c", ctypes.c_double), ("lam_max_reH", ctypes.c_double),
                 ("lam_max_A", ctypes.c_double), ("dt", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("rho", ctypes.c_double),
-                ("nP", ctypes.c_int), ("T", ctypes.c_int), ("steps", ctypes.c_longlong)]
+                ("nP", ctypes.c_int), ("T", ctypes.c_int), ("steps", ctypes.c_longlong),
+                ("steps_per_launch", ctypes.c_int), ("tile", ctypes.c_int * 3),
+                ("ctas_per_sm", ctypes.c_int), ("waves", ctypes.c_int),
+                ("step_kernel", ctypes.c_int)]
 
     def as_dict(self) -> dict:
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "tile"}
+        d["tile"] = list(self.tile)
+        return d
+
 
 
 class SolveInfo(ctypes.Structure):

@@ -127,6 +127,61 @@ def test_gmres_fp64_config1_converges_to_direct_solution():
     assert info["iterations"] == oinfo["iterations"]
 
 
+TB_CASES = [(37, 45), (1, 7), (3, 2), (130, 67), (101, 101), (64, 300)]
+TB_CONFIGS = [("4", "12"), ("4", "10"), ("8", "6"), ("8", "20"), (None, None)]
+
+
+@pytest.mark.parametrize("n", TB_CASES, ids=[f"{a}x{b}" for a, b in TB_CASES])
+@pytest.mark.parametrize("B,rpt", TB_CONFIGS, ids=[f"B{b}_r{r}" for b, r in TB_CONFIGS])
+@pytest.mark.parametrize("mode", ["table1", "exact"])
+def test_temporal_blocking_matches_one_step(n, B, rpt, mode, monkeypatch):
+    """The 2-D FP32 recurrence with B steps per launch (shared-memory tiles with a
+    halo of B, rows per thread rpt) against the one-step-per-launch kernel and the
+    FP64 oracle; None = the autotuner's own choice.  Step counts that are not
+    multiples of B and snapshots inside a launch included."""
+    p = het_problem(2, n, T=3) if min(n) > 1 else het_problem(2, n, T=2)
+    monkeypatch.setenv("HTD_TB", "0")
+    s0 = htd.Solver(p, precision="mixed", mode=mode)
+    assert s0.params["steps_per_launch"] == 1
+    monkeypatch.delenv("HTD_TB")
+    if B is not None:
+        monkeypatch.setenv("HTD_TB", B)
+        monkeypatch.setenv("HTD_TB_RPT", rpt)
+    s1 = htd.Solver(p, precision="mixed", mode=mode)
+    if B is not None:
+        assert s1.params["steps_per_launch"] == int(B)
+        row_groups = 16 if int(rpt) in (6, 10) else 8
+        assert s1.params["tile"][1] == row_groups * int(rpt) - 2 * int(B)
+    o = oracle.Oracle(p)
+    for F in (p.F, W.random_rhs(6, p.n)):
+        a = host(s0.precond(dev(F))).reshape(-1)
+        b = host(s1.precond(dev(F))).reshape(-1)
+        assert rel_l2(b, a) <= 1e-6, rel_l2(b, a)
+        assert rel_l2(b, o.precond(F, mode).reshape(-1)) <= 2e-5
+
+
+S3_CASES = [(13, 17, 19), (40, 9, 70), (1, 3, 1), (2, 2, 2), (64, 16, 33), (5, 33, 65)]
+
+
+@pytest.mark.parametrize("n", S3_CASES, ids=["x".join(map(str, c)) for c in S3_CASES])
+@pytest.mark.parametrize("mode", ["table1", "exact"])
+def test_streamed_3d_step_matches_register_kernel(n, mode, monkeypatch):
+    """The TMA-streamed 3-D FP32 step (32 x 8 column tiles, z chunks, a ring of
+    shared-memory stages) against the register z-march kernel and the FP64 oracle,
+    on ragged grids and several z chunks."""
+    p = het_problem(3, n, T=2)
+    monkeypatch.setenv("HTD_S3", "0")
+    s0 = htd.Solver(p, precision="mixed", mode=mode)
+    monkeypatch.delenv("HTD_S3")
+    s1 = htd.Solver(p, precision="mixed", mode=mode)
+    o = oracle.Oracle(p)
+    for F in (p.F, W.random_rhs(7, p.n)):
+        a = host(s0.precond(dev(F))).reshape(-1)
+        b = host(s1.precond(dev(F))).reshape(-1)
+        assert rel_l2(b, a) <= 1e-6, rel_l2(b, a)
+        assert rel_l2(b, o.precond(F, mode).reshape(-1)) <= 2e-5
+
+
 def test_mixed_precond_is_fp32_accurate():
     """FP32 recurrence against the FP64 oracle: the relative error stays at the
     FP32 level (unit roundoff 6e-8 times a modest growth over 120 steps)."""

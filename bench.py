@@ -57,8 +57,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="2d_grf_1001", choices=["2d_grf_1001", "3d_layered_256",
-                                                                   "2d_const_101"])
+    ap.add_argument("--workload", default="2d_grf_1001",
+                    choices=["2d_grf_1001", "3d_layered_256", "3d_layered_192", "2d_const_101"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--cpu-sample-s", type=float, default=10.0)
     ap.add_argument("--e2e-steps", type=int, default=5)
@@ -76,6 +76,10 @@ def make_workload(name, rank=0):
         p = W.config_3d_layered(256)
         desc = ("3-D 256^3 4-layer c [1.5..4.5] x (1+0.1 GRF), h=1/255, 8 ppw at min c, "
                 "24-cell layer R0=2w, point source, T=32, rho=0.25")
+    elif name == "3d_layered_192":
+        p = W.config_3d_layered(192, layer=18)
+        desc = ("3-D 192^3 (profiling size) 4-layer c [1.5..4.5] x (1+0.1 GRF), h=1/191, "
+                "8 ppw at min c, 18-cell layer R0=2w, point source, T=24, rho=0.25")
     else:
         p = W.config_2d_constant(101)
         desc = "2-D 101x101 constant c=1, h=0.01, 10 ppw, 20-cell layer, point source, T=10"

@@ -152,6 +152,7 @@ struct htd_ctx {
     htd::Stream3Maps s3maps{};
     bool use_s3 = false;
     int s3_zchunk = 0;
+    int s3_shape = 0;
     int *err_dev = nullptr;     // set by a kernel whose bounded device wait gave up
     float step_us = 0.f;        // autotuned time per recurrence step (microseconds)
     // captured step sequence
@@ -244,7 +245,8 @@ htd_status run_steps_direct(htd_ctx *c, cudaStream_t s)
                 int flags = 0;
                 if (j + 1 == jim) flags |= 1;
                 if (j + 1 == c->nsteps) flags |= 2;
-                htd::launch_stream3d(c->s3maps, (int)(j & 1), L, (j & 1) ? A : B, C, (T)c->atab[j],
+                htd::launch_stream3d(c->s3maps, (int)(j & 1), c->s3_shape, L, (j & 1) ? A : B, C,
+                                     (T)c->atab[j],
                                      (T)c->btab[j], c->slot, flags, c->s3_zchunk, c->err_dev, s);
             }
             HTD_CUDA(cudaGetLastError());
@@ -818,8 +820,14 @@ htd_status create_impl(const htd_grid *grid, const double *c_cell, const double 
         if (d == 3 && mixed && !(env && std::atoi(env) == 0)) {
             float *planes[6] = {(float *)c->u0, (float *)c->u1, (float *)c->kap, (float *)c->dco,
                                 (float *)c->fre, (float *)c->fim};
-            c->use_s3 = htd::make_stream3d_maps(L, planes, &c->s3maps);
-            if (c->use_s3) c->s3_zchunk = htd::stream3d_zchunk(L);
+            const char *envs = std::getenv("HTD_S3_TILE");       // tuning override
+            c->s3_shape = envs ? std::atoi(envs) : 0;
+            c->use_s3 = htd::make_stream3d_maps(L, c->s3_shape, planes, &c->s3maps);
+            if (c->use_s3) {
+                c->s3_zchunk = htd::stream3d_zchunk(L, c->s3_shape);
+                const char *envz = std::getenv("HTD_S3_ZCHUNK");   // tuning override
+                if (envz && std::atoi(envz) > 0) c->s3_zchunk = std::atoi(envz);
+            }
             (void)cudaGetLastError();
         }
     }

@@ -160,11 +160,11 @@ void launch_scale(const double2 *w, double scale, double2 *v, int64_t N, cudaStr
 struct Stream3Maps {
     CUtensorMap m[8];
 };
-size_t stream3d_smem_bytes();
-bool make_stream3d_maps(const Layout &L, float *const planes[6], Stream3Maps *maps);
-int stream3d_zchunk(const Layout &L);
+// tile shape: 0 = 32 x 8 columns, 1 = 64 x 4, 2 = 128 x 2
+bool make_stream3d_maps(const Layout &L, int shape, float *const planes[6], Stream3Maps *maps);
+int stream3d_zchunk(const Layout &L, int shape);
 // one step; from = 0: u_j in u0 and u_{j-1} (overwritten) in u1, from = 1 swapped
-void launch_stream3d(const Stream3Maps &maps, int from, const Layout &L, float *um,
+void launch_stream3d(const Stream3Maps &maps, int from, int shape, const Layout &L, float *um,
                      const StepCoef<float> &C, float a, float b, const OutSlot *slot, int flags,
                      int zchunk, int *err, cudaStream_t s);
 

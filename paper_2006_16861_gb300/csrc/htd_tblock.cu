@@ -39,15 +39,15 @@ constexpr unsigned long long kWaitLimitNs = 1000000000ull;   // 1 s bound on the
 __host__ __device__ inline size_t round128(size_t b) { return (b + 127) & ~(size_t)127; }
 
 template <typename T>
-__host__ __device__ inline size_t tb2d_array_bytes(int H)
+__host__ __device__ constexpr size_t tb2d_array_bytes(int H)
 {
-    return round128((size_t)(H + 2) * kBoxW * sizeof(T));
+    return (((size_t)(H + 2) * kBoxW * sizeof(T)) + 127) & ~(size_t)127;
 }
 
 template <typename T>
 size_t tb2d_smem_bytes(int H)
 {
-    return 3 * tb2d_array_bytes<T>(H) + 16 + 128;   // three boxes, the mbarrier, alignment slack
+    return 3 * tb2d_array_bytes<T>(H) + 16;   // three boxes and the mbarrier
 }
 
 __device__ __forceinline__ unsigned smem_u32(const void *p)
@@ -118,15 +118,20 @@ tb2d_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, T *__restrict
     constexpr int W = kW, TX = W - 2 * B, BW = kBoxW;
     constexpr int H = RG * RPT, TY = H - 2 * B;
     constexpr int kAlign = 16 / (int)sizeof(T);          // TMA column alignment in elements
-    extern __shared__ unsigned char smem_raw[];
-    const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127;
-    const size_t ab = tb2d_array_bytes<T>(H);
-    T *su0 = reinterpret_cast<T *>(base);                 // u_j   (box row r = stored row y0 + r)
-    T *su1 = reinterpret_cast<T *>(base + ab);            // u_{j-1}
-    T *sk = reinterpret_cast<T *>(base + 2 * ab);         // q*kappa per cell
-    uint64_t *bar = reinterpret_cast<uint64_t *>(base + 3 * ab);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    constexpr int ae = (int)(tb2d_array_bytes<T>(H) / sizeof(T));   // elements per box slot
+    T *smem_t = reinterpret_cast<T *>(smem_raw);
+    T *su0 = smem_t;                                      // u_j   (box row r = stored row y0 + r)
+    T *su1 = smem_t + ae;                                 // u_{j-1}
+    T *sk = smem_t + 2 * ae;                              // q*kappa per cell
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_t + 3 * ae);
 
     const int tid = threadIdx.x;
+    // TMA destinations must be 128-byte aligned; refuse to run otherwise
+    if (smem_u32(smem_raw) & 127u) {
+        if (tid == 0) atomicExch(err, 1);
+        return;
+    }
     const int64_t x0 = (int64_t)blockIdx.x * TX - B;      // global x of local column 0
     const int64_t y0 = (int64_t)blockIdx.y * TY - B;      // global y of local row 0
     // box origin: stored row y0 (local pad row 0 = global row y0 - 1), stored

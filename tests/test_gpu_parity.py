@@ -165,15 +165,20 @@ S3_CASES = [(13, 17, 19), (40, 9, 70), (1, 3, 1), (2, 2, 2), (64, 16, 33), (5, 3
 
 @pytest.mark.parametrize("n", S3_CASES, ids=["x".join(map(str, c)) for c in S3_CASES])
 @pytest.mark.parametrize("mode", ["table1", "exact"])
-def test_streamed_3d_step_matches_register_kernel(n, mode, monkeypatch):
-    """The TMA-streamed 3-D FP32 step (32 x 8 column tiles, z chunks, a ring of
-    shared-memory stages) against the register z-march kernel and the FP64 oracle,
-    on ragged grids and several z chunks."""
+@pytest.mark.parametrize("tile", ["0", "1", "2"])
+def test_streamed_3d_step_matches_register_kernel(n, mode, tile, monkeypatch):
+    """The TMA-streamed 3-D FP32 step (32 x 8, 64 x 4 or 128 x 2 column tiles, z
+    chunks, a ring of shared-memory stages fed by a producer warp) against the
+    register z-march kernel and the FP64 oracle, on ragged grids and several z
+    chunks (16 planes per chunk at these sizes)."""
     p = het_problem(3, n, T=2)
     monkeypatch.setenv("HTD_S3", "0")
     s0 = htd.Solver(p, precision="mixed", mode=mode)
+    assert s0.params["step_kernel"] == 0
     monkeypatch.delenv("HTD_S3")
+    monkeypatch.setenv("HTD_S3_TILE", tile)
     s1 = htd.Solver(p, precision="mixed", mode=mode)
+    assert s1.params["step_kernel"] == 2
     o = oracle.Oracle(p)
     for F in (p.F, W.random_rhs(7, p.n)):
         a = host(s0.precond(dev(F))).reshape(-1)

@@ -63,6 +63,8 @@ def parse_args():
     ap.add_argument("--cpu-sample-s", type=float, default=10.0)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--restart", type=int, default=20)
+    ap.add_argument("--secondary-3d", type=int, default=1,
+                    help="also time the FP32 recurrence on the 3-D 256^3 workload (HBM-bound)")
     return ap.parse_args()
 
 
@@ -172,6 +174,43 @@ def cpu_baseline(p, budget_s):
     ups = math.prod(p.n) * o.params.nsteps
     return ups / dt / 1e9, (f"oracle Table-1 preconditioner, {T_sample} periods "
                             f"({o.params.nsteps} steps) on the full grid, {dt:.1f} s")
+
+
+def secondary_3d(htd, stream, flush, peaks):
+    """Time preconditioner applications (T = 4, 48 steps each) on 3d_layered_256 with
+    CUDA events; report Gupd/s and the step kernel's HBM roofline fraction."""
+    import torch
+    from paper_2006_16861_gb300 import workloads as W
+    p3 = W.config_3d_layered(256, T=4)
+    N3 = math.prod(p3.n)
+    s3 = htd.Solver(p3, precision="mixed", restart=1)
+    prm = s3.params
+    F3 = torch.from_numpy(np.ascontiguousarray(p3.F)).cuda()
+    U3 = torch.zeros_like(F3)
+    s3.precond(F3, U3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    times = []
+    for _ in range(3):
+        flush.fill_(4)
+        e0.record(stream)
+        htd.htd_apply_precond(s3.handle, F3, U3, stream)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    s3.close()
+    ms = statistics.mean(times)
+    us_step = 1e3 * ms / prm["steps"]
+    bytes_step = N3 * 4 * WORDS_ONE_STEP
+    peak, kind = peaks()
+    achieved = bytes_step / (us_step * 1e-6) / 1e9
+    kern = {2: "stream3d_kernel", 0: "step3d_kernel<float>"}.get(prm["step_kernel"], "?")
+    return {"workload": "3d_layered_256 (T=4, 48 steps per application)",
+            "value": N3 * prm["steps"] / (ms * 1e-3) / 1e9, "unit": UNIT,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": kern,
+                         "bytes_per_launch": bytes_step, "avg_launch_us": us_step,
+                         "peak_kind": f"{kind} HBM copy bandwidth"}}
 
 
 def run_reference(args):
@@ -341,6 +380,12 @@ def run_ours(args):
         fp64_ms = allmax(statistics.mean(t))
         s64.close()
 
+    # secondary: the recurrence alone on the 3-D 256^3 layered workload, whose
+    # working set (470 MB per step) is far larger than L2
+    sec = None
+    if args.secondary_3d and p.ndim == 2:
+        sec = secondary_3d(htd, stream, flush, peaks)
+
     cpu = None
     if rank == 0 and world == 1 and args.cpu_sample_s > 0:
         import oracle
@@ -377,6 +422,7 @@ def run_ours(args):
                          "peak_kind": f"{peak_kind} HBM copy bandwidth",
                          "l2_resident": l2_resident},
             "cpu_baseline": cpu,
+            "secondary_3d": sec,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk,

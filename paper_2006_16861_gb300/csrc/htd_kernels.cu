@@ -358,22 +358,37 @@ __device__ __forceinline__ double2 block_sum(double re, double im)
     return out;
 }
 
+// One pass over the data for a group of up to kDotGroup basis vectors: each
+// thread reads w[i] once and accumulates conj(V_k[i]) w[i] for the group.
+constexpr int kDotGroup = 8;
+
 __global__ void __launch_bounds__(kRedThreads)
-dots_kernel(const double2 *__restrict__ V, int64_t ldv, const double2 *__restrict__ w,
+dots_kernel(const double2 *__restrict__ V, int64_t ldv, int kcount, const double2 *__restrict__ w,
             int64_t N, double2 *__restrict__ partial, int nb)
 {
-    const int k = blockIdx.y;
-    const double2 *v = V + (int64_t)k * ldv;
-    double re = 0.0, im = 0.0;
+    const int k0 = blockIdx.y * kDotGroup;
+    const int kn = min(kDotGroup, kcount - k0);
+    double re[kDotGroup], im[kDotGroup];
+#pragma unroll
+    for (int q = 0; q < kDotGroup; ++q) { re[q] = 0.0; im[q] = 0.0; }
     for (int64_t i = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; i < N;
          i += (int64_t)nb * kRedThreads) {
-        const double2 a = v[i], b = w[i];
-        // conj(a) * b
-        re += a.x * b.x + a.y * b.y;
-        im += a.x * b.y - a.y * b.x;
+        const double2 b = w[i];
+#pragma unroll
+        for (int q = 0; q < kDotGroup; ++q) {
+            if (q < kn) {
+                const double2 a = V[(int64_t)(k0 + q) * ldv + i];
+                // conj(a) * b
+                re[q] += a.x * b.x + a.y * b.y;
+                im[q] += a.x * b.y - a.y * b.x;
+            }
+        }
     }
-    const double2 t = block_sum(re, im);
-    if (threadIdx.x == 0) partial[(int64_t)k * nb + blockIdx.x] = t;
+    for (int q = 0; q < kn; ++q) {
+        const double2 t = block_sum(re[q], im[q]);
+        if (threadIdx.x == 0) partial[(int64_t)(k0 + q) * nb + blockIdx.x] = t;
+        __syncthreads();                       // block_sum's shared scratch is reused
+    }
 }
 
 int dots_blocks(int64_t N)
@@ -387,8 +402,8 @@ int dots_blocks(int64_t N)
 void launch_dots(const double2 *V, int64_t ldv, int kcount, const double2 *w, int64_t N,
                  double2 *partial, int nb, cudaStream_t s)
 {
-    dim3 grd((unsigned)nb, (unsigned)kcount);
-    dots_kernel<<<grd, kRedThreads, 0, s>>>(V, ldv, w, N, partial, nb);
+    dim3 grd((unsigned)nb, (unsigned)((kcount + kDotGroup - 1) / kDotGroup));
+    dots_kernel<<<grd, kRedThreads, 0, s>>>(V, ldv, kcount, w, N, partial, nb);
     ++g_launches;
 }
 
@@ -422,6 +437,7 @@ sub_combination_kernel(const double2 *__restrict__ V, int64_t ldv, int kcount,
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     double2 acc = w[i];
+#pragma unroll 4
     for (int k = 0; k < kcount; ++k) {
         const double2 v = V[(int64_t)k * ldv + i];
         const double2 c = sh[k];
@@ -449,6 +465,7 @@ add_combination_kernel(const double2 *__restrict__ Z, int64_t ldz, int kcount,
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     double2 acc = U[i];
+#pragma unroll 4
     for (int k = 0; k < kcount; ++k) {
         const double2 z = Z[(int64_t)k * ldz + i];
         const double2 c = sy[k];

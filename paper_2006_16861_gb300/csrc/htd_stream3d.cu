@@ -369,13 +369,12 @@ int zchunk_t(const Layout &L)
         (void)cudaGetLastError();
         occ = 1;
     }
-    // about two waves of (tile, z chunk) work items, chunks of at least 32 planes
-    // (measured on 256^3: 64-plane chunks best, 16 the worst by ~8%)
+    // 64-plane chunks (measured on 256^3: 64 best; 16 about 8% and 256 about 30%
+    // slower); smaller grids are split so that every SM still gets work
+    (void)occ;
     const int64_t tiles = ((L.nx + TXW - 1) / TXW) * ((L.ny + TYH - 1) / TYH);
-    int64_t chunks = (2 * (int64_t)nsm * occ + tiles - 1) / tiles;
-    if (chunks < 1) chunks = 1;
-    int64_t zc = (L.nz + chunks - 1) / chunks;
-    if (zc < 32) zc = 32;
+    int64_t zc = 64;
+    while (zc > 16 && tiles * ((L.nz + zc - 1) / zc) < nsm) zc /= 2;
     if (zc > L.nz) zc = L.nz;
     return (int)zc;
 }

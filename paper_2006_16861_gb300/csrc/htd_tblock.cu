@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "htd_internal.h"
@@ -200,7 +201,10 @@ tb2d_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, T *__restrict
     }
     __syncthreads();
 
-    for (int s = 0; s < S.nsub; ++s) {
+    // one step over this thread's rows; WITH_OUT: also write the owned nodes to
+    // the output vector (the snapshot / final steps only)
+    auto step = [&](int s, auto with_out) {
+        constexpr bool kOut = decltype(with_out)::value;
         const T *__restrict__ cur = (s & 1) ? su1 : su0;   // u_{j+s}
         T *__restrict__ prv = (s & 1) ? su0 : su1;         // u_{j+s-1}, overwritten by u_{j+s+1}
         const T a = s_a[s], b = s_b[s];
@@ -226,23 +230,28 @@ tb2d_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, T *__restrict
             const T hk1 = k10 + k11;
             const T acc = stencil2d(C, umm, um0, ump, u0m, u00, u0p, upm, up0, upp, k00, k01, k10,
                                     k11, pm, p0, pp, hk0, hk1);
-            if (col_ok && ly >= lo && ly < hi) {
-                const int ni = (ly + 1) * BW + cc + 1;
-                const T g = a * rfr[i] - b * rfi[i];
-                const T uprev = prv[ni];
-                const T unew = rd[i] * (acc + g - T(2) * uprev) + uprev;
-                prv[ni] = unew;
-                if (flags && col_owned && ly >= B && ly < B + TY) {
-                    const int64_t c = (y0 + ly) * L.nx + gx;
-                    if ((flags & 1) && slot->snap_part) slot->snap_part[2 * c] = (double)unew;
-                    if ((flags & 2) && slot->final_part) slot->final_part[2 * c] = (double)unew;
-                }
+            // every thread stores; outside the updated region it stores u_{j+s-1}
+            // back unchanged, so no per-row branch is needed
+            const int ni = (ly + 1) * BW + cc + 1;
+            const T g = a * rfr[i] - b * rfi[i];
+            const T uprev = prv[ni];
+            const T unew = rd[i] * (acc + g - T(2) * uprev) + uprev;
+            const bool upd = col_ok && ly >= lo && ly < hi;
+            prv[ni] = upd ? unew : uprev;
+            if (kOut && upd && col_owned && ly >= B && ly < B + TY) {
+                const int64_t c = (y0 + ly) * L.nx + gx;
+                if ((flags & 1) && slot->snap_part) slot->snap_part[2 * c] = (double)unew;
+                if ((flags & 2) && slot->final_part) slot->final_part[2 * c] = (double)unew;
             }
             umm = u0m; um0 = u00; ump = u0p; pm = p0;
             u0m = upm; u00 = up0; u0p = upp; p0 = pp;
             k00 = k10; k01 = k11; hk0 = hk1;
         }
         __syncthreads();
+    };
+    for (int s = 0; s < S.nsub; ++s) {
+        if (s_flags[s]) step(s, std::true_type{});
+        else step(s, std::false_type{});
     }
 
     // ---- store the owned core of the last two states ----------------------

@@ -50,6 +50,35 @@ TOL = 1e-6
 # last two states (8 words)
 WORDS_ONE_STEP, WORDS_BLOCKED = 7, 8
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
+# capture, valid only for the kernel source it was taken on (sha256 prefix of the
+# file); scaled by node count to other grid sizes.  The captures are summarised
+# under profiles/.
+NCU_TRAFFIC = {
+    "tb2d": {"file": "htd_tblock.cu", "sha16": "529e54e32fba3f34", "bytes": 25081088,
+             "nodes": 1001 * 1001},
+    "stream3d": {"file": "htd_stream3d.cu", "sha16": "4f289c964d28aa22",
+                 "bytes": 193680896 + 18157568, "nodes": 192 ** 3},
+}
+
+
+def ncu_traffic(key, nodes):
+    """Measured DRAM bytes per launch for `nodes` nodes, or None if the kernel
+    source changed since the capture."""
+    import hashlib
+    rec = NCU_TRAFFIC.get(key)
+    if rec is None:
+        return None
+    path = os.path.join(ROOT, "paper_2006_16861_gb300", "csrc", rec["file"])
+    try:
+        with open(path, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+    if sha != rec["sha16"]:
+        return None
+    return rec["bytes"] * nodes / rec["nodes"]
+
 
 def parse_args():
     ap = argparse.ArgumentParser()
@@ -208,7 +237,9 @@ def secondary_3d(htd, stream, flush, peaks):
     return {"workload": "3d_layered_256 (T=4, 48 steps per application)",
             "value": N3 * prm["steps"] / (ms * 1e-3) / 1e9, "unit": UNIT,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": kern,
+                         "frac": achieved / peak,
+                         "traffic": ncu_traffic("stream3d", N3) if prm["step_kernel"] == 2 else None,
+                         "kernel": kern,
                          "bytes_per_launch": bytes_step, "avg_launch_us": us_step,
                          "peak_kind": f"{kind} HBM copy bandwidth"}}
 
@@ -412,7 +443,11 @@ def run_ours(args):
             "iterations": its[-1], "rel_res_true": max(rels),
             "fp64_iterations": fp64_info["iterations"] if fp64_info else None,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": (ncu_traffic("tb2d", N) if prm.get("step_kernel") == 1 else
+                                     ncu_traffic("stream3d", N) if prm.get("step_kernel") == 2
+                                     else None),
+                         "effective_single_step_gbs": N * 4 * WORDS_ONE_STEP * spl / avg_launch_s / 1e9,
                          "kernel": {1: f"tb2d_kernel<float,{spl}>", 2: "stream3d_kernel"}.get(
                              prm.get("step_kernel"),
                              "step2d_kernel<float>" if p.ndim == 2 else "step3d_kernel<float>"),

@@ -81,6 +81,7 @@ def _load():
         lib.ora_acd_step.argtypes = [P, Q, vp, vp, vp, vp]
         lib.ora_precond.argtypes = [P, Q, ctypes.c_int, vp, vp]
         lib.ora_direct_solve.argtypes = [P, vp, vp]
+        lib.ora_grad.argtypes = [P, ctypes.c_int, vp, ctypes.c_int, vp, vp, vp, vp, vp]
         lib.ora_gmres.argtypes = [P, Q, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_double,
                                   ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                   ctypes.POINTER(_Info)]
@@ -188,6 +189,22 @@ class Oracle:
         if self.lib.ora_direct_solve(ctypes.byref(self._p), _ptr(F), _ptr(out)):
             raise ArithmeticError("singular H")
         return out.reshape(self.n)
+
+    def grad(self, F, rec_idx, d):
+        """Misfit 1/2 sum_s ||P U_s - d_s||^2 and its gradient with respect to
+        m = c^-2 per cell and R per node (direct solves).  F: (nsrc, *n), rec_idx:
+        node linear indices, d: (nsrc, nrec).  Returns (J, grad_m, grad_R)."""
+        F = np.ascontiguousarray(np.asarray(F, dtype=np.complex128).reshape(-1, self.N))
+        nsrc = F.shape[0]
+        rec = np.ascontiguousarray(np.asarray(rec_idx, dtype=np.int64).reshape(-1))
+        d = np.ascontiguousarray(np.asarray(d, dtype=np.complex128).reshape(nsrc, rec.size))
+        gm = np.zeros(self.c.shape)
+        gR = np.zeros(self.n)
+        J = ctypes.c_double()
+        if self.lib.ora_grad(ctypes.byref(self._p), nsrc, _ptr(F), int(rec.size), _ptr(rec),
+                             _ptr(d), _ptr(gm), _ptr(gR), ctypes.byref(J)):
+            raise ArithmeticError("singular H")
+        return J.value, gm, gR
 
     def gmres(self, F, krylov: str = "fgmres", precond: str = "table1", tol: float = 1e-6,
               restart: int = 20, maxit: int = 200, fixed: bool = False, U0=None):

@@ -783,3 +783,78 @@ done:
     band_free(&lu);
     return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* receiver misfit and its gradient (adjoint state)                           */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * J = 1/2 sum_s || P U_s - d_s ||^2 with H U_s = F_s (direct solves), P the
+ * sampling at the nodes rec_idx[0..nrec-1].  Gradient with respect to
+ * m = c^{-2} per cell and R per node.  With r_s = P^T (P U_s - d_s) and the
+ * adjoint field mu_s = H^{-1} conj(r_s) (H is complex symmetric, so this is the
+ * conjugate of the solution of H^H lambda = r):
+ *   dJ/dm_alpha = omega^2 sum_s Re sum_{beta,gamma in cell alpha}
+ *                 mu_{s,beta} M_{Delta(beta,gamma)} U_{s,gamma}
+ *   (Re H depends on m through -(h k)^2 M_cell h^{-2} = -omega^2 m M_cell),
+ *   dJ/dR_i = omega sum_s Im(mu_{s,i} U_{s,i})   ((Im H)_ii = omega R_i).
+ * F: nsrc x N complex, d: nsrc x nrec complex; grad_m: prod(n+1), grad_R: N.
+ * Returns 0, or -1 if H is singular.
+ */
+int ora_grad(const ora_problem *p, int nsrc, const cplx *F, int nrec, const long long *rec_idx,
+             const cplx *d, double *grad_m, double *grad_R, double *misfit)
+{
+    long long N = n_nodes(p), Nc = n_cells(p);
+    band_lu lu;
+    if (band_factor(p, &lu)) { band_free(&lu); return -1; }
+    double S[4], M[4];
+    ora_tables(p->ndim, p->stencil, S, M);
+    cplx *U = malloc(sizeof(cplx) * N), *r = malloc(sizeof(cplx) * N), *mu = malloc(sizeof(cplx) * N);
+    for (long long c = 0; c < Nc; ++c) grad_m[c] = 0.0;
+    for (long long i = 0; i < N; ++i) grad_R[i] = 0.0;
+    double J = 0.0;
+    double w = p->omega_phys;
+    int d3 = p->ndim;
+    for (int s = 0; s < nsrc; ++s) {
+        band_solve(&lu, F + (long long)s * N, U);
+        for (long long i = 0; i < N; ++i) r[i] = 0.0;
+        for (int k = 0; k < nrec; ++k) {
+            cplx res = U[rec_idx[k]] - d[(long long)s * nrec + k];
+            J += 0.5 * creal(res * conj(res));
+            r[rec_idx[k]] += conj(res);
+        }
+        band_solve(&lu, r, mu);
+        /* cell loop: omega^2 Re sum mu_beta M U_gamma */
+        long long a3[3], lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+        for (int t = 0; t < d3; ++t) { lo[t] = -1; hi[t] = p->n[t] - 1; }
+        int ncorner = 1 << d3;
+        for (a3[0] = lo[0]; a3[0] <= hi[0]; ++a3[0])
+        for (a3[1] = lo[1]; a3[1] <= hi[1]; ++a3[1])
+        for (a3[2] = (d3 == 3 ? lo[2] : 0); a3[2] <= (d3 == 3 ? hi[2] : 0); ++a3[2]) {
+            long long corner[8];
+            for (int b = 0; b < ncorner; ++b) {
+                long long ib[3];
+                int inside = 1;
+                for (int t = 0; t < d3; ++t) {
+                    ib[t] = a3[t] + ((b >> (d3 - 1 - t)) & 1);
+                    if (ib[t] < 0 || ib[t] >= p->n[t]) inside = 0;
+                }
+                corner[b] = inside ? node_lin(p, ib) : -1;
+            }
+            cplx acc = 0.0;
+            for (int b = 0; b < ncorner; ++b) {
+                if (corner[b] < 0) continue;
+                for (int g = 0; g < ncorner; ++g) {
+                    if (corner[g] < 0) continue;
+                    acc += mu[corner[b]] * M[popcount_small((unsigned)(b ^ g))] * U[corner[g]];
+                }
+            }
+            grad_m[cell_lin(p, a3)] += w * w * creal(acc);
+        }
+        for (long long i = 0; i < N; ++i) grad_R[i] += w * cimag(mu[i] * U[i]);
+    }
+    *misfit = J;
+    free(U); free(r); free(mu);
+    band_free(&lu);
+    return 0;
+}

@@ -219,3 +219,61 @@ def config_3d_layered(n: int = 256, layer: int = 24, seed: int = 2006168612,
     if T is None:
         T = periods_for(n, h, cmin, omega)
     return Problem(f"3d_layered_{n}", 3, (n, n, n), h, c, R, omega, F, T, rho)
+
+
+@dataclasses.dataclass
+class InversionSetup:
+    """Sources, receivers and data for a receiver-misfit problem."""
+    prob: Problem               # the model the misfit is evaluated at
+    F: np.ndarray               # (nsrc, *n) complex right-hand sides
+    rec_idx: np.ndarray         # int64 node linear indices of the receivers
+    c_true: np.ndarray          # per-cell speed the data would come from
+
+
+def seeded_sources(seed: int, ndim: int, n, h: float, nsrc: int, margin: int) -> np.ndarray:
+    """nsrc point sources (amplitude 1/h^d) at seeded uniform node positions at
+    least `margin` nodes from every face."""
+    n = list(n)
+    u = uniform01(seed, nsrc * ndim).reshape(nsrc, ndim)
+    F = np.zeros([nsrc] + n, dtype=np.complex128)
+    for s in range(nsrc):
+        pos = tuple(int(margin + u[s, a] * (n[a] - 2 * margin)) for a in range(ndim))
+        F[(s,) + pos] = 1.0 / h ** ndim
+    return F
+
+
+def top_row_receivers(n, row: int, margin: int) -> np.ndarray:
+    """Linear node indices of the receivers on row `row` (axis 0) of a 2-D grid,
+    columns margin .. n1 - 1 - margin."""
+    cols = np.arange(margin, n[1] - margin)
+    return (row * n[1] + cols).astype(np.int64)
+
+
+def gaussian_blob(n_cells, h: float, centre, sigma: float, amplitude: float) -> np.ndarray:
+    """1 + amplitude * exp(-|x - centre|^2 / (2 sigma^2)) at the cell centres."""
+    axes = [(np.arange(m) - 0.5) * h for m in n_cells]
+    grids = np.meshgrid(*axes, indexing="ij")
+    r2 = sum((g - c0) ** 2 for g, c0 in zip(grids, centre))
+    return 1.0 + amplitude * np.exp(-0.5 * r2 / sigma ** 2)
+
+
+def config_adjoint(n: int = 512, nsrc: int = 8, layer: int = 20, seed: int = 2006168615,
+                   corr_len: float = 0.05, ppw: float = 8.0, T: int | None = None,
+                   rho: float = 0.25) -> InversionSetup:
+    """2-D n x n model with a smooth random c (clip(3 + 0.75 g, 1.5, 4.5)), omega for
+    `ppw` points per wavelength at min c, `layer`-cell absorbing layer (R0 = 2 omega),
+    `nsrc` seeded point sources, receivers on the first row inside the top absorbing
+    layer, and a 'true' model c * (1 + 5% Gaussian blob, sigma 0.1, at the centre)."""
+    h = 1.0 / (n - 1)
+    g = gaussian_random_field(seed, (n + 1, n + 1), corr_len / h)
+    c = np.clip(3.0 + 0.75 * g, 1.5, 4.5)
+    cmin = float(c.min())
+    omega = 2.0 * math.pi * cmin / (ppw * h)
+    R = damping_profile(2, (n, n), layer, 2.0 * omega)
+    F = seeded_sources(seed + 1, 2, (n, n), h, nsrc, layer + 2)
+    if T is None:
+        T = periods_for(n, h, cmin, omega)
+    prob = Problem(f"2d_adjoint_{n}", 2, (n, n), h, c, R, omega, F[0], T, rho)
+    c_true = c * gaussian_blob((n + 1, n + 1), h, (0.5, 0.5), 0.1, 0.05)
+    rec = top_row_receivers((n, n), layer, layer)
+    return InversionSetup(prob, F, rec, c_true)

@@ -236,6 +236,38 @@ htd_status htd_gmres_solve(htd_handle h, const void *F_dev, void *U_dev, double 
 htd_status htd_gmres_solve_host(htd_handle h, const void *F_host, void *U_host, double tol,
                                 int max_iters, void *stream, htd_solve_info *info);
 
+/*
+ * Receiver misfit and its gradient (adjoint-state method for H U = F):
+ *   J = 1/2 sum_s || P U_s - d_s ||^2,   H U_s = F_s  (s < nsrc),
+ * P the sampling at the nodes rec_idx.  H is complex symmetric, so the adjoint
+ * field is mu_s = H^{-1} conj(r_s), r_s = P^T (P U_s - d_s), and
+ *   dJ/dm_alpha = omega_phys^2 sum_s Re sum_{beta,gamma in cell alpha}
+ *                 mu_{s,beta} M_{|beta-gamma|} U_{s,gamma}     (m = c^{-2} per cell),
+ *   dJ/dR_i     = omega_phys sum_s Im(mu_{s,i} U_{s,i})        (R per node),
+ * from the dependence of H on m (through -(omega/c)^2 in Sec. 1's damped
+ * Helmholtz equation, discretised with the cell mass M of App. A) and on R
+ * ((Im H)_ii = omega_phys R_i).  The paper has no gradient; this is the
+ * standard adjoint of its problem statement.  Both solves use
+ * htd_gmres_solve with the handle's preconditioner and tolerance `tol`.
+ *   F_dev       complex128[nsrc][N] right-hand sides (device).
+ *   rec_idx_host int64[nrec] receiver node indices in [0, N) (host).
+ *   d_dev       complex128[nsrc][nrec] data (device; may be NULL if nrec = 0).
+ *   grad_m_dev  double[prod(n+1)] (device, cell order of c_cell) or NULL.
+ *   grad_R_dev  double[N] (device) or NULL.  Both NULL: misfit only (no
+ *               adjoint solves).  Outputs are overwritten, not accumulated.
+ *   misfit      host double, J.
+ *   info        optional: iterations, applications, steps and times summed
+ *               over all solves; rel_res_true is the worst of them.
+ * Synchronises the stream.  Errors: HTD_ERR_ARG (bad sizes or indices), the
+ * solve errors of htd_gmres_solve (HTD_ERR_NOT_CONVERGED stops at the first
+ * solve that fails), HTD_ERR_CUDA, HTD_ERR_OOM (first call allocates the
+ * handle's gradient workspace: three complex vectors and the receiver buffers).
+ */
+htd_status htd_grad(htd_handle h, int nsrc, const void *F_dev, int nrec,
+                    const int64_t *rec_idx_host, const void *d_dev, double tol, int max_iters,
+                    void *grad_m_dev, void *grad_R_dev, double *misfit, void *stream,
+                    htd_solve_info *info);
+
 /* Static string for a status code. */
 const char *htd_status_string(htd_status s);
 

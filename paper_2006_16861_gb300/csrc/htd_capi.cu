@@ -155,6 +155,10 @@ struct htd_ctx {
     int s3_shape = 0;
     int *err_dev = nullptr;     // set by a kernel whose bounded device wait gave up
     float step_us = 0.f;        // autotuned time per recurrence step (microseconds)
+    // gradient workspace (htd_grad), allocated on first use
+    double2 *gU = nullptr, *gMu = nullptr, *gR = nullptr, *gres = nullptr;
+    int64_t *grec = nullptr;
+    int grec_cap = 0;
     // captured step sequence
     cudaGraphExec_t exec = nullptr;
     bool graph_tried = false;
@@ -194,7 +198,7 @@ void free_ctx(htd_ctx *c)
         if (e) cudaEventDestroy(e);
     void *dev[] = {c->kap, c->dco, c->fre, c->fim, c->u0, c->u1, c->kap64, c->imH, c->V, c->Z,
                    c->w, c->t, c->r, c->partial, c->hdev, c->slot, c->Fh, c->Uh, c->u2, c->u3,
-                   c->err_dev};
+                   c->err_dev, c->gU, c->gMu, c->gR, c->gres, c->grec};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (c->hhost) cudaFreeHost(c->hhost);
@@ -992,6 +996,89 @@ htd_status htd_gmres_solve_host(htd_handle h, const void *F_host, void *U_host, 
     if (st != HTD_OK && st != HTD_ERR_NOT_CONVERGED) return st;
     HTD_CUDA(cudaMemcpyAsync(U_host, h->Uh, vb, cudaMemcpyDeviceToHost, s));
     HTD_CUDA(cudaStreamSynchronize(s));
+    return st;
+}
+
+htd_status htd_grad(htd_handle h, int nsrc, const void *F_dev, int nrec,
+                    const int64_t *rec_idx_host, const void *d_dev, double tol, int max_iters,
+                    void *grad_m_dev, void *grad_R_dev, double *misfit, void *stream,
+                    htd_solve_info *info)
+{
+    if (!h || nsrc < 1 || !F_dev || nrec < 0 || !misfit || max_iters < 0 || !(tol > 0.0))
+        return HTD_ERR_ARG;
+    if (nrec > 0 && (!rec_idx_host || !d_dev)) return HTD_ERR_ARG;
+    const int64_t N = h->Lr.N;
+    for (int k = 0; k < nrec; ++k)
+        if (rec_idx_host[k] < 0 || rec_idx_host[k] >= N) return HTD_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t vb = sizeof(double2) * (size_t)N;
+    if (!h->gU) HTD_CUDA(cudaMalloc((void **)&h->gU, vb));
+    if (!h->gMu) HTD_CUDA(cudaMalloc((void **)&h->gMu, vb));
+    if (!h->gR) HTD_CUDA(cudaMalloc((void **)&h->gR, vb));
+    if (nrec > h->grec_cap) {
+        if (h->gres) cudaFree(h->gres);
+        if (h->grec) cudaFree(h->grec);
+        h->gres = nullptr;
+        h->grec = nullptr;
+        h->grec_cap = 0;
+        HTD_CUDA(cudaMalloc((void **)&h->gres, sizeof(double2) * nrec));
+        HTD_CUDA(cudaMalloc((void **)&h->grec, sizeof(int64_t) * nrec));
+        h->grec_cap = nrec;
+    }
+    if (nrec > 0)
+        HTD_CUDA(cudaMemcpyAsync(h->grec, rec_idx_host, sizeof(int64_t) * nrec,
+                                 cudaMemcpyHostToDevice, s));
+    const bool want_grad = grad_m_dev || grad_R_dev;
+    const int64_t ncell = (h->n[0] + 1) * (h->d >= 2 ? h->n[1] + 1 : 1) * (h->d == 3 ? h->n[2] + 1 : 1);
+    if (grad_m_dev) HTD_CUDA(cudaMemsetAsync(grad_m_dev, 0, sizeof(double) * ncell, s));
+    if (grad_R_dev) HTD_CUDA(cudaMemsetAsync(grad_R_dev, 0, sizeof(double) * N, s));
+    htd_solve_info tot;
+    std::memset(&tot, 0, sizeof(tot));
+    tot.converged = 1;
+    auto add = [&](const htd_solve_info &x) {
+        tot.iterations += x.iterations;
+        tot.restarts += x.restarts;
+        tot.precond_applies += x.precond_applies;
+        tot.steps += x.steps;
+        tot.ms_total += x.ms_total;
+        tot.ms_precond += x.ms_precond;
+        tot.launches += x.launches;
+        tot.rel_res_true = std::fmax(tot.rel_res_true, x.rel_res_true);
+        tot.converged = tot.converged && x.converged;
+    };
+    std::vector<double2> res(nrec > 0 ? nrec : 1);
+    double J = 0.0;
+    htd_status st = HTD_OK;
+    for (int src = 0; src < nsrc && st == HTD_OK; ++src) {
+        const double2 *Fs = static_cast<const double2 *>(F_dev) + (size_t)src * N;
+        htd_solve_info x;
+        HTD_CUDA(cudaMemsetAsync(h->gU, 0, vb, s));
+        st = gmres(h, Fs, h->gU, tol, max_iters, s, &x);
+        add(x);
+        if (st != HTD_OK) break;
+        HTD_CUDA(cudaMemsetAsync(h->gR, 0, vb, s));
+        if (nrec > 0) {
+            htd::launch_receiver_residual(h->gU, static_cast<const double2 *>(d_dev) + (size_t)src * nrec,
+                                          h->grec, nrec, h->gres, h->gR, s);
+            HTD_CUDA(cudaGetLastError());
+            HTD_CUDA(cudaMemcpyAsync(res.data(), h->gres, sizeof(double2) * nrec,
+                                     cudaMemcpyDeviceToHost, s));
+            HTD_CUDA(cudaStreamSynchronize(s));
+            for (int k = 0; k < nrec; ++k) J += 0.5 * (res[k].x * res[k].x + res[k].y * res[k].y);
+        }
+        if (!want_grad) continue;
+        HTD_CUDA(cudaMemsetAsync(h->gMu, 0, vb, s));
+        st = gmres(h, h->gR, h->gMu, tol, max_iters, s, &x);
+        add(x);
+        if (st != HTD_OK) break;
+        htd::launch_gradients(h->L64, h->M, h->omega_phys, h->gMu, h->gU,
+                              static_cast<double *>(grad_m_dev), static_cast<double *>(grad_R_dev), s);
+        HTD_CUDA(cudaGetLastError());
+    }
+    HTD_CUDA(cudaStreamSynchronize(s));
+    if (!std::isfinite(J) && st == HTD_OK) st = HTD_ERR_NONFINITE;
+    *misfit = J;
+    if (info) *info = tot;
     return st;
 }
 

@@ -168,6 +168,13 @@ void launch_stream3d(const Stream3Maps &maps, int from, int shape, const Layout 
                      const StepCoef<float> &C, float a, float b, const OutSlot *slot, int flags,
                      int zchunk, int *err, cudaStream_t s);
 
+// Receiver residual res = U[rec] - d, and r[rec] += conj(res) (r pre-zeroed).
+void launch_receiver_residual(const double2 *U, const double2 *d, const int64_t *rec, int nrec,
+                              double2 *res, double2 *r, cudaStream_t s);
+// gm[cell] += omega^2 Re sum_cell mu M U; gR[node] += omega Im(mu U) (either may be null)
+void launch_gradients(const Layout &L, const double M[4], double omega_phys, const double2 *mu,
+                      const double2 *U, double *gm, double *gR, cudaStream_t s);
+
 // Read-only view of a handle's FP64 operator data (defined in htd_capi.cu).
 struct OperatorView {
     Layout L64;             // layout of kap64 (compact N = L64.N)

@@ -500,3 +500,108 @@ void launch_scale(const double2 *w, double scale, double2 *v, int64_t N, cudaStr
 }
 
 }  // namespace htd
+
+namespace htd {
+
+// ---------------------------------------------------------------------------
+// receiver misfit and gradient (adjoint state)
+// ---------------------------------------------------------------------------
+
+__global__ void gather_residual_kernel(const double2 *__restrict__ U, const double2 *__restrict__ d,
+                                       const int64_t *__restrict__ rec, int nrec,
+                                       double2 *__restrict__ res)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nrec) return;
+    const double2 u = U[rec[k]], dd = d[k];
+    res[k] = make_double2(u.x - dd.x, u.y - dd.y);
+}
+
+__global__ void scatter_conj_kernel(const double2 *__restrict__ res, const int64_t *__restrict__ rec,
+                                    int nrec, double2 *__restrict__ r)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nrec) return;
+    double *p = reinterpret_cast<double *>(r + rec[k]);
+    atomicAdd(p, res[k].x);          // receivers may repeat: accumulate conj(res)
+    atomicAdd(p + 1, -res[k].y);
+}
+
+void launch_receiver_residual(const double2 *U, const double2 *d, const int64_t *rec, int nrec,
+                              double2 *res, double2 *r, cudaStream_t s)
+{
+    if (nrec <= 0) return;
+    const int bs = 256;
+    gather_residual_kernel<<<(nrec + bs - 1) / bs, bs, 0, s>>>(U, d, rec, nrec, res);
+    ++g_launches;
+    scatter_conj_kernel<<<(nrec + bs - 1) / bs, bs, 0, s>>>(res, rec, nrec, r);
+    ++g_launches;
+}
+
+struct GradCoef {
+    double M[4];
+    double w2;      // omega_phys^2
+    double w;       // omega_phys
+};
+
+// per cell alpha: gm[alpha] += omega^2 Re sum_{beta,gamma in cell} mu_beta M_{|beta-gamma|} U_gamma
+// (cells in the compact (n+1)^d order of the speed input; ghost corners are zero)
+__global__ void __launch_bounds__(256)
+grad_cells_kernel(Layout L, GradCoef G, const double2 *__restrict__ mu,
+                  const double2 *__restrict__ U, double *__restrict__ gm)
+{
+    const int64_t cx_n = L.nx + 1, cy_n = L.ny + 1, cz_n = (L.d == 3) ? L.nz + 1 : 1;
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cx_n * cy_n * cz_n) return;
+    const int64_t ax = c % cx_n - 1;
+    const int64_t rr = c / cx_n;
+    const int64_t ay = rr % cy_n - 1;
+    const int64_t az = (L.d == 3) ? rr / cy_n - 1 : 0;
+    const int nc = (L.d == 3) ? 8 : 4;
+    double2 m8[8], u8[8];
+    for (int b = 0; b < nc; ++b) {
+        const int64_t x = ax + (b & 1), y = ay + ((b >> 1) & 1), z = az + ((b >> 2) & 1);
+        const bool in = x >= 0 && x < L.nx && y >= 0 && y < L.ny && z >= 0 && z < L.nz;
+        const int64_t i = (z * L.ny + y) * L.nx + x;
+        m8[b] = in ? mu[i] : make_double2(0.0, 0.0);
+        u8[b] = in ? U[i] : make_double2(0.0, 0.0);
+    }
+    double acc = 0.0;
+    for (int b = 0; b < nc; ++b)
+        for (int g = 0; g < nc; ++g) {
+            const double wgt = G.M[__popc(b ^ g)];
+            acc += wgt * (m8[b].x * u8[g].x - m8[b].y * u8[g].y);   // Re(mu_b U_g)
+        }
+    gm[c] += G.w2 * acc;
+}
+
+// per node: gR[i] += omega Im(mu_i U_i)
+__global__ void grad_nodes_kernel(int64_t N, double w, const double2 *__restrict__ mu,
+                                  const double2 *__restrict__ U, double *__restrict__ gR)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double2 a = mu[i], b = U[i];
+    gR[i] += w * (a.x * b.y + a.y * b.x);
+}
+
+void launch_gradients(const Layout &L, const double M[4], double omega_phys, const double2 *mu,
+                      const double2 *U, double *gm, double *gR, cudaStream_t s)
+{
+    GradCoef G;
+    for (int k = 0; k < 4; ++k) G.M[k] = M[k];
+    G.w2 = omega_phys * omega_phys;
+    G.w = omega_phys;
+    const int bs = 256;
+    if (gm) {
+        const int64_t ncell = (L.nx + 1) * (L.ny + 1) * ((L.d == 3) ? L.nz + 1 : 1);
+        grad_cells_kernel<<<(unsigned)((ncell + bs - 1) / bs), bs, 0, s>>>(L, G, mu, U, gm);
+        ++g_launches;
+    }
+    if (gR) {
+        grad_nodes_kernel<<<(unsigned)((L.N + bs - 1) / bs), bs, 0, s>>>(L.N, omega_phys, mu, U, gR);
+        ++g_launches;
+    }
+}
+
+}  // namespace htd

@@ -29,7 +29,7 @@ BC_DIRICHLET = 0
 #: every function include/htd.h declares (checked by the ABI test)
 EXPORTS = ("htd_default_options", "htd_create", "htd_destroy", "htd_plan", "htd_get_params",
            "htd_apply_precond", "htd_apply_H", "htd_residual_norm", "htd_residual_norm_noalloc",
-           "htd_gmres_solve",
+           "htd_gmres_solve", "htd_grad",
            "htd_gmres_solve_host", "htd_status_string")
 
 
@@ -111,6 +111,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.htd_residual_norm_noalloc.argtypes = [vp, vp, vp, ctypes.POINTER(d), vp]
     lib.htd_gmres_solve.argtypes = [vp, vp, vp, d, i, vp, ctypes.POINTER(SolveInfo)]
     lib.htd_gmres_solve_host.argtypes = [vp, vp, vp, d, i, vp, ctypes.POINTER(SolveInfo)]
+    lib.htd_grad.argtypes = [vp, i, vp, i, vp, vp, d, i, vp, vp, ctypes.POINTER(d), vp,
+                             ctypes.POINTER(SolveInfo)]
     lib.htd_status_string.argtypes = [i]
     lib.htd_status_string.restype = ctypes.c_char_p
     for f in EXPORTS:
@@ -264,6 +266,30 @@ def htd_gmres_solve_host(handle: int, F_host: np.ndarray, U_host: np.ndarray, to
     return d
 
 
+def htd_grad(handle: int, F, rec_idx: np.ndarray, d, tol: float, max_iters: int,
+             grad_m=None, grad_R=None, stream=None) -> tuple:
+    """Receiver misfit J = 1/2 sum_s ||P U_s - d_s||^2 and (if grad_m / grad_R, float64
+    CUDA tensors of the cell / node shapes, are given) its gradient with respect to
+    c^-2 per cell and R per node.  F: (nsrc, *n) complex128 CUDA tensor; rec_idx:
+    int64 node indices (host); d: (nsrc, nrec) complex128 CUDA tensor."""
+    import torch
+    nsrc = int(F.shape[0])
+    rec = np.ascontiguousarray(np.asarray(rec_idx, dtype=np.int64).reshape(-1))
+    for g in (grad_m, grad_R):
+        if g is not None and not (isinstance(g, torch.Tensor) and g.is_cuda and
+                                  g.dtype == torch.float64 and g.is_contiguous()):
+            raise TypeError("gradients must be contiguous float64 CUDA tensors")
+    J = ctypes.c_double()
+    info = SolveInfo()
+    st = load().htd_grad(handle, nsrc, _dev_ptr(F), int(rec.size), rec.ctypes.data,
+                         _dev_ptr(d) if rec.size else None, float(tol), int(max_iters),
+                         None if grad_m is None else grad_m.data_ptr(),
+                         None if grad_R is None else grad_R.data_ptr(), ctypes.byref(J),
+                         _stream_ptr(stream), ctypes.byref(info))
+    _check(st, "htd_grad")
+    return J.value, info.as_dict()
+
+
 def htd_status_string(status: int) -> str:
     return load().htd_status_string(int(status)).decode()
 
@@ -331,6 +357,16 @@ class Solver:
         Y = self.zeros() if Y is None else Y
         htd_apply_H(self.handle, X, Y, stream)
         return Y
+
+    def grad(self, F, rec_idx, d, tol=1e-10, max_iters=400, stream=None, want_grad=True):
+        """(J, grad_m, grad_R, info): misfit and gradient w.r.t. c^-2 per cell and R per node."""
+        import torch
+        gm = gR = None
+        if want_grad:
+            gm = torch.empty([m + 1 for m in self.n], dtype=torch.float64, device="cuda")
+            gR = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        J, info = htd_grad(self.handle, F, rec_idx, d, tol, max_iters, gm, gR, stream)
+        return J, gm, gR, info
 
     def solve(self, F, U=None, tol=1e-6, max_iters=400, stream=None, allow_not_converged=False):
         U = self.zeros() if U is None else U

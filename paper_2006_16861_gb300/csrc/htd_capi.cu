@@ -26,6 +26,10 @@ namespace {
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kMaxRestart = 64;
+// streamed 3-D step kernels: shapes 0..2 one node per thread (32 x 8, 64 x 4,
+// 128 x 2 tiles), 3 = node pairs in paired FP32 instructions (64 x 8 tiles)
+constexpr int kS3Pair = 3;
+constexpr int kS3Default = kS3Pair;
 
 // ---------------------------------------------------------------------------
 // stencil weights per Hamming distance (App. A cell form, h = 1)
@@ -153,6 +157,7 @@ struct htd_ctx {
     bool use_s3 = false;
     int s3_zchunk = 0;
     int s3_shape = 0;
+    int s3_stages = 6;
     int *err_dev = nullptr;     // set by a kernel whose bounded device wait gave up
     float step_us = 0.f;        // autotuned time per recurrence step (microseconds)
     // gradient workspace (htd_grad), allocated on first use
@@ -249,9 +254,14 @@ htd_status run_steps_direct(htd_ctx *c, cudaStream_t s)
                 int flags = 0;
                 if (j + 1 == jim) flags |= 1;
                 if (j + 1 == c->nsteps) flags |= 2;
-                htd::launch_stream3d(c->s3maps, (int)(j & 1), c->s3_shape, L, (j & 1) ? A : B, C,
-                                     (T)c->atab[j],
-                                     (T)c->btab[j], c->slot, flags, c->s3_zchunk, c->err_dev, s);
+                if (c->s3_shape == kS3Pair)
+                    htd::launch_stream3d_pair(c->s3maps, (int)(j & 1), L, (j & 1) ? A : B, C,
+                                              (T)c->atab[j], (T)c->btab[j], c->slot, flags,
+                                              c->s3_zchunk, c->s3_stages, c->err_dev, s);
+                else
+                    htd::launch_stream3d(c->s3maps, (int)(j & 1), c->s3_shape, L,
+                                         (j & 1) ? A : B, C, (T)c->atab[j], (T)c->btab[j],
+                                         c->slot, flags, c->s3_zchunk, c->err_dev, s);
             }
             HTD_CUDA(cudaGetLastError());
             return HTD_OK;
@@ -616,6 +626,69 @@ htd_status autotune_tb2d(htd_ctx *c, int want_B, int want_RPT)
     return HTD_OK;
 }
 
+// z-chunk length of the streamed 3-D step, chosen by timing: every chunk count k
+// whose chunk length ceil(nz / k) lies in [16, 128] (nz itself when nz < 16),
+// one step each on the context's own buffers with zero forcing and no outputs.
+// How the CTAs of the last wave fill the GPU decides the best length, which no
+// simple rule predicts well (at 256^3: 37 planes beats 32 and 64 by 3-8 %).
+htd_status autotune_s3_zchunk(htd_ctx *c)
+{
+    const Layout &L = c->Lr;
+    std::vector<int> cands;
+    for (int64_t k = 1; k <= L.nz; ++k) {
+        const int64_t zc = (L.nz + k - 1) / k;
+        if (zc > 128) continue;
+        if (zc < 16 && !cands.empty()) break;
+        if (cands.empty() || cands.back() != (int)zc) cands.push_back((int)zc);
+        if (zc < 16) break;
+    }
+    if (cands.size() < 2) {
+        if (!cands.empty()) c->s3_zchunk = cands[0];
+        return HTD_OK;
+    }
+    cudaStream_t s;
+    HTD_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    cudaEvent_t e0, e1;
+    HTD_CUDA(cudaEventCreate(&e0));
+    HTD_CUDA(cudaEventCreate(&e1));
+    const StepCoef<float> C = cast_coef<float>(c->C);
+    const int reps = 4;
+    float best_us = INFINITY;
+    int best = c->s3_zchunk;
+    for (int zc : cands) {
+        for (int r = 0; r < 2 + reps; ++r) {
+            if (r == 2) HTD_CUDA(cudaEventRecord(e0, s));
+            if (c->s3_shape == kS3Pair)
+                htd::launch_stream3d_pair(c->s3maps, r & 1, L, (r & 1) ? (float *)c->u0
+                                                                        : (float *)c->u1,
+                                          C, 0.f, 0.f, c->slot, 0, zc, c->s3_stages, c->err_dev, s);
+            else
+                htd::launch_stream3d(c->s3maps, r & 1, c->s3_shape, L,
+                                     (r & 1) ? (float *)c->u0 : (float *)c->u1, C, 0.f, 0.f,
+                                     c->slot, 0, zc, c->err_dev, s);
+        }
+        HTD_CUDA(cudaEventRecord(e1, s));
+        HTD_CUDA(cudaEventSynchronize(e1));
+        HTD_CUDA(cudaGetLastError());
+        float ms = 0.f;
+        HTD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        const float us = 1e3f * ms / reps;
+        if (us < best_us) {
+            best_us = us;
+            best = zc;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    int flag = 0;
+    HTD_CUDA(cudaMemcpy(&flag, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) return HTD_ERR_TIMEOUT;
+    c->s3_zchunk = best;
+    c->step_us = best_us;
+    return HTD_OK;
+}
+
 // Host-only validation and parameter selection (Sec. 2.2, App. A).
 struct Plan {
     htd_options opt;
@@ -825,12 +898,28 @@ htd_status create_impl(const htd_grid *grid, const double *c_cell, const double 
             float *planes[6] = {(float *)c->u0, (float *)c->u1, (float *)c->kap, (float *)c->dco,
                                 (float *)c->fre, (float *)c->fim};
             const char *envs = std::getenv("HTD_S3_TILE");       // tuning override
-            c->s3_shape = envs ? std::atoi(envs) : 0;
-            c->use_s3 = htd::make_stream3d_maps(L, c->s3_shape, planes, &c->s3maps);
+            c->s3_shape = envs ? std::atoi(envs) : kS3Default;
+            if (c->s3_shape == kS3Pair) {
+                c->use_s3 = htd::make_stream3d_pair_maps(L, planes, &c->s3maps);
+                if (!c->use_s3) {                                  // odd layout: one node per thread
+                    (void)cudaGetLastError();
+                    c->s3_shape = 0;
+                }
+            }
+            if (c->s3_shape != kS3Pair)
+                c->use_s3 = htd::make_stream3d_maps(L, c->s3_shape, planes, &c->s3maps);
             if (c->use_s3) {
-                c->s3_zchunk = htd::stream3d_zchunk(L, c->s3_shape);
+                const char *envst = std::getenv("HTD_S3_STAGES");  // tuning override
+                c->s3_stages = (envst && std::atoi(envst) == 4) ? 4 : 6;
+                c->s3_zchunk = c->s3_shape == kS3Pair ? htd::stream3d_pair_zchunk(L, c->s3_stages)
+                                                      : htd::stream3d_zchunk(L, c->s3_shape);
                 const char *envz = std::getenv("HTD_S3_ZCHUNK");   // tuning override
-                if (envz && std::atoi(envz) > 0) c->s3_zchunk = std::atoi(envz);
+                if (envz && std::atoi(envz) > 0) {
+                    c->s3_zchunk = std::atoi(envz);
+                } else {
+                    htd_status ts = autotune_s3_zchunk(c);
+                    if (ts != HTD_OK) return ts;
+                }
             }
             (void)cudaGetLastError();
         }
@@ -942,6 +1031,22 @@ htd_status htd_get_params(htd_handle h, htd_params *out)
     P.tile[2] = 0;
     P.ctas_per_sm = h->use_tb ? h->tb.occ : 0;
     P.waves = h->use_tb ? h->tb.waves : 0;
+    if (h->use_s3) {
+        static const int tx[4] = {32, 64, 128, 64}, ty[4] = {8, 4, 2, 8};
+        const int sh = (h->s3_shape >= 0 && h->s3_shape < 4) ? h->s3_shape : 0;
+        const Layout &L = h->Lr;
+        P.tile[0] = tx[sh];
+        P.tile[1] = ty[sh];
+        P.tile[2] = h->s3_zchunk;
+        P.ctas_per_sm = (sh == kS3Pair && h->s3_stages == 4) ? 3 : 2;
+        int dev = 0, nsm = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        const int64_t ctas = ((L.nx + tx[sh] - 1) / tx[sh]) * ((L.ny + ty[sh] - 1) / ty[sh]) *
+                             ((L.nz + h->s3_zchunk - 1) / h->s3_zchunk);
+        const int64_t slots = (int64_t)P.ctas_per_sm * nsm;
+        P.waves = (int)((ctas + slots - 1) / slots);
+    }
     P.step_kernel = h->use_tb ? 1 : (h->use_s3 ? 2 : 0);
     return HTD_OK;
 }

@@ -160,13 +160,23 @@ void launch_scale(const double2 *w, double scale, double2 *v, int64_t N, cudaStr
 struct Stream3Maps {
     CUtensorMap m[8];
 };
-// tile shape: 0 = 32 x 8 columns, 1 = 64 x 4, 2 = 128 x 2
+// tile shape: 0 = 32 x 8 columns, 1 = 64 x 4, 2 = 128 x 2 (one node per thread)
 bool make_stream3d_maps(const Layout &L, int shape, float *const planes[6], Stream3Maps *maps);
 int stream3d_zchunk(const Layout &L, int shape);
 // one step; from = 0: u_j in u0 and u_{j-1} (overwritten) in u1, from = 1 swapped
 void launch_stream3d(const Stream3Maps &maps, int from, int shape, const Layout &L, float *um,
                      const StepCoef<float> &C, float a, float b, const OutSlot *slot, int flags,
                      int zchunk, int *err, cudaStream_t s);
+
+// Same step with two x-adjacent nodes per thread in paired FP32 instructions
+// (htd_stream3d_pair.cu): 64 x 8 column tiles, same maps layout (halo boxes
+// 72 x 10).  Needs an even x lead and pitch.
+bool make_stream3d_pair_maps(const Layout &L, float *const planes[6], Stream3Maps *maps);
+// stages: 6 (2 CTAs per SM) or 4 (3 CTAs per SM)
+int stream3d_pair_zchunk(const Layout &L, int stages);
+void launch_stream3d_pair(const Stream3Maps &maps, int from, const Layout &L, float *um,
+                          const StepCoef<float> &C, float a, float b, const OutSlot *slot,
+                          int flags, int zchunk, int stages, int *err, cudaStream_t s);
 
 // Receiver residual res = U[rec] - d, and r[rec] += conj(res) (r pre-zeroed).
 void launch_receiver_residual(const double2 *U, const double2 *d, const int64_t *rec, int nrec,

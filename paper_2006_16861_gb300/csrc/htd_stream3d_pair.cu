@@ -1,0 +1,382 @@
+// 3-D recurrence step streamed by TMA, two x-adjacent nodes per thread (FP32).
+//
+// Same method and pipeline as stream3d_kernel (one step of I_acd with Table 1's
+// windowed forcing; a producer warp streams z planes of a column tile through
+// a ring of shared-memory stages with full/empty mbarriers; consumer warps keep
+// register windows over three planes), but each consumer thread updates the
+// pair of nodes (x, x+1), x = x0 + 2 tx, so that the 27-term stencil sum, the
+// cell sums of q*kappa and the update run on float2 pairs with the paired FP32
+// instructions of sm_100+ (__ffma2_rn, __fadd2_rn, __fmul2_rn): about half the
+// FP instructions and half the per-node bookkeeping of the one-node kernel.
+//
+// Tile: 64 x 8 columns (256 consumer threads).  Stage = u_j box and q*kappa box
+// (72 x 10: columns x0-1 .. x0+64 with the 16-byte aligned start, rows
+// y0-1 .. y0+8) and exact 64 x 8 boxes of d, Re F, Im F, u_{j-1}.  In the halo
+// boxes node column x sits at box column x - x0 + 1 + off with off = 3 (the
+// padded layout puts column x0 - 1 at 3 mod 4), so (x, x+1) for even x - x0
+// is an aligned 64-bit pair and x - 1, x + 2 are single loads.
+//
+// Per node the arithmetic is the one-node kernel's, in the same order, with
+// each scalar operation replaced by the same operation on a pair; paired
+// instructions round each lane exactly like the scalar ones.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "htd_internal.h"
+
+namespace htd {
+
+namespace {
+
+constexpr int kTX = 64, kTY = 8;
+constexpr int kThreads = 256;                   // consumer threads, 2 nodes each
+constexpr int kHaloW = 72, kHaloH = kTY + 2;
+constexpr int kHaloElems = kHaloW * kHaloH;     // 720 floats copied
+constexpr int kHaloStride = 768;                // padded to 3072 bytes (128-byte multiple)
+constexpr int kNodeElems = kTX * kTY;           // 512 floats
+constexpr int kStageElems = 2 * kHaloStride + 4 * kNodeElems;
+constexpr unsigned kStageTxBytes = (2 * kHaloElems + 4 * kNodeElems) * 4;
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool wait_bounded(uint64_t *bar, unsigned phase, volatile int *abort_flag)
+{
+    if (mbar_try_wait(bar, phase)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, phase)) {
+        if (*abort_flag) return false;
+        if (global_ns() - t0 > kWaitLimitNs) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void load_stage(const Stream3Maps &maps, int iu, int ium, float *stage,
+                                           uint64_t *bar, int xs, int xn, int y0, int p)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(kStageTxBytes)
+                 : "memory");
+    tma_load_3d(stage, &maps.m[iu], xs, y0, p, bar);
+    tma_load_3d(stage + kHaloStride, &maps.m[2], xs, y0, p, bar);
+    tma_load_3d(stage + 2 * kHaloStride, &maps.m[3], xn, y0 + 1, p, bar);
+    tma_load_3d(stage + 2 * kHaloStride + kNodeElems, &maps.m[4], xn, y0 + 1, p, bar);
+    tma_load_3d(stage + 2 * kHaloStride + 2 * kNodeElems, &maps.m[5], xn, y0 + 1, p, bar);
+    tma_load_3d(stage + 2 * kHaloStride + 3 * kNodeElems, &maps.m[ium], xn, y0 + 1, p, bar);
+}
+
+// pair helpers
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 bc(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// NS shared-memory stages: a node plane holds three of them, the rest is the
+// producer's lead; 6 stages (86 KB) fit 2 CTAs per SM, 4 stages (57 KB) fit 3
+template <int NS>
+__global__ void __launch_bounds__(kThreads + 32, NS >= 6 ? 2 : 3)
+stream3d_pair_kernel(const __grid_constant__ Stream3Maps maps, int iu, int ium,
+                     float *__restrict__ um, Layout L, StepCoef<float> C, float a, float b,
+                     const OutSlot *__restrict__ slot, int flags, int zchunk, int *__restrict__ err)
+{
+    extern __shared__ __align__(128) float ring[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(ring + NS * kStageElems);
+    uint64_t *empty = full + NS;
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x;
+    if (smem_u32(ring) & 127u) {              // TMA destinations must be 128-byte aligned
+        if (tid == 0) atomicExch(err, 1);
+        return;
+    }
+    const int64_t x0 = (int64_t)blockIdx.x * kTX, y0 = (int64_t)blockIdx.y * kTY;
+    const int64_t zb = (int64_t)blockIdx.z * zchunk;
+    const int64_t ze = min((int64_t)L.nz, zb + zchunk);
+    if (zb >= ze) return;
+    const int64_t c0 = L.xl + x0 - 1;
+    const int xs = (int)(c0 & ~(int64_t)3);
+    const int xn = (int)(L.xl + x0);
+    const int nplanes = (int)(ze - zb) + 2;
+    const int nq = nplanes - 2;
+
+    if (tid == 0) {
+        for (int st = 0; st < NS; ++st) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[st])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[st])),
+                         "r"(kThreads / 32));
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_flag = 0;
+    }
+    __syncthreads();
+
+    // ---- producer warp ----------------------------------------------------
+    if (tid >= kThreads) {
+        if (tid == kThreads) {
+            for (int p = 0; p < nplanes; ++p) {
+                const int st = p % NS;
+                if (p >= NS && !wait_bounded(&empty[st], (unsigned)(((p / NS) - 1) & 1),
+                                                  &abort_flag))
+                    break;
+                load_stage(maps, iu, ium, ring + st * kStageElems, &full[st], xs, xn, (int)y0,
+                           (int)(zb + p));
+            }
+            if (abort_flag) {
+                atomicExch(err, 1);
+                for (int st = 0; st < NS && st < nplanes; ++st) {
+                    const int last = (nplanes - 1 - st) / NS;
+                    const unsigned long long t0 = global_ns();
+                    while (!mbar_try_wait(&full[st], (unsigned)(last & 1)) &&
+                           global_ns() - t0 < kWaitLimitNs) {
+                    }
+                }
+            }
+        }
+        return;
+    }
+
+    // ---- consumer warps: nodes (x, x+1), x = x0 + 2 tx, row y = y0 + ty ----
+    const int tx = tid & 31, ty = tid >> 5;
+    const int lane = tid & 31;
+    const int64_t gx = x0 + 2 * tx, gy = y0 + ty;
+    const bool rowok = gy < L.ny;
+    const bool actA = rowok && gx < L.nx, actB = rowok && gx + 1 < L.nx;
+    const float2 cc0 = bc(C.c0), m0 = bc(C.mt[0]);
+    const float2 mf[4] = {bc(C.mt[0]), bc(C.mt[1]), bc(C.mt[2]), bc(C.mt[3])};
+    const float2 ncf[4] = {bc(0.f), bc(-C.cs[1]), bc(-C.cs[2]), bc(-C.cs[3])};
+    const float2 a2 = bc(a), nb2 = bc(-b), ntwo = bc(-2.f);
+    int wst = 0;
+    unsigned wph = 0;
+    auto full_wait_next = [&]() -> bool {
+        const bool r = wait_bounded(&full[wst], wph, &abort_flag);
+        if (++wst == NS) { wst = 0; wph ^= 1u; }
+        return r;
+    };
+    int rst = 0;
+    auto release_next = [&]() {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[rst]);
+        if (++rst == NS) rst = 0;
+    };
+    // box offsets: row ty (= node row - 1), column of node x - 1 in the halo boxes,
+    // (ty, 2 tx) in the node boxes
+    const int uo = ty * kHaloW + 2 * tx + 3;
+    const int no = ty * kTX + 2 * tx;
+    float *ump = um + (zb + 1) * L.plane + (gy + 1) * L.pitch + L.xl + gx;   // u_{j+1} at node zb
+    int64_t cidx = (zb * L.ny + gy) * L.nx + gx;
+    const int64_t cstride = L.ny * L.nx;
+
+    // u_j of one stored plane at row oy as the three pairs (u(x-1+ox), u(x+ox))
+    auto load_u = [&](float2 (&w)[3], const float *stage, int oy) {
+        const float *r = stage + uo + oy * kHaloW;
+        const float um1 = r[0];
+        const float2 mid = *reinterpret_cast<const float2 *>(r + 1);
+        const float up2 = r[3];
+        w[0] = f2(um1, mid.x);
+        w[1] = mid;
+        w[2] = f2(mid.y, up2);
+    };
+    // sums of q*kappa of one cell plane over the cells shared with the neighbour at
+    // (oy, ox) - 1 (-1 keeps the lower cell, +1 the upper, 0 both), same order of
+    // additions as the one-node kernel: along x first, then across y
+    auto load_k = [&](float2 (&kk)[3][3], const float *stage) {
+        const float *r = stage + kHaloStride + uo;
+        float2 kx[2][3];
+#pragma unroll
+        for (int ay = 0; ay < 2; ++ay) {
+            const float km = r[ay * kHaloW];
+            const float2 k2 = *reinterpret_cast<const float2 *>(r + ay * kHaloW + 1);
+            kx[ay][0] = f2(km, k2.x);
+            kx[ay][2] = k2;
+            kx[ay][1] = add2(kx[ay][0], kx[ay][2]);
+        }
+#pragma unroll
+        for (int ox = 0; ox < 3; ++ox) {
+            kk[0][ox] = kx[0][ox];
+            kk[1][ox] = add2(kx[0][ox], kx[1][ox]);
+            kk[2][ox] = kx[1][ox];
+        }
+    };
+    // node plane iz: u of stored iz, iz+1, iz+2 (stages s0, s1, s2), cells of stored
+    // iz and iz+1, node data of stored iz+1; every operand is read from the ring,
+    // so a thread keeps no plane windows in registers
+    auto update = [&](const float *s0, const float *s1, const float *s2) {
+        float2 kl[3][3], kh[3][3];
+        load_k(kl, s0);
+        load_k(kh, s1);
+        const float *sp[3] = {s0, s1, s2};
+        float2 acc = bc(0.f);
+#pragma unroll
+        for (int oz = 0; oz < 3; ++oz)
+#pragma unroll
+            for (int oy = 0; oy < 3; ++oy) {
+                float2 uv[3];
+                load_u(uv, sp[oz], oy);
+#pragma unroll
+                for (int ox = 0; ox < 3; ++ox) {
+                    const int sh = (oz != 1) + (oy != 1) + (ox != 1);
+                    const float2 ks = (oz == 0) ? kl[oy][ox] : (oz == 2) ? kh[oy][ox]
+                                                                       : add2(kl[oy][ox], kh[oy][ox]);
+                    const float2 coef = (sh == 0) ? fma2(m0, ks, cc0) : fma2(mf[sh], ks, ncf[sh]);
+                    acc = fma2(coef, uv[ox], acc);
+                }
+            }
+        const float *nd = s1 + 2 * kHaloStride + no;
+        const float2 d = *reinterpret_cast<const float2 *>(nd);
+        const float2 fr = *reinterpret_cast<const float2 *>(nd + kNodeElems);
+        const float2 fi = *reinterpret_cast<const float2 *>(nd + 2 * kNodeElems);
+        const float2 uprev = *reinterpret_cast<const float2 *>(nd + 3 * kNodeElems);
+        const float2 g = fma2(a2, fr, mul2(nb2, fi));
+        const float2 t = fma2(ntwo, uprev, add2(acc, g));
+        const float2 unew = fma2(d, t, uprev);
+        if (actB) {
+            *reinterpret_cast<float2 *>(ump) = unew;
+        } else if (actA) {
+            *ump = unew.x;
+        }
+        if (flags && actA) {
+            if ((flags & 1) && slot->snap_part) {
+                slot->snap_part[2 * cidx] = (double)unew.x;
+                if (actB) slot->snap_part[2 * cidx + 2] = (double)unew.y;
+            }
+            if ((flags & 2) && slot->final_part) {
+                slot->final_part[2 * cidx] = (double)unew.x;
+                if (actB) slot->final_part[2 * cidx + 2] = (double)unew.y;
+            }
+        }
+        ump += L.plane;
+        cidx += cstride;
+    };
+
+    // stored planes zb, zb + 1 first; node plane q then waits for stored q + 2 and
+    // frees stored q when it is done
+    bool ok = full_wait_next() && full_wait_next();
+    int s0 = 0, s1 = 1, s2 = 2;
+    for (int q = 0; ok && q < nq; ++q) {
+        if (!(ok = full_wait_next())) break;
+        update(ring + s0 * kStageElems, ring + s1 * kStageElems, ring + s2 * kStageElems);
+        release_next();
+        s0 = s1;
+        s1 = s2;
+        if (++s2 == NS) s2 = 0;
+    }
+}
+
+}  // namespace
+
+size_t stream3d_pair_smem_bytes(int stages)
+{
+    return (size_t)stages * kStageElems * sizeof(float) + 2 * stages * sizeof(uint64_t);
+}
+
+bool make_stream3d_pair_maps(const Layout &L, float *const planes[6], Stream3Maps *maps)
+{
+    typedef CUresult (*EncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                 const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                 const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    // node pairs need even columns: the padded layout's x lead must be even
+    if (L.d != 3 || (L.xl % 4) != 0) return false;
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    EncodeFn encode = reinterpret_cast<EncodeFn>(fn);
+    const cuuint64_t dims[3] = {(cuuint64_t)L.pitch, (cuuint64_t)(L.ny + 2), (cuuint64_t)(L.nz + 2)};
+    const cuuint64_t strides[2] = {(cuuint64_t)(L.pitch * sizeof(float)),
+                                   (cuuint64_t)(L.plane * sizeof(float))};
+    const cuuint32_t halo[3] = {(cuuint32_t)kHaloW, (cuuint32_t)kHaloH, 1};
+    const cuuint32_t node[3] = {(cuuint32_t)kTX, (cuuint32_t)kTY, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    float *src[8] = {planes[0], planes[1], planes[2], planes[3], planes[4], planes[5], planes[0],
+                     planes[1]};
+    for (int i = 0; i < 8; ++i) {
+        const cuuint32_t *box = (i < 3) ? halo : node;
+        if (encode(&maps->m[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)src[i], dims, strides,
+                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+            CUDA_SUCCESS)
+            return false;
+    }
+    return cudaFuncSetAttribute(stream3d_pair_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)stream3d_pair_smem_bytes(6)) == cudaSuccess &&
+           cudaFuncSetAttribute(stream3d_pair_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)stream3d_pair_smem_bytes(4)) == cudaSuccess;
+}
+
+int stream3d_pair_zchunk(const Layout &L, int stages)
+{
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t tiles = ((L.nx + kTX - 1) / kTX) * ((L.ny + kTY - 1) / kTY);
+    int64_t zc = 64;
+    const int per_sm = stages == 4 ? 3 : 2;
+    while (zc > 16 && tiles * ((L.nz + zc - 1) / zc) < per_sm * nsm) zc /= 2;
+    if (zc > L.nz) zc = L.nz;
+    return (int)zc;
+}
+
+void launch_stream3d_pair(const Stream3Maps &maps, int from, const Layout &L, float *um,
+                          const StepCoef<float> &C, float a, float b, const OutSlot *slot,
+                          int flags, int zchunk, int stages, int *err, cudaStream_t s)
+{
+    const int iu = from ? 1 : 0, ium = from ? 6 : 7;
+    dim3 grd((unsigned)((L.nx + kTX - 1) / kTX), (unsigned)((L.ny + kTY - 1) / kTY),
+             (unsigned)((L.nz + zchunk - 1) / zchunk));
+    if (stages == 4)
+        stream3d_pair_kernel<4><<<grd, kThreads + 32, stream3d_pair_smem_bytes(4), s>>>(
+            maps, iu, ium, um, L, C, a, b, slot, flags, zchunk, err);
+    else
+        stream3d_pair_kernel<6><<<grd, kThreads + 32, stream3d_pair_smem_bytes(6), s>>>(
+            maps, iu, ium, um, L, C, a, b, slot, flags, zchunk, err);
+    ++g_launches;
+}
+
+}  // namespace htd

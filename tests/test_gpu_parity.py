@@ -165,18 +165,22 @@ S3_CASES = [(13, 17, 19), (40, 9, 70), (1, 3, 1), (2, 2, 2), (64, 16, 33), (5, 3
 
 @pytest.mark.parametrize("n", S3_CASES, ids=["x".join(map(str, c)) for c in S3_CASES])
 @pytest.mark.parametrize("mode", ["table1", "exact"])
-@pytest.mark.parametrize("tile", ["0", "1", "2"])
+@pytest.mark.parametrize("tile", ["0", "1", "2", "3", "3:4"])
 def test_streamed_3d_step_matches_register_kernel(n, mode, tile, monkeypatch):
-    """The TMA-streamed 3-D FP32 step (32 x 8, 64 x 4 or 128 x 2 column tiles, z
-    chunks, a ring of shared-memory stages fed by a producer warp) against the
-    register z-march kernel and the FP64 oracle, on ragged grids and several z
-    chunks (16 planes per chunk at these sizes)."""
+    """The TMA-streamed 3-D FP32 step (one node per thread on 32 x 8, 64 x 4 or
+    128 x 2 column tiles, or node pairs in paired FP32 instructions on 64 x 8
+    tiles; z chunks, a ring of shared-memory stages fed by a producer warp)
+    against the register z-march kernel and the FP64 oracle, on ragged grids
+    (odd nx leaves the last pair half-used) and several z chunks (16 planes per
+    chunk at these sizes); "3:4" runs the pair kernel with 4 ring stages."""
     p = het_problem(3, n, T=2)
     monkeypatch.setenv("HTD_S3", "0")
     s0 = htd.Solver(p, precision="mixed", mode=mode)
     assert s0.params["step_kernel"] == 0
     monkeypatch.delenv("HTD_S3")
-    monkeypatch.setenv("HTD_S3_TILE", tile)
+    monkeypatch.setenv("HTD_S3_TILE", tile.split(":")[0])
+    if ":" in tile:                                     # shared-memory stages of the pair kernel
+        monkeypatch.setenv("HTD_S3_STAGES", tile.split(":")[1])
     s1 = htd.Solver(p, precision="mixed", mode=mode)
     assert s1.params["step_kernel"] == 2
     o = oracle.Oracle(p)
@@ -185,6 +189,26 @@ def test_streamed_3d_step_matches_register_kernel(n, mode, tile, monkeypatch):
         b = host(s1.precond(dev(F))).reshape(-1)
         assert rel_l2(b, a) <= 1e-6, rel_l2(b, a)
         assert rel_l2(b, o.precond(F, mode).reshape(-1)) <= 2e-5
+
+
+@pytest.mark.parametrize("zchunk", ["1", "5", "7"])
+@pytest.mark.parametrize("tile", ["0", "3"])
+def test_streamed_3d_forced_z_chunks(zchunk, tile, monkeypatch):
+    """Short and ragged z chunks (19 planes as 19 x 1, 5+5+5+4, 7+7+5): every
+    chunk boundary re-reads its two halo planes, and the result is the same as
+    one-chunk streaming and the register z-march kernel, to rounding."""
+    p = het_problem(3, (37, 21, 19), T=2)
+    monkeypatch.setenv("HTD_S3", "0")
+    s0 = htd.Solver(p, precision="mixed")
+    monkeypatch.delenv("HTD_S3")
+    monkeypatch.setenv("HTD_S3_TILE", tile)
+    monkeypatch.setenv("HTD_S3_ZCHUNK", zchunk)
+    s1 = htd.Solver(p, precision="mixed")
+    assert s1.params["step_kernel"] == 2
+    F = W.random_rhs(8, p.n)
+    a = host(s0.precond(dev(F))).reshape(-1)
+    b = host(s1.precond(dev(F))).reshape(-1)
+    assert rel_l2(b, a) <= 1e-6, rel_l2(b, a)
 
 
 def test_mixed_precond_is_fp32_accurate():

@@ -59,7 +59,21 @@ NCU_TRAFFIC = {
              "nodes": 1001 * 1001},
     "stream3d": {"file": "htd_stream3d.cu", "sha16": "4f289c964d28aa22",
                  "bytes": 193680896 + 18157568, "nodes": 192 ** 3},
+    "stream3d_pair": {"file": "htd_stream3d_pair.cu", "sha16": "710f53e4e0917f1c",
+                      "bytes": 197462272 + 16750848, "nodes": 192 ** 3},
 }
+
+
+def step_kernel_name(prm, ndim):
+    """(name, traffic key) of the recurrence kernel a context uses."""
+    sk = prm.get("step_kernel")
+    if sk == 1:
+        return f"tb2d_kernel<float,{prm['steps_per_launch']}>", "tb2d"
+    if sk == 2:
+        if list(prm["tile"][:2]) == [64, 8]:
+            return "stream3d_pair_kernel<6>", "stream3d_pair"
+        return "stream3d_kernel", "stream3d"
+    return ("step2d_kernel<float>" if ndim == 2 else "step3d_kernel<float>"), None
 
 
 def ncu_traffic(key, nodes):
@@ -233,12 +247,13 @@ def secondary_3d(htd, stream, flush, peaks):
     bytes_step = N3 * 4 * WORDS_ONE_STEP
     peak, kind = peaks()
     achieved = bytes_step / (us_step * 1e-6) / 1e9
-    kern = {2: "stream3d_kernel", 0: "step3d_kernel<float>"}.get(prm["step_kernel"], "?")
+    kern, tkey = step_kernel_name(prm, 3)
     return {"workload": "3d_layered_256 (T=4, 48 steps per application)",
             "value": N3 * prm["steps"] / (ms * 1e-3) / 1e9, "unit": UNIT,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
-                         "traffic": ncu_traffic("stream3d", N3) if prm["step_kernel"] == 2 else None,
+                         "traffic": ncu_traffic(tkey, N3) if tkey else None,
+                         "tile": prm["tile"],
                          "kernel": kern,
                          "bytes_per_launch": bytes_step, "avg_launch_us": us_step,
                          "peak_kind": f"{kind} HBM copy bandwidth"}}
@@ -425,6 +440,7 @@ def run_ours(args):
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
 
     ms_per_step = total_ms / args.steps
+    kern, tkey = step_kernel_name(prm, p.ndim)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -444,13 +460,9 @@ def run_ours(args):
             "fp64_iterations": fp64_info["iterations"] if fp64_info else None,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
-                         "traffic": (ncu_traffic("tb2d", N) if prm.get("step_kernel") == 1 else
-                                     ncu_traffic("stream3d", N) if prm.get("step_kernel") == 2
-                                     else None),
+                         "traffic": ncu_traffic(tkey, N) if tkey else None,
                          "effective_single_step_gbs": N * 4 * WORDS_ONE_STEP * spl / avg_launch_s / 1e9,
-                         "kernel": {1: f"tb2d_kernel<float,{spl}>", 2: "stream3d_kernel"}.get(
-                             prm.get("step_kernel"),
-                             "step2d_kernel<float>" if p.ndim == 2 else "step3d_kernel<float>"),
+                         "kernel": kern,
                          "steps_per_launch": spl,
                          "bytes_per_launch": bytes_per_launch,
                          "avg_launch_us": avg_launch_s * 1e6,

@@ -39,6 +39,7 @@ extern "C" {
 #endif
 
 typedef struct htd_ctx *htd_handle;
+typedef struct htd_batch_s *htd_batch;
 
 typedef enum {
     HTD_OK = 0,
@@ -78,6 +79,11 @@ typedef struct {
     int nP;            /* time steps per period; 0 = smallest stable multiple of 4 */
     int stencil;       /* HTD_STENCIL_Q1MIX or HTD_STENCIL_FD5 */
     int restart;       /* Krylov restart length m for htd_gmres_solve, 1..64 */
+    int max_rhs;       /* right-hand sides one batched application may carry for
+                          this handle (htd_batch_*), 1..256; 0 means 1.  The
+                          per-rhs device arrays (two states, two forcing planes,
+                          and two more states for the blocked 2-D kernel) are
+                          allocated max_rhs times */
 } htd_options;
 
 typedef struct {
@@ -97,7 +103,7 @@ typedef struct {
 } htd_solve_info;
 
 /* Fill *opt with the defaults: FP64, TABLE1, FGMRES, T = 10, rho = 0.25,
- * nP = 0 (automatic), Q1MIX stencil, restart 20. */
+ * nP = 0 (automatic), Q1MIX stencil, restart 20, max_rhs 1. */
 void htd_default_options(htd_options *opt);
 
 /*
@@ -269,6 +275,49 @@ htd_status htd_grad(htd_handle h, int nsrc, const void *F_dev, int nrec,
                     const int64_t *rec_idx_host, const void *d_dev, double tol, int max_iters,
                     void *grad_m_dev, void *grad_R_dev, double *misfit, void *stream,
                     htd_solve_info *info);
+
+/*
+ * Batches.  The paper solves one right-hand side of one problem at a time
+ * (Sec. 5); these calls run many independent systems together: several
+ * right-hand sides of one handle (sharing its coefficient arrays) and several
+ * handles of different sizes and step counts.  Each system is the problem of
+ * htd_gmres_solve; only the scheduling differs.
+ *
+ * htd_batch_create: ninst distinct handles on the current device, instance i
+ * carrying nrhs[i] right-hand sides (1 <= nrhs[i] <= its max_rhs option).  The
+ * batch owns the Krylov workspace of every system (2 m + 3 complex vectors of
+ * the instance's N each); the handles stay owned by the caller and must
+ * outlive the batch.  Errors: HTD_ERR_ARG (null, repeated handle, bad nrhs,
+ * a LEFT_GMRES handle), HTD_ERR_OOM, HTD_ERR_CUDA.
+ */
+htd_status htd_batch_create(int ninst, const htd_handle *handles, const int *nrhs,
+                            htd_batch *out);
+htd_status htd_batch_destroy(htd_batch b);
+
+/*
+ * U_i[r] = P_i F_i[r] for every system: F_dev[i], U_dev[i] are complex128
+ * [nrhs[i]][N_i] (device, distinct).  One application of every preconditioner
+ * (both runs in mode EXACT) as one CUDA-graph launch per run: the captured
+ * step sequences of all handles are child graphs of one graph, and each step
+ * kernel covers all right-hand sides of its handle.  Asynchronous on stream.
+ */
+htd_status htd_batch_apply_precond(htd_batch b, const void *const *F_dev, void *const *U_dev,
+                                   void *stream);
+
+/*
+ * Solve every system H_i U_i[r] = F_i[r] by FGMRES(m_i) with the handle's
+ * preconditioner, all systems in lockstep: each Arnoldi step applies the
+ * preconditioners of all systems still running in one graph launch, then
+ * runs the FP64 Krylov updates of each system; a system leaves when its true
+ * relative residual <= tol (or after max_iters steps) and its slots go idle.
+ * U_dev[i] holds the initial guesses on entry.  info: sum(nrhs) entries in
+ * instance-major order, or NULL.  Synchronises the stream.  Returns
+ * HTD_ERR_NOT_CONVERGED if any system did not converge (all are still
+ * solved as far as they went), HTD_ERR_NONFINITE, HTD_ERR_TIMEOUT,
+ * HTD_ERR_CUDA.
+ */
+htd_status htd_batch_gmres_solve(htd_batch b, const void *const *F_dev, void *const *U_dev,
+                                 double tol, int max_iters, void *stream, htd_solve_info *info);
 
 /* Static string for a status code. */
 const char *htd_status_string(htd_status s);

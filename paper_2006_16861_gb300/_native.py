@@ -19,7 +19,11 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libhtd.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# Host code: no FMA contraction, so that the host-side Krylov arithmetic
+# (Givens rotations, the triangular solve) rounds the same way on x86-64 and
+# aarch64 and in every translation unit that repeats it.
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+              "-Xcompiler", "-ffp-contract=off",
               "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
 
 

@@ -16,6 +16,7 @@
 
 #include "htd.h"
 #include "htd_internal.h"
+#include "htd_krylov_host.h"
 
 using htd::Layout;
 using htd::OutSlot;
@@ -158,6 +159,11 @@ struct htd_ctx {
     int s3_zchunk = 0;
     int s3_shape = 0;
     int s3_stages = 6;
+    // right-hand-side batch: rcap rhs slots in every per-rhs array (u0, u1, u2,
+    // u3, fre, fim, slot); act_dev = active list read by the step kernels
+    int rcap = 1;
+    int *act_dev = nullptr;
+    htd::RhsSet Rs{};
     int *err_dev = nullptr;     // set by a kernel whose bounded device wait gave up
     float step_us = 0.f;        // autotuned time per recurrence step (microseconds)
     // gradient workspace (htd_grad), allocated on first use
@@ -165,6 +171,7 @@ struct htd_ctx {
     int64_t *grec = nullptr;
     int grec_cap = 0;
     // captured step sequence
+    cudaGraph_t graph = nullptr;          // kept for batches (child graph nodes)
     cudaGraphExec_t exec = nullptr;
     bool graph_tried = false;
     long long steps_run = 0;
@@ -199,11 +206,12 @@ void free_ctx(htd_ctx *c)
 {
     if (!c) return;
     if (c->exec) cudaGraphExecDestroy(c->exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
     for (cudaEvent_t e : c->pev)
         if (e) cudaEventDestroy(e);
     void *dev[] = {c->kap, c->dco, c->fre, c->fim, c->u0, c->u1, c->kap64, c->imH, c->V, c->Z,
                    c->w, c->t, c->r, c->partial, c->hdev, c->slot, c->Fh, c->Uh, c->u2, c->u3,
-                   c->err_dev, c->gU, c->gMu, c->gR, c->gres, c->grec};
+                   c->err_dev, c->gU, c->gMu, c->gR, c->gres, c->grec, c->act_dev};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (c->hhost) cudaFreeHost(c->hhost);
@@ -217,8 +225,8 @@ htd_status run_steps_direct(htd_ctx *c, cudaStream_t s)
     const Layout &L = c->Lr;
     const StepCoef<T> C = cast_coef<T>(c->C);
     T *A = (T *)c->u0, *B = (T *)c->u1;
-    HTD_CUDA(cudaMemsetAsync(A, 0, sizeof(T) * L.total, s));
-    HTD_CUDA(cudaMemsetAsync(B, 0, sizeof(T) * L.total, s));
+    HTD_CUDA(cudaMemsetAsync(A, 0, sizeof(T) * L.total * c->rcap, s));
+    HTD_CUDA(cudaMemsetAsync(B, 0, sizeof(T) * L.total * c->rcap, s));
     const long long jim = c->nsteps - c->nP / 4;
     if constexpr (std::is_same<T, float>::value) {
       if (c->use_tb) {
@@ -241,7 +249,7 @@ htd_status run_steps_direct(htd_ctx *c, cudaStream_t s)
             htd::launch_tb2d<T>(c->tb, c->tbmaps, map_of[from][0], map_of[from][1], L,
                                 pairs[1 - from][0], pairs[1 - from][1], (const T *)c->dco,
                                 (const T *)c->fre, (const T *)c->fim, C, S, c->slot,
-                                c->err_dev, s);
+                                c->err_dev, s, c->Rs);
             from = 1 - from;
         }
         HTD_CUDA(cudaGetLastError());
@@ -257,7 +265,7 @@ htd_status run_steps_direct(htd_ctx *c, cudaStream_t s)
                 if (c->s3_shape == kS3Pair)
                     htd::launch_stream3d_pair(c->s3maps, (int)(j & 1), L, (j & 1) ? A : B, C,
                                               (T)c->atab[j], (T)c->btab[j], c->slot, flags,
-                                              c->s3_zchunk, c->s3_stages, c->err_dev, s);
+                                              c->s3_zchunk, c->s3_stages, c->err_dev, s, c->Rs);
                 else
                     htd::launch_stream3d(c->s3maps, (int)(j & 1), c->s3_shape, L,
                                          (j & 1) ? A : B, C, (T)c->atab[j], (T)c->btab[j],
@@ -274,38 +282,56 @@ htd_status run_steps_direct(htd_ctx *c, cudaStream_t s)
         if (j + 1 == jim) flags |= 1;
         if (j + 1 == c->nsteps) flags |= 2;
         htd::launch_step<T>(L, cur, oth, (const T *)c->kap, (const T *)c->dco, (const T *)c->fre,
-                            (const T *)c->fim, C, (T)c->atab[j], (T)c->btab[j], c->slot, flags, s);
+                            (const T *)c->fim, C, (T)c->atab[j], (T)c->btab[j], c->slot, flags, s,
+                            c->Rs);
     }
     HTD_CUDA(cudaGetLastError());
     return HTD_OK;
 }
 
+bool graphs_disabled()
+{
+    static const bool no_graph = std::getenv("HTD_NO_GRAPH") != nullptr;
+    return no_graph;
+}
+
+// Capture the whole step sequence of one run into a graph (once per handle):
+// c->graph keeps it (a batch adds it as a child graph), c->exec replays it.
+template <typename T>
+void capture_steps(htd_ctx *c)
+{
+    if (c->graph_tried) return;
+    c->graph_tried = true;
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return;
+    }
+    cudaGraph_t g = nullptr;
+    bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        const long long before = htd::g_launches;
+        htd_status st = run_steps_direct<T>(c, cs);
+        ok = cudaStreamEndCapture(cs, &g) == cudaSuccess && st == HTD_OK;
+        htd::g_launches = before;            // captured, not launched
+    }
+    if (ok && cudaGraphInstantiate(&c->exec, g, 0) != cudaSuccess) {
+        c->exec = nullptr;
+        ok = false;
+    }
+    if (ok) {
+        c->graph = g;
+        g = nullptr;
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    (void)cudaGetLastError();
+}
+
 template <typename T>
 htd_status run_steps(htd_ctx *c, cudaStream_t s)
 {
-    static const bool no_graph = std::getenv("HTD_NO_GRAPH") != nullptr;
-    if (!no_graph && !c->graph_tried) {
-        c->graph_tried = true;
-        cudaStream_t cs;
-        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess) {
-            cudaGraph_t g = nullptr;
-            bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-            if (ok) {
-                const long long before = htd::g_launches;
-                htd_status st = run_steps_direct<T>(c, cs);
-                ok = cudaStreamEndCapture(cs, &g) == cudaSuccess && st == HTD_OK;
-                htd::g_launches = before;        // captured, not launched
-            }
-            if (ok && cudaGraphInstantiate(&c->exec, g, 0) != cudaSuccess) {
-                c->exec = nullptr;
-                ok = false;
-            }
-            if (g) cudaGraphDestroy(g);
-            cudaStreamDestroy(cs);
-            (void)cudaGetLastError();
-            if (!ok) c->exec = nullptr;
-        }
-    }
+    if (!graphs_disabled()) capture_steps<T>(c);
     if (c->exec) {
         HTD_CUDA(cudaGraphLaunch(c->exec, s));
         htd::g_launches += c->nsteps;            // one step kernel per graph node
@@ -333,6 +359,8 @@ htd_status precond(htd_ctx *c, const double2 *F, double2 *U, cudaStream_t s)
     htd_status cst = collect_precond_time(c);
     if (cst != HTD_OK) return cst;
     HTD_CUDA(cudaEventRecord(c->pev[0], s));
+    const int only0 = 0;
+    htd::launch_set_act(c->act_dev, 1, &only0, s);       // one rhs: slot 0 -> rhs 0
     double *Ure = reinterpret_cast<double *>(U);
     const int runs = (c->opt.mode == HTD_MODE_EXACT) ? 2 : 1;
     for (int run = 0; run < runs; ++run) {
@@ -468,23 +496,7 @@ htd_status gmres(htd_ctx *c, const double2 *F, double2 *U, double tol, int maxit
             col[j + 1] = hn;
             if (hn > 0.0) htd::launch_scale(c->w, 1.0 / hn, c->V + (int64_t)(j + 1) * N, N, s);
             // previous rotations, then a new one zeroing col[j+1]
-            for (int i = 0; i < j; ++i) {
-                const zc a = col[i], b = col[i + 1];
-                col[i] = std::conj(cs[i]) * a + sn[i] * b;
-                col[i + 1] = -sn[i] * a + cs[i] * b;
-            }
-            {
-                const zc a = col[j];
-                const double b = col[j + 1].real();
-                const double rr = std::sqrt(std::norm(a) + b * b);
-                if (rr == 0.0) { cs[j] = 1.0; sn[j] = 0.0; }
-                else { cs[j] = a / rr; sn[j] = b / rr; }
-                col[j] = std::conj(cs[j]) * a + sn[j] * b;
-                col[j + 1] = 0.0;
-                const zc gj = g[j];
-                g[j] = std::conj(cs[j]) * gj;
-                g[j + 1] = -sn[j] * gj;
-            }
+            htd::givens_column(col, cs.data(), sn.data(), g.data(), j);
             ++its;
             ++j;
             const double est = std::abs(g[j]) / bnorm;
@@ -495,11 +507,7 @@ htd_status gmres(htd_ctx *c, const double2 *F, double2 *U, double tol, int maxit
             if (hn == 0.0) break;
         }
         // y = R^{-1} g; U += basis y
-        for (int i = j - 1; i >= 0; --i) {
-            zc acc = g[i];
-            for (int k2 = i + 1; k2 < j; ++k2) acc -= Hm[(size_t)k2 * (m + 1) + i] * y[k2];
-            y[i] = acc / Hm[(size_t)i * (m + 1) + i];
-        }
+        htd::solve_upper(Hm.data(), m, g.data(), y.data(), j);
         for (int i = 0; i < j; ++i) c->hhost[i] = make_double2(y[i].real(), y[i].imag());
         HTD_CUDA(cudaMemcpyAsync(c->hdev, c->hhost, sizeof(double2) * j, cudaMemcpyHostToDevice, s));
         htd::launch_add_combination(left ? c->V : c->Z, N, j, c->hdev, U, N, s);
@@ -553,7 +561,7 @@ htd_status autotune_tb2d(htd_ctx *c, int want_B, int want_RPT)
     for (const htd::TbPlan &p : all)
         if (want_RPT == 0 || p.RPT == want_RPT) cands.push_back(p);
     if (cands.empty()) return HTD_OK;
-    const size_t bytes = sizeof(float) * (size_t)L.total;
+    const size_t bytes = sizeof(float) * (size_t)L.total * c->rcap;
     HTD_CUDA(cudaMalloc(&c->u2, bytes));
     HTD_CUDA(cudaMemset(c->u2, 0, bytes));
     HTD_CUDA(cudaMalloc(&c->u3, bytes));
@@ -588,7 +596,7 @@ htd_status autotune_tb2d(htd_ctx *c, int want_B, int want_RPT)
     htd::TbMaps best_maps{};
     for (size_t k = 0; k < cands.size(); ++k) {
         htd::TbMaps maps;
-        if (!htd::make_tb2d_maps<float>(L, cands[k], planes, &maps)) continue;
+        if (!htd::make_tb2d_maps<float>(L, cands[k], planes, &maps, c->rcap)) continue;
         htd::TbSteps<float> S;
         S.nsub = cands[k].B;
         for (int q = 0; q < htd::kTbMaxSteps; ++q) { S.a[q] = 0.f; S.b[q] = 0.f; S.flags[q] = 0; }
@@ -714,6 +722,8 @@ htd_status plan_impl(const htd_grid *grid, const double *c_cell, const double *R
     if (opt.krylov != HTD_FGMRES && opt.krylov != HTD_LEFT_GMRES) return HTD_ERR_ARG;
     if (opt.T < 1 || !(opt.rho >= 0.0 && opt.rho <= 1.0) || opt.nP < 0) return HTD_ERR_ARG;
     if (opt.restart < 1 || opt.restart > kMaxRestart) return HTD_ERR_ARG;
+    if (opt.max_rhs == 0) opt.max_rhs = 1;
+    if (opt.max_rhs < 1 || opt.max_rhs > htd::kMaxRhs) return HTD_ERR_ARG;
     const int d = grid->ndim;
     pl->d = d;
     pl->N = 1;
@@ -837,15 +847,26 @@ htd_status create_impl(const htd_grid *grid, const double *c_cell, const double 
     c->L64 = make_layout(d, c->n, sizeof(double));
     const Layout &L = c->Lr;
     const size_t bytes = c->esz * (size_t)L.total;
-    void **arrs[] = {&c->kap, &c->dco, &c->fre, &c->fim, &c->u0, &c->u1};
-    for (void **pp : arrs) {
+    c->rcap = opt.max_rhs;
+    void **shared_arrs[] = {&c->kap, &c->dco};
+    for (void **pp : shared_arrs) {
         HTD_CUDA(cudaMalloc(pp, bytes));
         HTD_CUDA(cudaMemset(*pp, 0, bytes));
     }
+    void **rhs_arrs[] = {&c->fre, &c->fim, &c->u0, &c->u1};
+    for (void **pp : rhs_arrs) {
+        HTD_CUDA(cudaMalloc(pp, bytes * c->rcap));
+        HTD_CUDA(cudaMemset(*pp, 0, bytes * c->rcap));
+    }
     HTD_CUDA(cudaMalloc((void **)&c->err_dev, sizeof(int)));
     HTD_CUDA(cudaMemset(c->err_dev, 0, sizeof(int)));
-    HTD_CUDA(cudaMalloc((void **)&c->slot, sizeof(OutSlot)));
-    HTD_CUDA(cudaMemset(c->slot, 0, sizeof(OutSlot)));
+    HTD_CUDA(cudaMalloc((void **)&c->slot, sizeof(OutSlot) * c->rcap));
+    HTD_CUDA(cudaMemset(c->slot, 0, sizeof(OutSlot) * c->rcap));
+    HTD_CUDA(cudaMalloc((void **)&c->act_dev, sizeof(int) * (1 + c->rcap)));
+    HTD_CUDA(cudaMemset(c->act_dev, 0, sizeof(int) * (1 + c->rcap)));
+    c->Rs.act = c->act_dev;
+    c->Rs.slots = c->rcap;
+    c->Rs.stride = L.total;
     HTD_CUDA(cudaMalloc((void **)&c->kap64, sizeof(double) * c->L64.total));
     HTD_CUDA(cudaMalloc((void **)&c->imH, sizeof(double) * N));
 
@@ -899,14 +920,15 @@ htd_status create_impl(const htd_grid *grid, const double *c_cell, const double 
                                 (float *)c->fre, (float *)c->fim};
             const char *envs = std::getenv("HTD_S3_TILE");       // tuning override
             c->s3_shape = envs ? std::atoi(envs) : kS3Default;
+            if (c->s3_shape != kS3Pair && c->rcap > 1) c->s3_shape = kS3Pair;   // rhs batches
             if (c->s3_shape == kS3Pair) {
-                c->use_s3 = htd::make_stream3d_pair_maps(L, planes, &c->s3maps);
+                c->use_s3 = htd::make_stream3d_pair_maps(L, planes, &c->s3maps, c->rcap);
                 if (!c->use_s3) {                                  // odd layout: one node per thread
                     (void)cudaGetLastError();
                     c->s3_shape = 0;
                 }
             }
-            if (c->s3_shape != kS3Pair)
+            if (c->s3_shape != kS3Pair && c->rcap == 1)
                 c->use_s3 = htd::make_stream3d_maps(L, c->s3_shape, planes, &c->s3maps);
             if (c->use_s3) {
                 const char *envst = std::getenv("HTD_S3_STAGES");  // tuning override
@@ -959,6 +981,78 @@ void operator_view(const htd_ctx *c, OperatorView *out)
     out->device = c->device;
 }
 
+void ctx_info(const htd_ctx *c, CtxInfo *out)
+{
+    out->N = c->Lr.N;
+    out->m = c->m;
+    out->rcap = c->rcap;
+    out->runs = (c->opt.mode == HTD_MODE_EXACT) ? 2 : 1;
+    out->krylov = c->opt.krylov;
+    out->device = c->device;
+    out->nsteps = c->nsteps;
+}
+
+htd_status ctx_stage_run(htd_ctx *c, int run, int n, const int *idx, const double2 *const *Fp,
+                         double2 *const *Up, cudaStream_t s)
+{
+    if (n < 0 || n > c->rcap) return HTD_ERR_ARG;
+    launch_set_act(c->act_dev, n, idx, s);
+    if (n > 0) {
+        if (c->opt.precision == HTD_MIXED)
+            launch_split_batch<float>(c->Lr, Fp, (float *)c->fre, (float *)c->fim, c->Lr.total,
+                                      run, c->act_dev, c->rcap, s);
+        else
+            launch_split_batch<double>(c->Lr, Fp, (double *)c->fre, (double *)c->fim, c->Lr.total,
+                                       run, c->act_dev, c->rcap, s);
+        launch_set_slots(c->slot, Up, run, (c->opt.mode == HTD_MODE_EXACT) ? 2 : 1, c->act_dev,
+                         c->rcap, s);
+    }
+    HTD_CUDA(cudaGetLastError());
+    return HTD_OK;
+}
+
+cudaGraph_t ctx_step_graph(htd_ctx *c)
+{
+    if (graphs_disabled()) return nullptr;
+    if (c->opt.precision == HTD_MIXED) capture_steps<float>(c);
+    else capture_steps<double>(c);
+    return c->exec ? c->graph : nullptr;
+}
+
+htd_status ctx_run_steps(htd_ctx *c, cudaStream_t s)
+{
+    return (c->opt.precision == HTD_MIXED) ? run_steps<float>(c, s) : run_steps<double>(c, s);
+}
+
+void ctx_account(htd_ctx *c, int applies, long long steps)
+{
+    c->applies += applies;
+    c->steps_run += steps;
+}
+
+void ctx_apply_H(htd_ctx *c, const double2 *X, const double2 *F, double2 *Y, cudaStream_t s)
+{
+    apply_H(c, X, F, Y, s);
+}
+
+void ctx_dots(htd_ctx *c, const double2 *V, int64_t ldv, int kcount, const double2 *w,
+              double2 *out, cudaStream_t s)
+{
+    launch_dots(V, ldv, kcount, w, c->Lr.N, c->partial, c->nb, s);
+    launch_reduce(c->partial, c->nb, kcount, out, s);
+}
+
+htd_status ctx_take_error(htd_ctx *c)
+{
+    int flag = 0;
+    HTD_CUDA(cudaMemcpy(&flag, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        HTD_CUDA(cudaMemset(c->err_dev, 0, sizeof(int)));
+        return HTD_ERR_TIMEOUT;
+    }
+    return HTD_OK;
+}
+
 }  // namespace htd
 
 extern "C" {
@@ -974,6 +1068,7 @@ void htd_default_options(htd_options *opt)
     opt->nP = 0;
     opt->stencil = HTD_STENCIL_Q1MIX;
     opt->restart = 20;
+    opt->max_rhs = 1;
 }
 
 htd_status htd_create(const htd_grid *grid, const double *c_cell_host, const double *R_node_host,

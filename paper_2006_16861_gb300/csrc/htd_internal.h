@@ -70,6 +70,32 @@ struct OutSlot {
     double *snap_part;    // &U[0].im (stride 2), or null
 };
 
+// Right-hand sides of one step launch.  The launch has `slots` rhs slots per
+// tile; slot k processes rhs act[1 + k] when k < act[0] and returns at once
+// otherwise.  The list lives in device memory, so one captured step sequence
+// serves every subset of a batch (converged systems drop out without a new
+// capture).  act == null: a single rhs, index 0, slot 0.  The per-rhs planes
+// (u_j, u_{j-1}, Re F, Im F, the second state pair of the blocked kernel) lie
+// `stride` elements apart; q*kappa and d are shared by all rhs; the output
+// slot of rhs r is slot[r].
+struct RhsSet {
+    const int *act = nullptr;
+    int slots = 1;
+    int64_t stride = 0;
+};
+
+// rhs of slot k, false if the slot is idle
+__device__ __forceinline__ bool rhs_of_slot(const RhsSet &R, int k, int &rhs)
+{
+    if (!R.act) {
+        rhs = 0;
+        return k == 0;
+    }
+    if (k >= __ldg(R.act)) return false;
+    rhs = __ldg(R.act + 1 + k);
+    return true;
+}
+
 // ---- kernel launchers (htd_kernels.cu) --------------------------------------
 
 // Number of kernels enqueued by this library (host counter, not thread-safe
@@ -79,12 +105,61 @@ extern long long g_launches;
 template <typename T>
 void launch_step(const Layout &L, const T *u, T *um, const T *kap, const T *dco,
                  const T *fre, const T *fim, const StepCoef<T> &C, T a, T b,
-                 const OutSlot *slot, int flags, cudaStream_t s);
+                 const OutSlot *slot, int flags, cudaStream_t s, const RhsSet &R = RhsSet{});
 
 template <typename T>
 void launch_split(const Layout &L, const double2 *F, T *fre, T *fim, int flip, cudaStream_t s);
 
 void launch_set_slot(OutSlot *slot, double *final_part, double *snap_part, cudaStream_t s);
+
+// ---- right-hand-side batches --------------------------------------------------
+
+constexpr int kMaxRhs = 256;     // rhs per handle (act list entries)
+
+// act[0] = n, act[1 + k] = idx[k] (n <= kMaxRhs; the list travels as a kernel
+// parameter, so the host array may be reused at once)
+void launch_set_act(int *act, int n, const int *idx, cudaStream_t s);
+// Re/Im planes of the listed rhs r: Fp[r] (device table of compact complex128
+// vectors) -> fre/fim + r * stride
+template <typename T>
+void launch_split_batch(const Layout &L, const double2 *const *Fp, T *fre, T *fim, int64_t stride,
+                        int flip, const int *act, int slots, cudaStream_t s);
+// slot[r] of the listed rhs r -> parts of Up[r] (see set_slots_kernel)
+void launch_set_slots(OutSlot *slot, double2 *const *Up, int run, int runs, const int *act,
+                      int slots, cudaStream_t s);
+
+// ---- handle internals used by the batch driver (htd_capi.cu) ------------------
+
+struct CtxInfo {
+    int64_t N;          // unknowns
+    int m;              // restart length
+    int rcap;           // rhs slots (max_rhs)
+    int runs;           // real runs per application: 1 (Table 1) or 2 (EXACT)
+    int krylov;         // HTD_FGMRES or HTD_LEFT_GMRES
+    int device;
+    long long nsteps;   // recurrence steps per run
+};
+void ctx_info(const htd_ctx *c, CtxInfo *out);
+// stage run `run` of one application for the rhs idx[0..n) (n = 0: the
+// handle's step kernels idle): active list, Re/Im planes from Fp[r], output
+// slots into Up[r] (Fp, Up: device tables indexed by rhs)
+htd_status ctx_stage_run(htd_ctx *c, int run, int n, const int *idx, const double2 *const *Fp,
+                         double2 *const *Up, cudaStream_t s);
+// the handle's captured step sequence (captured on first use), or null if
+// graphs are off or the capture failed
+cudaGraph_t ctx_step_graph(htd_ctx *c);
+// the step sequence on a stream (graph launch or direct launches)
+htd_status ctx_run_steps(htd_ctx *c, cudaStream_t s);
+// statistics of runs launched through a batch graph
+void ctx_account(htd_ctx *c, int applies, long long steps);
+// Y = H X or F - H X (FP64)
+void ctx_apply_H(htd_ctx *c, const double2 *X, const double2 *F, double2 *Y, cudaStream_t s);
+// out[k] = conj(V + k ldv) . w for k < kcount (device), through the handle's
+// partial-sum buffer (kcount <= 65)
+void ctx_dots(htd_ctx *c, const double2 *V, int64_t ldv, int kcount, const double2 *w,
+              double2 *out, cudaStream_t s);
+// read and clear the device error word: HTD_ERR_TIMEOUT if a bounded wait gave up
+htd_status ctx_take_error(htd_ctx *c);
 
 // ---- temporally blocked 2-D recurrence (htd_tblock.cu) ------------------------
 
@@ -123,15 +198,19 @@ struct TbMaps {
 template <typename T>
 std::vector<TbPlan> tb2d_candidates(const Layout &L, int want_B);
 
+// The four state planes are nrhs stacks of planes L.total elements apart (one
+// per rhs, 3-D maps with the rhs as the outer coordinate); q*kappa is shared.
 template <typename T>
-bool make_tb2d_maps(const Layout &L, const TbPlan &p, T *const planes[5], TbMaps *maps);
+bool make_tb2d_maps(const Layout &L, const TbPlan &p, T *const planes[5], TbMaps *maps,
+                    int nrhs = 1);
 
 // nsub <= B steps from the state pair (maps in0, in1) into the planes uC, uD;
 // a timed-out TMA wait sets *err = 1.
 template <typename T>
 void launch_tb2d(const TbPlan &p, const TbMaps &maps, int in0, int in1, const Layout &L, T *uC,
                  T *uD, const T *dco, const T *fre, const T *fim, const StepCoef<T> &C,
-                 const TbSteps<T> &S, const OutSlot *slot, int *err, cudaStream_t s);
+                 const TbSteps<T> &S, const OutSlot *slot, int *err, cudaStream_t s,
+                 const RhsSet &R = RhsSet{});
 
 // Y = H X (F == null) or Y = F - H X, complex128 compact vectors.
 void launch_apply_H(const Layout &L, const double *kap64, const double *imH,
@@ -170,13 +249,17 @@ void launch_stream3d(const Stream3Maps &maps, int from, int shape, const Layout 
 
 // Same step with two x-adjacent nodes per thread in paired FP32 instructions
 // (htd_stream3d_pair.cu): 64 x 8 column tiles, same maps layout (halo boxes
-// 72 x 10).  Needs an even x lead and pitch.
-bool make_stream3d_pair_maps(const Layout &L, float *const planes[6], Stream3Maps *maps);
+// 72 x 10).  Needs an even x lead and pitch.  The per-rhs planes (u0, u1,
+// Re F, Im F) are nrhs stacks L.total elements apart (4-D maps, rhs
+// outermost); q*kappa and d are shared.
+bool make_stream3d_pair_maps(const Layout &L, float *const planes[6], Stream3Maps *maps,
+                             int nrhs = 1);
 // stages: 6 (2 CTAs per SM) or 4 (3 CTAs per SM)
 int stream3d_pair_zchunk(const Layout &L, int stages);
 void launch_stream3d_pair(const Stream3Maps &maps, int from, const Layout &L, float *um,
                           const StepCoef<float> &C, float a, float b, const OutSlot *slot,
-                          int flags, int zchunk, int stages, int *err, cudaStream_t s);
+                          int flags, int zchunk, int stages, int *err, cudaStream_t s,
+                          const RhsSet &R = RhsSet{});
 
 // Receiver residual res = U[rec] - d, and r[rec] += conj(res) (r pre-zeroed).
 void launch_receiver_residual(const double2 *U, const double2 *d, const int64_t *rec, int nrec,

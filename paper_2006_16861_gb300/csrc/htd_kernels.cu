@@ -40,11 +40,19 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 step2d_kernel(const T *__restrict__ u, T *__restrict__ um, const T *__restrict__ kap,
               const T *__restrict__ dco, const T *__restrict__ fre, const T *__restrict__ fim,
-              Layout L, StepCoef<T> C, T a, T b, const OutSlot *__restrict__ slot, int flags)
+              Layout L, StepCoef<T> C, T a, T b, const OutSlot *__restrict__ slot, int flags,
+              RhsSet R)
 {
     const int64_t ix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t iy = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
+    int rhs;
+    if (!rhs_of_slot(R, (int)blockIdx.z, rhs)) return;
     if (ix >= L.nx || iy >= L.ny) return;
+    u += rhs * R.stride;
+    um += rhs * R.stride;
+    fre += rhs * R.stride;
+    fim += rhs * R.stride;
+    slot += rhs;
     const int64_t P = L.pitch;
     const int64_t i = (iy + 1) * P + L.xl + ix;
     // u_j on the 3x3 neighbourhood; first index = y offset, second = x offset
@@ -80,13 +88,21 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 step3d_kernel(const T *__restrict__ u, T *__restrict__ um, const T *__restrict__ kap,
               const T *__restrict__ dco, const T *__restrict__ fre, const T *__restrict__ fim,
-              Layout L, StepCoef<T> C, T a, T b, const OutSlot *__restrict__ slot, int flags)
+              Layout L, StepCoef<T> C, T a, T b, const OutSlot *__restrict__ slot, int flags,
+              RhsSet R, int nchunks)
 {
     const int64_t ix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t iy = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
-    const int64_t z0 = (int64_t)blockIdx.z * kZChunk;
+    int rhs;
+    if (!rhs_of_slot(R, (int)blockIdx.z / nchunks, rhs)) return;
+    const int64_t z0 = (int64_t)(blockIdx.z % nchunks) * kZChunk;
     const int64_t z1 = min((int64_t)L.nz, z0 + kZChunk);
     if (ix >= L.nx || iy >= L.ny) return;
+    u += rhs * R.stride;
+    um += rhs * R.stride;
+    fre += rhs * R.stride;
+    fim += rhs * R.stride;
+    slot += rhs;
     const int64_t P = L.pitch, Q = L.plane;
     const int64_t col = (iy + 1) * P + L.xl + ix;     // (y, x) offset of the node in any plane
     // w[p][oy][ox]: u_j at stored plane (iz + p), row offset oy-1, column offset ox-1
@@ -177,18 +193,21 @@ step3d_kernel(const T *__restrict__ u, T *__restrict__ um, const T *__restrict__
 template <typename T>
 void launch_step(const Layout &L, const T *u, T *um, const T *kap, const T *dco,
                  const T *fre, const T *fim, const StepCoef<T> &C, T a, T b,
-                 const OutSlot *slot, int flags, cudaStream_t s)
+                 const OutSlot *slot, int flags, cudaStream_t s, const RhsSet &R)
 {
     if (L.d == 2) {
         dim3 blk(32, 8);
-        dim3 grd((unsigned)((L.nx + 31) / 32), (unsigned)((L.ny + 7) / 8));
-        step2d_kernel<T><<<grd, blk, 0, s>>>(u, um, kap, dco, fre, fim, L, C, a, b, slot, flags);
+        dim3 grd((unsigned)((L.nx + 31) / 32), (unsigned)((L.ny + 7) / 8), (unsigned)R.slots);
+        step2d_kernel<T><<<grd, blk, 0, s>>>(u, um, kap, dco, fre, fim, L, C, a, b, slot, flags,
+                                             R);
         ++g_launches;
     } else {
+        const int nchunks = (int)((L.nz + kZChunk - 1) / kZChunk);
         dim3 blk(32, 8);
         dim3 grd((unsigned)((L.nx + 31) / 32), (unsigned)((L.ny + 7) / 8),
-                 (unsigned)((L.nz + kZChunk - 1) / kZChunk));
-        step3d_kernel<T><<<grd, blk, 0, s>>>(u, um, kap, dco, fre, fim, L, C, a, b, slot, flags);
+                 (unsigned)(nchunks * R.slots));
+        step3d_kernel<T><<<grd, blk, 0, s>>>(u, um, kap, dco, fre, fim, L, C, a, b, slot, flags,
+                                             R, nchunks);
         ++g_launches;
     }
 }
@@ -196,11 +215,11 @@ void launch_step(const Layout &L, const T *u, T *um, const T *kap, const T *dco,
 template void launch_step<float>(const Layout &, const float *, float *, const float *,
                                  const float *, const float *, const float *,
                                  const StepCoef<float> &, float, float, const OutSlot *, int,
-                                 cudaStream_t);
+                                 cudaStream_t, const RhsSet &);
 template void launch_step<double>(const Layout &, const double *, double *, const double *,
                                   const double *, const double *, const double *,
                                   const StepCoef<double> &, double, double, const OutSlot *,
-                                  int, cudaStream_t);
+                                  int, cudaStream_t, const RhsSet &);
 
 // ---------------------------------------------------------------------------
 // split / output slot
@@ -232,6 +251,85 @@ void launch_split(const Layout &L, const double2 *F, T *fre, T *fim, int flip, c
 }
 template void launch_split<float>(const Layout &, const double2 *, float *, float *, int, cudaStream_t);
 template void launch_split<double>(const Layout &, const double2 *, double *, double *, int, cudaStream_t);
+
+// batched forms: the active rhs list act (see RhsSet) selects the slots
+
+template <typename T>
+__global__ void split_batch_kernel(Layout L, const double2 *const *__restrict__ Fp,
+                                   T *__restrict__ fre, T *__restrict__ fim, int64_t stride,
+                                   int flip, const int *__restrict__ act)
+{
+    const int k = (int)blockIdx.y;
+    if (k >= act[0]) return;
+    const int r = act[1 + k];
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= L.N) return;
+    const int64_t ix = c % L.nx;
+    const int64_t q = c / L.nx;
+    const int64_t iy = q % L.ny;
+    const int64_t iz = q / L.ny;
+    const int64_t i = L.node(ix, iy, iz) + r * stride;
+    const double2 f = Fp[r][c];
+    fre[i] = (T)(flip ? f.y : f.x);
+    fim[i] = (T)(flip ? -f.x : f.y);
+}
+
+template <typename T>
+void launch_split_batch(const Layout &L, const double2 *const *Fp, T *fre, T *fim, int64_t stride,
+                        int flip, const int *act, int slots, cudaStream_t s)
+{
+    const int bs = 256;
+    dim3 grd((unsigned)((L.N + bs - 1) / bs), (unsigned)slots);
+    split_batch_kernel<T><<<grd, bs, 0, s>>>(L, Fp, fre, fim, stride, flip, act);
+    ++g_launches;
+}
+template void launch_split_batch<float>(const Layout &, const double2 *const *, float *, float *,
+                                        int64_t, int, const int *, int, cudaStream_t);
+template void launch_split_batch<double>(const Layout &, const double2 *const *, double *, double *,
+                                         int64_t, int, const int *, int, cudaStream_t);
+
+struct ActList {
+    int n;
+    int idx[kMaxRhs];
+};
+
+__global__ void set_act_kernel(int *act, ActList a)
+{
+    const int t = threadIdx.x;
+    if (t == 0) act[0] = a.n;
+    if (t < a.n) act[1 + t] = a.idx[t];
+}
+
+void launch_set_act(int *act, int n, const int *idx, cudaStream_t s)
+{
+    ActList a;
+    a.n = n;
+    for (int k = 0; k < n && k < kMaxRhs; ++k) a.idx[k] = idx[k];
+    for (int k = n; k < kMaxRhs; ++k) a.idx[k] = 0;
+    set_act_kernel<<<1, kMaxRhs, 0, s>>>(act, a);
+    ++g_launches;
+}
+
+// output slots of the listed rhs r: the final state of run `run` goes to the
+// real (run 0) or imaginary (run 1) part of Up[r]; with one run (Table 1) the
+// snapshot goes to the imaginary part
+__global__ void set_slots_kernel(OutSlot *slot, double2 *const *Up, int run, int runs,
+                                 const int *act)
+{
+    const int k = threadIdx.x;
+    if (k >= act[0]) return;
+    const int r = act[1 + k];
+    double *base = reinterpret_cast<double *>(Up[r]);
+    slot[r].final_part = base + run;
+    slot[r].snap_part = (runs == 1) ? base + 1 : nullptr;
+}
+
+void launch_set_slots(OutSlot *slot, double2 *const *Up, int run, int runs, const int *act,
+                      int slots, cudaStream_t s)
+{
+    set_slots_kernel<<<1, slots, 0, s>>>(slot, Up, run, runs, act);
+    ++g_launches;
+}
 
 __global__ void set_slot_kernel(OutSlot *slot, double *final_part, double *snap_part)
 {

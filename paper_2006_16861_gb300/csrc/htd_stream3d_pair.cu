@@ -92,18 +92,30 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
+// per-rhs planes: (column, row, plane, rhs)
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int x, int y, int z,
+                                            int r, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(r), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// stored plane p of rhs r: u_j and q*kappa with the halo, d, Re F, Im F, u_{j-1}
 __device__ __forceinline__ void load_stage(const Stream3Maps &maps, int iu, int ium, float *stage,
-                                           uint64_t *bar, int xs, int xn, int y0, int p)
+                                           uint64_t *bar, int xs, int xn, int y0, int p, int r)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                  "r"(kStageTxBytes)
                  : "memory");
-    tma_load_3d(stage, &maps.m[iu], xs, y0, p, bar);
+    tma_load_4d(stage, &maps.m[iu], xs, y0, p, r, bar);
     tma_load_3d(stage + kHaloStride, &maps.m[2], xs, y0, p, bar);
     tma_load_3d(stage + 2 * kHaloStride, &maps.m[3], xn, y0 + 1, p, bar);
-    tma_load_3d(stage + 2 * kHaloStride + kNodeElems, &maps.m[4], xn, y0 + 1, p, bar);
-    tma_load_3d(stage + 2 * kHaloStride + 2 * kNodeElems, &maps.m[5], xn, y0 + 1, p, bar);
-    tma_load_3d(stage + 2 * kHaloStride + 3 * kNodeElems, &maps.m[ium], xn, y0 + 1, p, bar);
+    tma_load_4d(stage + 2 * kHaloStride + kNodeElems, &maps.m[4], xn, y0 + 1, p, r, bar);
+    tma_load_4d(stage + 2 * kHaloStride + 2 * kNodeElems, &maps.m[5], xn, y0 + 1, p, r, bar);
+    tma_load_4d(stage + 2 * kHaloStride + 3 * kNodeElems, &maps.m[ium], xn, y0 + 1, p, r, bar);
 }
 
 // pair helpers
@@ -119,7 +131,8 @@ template <int NS>
 __global__ void __launch_bounds__(kThreads + 32, NS >= 6 ? 2 : 3)
 stream3d_pair_kernel(const __grid_constant__ Stream3Maps maps, int iu, int ium,
                      float *__restrict__ um, Layout L, StepCoef<float> C, float a, float b,
-                     const OutSlot *__restrict__ slot, int flags, int zchunk, int *__restrict__ err)
+                     const OutSlot *__restrict__ slot, int flags, int zchunk, int *__restrict__ err,
+                     RhsSet R)
 {
     extern __shared__ __align__(128) float ring[];
     uint64_t *full = reinterpret_cast<uint64_t *>(ring + NS * kStageElems);
@@ -127,11 +140,18 @@ stream3d_pair_kernel(const __grid_constant__ Stream3Maps maps, int iu, int ium,
     __shared__ int abort_flag;
 
     const int tid = threadIdx.x;
+    // the rhs slot varies fastest over the CTAs, so the rhs of one column tile
+    // run side by side and share its q*kappa and d through L2
+    int rhs;
+    if (!rhs_of_slot(R, (int)(blockIdx.x % (unsigned)R.slots), rhs)) return;
     if (smem_u32(ring) & 127u) {              // TMA destinations must be 128-byte aligned
         if (tid == 0) atomicExch(err, 1);
         return;
     }
-    const int64_t x0 = (int64_t)blockIdx.x * kTX, y0 = (int64_t)blockIdx.y * kTY;
+    const int64_t x0 = (int64_t)(blockIdx.x / (unsigned)R.slots) * kTX;
+    const int64_t y0 = (int64_t)blockIdx.y * kTY;
+    um += rhs * R.stride;
+    slot += rhs;
     const int64_t zb = (int64_t)blockIdx.z * zchunk;
     const int64_t ze = min((int64_t)L.nz, zb + zchunk);
     if (zb >= ze) return;
@@ -161,7 +181,7 @@ stream3d_pair_kernel(const __grid_constant__ Stream3Maps maps, int iu, int ium,
                                                   &abort_flag))
                     break;
                 load_stage(maps, iu, ium, ring + st * kStageElems, &full[st], xs, xn, (int)y0,
-                           (int)(zb + p));
+                           (int)(zb + p), rhs);
             }
             if (abort_flag) {
                 atomicExch(err, 1);
@@ -311,14 +331,14 @@ size_t stream3d_pair_smem_bytes(int stages)
     return (size_t)stages * kStageElems * sizeof(float) + 2 * stages * sizeof(uint64_t);
 }
 
-bool make_stream3d_pair_maps(const Layout &L, float *const planes[6], Stream3Maps *maps)
+bool make_stream3d_pair_maps(const Layout &L, float *const planes[6], Stream3Maps *maps, int nrhs)
 {
     typedef CUresult (*EncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
     // node pairs need even columns: the padded layout's x lead must be even
-    if (L.d != 3 || (L.xl % 4) != 0) return false;
+    if (L.d != 3 || (L.xl % 4) != 0 || nrhs < 1) return false;
     void *fn = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
@@ -328,17 +348,20 @@ bool make_stream3d_pair_maps(const Layout &L, float *const planes[6], Stream3Map
         return false;
     }
     EncodeFn encode = reinterpret_cast<EncodeFn>(fn);
-    const cuuint64_t dims[3] = {(cuuint64_t)L.pitch, (cuuint64_t)(L.ny + 2), (cuuint64_t)(L.nz + 2)};
-    const cuuint64_t strides[2] = {(cuuint64_t)(L.pitch * sizeof(float)),
-                                   (cuuint64_t)(L.plane * sizeof(float))};
-    const cuuint32_t halo[3] = {(cuuint32_t)kHaloW, (cuuint32_t)kHaloH, 1};
-    const cuuint32_t node[3] = {(cuuint32_t)kTX, (cuuint32_t)kTY, 1};
-    const cuuint32_t estr[3] = {1, 1, 1};
+    const cuuint64_t dims[4] = {(cuuint64_t)L.pitch, (cuuint64_t)(L.ny + 2), (cuuint64_t)(L.nz + 2),
+                                (cuuint64_t)nrhs};
+    const cuuint64_t strides[3] = {(cuuint64_t)(L.pitch * sizeof(float)),
+                                   (cuuint64_t)(L.plane * sizeof(float)),
+                                   (cuuint64_t)(L.total * sizeof(float))};
+    const cuuint32_t halo[4] = {(cuuint32_t)kHaloW, (cuuint32_t)kHaloH, 1, 1};
+    const cuuint32_t node[4] = {(cuuint32_t)kTX, (cuuint32_t)kTY, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
     float *src[8] = {planes[0], planes[1], planes[2], planes[3], planes[4], planes[5], planes[0],
                      planes[1]};
     for (int i = 0; i < 8; ++i) {
         const cuuint32_t *box = (i < 3) ? halo : node;
-        if (encode(&maps->m[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)src[i], dims, strides,
+        const cuuint32_t rank = (i == 2 || i == 3) ? 3 : 4;     // q*kappa and d are shared
+        if (encode(&maps->m[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, (void *)src[i], dims, strides,
                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
             CUDA_SUCCESS)
@@ -365,17 +388,18 @@ int stream3d_pair_zchunk(const Layout &L, int stages)
 
 void launch_stream3d_pair(const Stream3Maps &maps, int from, const Layout &L, float *um,
                           const StepCoef<float> &C, float a, float b, const OutSlot *slot,
-                          int flags, int zchunk, int stages, int *err, cudaStream_t s)
+                          int flags, int zchunk, int stages, int *err, cudaStream_t s,
+                          const RhsSet &R)
 {
     const int iu = from ? 1 : 0, ium = from ? 6 : 7;
-    dim3 grd((unsigned)((L.nx + kTX - 1) / kTX), (unsigned)((L.ny + kTY - 1) / kTY),
+    dim3 grd((unsigned)(((L.nx + kTX - 1) / kTX) * R.slots), (unsigned)((L.ny + kTY - 1) / kTY),
              (unsigned)((L.nz + zchunk - 1) / zchunk));
     if (stages == 4)
         stream3d_pair_kernel<4><<<grd, kThreads + 32, stream3d_pair_smem_bytes(4), s>>>(
-            maps, iu, ium, um, L, C, a, b, slot, flags, zchunk, err);
+            maps, iu, ium, um, L, C, a, b, slot, flags, zchunk, err, R);
     else
         stream3d_pair_kernel<6><<<grd, kThreads + 32, stream3d_pair_smem_bytes(6), s>>>(
-            maps, iu, ium, um, L, C, a, b, slot, flags, zchunk, err);
+            maps, iu, ium, um, L, C, a, b, slot, flags, zchunk, err, R);
     ++g_launches;
 }
 

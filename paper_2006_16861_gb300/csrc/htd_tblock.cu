@@ -37,8 +37,6 @@ constexpr int kBoxW = 72;        // TMA box width: 64 + 2 pad columns + up to 3 
 // threads = 64 columns x RG row groups (RG = 8 or 16)
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;   // 1 s bound on the mbarrier wait
 
-__host__ __device__ inline size_t round128(size_t b) { return (b + 127) & ~(size_t)127; }
-
 template <typename T>
 __host__ __device__ constexpr size_t tb2d_array_bytes(int H)
 {
@@ -109,12 +107,23 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
+// state planes: (column, row, rhs)
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
 template <typename T, int B, int RPT, int RG>
 __global__ void __launch_bounds__(kW * RG, 1)
 tb2d_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, T *__restrict__ uC,
             T *__restrict__ uD, const T *__restrict__ dco, const T *__restrict__ fre,
             const T *__restrict__ fim, Layout L, StepCoef<T> C, TbSteps<T> S,
-            const OutSlot *__restrict__ slot, int *__restrict__ err)
+            const OutSlot *__restrict__ slot, int *__restrict__ err, RhsSet R)
 {
     constexpr int W = kW, TX = W - 2 * B, BW = kBoxW;
     constexpr int H = RG * RPT, TY = H - 2 * B;
@@ -128,11 +137,18 @@ tb2d_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, T *__restrict
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_t + 3 * ae);
 
     const int tid = threadIdx.x;
+    int rhs;
+    if (!rhs_of_slot(R, (int)blockIdx.z, rhs)) return;
     // TMA destinations must be 128-byte aligned; refuse to run otherwise
     if (smem_u32(smem_raw) & 127u) {
         if (tid == 0) atomicExch(err, 1);
         return;
     }
+    uC += rhs * R.stride;
+    uD += rhs * R.stride;
+    fre += rhs * R.stride;
+    fim += rhs * R.stride;
+    slot += rhs;
     const int64_t x0 = (int64_t)blockIdx.x * TX - B;      // global x of local column 0
     const int64_t y0 = (int64_t)blockIdx.y * TY - B;      // global y of local row 0
     // box origin: stored row y0 (local pad row 0 = global row y0 - 1), stored
@@ -145,8 +161,8 @@ tb2d_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, T *__restrict
         mbar_init(bar, 1);
         mbar_expect_tx(bar, (unsigned)(3 * (size_t)(H + 2) * BW * sizeof(T)));
         const int ys = (int)y0;
-        tma_load_2d(su0, &maps.m[in0], xs, ys, bar);
-        tma_load_2d(su1, &maps.m[in1], xs, ys, bar);
+        tma_load_3d(su0, &maps.m[in0], xs, ys, rhs, bar);
+        tma_load_3d(su1, &maps.m[in1], xs, ys, rhs, bar);
         tma_load_2d(sk, &maps.m[4], xs, ys, bar);
     }
 
@@ -327,10 +343,10 @@ std::vector<TbPlan> tb2d_candidates(const Layout &L, int want_B)
     return v;
 }
 
-// Tensor maps of the planes u0, u1, u2, u3 and q*kappa as 2-D arrays
-// (pitch x rows) with a kBoxW x (H + 2) box.
+// Tensor maps of the planes u0, u1, u2, u3 (3-D: pitch x rows x nrhs) and
+// q*kappa (2-D: pitch x rows) with a kBoxW x (H + 2) box.
 template <typename T>
-bool make_tb2d_maps(const Layout &L, const TbPlan &p, T *const planes[5], TbMaps *maps)
+bool make_tb2d_maps(const Layout &L, const TbPlan &p, T *const planes[5], TbMaps *maps, int nrhs)
 {
     typedef CUresult (*EncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
@@ -345,14 +361,17 @@ bool make_tb2d_maps(const Layout &L, const TbPlan &p, T *const planes[5], TbMaps
         return false;
     }
     EncodeFn encode = reinterpret_cast<EncodeFn>(fn);
-    const cuuint64_t dims[2] = {(cuuint64_t)L.pitch, (cuuint64_t)(L.ny + 2)};
-    const cuuint64_t strides[1] = {(cuuint64_t)(L.pitch * sizeof(T))};
-    const cuuint32_t box[2] = {(cuuint32_t)kBoxW, (cuuint32_t)(p.H + 2)};
-    const cuuint32_t estr[2] = {1, 1};
+    if (nrhs < 1) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)L.pitch, (cuuint64_t)(L.ny + 2), (cuuint64_t)nrhs};
+    const cuuint64_t strides[2] = {(cuuint64_t)(L.pitch * sizeof(T)),
+                                   (cuuint64_t)(L.total * sizeof(T))};
+    const cuuint32_t box[3] = {(cuuint32_t)kBoxW, (cuuint32_t)(p.H + 2), 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
     const CUtensorMapDataType dt =
         sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
     for (int i = 0; i < 5; ++i) {
-        if (encode(&maps->m[i], dt, 2, (void *)planes[i], dims, strides, box, estr,
+        const cuuint32_t rank = (i < 4) ? 3 : 2;
+        if (encode(&maps->m[i], dt, rank, (void *)planes[i], dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
             CUDA_SUCCESS)
@@ -364,13 +383,14 @@ bool make_tb2d_maps(const Layout &L, const TbPlan &p, T *const planes[5], TbMaps
 template <typename T>
 void launch_tb2d(const TbPlan &p, const TbMaps &maps, int in0, int in1, const Layout &L, T *uC,
                  T *uD, const T *dco, const T *fre, const T *fim, const StepCoef<T> &C,
-                 const TbSteps<T> &S, const OutSlot *slot, int *err, cudaStream_t s)
+                 const TbSteps<T> &S, const OutSlot *slot, int *err, cudaStream_t s,
+                 const RhsSet &R)
 {
-    dim3 grd((unsigned)p.grid_x, (unsigned)p.grid_y);
+    dim3 grd((unsigned)p.grid_x, (unsigned)p.grid_y, (unsigned)R.slots);
 #define HTD_TB2D_CASE(BB, RR, GG)                                                              \
     if (p.B == BB && p.RPT == RR && p.RG == GG) {                                              \
         tb2d_kernel<T, BB, RR, GG><<<grd, kW * GG, p.smem, s>>>(maps, in0, in1, uC, uD, dco,   \
-                                                               fre, fim, L, C, S, slot, err);  \
+                                                               fre, fim, L, C, S, slot, err, R); \
         ++g_launches;                                                                          \
         return;                                                                                \
     }
@@ -386,10 +406,10 @@ void launch_tb2d(const TbPlan &p, const TbMaps &maps, int in0, int in1, const La
 }
 
 template std::vector<TbPlan> tb2d_candidates<float>(const Layout &, int);
-template bool make_tb2d_maps<float>(const Layout &, const TbPlan &, float *const[5], TbMaps *);
+template bool make_tb2d_maps<float>(const Layout &, const TbPlan &, float *const[5], TbMaps *, int);
 template void launch_tb2d<float>(const TbPlan &, const TbMaps &, int, int, const Layout &, float *,
                                  float *, const float *, const float *, const float *,
                                  const StepCoef<float> &, const TbSteps<float> &, const OutSlot *,
-                                 int *, cudaStream_t);
+                                 int *, cudaStream_t, const RhsSet &);
 
 }  // namespace htd

@@ -30,7 +30,8 @@ BC_DIRICHLET = 0
 EXPORTS = ("htd_default_options", "htd_create", "htd_destroy", "htd_plan", "htd_get_params",
            "htd_apply_precond", "htd_apply_H", "htd_residual_norm", "htd_residual_norm_noalloc",
            "htd_gmres_solve", "htd_grad",
-           "htd_gmres_solve_host", "htd_status_string")
+           "htd_gmres_solve_host", "htd_batch_create", "htd_batch_destroy",
+           "htd_batch_apply_precond", "htd_batch_gmres_solve", "htd_status_string")
 
 
 class HtdError(RuntimeError):
@@ -46,7 +47,7 @@ class Grid(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("mode", ctypes.c_int), ("krylov", ctypes.c_int),
                 ("T", ctypes.c_int), ("rho", ctypes.c_double), ("nP", ctypes.c_int),
-                ("stencil", ctypes.c_int), ("restart", ctypes.c_int)]
+                ("stencil", ctypes.c_int), ("restart", ctypes.c_int), ("max_rhs", ctypes.c_int)]
 
 
 class Params(ctypes.Structure):
@@ -113,6 +114,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.htd_gmres_solve_host.argtypes = [vp, vp, vp, d, i, vp, ctypes.POINTER(SolveInfo)]
     lib.htd_grad.argtypes = [vp, i, vp, i, vp, vp, d, i, vp, vp, ctypes.POINTER(d), vp,
                              ctypes.POINTER(SolveInfo)]
+    lib.htd_batch_create.argtypes = [i, vp, vp, ctypes.POINTER(vp)]
+    lib.htd_batch_destroy.argtypes = [vp]
+    lib.htd_batch_apply_precond.argtypes = [vp, vp, vp, vp]
+    lib.htd_batch_gmres_solve.argtypes = [vp, vp, vp, d, i, vp, vp]
     lib.htd_status_string.argtypes = [i]
     lib.htd_status_string.restype = ctypes.c_char_p
     for f in EXPORTS:
@@ -290,6 +295,44 @@ def htd_grad(handle: int, F, rec_idx: np.ndarray, d, tol: float, max_iters: int,
     return J.value, info.as_dict()
 
 
+def htd_batch_create(handles, nrhs) -> int:
+    """A batch of instances (handles) carrying nrhs[i] right-hand sides each."""
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*handles)
+    rs = (ctypes.c_int * n)(*[int(r) for r in nrhs])
+    out = ctypes.c_void_p()
+    _check(load().htd_batch_create(n, hs, rs, ctypes.byref(out)), "htd_batch_create")
+    return out.value
+
+
+def htd_batch_destroy(batch: int) -> None:
+    _check(load().htd_batch_destroy(batch), "htd_batch_destroy")
+
+
+def _ptr_array(ts) -> ctypes.Array:
+    return (ctypes.c_void_p * len(ts))(*[_dev_ptr(t) for t in ts])
+
+
+def htd_batch_apply_precond(batch: int, Fs, Us, stream=None) -> None:
+    """Fs[i], Us[i]: contiguous complex128 CUDA tensors of shape (nrhs[i], *n_i)."""
+    _check(load().htd_batch_apply_precond(batch, _ptr_array(Fs), _ptr_array(Us),
+                                          _stream_ptr(stream)), "htd_batch_apply_precond")
+
+
+def htd_batch_gmres_solve(batch: int, Fs, Us, tol: float, max_iters: int, nsys: int,
+                          stream=None, allow_not_converged: bool = False) -> list:
+    """Lockstep FGMRES of every system; one info dict per system (instance-major)."""
+    infos = (SolveInfo * nsys)()
+    allow = (HTD_OK, 6) if allow_not_converged else (HTD_OK,)
+    st = load().htd_batch_gmres_solve(batch, _ptr_array(Fs), _ptr_array(Us), float(tol),
+                                      int(max_iters), _stream_ptr(stream), infos)
+    _check(st, "htd_batch_gmres_solve", allow)
+    out = [infos[k].as_dict() for k in range(nsys)]
+    for d in out:
+        d["status"] = STATUS[st]
+    return out
+
+
 def htd_status_string(status: int) -> str:
     return load().htd_status_string(int(status)).decode()
 
@@ -298,9 +341,11 @@ def htd_status_string(status: int) -> str:
 
 def make_options(prob=None, precision: str = "fp64", mode: str = "table1",
                  krylov: str = "fgmres", stencil: str = "q1mix", restart: int = 20,
-                 nP: int = 0, T: int | None = None, rho: float | None = None) -> Options:
+                 nP: int = 0, T: int | None = None, rho: float | None = None,
+                 max_rhs: int = 1) -> Options:
     """htd_options from names; T and rho default to the problem's."""
     o = htd_default_options()
+    o.max_rhs = int(max_rhs)
     o.precision = {"fp64": FP64, "mixed": MIXED}[precision]
     o.mode = {"table1": MODE_TABLE1, "exact": MODE_EXACT}[mode]
     o.krylov = {"fgmres": FGMRES, "left": LEFT_GMRES}[krylov]
@@ -325,8 +370,10 @@ class Solver:
 
     def __init__(self, prob, precision: str = "fp64", mode: str = "table1",
                  krylov: str = "fgmres", stencil: str = "q1mix", restart: int = 20,
-                 nP: int = 0, T: int | None = None, rho: float | None = None):
-        o = make_options(prob, precision, mode, krylov, stencil, restart, nP, T, rho)
+                 nP: int = 0, T: int | None = None, rho: float | None = None,
+                 max_rhs: int = 1):
+        o = make_options(prob, precision, mode, krylov, stencil, restart, nP, T, rho, max_rhs)
+        self.max_rhs = int(max_rhs)
         self.prob = prob
         self.n = tuple(prob.n)
         self.handle = htd_create(prob.ndim, prob.n, prob.h, prob.c_cell, prob.R_node, prob.omega,
@@ -372,3 +419,46 @@ class Solver:
         U = self.zeros() if U is None else U
         info = htd_gmres_solve(self.handle, F, U, tol, max_iters, stream, allow_not_converged)
         return U, info
+
+
+class Batch:
+    """Several Solvers, solver i carrying nrhs[i] right-hand sides, run together:
+    one graph launch applies every preconditioner, FGMRES advances all systems
+    in lockstep (htd_batch_*).  The solvers must outlive the batch."""
+
+    def __init__(self, solvers, nrhs):
+        self.solvers = list(solvers)
+        self.nrhs = [int(r) for r in nrhs]
+        self.handle = htd_batch_create([s.handle for s in self.solvers], self.nrhs)
+
+    @property
+    def nsys(self) -> int:
+        return sum(self.nrhs)
+
+    def close(self):
+        if self.handle:
+            htd_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+    def zeros(self):
+        import torch
+        return [torch.zeros((r, *s.n), dtype=torch.complex128, device="cuda")
+                for s, r in zip(self.solvers, self.nrhs)]
+
+    def precond(self, Fs, Us=None, stream=None):
+        Us = self.zeros() if Us is None else Us
+        htd_batch_apply_precond(self.handle, Fs, Us, stream)
+        return Us
+
+    def solve(self, Fs, Us=None, tol=1e-6, max_iters=400, stream=None,
+              allow_not_converged=False):
+        Us = self.zeros() if Us is None else Us
+        infos = htd_batch_gmres_solve(self.handle, Fs, Us, tol, max_iters, self.nsys, stream,
+                                      allow_not_converged)
+        return Us, infos

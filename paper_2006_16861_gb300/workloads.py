@@ -277,3 +277,35 @@ def config_adjoint(n: int = 512, nsrc: int = 8, layer: int = 20, seed: int = 200
     c_true = c * gaussian_blob((n + 1, n + 1), h, (0.5, 0.5), 0.1, 0.05)
     rec = top_row_receivers((n, n), layer, layer)
     return InversionSetup(prob, F, rec, c_true)
+
+
+@dataclasses.dataclass
+class BatchSetup:
+    """Independent systems run as one batch: instance i is the problem probs[i]
+    with the right-hand sides F[i] (shape (nrhs_i, *n_i))."""
+    probs: list
+    F: list
+
+
+def config_batched(n3: int = 128, nsrc: int = 32, ninst: int = 64, side_lo: int = 200,
+                   side_hi: int = 1000, seed: int = 2006168614, ppw: float = 8.0,
+                   rho: float = 0.25) -> BatchSetup:
+    """The 3-D layered model at n3^3 (absorbing layer 24 cells per 256, so the same
+    physical width) with `nsrc` seeded point sources as right-hand sides, plus
+    `ninst` 2-D instances whose sides are drawn uniformly from [side_lo, side_hi]:
+    smooth random c = clip(3 + 0.75 g, 1.5, 4.5) (correlation length 0.05, own
+    seed per instance), omega for `ppw` points per wavelength at its min c, an
+    absorbing layer of 4 % of the side (R0 = 2 omega) and a centre point source."""
+    layer3 = max(2, int(round(24 * n3 / 256)))
+    p3 = config_3d_layered(n3, layer=layer3, seed=seed - 2, ppw=ppw, rho=rho)
+    F3 = seeded_sources(seed, 3, p3.n, p3.h, nsrc, layer3 + 2)
+    probs, Fs = [p3], [F3]
+    u = uniform01(seed + 1, ninst)
+    for i in range(ninst):
+        side = side_lo + int(u[i] * (side_hi - side_lo + 1))
+        side = min(side, side_hi)
+        layer = max(4, int(round(0.04 * (side - 1))))
+        p = config_2d_heterogeneous(side, layer=layer, seed=seed + 100 + i, ppw=ppw, rho=rho)
+        probs.append(p)
+        Fs.append(p.F[None].astype(np.complex128))
+    return BatchSetup(probs, Fs)

@@ -1,0 +1,135 @@
+"""GPU tests of the batch calls (htd_batch_*): several right-hand sides of one
+handle and several handles of different sizes, kernels and step counts, run
+as one batch.
+
+A batch only schedules; every system keeps the arithmetic of the single-system
+calls.  So the batched preconditioner must reproduce each handle's own
+htd_apply_precond bit for bit (same kernels, same configuration, only the
+right-hand-side slot differs), the batched FGMRES must take the same
+iterations and give the same solution as htd_gmres_solve per system, and
+both are tied to the FP64 oracle as in test_gpu_parity.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2006_16861_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2006_16861_gb300 import htd  # noqa: E402
+from test_gpu_parity import dev, het_problem, host, rel_l2  # noqa: E402
+
+
+def rhs_stack(p, nrhs, seed):
+    """nrhs right-hand sides: the problem's point source, then seeded random fields."""
+    F = [p.F] + [W.random_rhs(seed + k, p.n) for k in range(nrhs - 1)]
+    return np.stack(F).astype(np.complex128)
+
+
+CASES = [  # (ndim, n, precision, mode)
+    (2, (45, 37), "fp64", "table1"),
+    (2, (70, 66), "mixed", "table1"),
+    (2, (41, 29), "mixed", "exact"),
+    (3, (13, 17, 19), "fp64", "table1"),
+    (3, (21, 70, 33), "mixed", "table1"),
+    (3, (11, 9, 15), "mixed", "exact"),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"{c[0]}d-{'x'.join(map(str, c[1]))}-{c[2]}-{c[3]}"
+                                             for c in CASES])
+def test_rhs_batch_precond_equals_single(case):
+    """Three right-hand sides of one handle (max_rhs 4, so one slot idles) in one
+    batched application: each equals the handle's single application exactly,
+    and the FP64 ones equal the oracle to 1e-10."""
+    ndim, n, precision, mode = case
+    p = het_problem(ndim, n, T=2)
+    s = htd.Solver(p, precision=precision, mode=mode, max_rhs=4)
+    F = rhs_stack(p, 3, 40)
+    b = htd.Batch([s], [3])
+    U = b.precond([dev(F)])[0]
+    Ub = host(U)
+    o = oracle.Oracle(p)
+    for r in range(3):
+        single = host(s.precond(dev(F[r])))
+        assert np.array_equal(Ub[r], single), rel_l2(Ub[r].reshape(-1), single.reshape(-1))
+        ref = o.precond(F[r], mode).reshape(-1)
+        tol = 1e-10 if precision == "fp64" else 2e-5
+        assert rel_l2(Ub[r].reshape(-1), ref) <= tol
+    b.close()
+
+
+def test_multi_instance_batch_precond():
+    """Handles of different dimension, size, precision and step count (a 3-D
+    handle with two right-hand sides, 2-D handles with one) in one graph launch:
+    each output equals that handle's own application."""
+    setup = W.config_batched(n3=20, nsrc=2, ninst=3, side_lo=30, side_hi=90)
+    precisions = ["mixed", "mixed", "fp64", "mixed"]
+    solvers = [htd.Solver(p, precision=pr, max_rhs=F.shape[0])
+               for p, F, pr in zip(setup.probs, setup.F, precisions)]
+    assert len({s.params["steps"] for s in solvers}) > 1      # different step counts
+    b = htd.Batch(solvers, [F.shape[0] for F in setup.F])
+    Us = b.precond([dev(F) for F in setup.F])
+    for s, F, U in zip(solvers, setup.F, Us):
+        Ub = host(U)
+        for r in range(F.shape[0]):
+            single = host(s.precond(dev(F[r])))
+            assert np.array_equal(Ub[r], single)
+    b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_gmres_matches_single_solves(precision):
+    """Lockstep FGMRES over a 3-D handle with three right-hand sides (which
+    converge after different numbers of steps, so slots go idle) and two 2-D
+    handles: per system the same iteration count as htd_gmres_solve, the same
+    solution bit for bit (identical operations; the host-side Givens and
+    triangular solve are shared code built without FMA contraction), and a true
+    residual <= 1e-6 by the oracle's FP64 operator."""
+    setup = W.config_batched(n3=18, nsrc=2, ninst=2, side_lo=40, side_hi=80)
+    Fs = [np.concatenate([F, W.random_rhs(7, F.shape[1:])[None]]) if k == 0 else F
+          for k, F in enumerate(setup.F)]
+    solvers = [htd.Solver(p, precision=precision, max_rhs=F.shape[0], restart=8)
+               for p, F in zip(setup.probs, Fs)]
+    b = htd.Batch(solvers, [F.shape[0] for F in Fs])
+    Us, infos = b.solve([dev(F) for F in Fs], tol=1e-6, max_iters=200)
+    k = 0
+    its = []
+    for s, p, F, U in zip(solvers, setup.probs, Fs, Us):
+        Ub = host(U)
+        o = oracle.Oracle(p)
+        for r in range(F.shape[0]):
+            info = infos[k]
+            k += 1
+            Us1, info1 = s.solve(dev(F[r]), tol=1e-6, max_iters=200)
+            assert info["converged"] and info1["converged"]
+            assert info["iterations"] == info1["iterations"]
+            its.append(info["iterations"])
+            assert np.array_equal(Ub[r], host(Us1))
+            res = np.linalg.norm(F[r] - o.apply_H(Ub[r])) / np.linalg.norm(F[r])
+            assert res <= 1e-6
+    assert len(set(its)) > 1                  # systems left the batch at different steps
+    b.close()
+
+
+def test_batch_rejects_bad_arguments():
+    p = het_problem(2, (20, 22), T=2)
+    s1 = htd.Solver(p, precision="mixed", max_rhs=2)
+    s2 = htd.Solver(p, precision="mixed", krylov="left")
+    for handles, nrhs in (([s1.handle, s1.handle], [1, 1]),   # repeated handle
+                          ([s1.handle], [3]),                  # more rhs than max_rhs
+                          ([s1.handle], [0]),
+                          ([s2.handle], [1])):                 # left GMRES
+        with pytest.raises(htd.HtdError) as e:
+            htd.htd_batch_create(handles, nrhs)
+        assert e.value.status == 1
+    b = htd.Batch([s1], [2])
+    F = dev(rhs_stack(p, 2, 3))
+    with pytest.raises(htd.HtdError) as e:
+        htd.htd_batch_gmres_solve(b.handle, [F], [F], 1e-6, 10, 2)     # F aliases U
+    assert e.value.status == 1
+    b.close()

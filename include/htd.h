@@ -285,7 +285,7 @@ htd_status htd_grad(htd_handle h, int nsrc, const void *F_dev, int nrec,
  *
  * htd_batch_create: ninst distinct handles on the current device, instance i
  * carrying nrhs[i] right-hand sides (1 <= nrhs[i] <= its max_rhs option).  The
- * batch owns the Krylov workspace of every system (2 m + 3 complex vectors of
+ * batch owns the Krylov workspace of every system (2 m + 2 complex vectors of
  * the instance's N each); the handles stay owned by the caller and must
  * outlive the batch.  Errors: HTD_ERR_ARG (null, repeated handle, bad nrhs,
  * a LEFT_GMRES handle), HTD_ERR_OOM, HTD_ERR_CUDA.

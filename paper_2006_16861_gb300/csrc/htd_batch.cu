@@ -52,7 +52,7 @@ struct Sys {
     int m = 0;
     const double2 *F = nullptr;
     double2 *U = nullptr;
-    double2 *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr;   // Krylov workspace
+    double2 *V = nullptr, *Z = nullptr, *r = nullptr;   // Krylov workspace
     // FGMRES state
     bool done = false, restart = true;
     int j = 0, its = 0;
@@ -320,19 +320,19 @@ htd_status batch_gmres(htd_batch b, const void *const *F_dev, void *const *U_dev
         }
         if ((st = precond_round(b, sel, in, out, s)) != HTD_OK) return st;
 
-        // ---- w = H Z_j, CGS2 against V_0..V_j, ||w|| --------------------------
+        // ---- w = H Z_j built in basis slot j + 1, CGS2 against V_0..V_j -------
         for (size_t k = 0; k < ns; ++k) {
             if (!sel[k]) continue;
             Sys &y = b->sys[k];
             htd_ctx *c = b->ctx[y.inst];
             const int kc = y.j + 1;
-            double2 *hb = b->hdev + k * kHBlock;
-            htd::ctx_apply_H(c, y.Z + (int64_t)y.j * y.N, nullptr, y.w, s);
-            htd::ctx_dots(c, y.V, y.N, kc, y.w, hb, s);
-            htd::launch_sub_combination(y.V, y.N, kc, hb, y.w, y.N, s);
-            htd::ctx_dots(c, y.V, y.N, kc, y.w, hb + 72, s);
-            htd::launch_sub_combination(y.V, y.N, kc, hb + 72, y.w, y.N, s);
-            htd::ctx_dots(c, y.w, 0, 1, y.w, hb + 144, s);
+            double2 *vn = y.V + (int64_t)kc * y.N;
+            htd::ctx_apply_H(c, y.Z + (int64_t)y.j * y.N, nullptr, vn, s);
+            for (int pass = 0; pass < 2; ++pass) {
+                double2 *hb = b->hdev + k * kHBlock + 72 * pass;
+                htd::ctx_dots(c, y.V, y.N, kc + 1, vn, hb, s);     // V_i^H w and ||w||^2
+                htd::launch_sub_combination(y.V, y.N, kc, hb, vn, y.N, s);
+            }
         }
         if ((st = fetch_blocks(b, s)) != HTD_OK) return st;
         const double ms = round_ms(b);
@@ -348,13 +348,12 @@ htd_status batch_gmres(htd_batch b, const void *const *F_dev, void *const *U_dev
             y.info.steps += b->ci[y.inst].nsteps * b->ci[y.inst].runs;
             y.info.ms_precond += ms;
             zc *col = &y.Hm[(size_t)j * (m + 1)];
-            for (int i = 0; i <= j; ++i) col[i] = zc(hh[i].x + hh[72 + i].x, hh[i].y + hh[72 + i].y);
-            const double hn2 = hh[144].x;
+            const double hn2 = htd::cgs2_column(hh, hh + 72, j + 1, col);
             if (!std::isfinite(hn2)) return HTD_ERR_NONFINITE;
             const double hn = std::sqrt(hn2 > 0 ? hn2 : 0.0);
             col[j + 1] = hn;
-            if (hn > 0.0 && j + 1 < m + 1)
-                htd::launch_scale(y.w, 1.0 / hn, y.V + (int64_t)(j + 1) * y.N, y.N, s);
+            double2 *vn = y.V + (int64_t)(j + 1) * y.N;
+            if (hn > 0.0) htd::launch_scale(vn, 1.0 / hn, vn, y.N, s);
             htd::givens_column(col, y.cs.data(), y.sn.data(), y.g.data(), j);
             ++y.its;
             ++y.j;
@@ -430,7 +429,7 @@ htd_status create_batch(int ninst, const htd_handle *handles, const int *nrhs, h
             y.N = ci.N;
             y.m = ci.m;
             b->sys.push_back(y);
-            ws += (size_t)(2 * ci.m + 3) * (size_t)ci.N;
+            ws += (size_t)(2 * ci.m + 2) * (size_t)ci.N;
         }
         tab += 2 * ci.rcap;
         b->tab_off.push_back(tab);
@@ -442,8 +441,6 @@ htd_status create_batch(int ninst, const htd_handle *handles, const int *nrhs, h
         off += (size_t)(y.m + 1) * y.N;
         y.Z = b->ws + off;
         off += (size_t)y.m * y.N;
-        y.w = b->ws + off;
-        off += (size_t)y.N;
         y.r = b->ws + off;
         off += (size_t)y.N;
     }

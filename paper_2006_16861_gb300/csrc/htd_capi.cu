@@ -141,6 +141,7 @@ struct htd_ctx {
     StepCoef<double> C{};
     // FP64 operator data
     double *kap64 = nullptr, *imH = nullptr;
+    double *coefP = nullptr;    // assembled operator, h_planes(d) planes of N
     // Krylov workspace
     int m = 20;
     double2 *V = nullptr, *Z = nullptr, *w = nullptr, *t = nullptr, *r = nullptr;
@@ -209,7 +210,7 @@ void free_ctx(htd_ctx *c)
     if (c->graph) cudaGraphDestroy(c->graph);
     for (cudaEvent_t e : c->pev)
         if (e) cudaEventDestroy(e);
-    void *dev[] = {c->kap, c->dco, c->fre, c->fim, c->u0, c->u1, c->kap64, c->imH, c->V, c->Z,
+    void *dev[] = {c->kap, c->dco, c->fre, c->fim, c->u0, c->u1, c->kap64, c->imH, c->coefP, c->V, c->Z,
                    c->w, c->t, c->r, c->partial, c->hdev, c->slot, c->Fh, c->Uh, c->u2, c->u3,
                    c->err_dev, c->gU, c->gMu, c->gR, c->gres, c->grec, c->act_dev};
     for (void *p : dev)
@@ -386,9 +387,7 @@ htd_status precond(htd_ctx *c, const double2 *F, double2 *U, cudaStream_t s)
 
 void apply_H(htd_ctx *c, const double2 *X, const double2 *F, double2 *Y, cudaStream_t s)
 {
-    double S2[4];
-    for (int k = 0; k < 4; ++k) S2[k] = std::ldexp(c->S[k], c->d - k);
-    htd::launch_apply_H(c->L64, c->kap64, c->imH, S2, c->M, 1.0 / (c->h * c->h), X, F, Y, s);
+    htd::launch_apply_H(c->L64, c->coefP, c->imH, 1.0 / (c->h * c->h), X, F, Y, s);
 }
 
 // dots of w with V_0..V_{k-1} into hdev + off (device); does not synchronise
@@ -468,33 +467,32 @@ htd_status gmres(htd_ctx *c, const double2 *F, double2 *U, double tol, int maxit
         int j = 0;
         while (j < m && its < maxit) {
             double2 *vj = c->V + (int64_t)j * N;
+            double2 *vn = c->V + (int64_t)(j + 1) * N;     // the new vector, built in place
             if (!left) {
                 double2 *zj = c->Z + (int64_t)j * N;
                 if ((st = precond(c, vj, zj, s)) != HTD_OK) goto out;
-                apply_H(c, zj, nullptr, c->w, s);
+                apply_H(c, zj, nullptr, vn, s);
             } else {
                 apply_H(c, vj, nullptr, c->t, s);
-                if ((st = precond(c, c->t, c->w, s)) != HTD_OK) goto out;
+                if ((st = precond(c, c->t, vn, s)) != HTD_OK) goto out;
             }
-            // classical Gram-Schmidt with one reorthogonalisation, FP64
+            // classical Gram-Schmidt with one reorthogonalisation, FP64: per pass
+            // V_i^H w for i <= j and ||w||^2 in one kernel, then w -= V h
             const int k = j + 1;
-            dots_to(c, c->V, k, c->w, 0, s);
-            htd::launch_sub_combination(c->V, N, k, c->hdev, c->w, N, s);
-            dots_to(c, c->V, k, c->w, 72, s);
-            htd::launch_sub_combination(c->V, N, k, c->hdev + 72, c->w, N, s);
-            dots_to(c, c->w, 1, c->w, 144, s);
-            HTD_CUDA(cudaMemcpyAsync(c->hhost, c->hdev, sizeof(double2) * 145,
+            for (int pass = 0; pass < 2; ++pass) {
+                dots_to(c, c->V, k + 1, vn, 72 * pass, s);
+                htd::launch_sub_combination(c->V, N, k, c->hdev + 72 * pass, vn, N, s);
+            }
+            HTD_CUDA(cudaMemcpyAsync(c->hhost, c->hdev, sizeof(double2) * (72 + k + 1),
                                      cudaMemcpyDeviceToHost, s));
             HTD_CUDA(cudaStreamSynchronize(s));
             HTD_CUDA(cudaGetLastError());
             zc *col = &Hm[(size_t)j * (m + 1)];
-            for (int i = 0; i < k; ++i)
-                col[i] = zc(c->hhost[i].x + c->hhost[72 + i].x, c->hhost[i].y + c->hhost[72 + i].y);
-            const double hn2 = c->hhost[144].x;
+            const double hn2 = htd::cgs2_column(c->hhost, c->hhost + 72, k, col);
             if (!std::isfinite(hn2)) { st = HTD_ERR_NONFINITE; goto out; }
             const double hn = std::sqrt(hn2 > 0 ? hn2 : 0.0);
             col[j + 1] = hn;
-            if (hn > 0.0) htd::launch_scale(c->w, 1.0 / hn, c->V + (int64_t)(j + 1) * N, N, s);
+            if (hn > 0.0) htd::launch_scale(vn, 1.0 / hn, vn, N, s);
             // previous rotations, then a new one zeroing col[j+1]
             htd::givens_column(col, cs.data(), sn.data(), g.data(), j);
             ++its;
@@ -896,6 +894,13 @@ htd_status create_impl(const htd_grid *grid, const double *c_cell, const double 
     htd_status st = mixed ? upload_recurrence<float>(c, qk, dc) : upload_recurrence<double>(c, qk, dc);
     if (st != HTD_OK) return st;
     HTD_CUDA(cudaMemcpy(c->kap64, k64.data(), sizeof(double) * c->L64.total, cudaMemcpyHostToDevice));
+    {
+        double S2[4];
+        for (int k = 0; k < 4; ++k) S2[k] = std::ldexp(c->S[k], d - k);
+        HTD_CUDA(cudaMalloc((void **)&c->coefP, sizeof(double) * htd::h_planes(d) * (size_t)N));
+        htd::launch_assemble_H(c->L64, c->kap64, S2, c->M, c->coefP, 0);
+        HTD_CUDA(cudaGetLastError());
+    }
     HTD_CUDA(cudaMemcpy(c->imH, imh.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
 
     // temporal blocking for the 2-D FP32 recurrence, picked by timing against the
@@ -972,6 +977,7 @@ void operator_view(const htd_ctx *c, OperatorView *out)
 {
     out->L64 = c->L64;
     out->kap64 = c->kap64;
+    out->coefP = c->coefP;
     out->imH = c->imH;
     for (int k = 0; k < 4; ++k) {
         out->S2[k] = std::ldexp(c->S[k], c->d - k);

@@ -212,9 +212,14 @@ void launch_tb2d(const TbPlan &p, const TbMaps &maps, int in0, int in1, const La
                  const TbSteps<T> &S, const OutSlot *slot, int *err, cudaStream_t s,
                  const RhsSet &R = RhsSet{});
 
+// Assembled FP64 operator: coefficient planes (N doubles each) of the centre
+// and of the positive offsets (the other half follows from symmetry):
+// 14 planes in 3-D, 5 in 2-D, not yet scaled by 1/h^2.
+__host__ __device__ constexpr int h_planes(int d) { return d == 3 ? 14 : 5; }
+void launch_assemble_H(const Layout &L, const double *kap64, const double S2[4], const double M[4],
+                       double *coefP, cudaStream_t s);
 // Y = H X (F == null) or Y = F - H X, complex128 compact vectors.
-void launch_apply_H(const Layout &L, const double *kap64, const double *imH,
-                    const double S2[4], const double M[4], double ih2,
+void launch_apply_H(const Layout &L, const double *coefP, const double *imH, double ih2,
                     const double2 *X, const double2 *F, double2 *Y, cudaStream_t s);
 
 // partial[k * nb + b] = sum over block b of conj(V_k) w, k < kcount
@@ -229,7 +234,7 @@ void launch_sub_combination(const double2 *V, int64_t ldv, int kcount, const dou
 // U += sum_k y[k] Z_k  (y on the device)
 void launch_add_combination(const double2 *Z, int64_t ldz, int kcount, const double2 *y,
                             double2 *U, int64_t N, cudaStream_t s);
-// v = w * scale
+// v = w * scale (w == v allowed: scaled in place)
 void launch_scale(const double2 *w, double scale, double2 *v, int64_t N, cudaStream_t s);
 
 // ---- TMA-streamed 3-D step, FP32 (htd_stream3d.cu) -----------------------------
@@ -272,6 +277,7 @@ void launch_gradients(const Layout &L, const double M[4], double omega_phys, con
 struct OperatorView {
     Layout L64;             // layout of kap64 (compact N = L64.N)
     const double *kap64;    // (h k)^2 per cell
+    const double *coefP;    // assembled operator (launch_assemble_H)
     const double *imH;      // omega_phys R per node
     double S2[4], M[4], ih2;
     int device;

@@ -350,59 +350,108 @@ void launch_set_slot(OutSlot *slot, double *final_part, double *snap_part, cudaS
 struct HCoef {
     double S2[4];   // 2^{d-s} S_s
     double M[4];
-    double ih2;
 };
 
-__global__ void __launch_bounds__(256)
-apply_H_kernel(Layout L, const double *__restrict__ kap64, const double *__restrict__ imH,
-               HCoef C, const double2 *__restrict__ X, const double2 *__restrict__ F,
-               double2 *__restrict__ Y)
+// Linear index of the offset (oz, oy, ox) in {-1,0,1}^3: (oz+1) 9 + (oy+1) 3 + (ox+1);
+// the centre is 13.  H is symmetric, so only the centre and the offsets with a
+// larger index ("positive": first non-zero of (oz, oy, ox) is +1) are stored:
+// plane lin - 13.  The coefficient of a negative offset o at node beta is the
+// stored coefficient of -o at the node beta + o.
+__host__ __device__ constexpr int hlin(int oz, int oy, int ox)
 {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= L.N) return;
-    const int64_t ix = c % L.nx;
-    const int64_t r = c / L.nx;
-    const int64_t iy = r % L.ny;
-    const int64_t iz = r / L.ny;
-    const int64_t i = L.node(ix, iy, iz);   // position in the padded cell array
+    return (oz + 1) * 9 + (oy + 1) * 3 + (ox + 1);
+}
+
+// plane p (0 = centre, 1..13 positive offsets; 2-D: oz = 0, planes 0..4) of
+// node (ix, iy, iz): 2^{d-s} S_s - M_s * (sum of kappa over the cells that
+// contain the node and its neighbour), not yet scaled by 1/h^2; 0 where the
+// neighbour is outside the grid
+__global__ void __launch_bounds__(256)
+assemble_H_kernel(Layout L, const double *__restrict__ kap64, HCoef C, double *__restrict__ coefP,
+                  int nplanes)
+{
+    const int64_t ix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t iy = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
+    const int64_t iz = blockIdx.z;
+    if (ix >= L.nx || iy >= L.ny) return;
+    const int64_t c = (iz * L.ny + iy) * L.nx + ix;
+    const int64_t i = L.node(ix, iy, iz);    // position in the padded cell array
     const int64_t P = L.pitch, Q = L.plane;
-    const int zlo = (L.d == 3) ? -1 : 0, zhi = (L.d == 3) ? 1 : 0;
-    double re = 0.0, im = 0.0;
-    for (int oz = zlo; oz <= zhi; ++oz) {
-        const int64_t jz = iz + oz;
-        if (jz < 0 || jz >= L.nz) continue;
-        for (int oy = -1; oy <= 1; ++oy) {
-            const int64_t jy = iy + oy;
-            if (jy < 0 || jy >= L.ny) continue;
-            for (int ox = -1; ox <= 1; ++ox) {
-                const int64_t jx = ix + ox;
-                if (jx < 0 || jx >= L.nx) continue;
-                const int s = (oz != 0) + (oy != 0) + (ox != 0);
-                // cells shared by the node and its neighbour: lower (offset -1),
-                // upper (+1) or both (0) per axis
-                double ks = 0.0;
-                for (int az = (L.d == 3 ? 0 : 1); az < 2; ++az) {
-                    if (L.d == 3 && ((oz < 0 && az == 1) || (oz > 0 && az == 0))) continue;
-                    for (int ay = 0; ay < 2; ++ay) {
-                        if ((oy < 0 && ay == 1) || (oy > 0 && ay == 0)) continue;
-                        for (int ax = 0; ax < 2; ++ax) {
-                            if ((ox < 0 && ax == 1) || (ox > 0 && ax == 0)) continue;
-                            ks += kap64[i - (L.d == 3 ? (1 - az) * Q : 0) - (1 - ay) * P - (1 - ax)];
-                        }
+    for (int p = 0; p < nplanes; ++p) {
+        const int lin = p + 13;
+        const int oz = lin / 9 - 1, oy = (lin / 3) % 3 - 1, ox = lin % 3 - 1;
+        const int64_t jz = iz + oz, jy = iy + oy, jx = ix + ox;
+        double w = 0.0;
+        if (jz >= 0 && jz < L.nz && jy >= 0 && jy < L.ny && jx >= 0 && jx < L.nx) {
+            const int s = (oz != 0) + (oy != 0) + (ox != 0);
+            // cells shared by the node and its neighbour: lower (offset -1), upper
+            // (+1) or both (0) per axis
+            double ks = 0.0;
+            for (int az = (L.d == 3 ? 0 : 1); az < 2; ++az) {
+                if (L.d == 3 && ((oz < 0 && az == 1) || (oz > 0 && az == 0))) continue;
+                for (int ay = 0; ay < 2; ++ay) {
+                    if ((oy < 0 && ay == 1) || (oy > 0 && ay == 0)) continue;
+                    for (int ax = 0; ax < 2; ++ax) {
+                        if ((ox < 0 && ax == 1) || (ox > 0 && ax == 0)) continue;
+                        ks += kap64[i - (L.d == 3 ? (1 - az) * Q : 0) - (1 - ay) * P - (1 - ax)];
                     }
                 }
-                const double w = C.S2[s] - C.M[s] * ks;
-                const double2 x = X[(jz * L.ny + jy) * L.nx + jx];
-                re += w * x.x;
-                im += w * x.y;
             }
+            w = C.S2[s] - C.M[s] * ks;
         }
+        coefP[p * L.N + c] = w;
     }
+}
+
+void launch_assemble_H(const Layout &L, const double *kap64, const double S2[4], const double M[4],
+                       double *coefP, cudaStream_t s)
+{
+    HCoef C;
+    for (int k = 0; k < 4; ++k) { C.S2[k] = S2[k]; C.M[k] = M[k]; }
+    dim3 blk(32, 8);
+    dim3 grd((unsigned)((L.nx + 31) / 32), (unsigned)((L.ny + 7) / 8), (unsigned)L.nz);
+    assemble_H_kernel<<<grd, blk, 0, s>>>(L, kap64, C, coefP, h_planes(L.d));
+    ++g_launches;
+}
+
+// Y = H X (or F - H X) from the assembled coefficients: per node 3^D
+// coefficient x neighbour products for the real and the imaginary part, one
+// FP64 FMA each; neighbours outside the grid are the zero Dirichlet ghosts
+template <int D>
+__global__ void __launch_bounds__(256)
+apply_H_asm_kernel(int64_t nx, int64_t ny, int64_t nz, const double *__restrict__ coefP,
+                   const double *__restrict__ imH, double ih2, const double2 *__restrict__ X,
+                   const double2 *__restrict__ F, double2 *__restrict__ Y)
+{
+    const int64_t ix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t iy = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
+    const int64_t iz = blockIdx.z;
+    if (ix >= nx || iy >= ny) return;
+    const int64_t N = nx * ny * nz;
+    const int64_t c = (iz * ny + iy) * nx + ix;
+    double re = 0.0, im = 0.0;
+#pragma unroll
+    for (int oz = (D == 3 ? -1 : 0); oz <= (D == 3 ? 1 : 0); ++oz)
+#pragma unroll
+        for (int oy = -1; oy <= 1; ++oy)
+#pragma unroll
+            for (int ox = -1; ox <= 1; ++ox) {
+                const bool in = iz + oz >= 0 && iz + oz < nz && iy + oy >= 0 && iy + oy < ny &&
+                                ix + ox >= 0 && ix + ox < nx;
+                if (!in) continue;
+                const int64_t cn = c + ((int64_t)oz * ny + oy) * nx + ox;
+                const int lin = hlin(oz, oy, ox);
+                const double w = (lin >= 13) ? coefP[(lin - 13) * N + c]
+                                             : coefP[(13 - lin) * N + cn];
+                const double2 x = X[cn];
+                re = fma(w, x.x, re);
+                im = fma(w, x.y, im);
+            }
     const double2 xc = X[c];
     const double damp = imH[c];
     double2 y;
-    y.x = C.ih2 * re - damp * xc.y;
-    y.y = C.ih2 * im + damp * xc.x;
+    y.x = ih2 * re - damp * xc.y;
+    y.y = ih2 * im + damp * xc.x;
     if (F) {
         const double2 f = F[c];
         y.x = f.x - y.x;
@@ -411,15 +460,15 @@ apply_H_kernel(Layout L, const double *__restrict__ kap64, const double *__restr
     Y[c] = y;
 }
 
-void launch_apply_H(const Layout &L, const double *kap64, const double *imH, const double S2[4],
-                    const double M[4], double ih2, const double2 *X, const double2 *F,
-                    double2 *Y, cudaStream_t s)
+void launch_apply_H(const Layout &L, const double *coefP, const double *imH, double ih2,
+                    const double2 *X, const double2 *F, double2 *Y, cudaStream_t s)
 {
-    HCoef C;
-    for (int k = 0; k < 4; ++k) { C.S2[k] = S2[k]; C.M[k] = M[k]; }
-    C.ih2 = ih2;
-    const int bs = 256;
-    apply_H_kernel<<<(unsigned)((L.N + bs - 1) / bs), bs, 0, s>>>(L, kap64, imH, C, X, F, Y);
+    dim3 blk(32, 8);
+    dim3 grd((unsigned)((L.nx + 31) / 32), (unsigned)((L.ny + 7) / 8), (unsigned)L.nz);
+    if (L.d == 3)
+        apply_H_asm_kernel<3><<<grd, blk, 0, s>>>(L.nx, L.ny, L.nz, coefP, imH, ih2, X, F, Y);
+    else
+        apply_H_asm_kernel<2><<<grd, blk, 0, s>>>(L.nx, L.ny, L.nz, coefP, imH, ih2, X, F, Y);
     ++g_launches;
 }
 
@@ -457,8 +506,20 @@ __device__ __forceinline__ double2 block_sum(double re, double im)
 }
 
 // One pass over the data for a group of up to kDotGroup basis vectors: each
-// thread reads w[i] once and accumulates conj(V_k[i]) w[i] for the group.
+// thread reads w[i] once and accumulates conj(V_k[i]) w[i] for the group, two
+// elements per loop trip (more loads in flight).  Every complex product costs
+// four FP64 FMAs on GB300's narrow FP64 pipe, so the kernel is FP64-bound; the
+// block's 2 x kDotGroup sums are reduced together at the end.
 constexpr int kDotGroup = 8;
+
+// (re, im) += conj(a) b as four FP64 FMAs
+__device__ __forceinline__ void cmac_conj(double &re, double &im, double2 a, double2 b)
+{
+    re = fma(a.x, b.x, re);
+    re = fma(a.y, b.y, re);
+    im = fma(a.x, b.y, im);
+    im = fma(-a.y, b.x, im);
+}
 
 __global__ void __launch_bounds__(kRedThreads)
 dots_kernel(const double2 *__restrict__ V, int64_t ldv, int kcount, const double2 *__restrict__ w,
@@ -469,30 +530,52 @@ dots_kernel(const double2 *__restrict__ V, int64_t ldv, int kcount, const double
     double re[kDotGroup], im[kDotGroup];
 #pragma unroll
     for (int q = 0; q < kDotGroup; ++q) { re[q] = 0.0; im[q] = 0.0; }
-    for (int64_t i = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; i < N;
-         i += (int64_t)nb * kRedThreads) {
-        const double2 b = w[i];
+    const int64_t stride = (int64_t)nb * kRedThreads;
+    int64_t i = (int64_t)blockIdx.x * kRedThreads + threadIdx.x;
+    for (; i + stride < N; i += 2 * stride) {
+        const double2 b0 = w[i], b1 = w[i + stride];
 #pragma unroll
         for (int q = 0; q < kDotGroup; ++q) {
             if (q < kn) {
-                const double2 a = V[(int64_t)(k0 + q) * ldv + i];
-                // conj(a) * b
-                re[q] += a.x * b.x + a.y * b.y;
-                im[q] += a.x * b.y - a.y * b.x;
+                const double2 *vq = V + (int64_t)(k0 + q) * ldv;
+                const double2 a0 = vq[i], a1 = vq[i + stride];
+                cmac_conj(re[q], im[q], a0, b0);
+                cmac_conj(re[q], im[q], a1, b1);
             }
         }
     }
-    for (int q = 0; q < kn; ++q) {
-        const double2 t = block_sum(re[q], im[q]);
-        if (threadIdx.x == 0) partial[(int64_t)(k0 + q) * nb + blockIdx.x] = t;
-        __syncthreads();                       // block_sum's shared scratch is reused
+    if (i < N) {
+        const double2 b = w[i];
+#pragma unroll
+        for (int q = 0; q < kDotGroup; ++q)
+            if (q < kn) cmac_conj(re[q], im[q], V[(int64_t)(k0 + q) * ldv + i], b);
+    }
+    // block reduction of all 2 x kDotGroup sums: within warps, then across warps
+    __shared__ double red[kRedThreads / 32][2 * kDotGroup];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < kDotGroup; ++q) {
+        const double r = warp_sum(re[q]), m = warp_sum(im[q]);
+        if (lane == 0) {
+            red[warp][2 * q] = r;
+            red[warp][2 * q + 1] = m;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * kDotGroup && (int)threadIdx.x / 2 < kn) {
+        double t = 0.0;
+#pragma unroll
+        for (int wv = 0; wv < kRedThreads / 32; ++wv) t += red[wv][threadIdx.x];
+        double *out = reinterpret_cast<double *>(partial + (int64_t)(k0 + threadIdx.x / 2) * nb +
+                                                 blockIdx.x);
+        out[threadIdx.x & 1] = t;
     }
 }
 
 int dots_blocks(int64_t N)
 {
-    int64_t nb = (N + 4 * kRedThreads - 1) / (4 * kRedThreads);
-    if (nb > 1216) nb = 1216;   // 8 blocks per SM on 152 SMs
+    int64_t nb = (N + 8 * kRedThreads - 1) / (8 * kRedThreads);
+    if (nb > 608) nb = 608;     // 4 blocks per SM on 152 SMs
     if (nb < 1) nb = 1;
     return (int)nb;
 }
@@ -525,59 +608,58 @@ void launch_reduce(const double2 *partial, int nb, int kcount, double2 *out, cud
     ++g_launches;
 }
 
-__global__ void __launch_bounds__(256)
-sub_combination_kernel(const double2 *__restrict__ V, int64_t ldv, int kcount,
-                       const double2 *__restrict__ h, double2 *__restrict__ w, int64_t N)
+// w -= sum_k h_k V_k and U += sum_k y_k Z_k: two elements per thread (256
+// apart, so that loads stay coalesced) for two independent FP64 chains, four
+// FMAs per complex product
+constexpr int kCombThreads = 256;
+
+template <bool kAdd>
+__global__ void __launch_bounds__(kCombThreads)
+combination_kernel(const double2 *__restrict__ V, int64_t ldv, int kcount,
+                   const double2 *__restrict__ h, double2 *__restrict__ w, int64_t N)
 {
     __shared__ double2 sh[72];
     for (int k = threadIdx.x; k < kcount; k += blockDim.x) sh[k] = h[k];
     __syncthreads();
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    double2 acc = w[i];
+    const int64_t i0 = (int64_t)blockIdx.x * (2 * kCombThreads) + threadIdx.x;
+    const int64_t i1 = i0 + kCombThreads;
+    const bool has1 = i1 < N;
+    if (i0 >= N) return;
+    double2 acc0 = w[i0];
+    double2 acc1 = has1 ? w[i1] : make_double2(0.0, 0.0);
 #pragma unroll 4
     for (int k = 0; k < kcount; ++k) {
-        const double2 v = V[(int64_t)k * ldv + i];
+        const double2 *vk = V + (int64_t)k * ldv;
         const double2 c = sh[k];
-        acc.x -= c.x * v.x - c.y * v.y;
-        acc.y -= c.x * v.y + c.y * v.x;
+        const double cx = kAdd ? c.x : -c.x, cy = kAdd ? c.y : -c.y;
+        const double2 v0 = vk[i0];
+        const double2 v1 = has1 ? vk[i1] : make_double2(0.0, 0.0);
+        acc0.x = fma(cx, v0.x, acc0.x);
+        acc0.x = fma(-cy, v0.y, acc0.x);
+        acc0.y = fma(cx, v0.y, acc0.y);
+        acc0.y = fma(cy, v0.x, acc0.y);
+        acc1.x = fma(cx, v1.x, acc1.x);
+        acc1.x = fma(-cy, v1.y, acc1.x);
+        acc1.y = fma(cx, v1.y, acc1.y);
+        acc1.y = fma(cy, v1.x, acc1.y);
     }
-    w[i] = acc;
+    w[i0] = acc0;
+    if (has1) w[i1] = acc1;
 }
 
 void launch_sub_combination(const double2 *V, int64_t ldv, int kcount, const double2 *h,
                             double2 *w, int64_t N, cudaStream_t s)
 {
-    const int bs = 256;
-    sub_combination_kernel<<<(unsigned)((N + bs - 1) / bs), bs, 0, s>>>(V, ldv, kcount, h, w, N);
+    const unsigned nblk = (unsigned)((N + 2 * kCombThreads - 1) / (2 * kCombThreads));
+    combination_kernel<false><<<nblk, kCombThreads, 0, s>>>(V, ldv, kcount, h, w, N);
     ++g_launches;
-}
-
-__global__ void __launch_bounds__(256)
-add_combination_kernel(const double2 *__restrict__ Z, int64_t ldz, int kcount,
-                       const double2 *__restrict__ y, double2 *__restrict__ U, int64_t N)
-{
-    __shared__ double2 sy[72];
-    for (int k = threadIdx.x; k < kcount; k += blockDim.x) sy[k] = y[k];
-    __syncthreads();
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    double2 acc = U[i];
-#pragma unroll 4
-    for (int k = 0; k < kcount; ++k) {
-        const double2 z = Z[(int64_t)k * ldz + i];
-        const double2 c = sy[k];
-        acc.x += c.x * z.x - c.y * z.y;
-        acc.y += c.x * z.y + c.y * z.x;
-    }
-    U[i] = acc;
 }
 
 void launch_add_combination(const double2 *Z, int64_t ldz, int kcount, const double2 *y,
                             double2 *U, int64_t N, cudaStream_t s)
 {
-    const int bs = 256;
-    add_combination_kernel<<<(unsigned)((N + bs - 1) / bs), bs, 0, s>>>(Z, ldz, kcount, y, U, N);
+    const unsigned nblk = (unsigned)((N + 2 * kCombThreads - 1) / (2 * kCombThreads));
+    combination_kernel<true><<<nblk, kCombThreads, 0, s>>>(Z, ldz, kcount, y, U, N);
     ++g_launches;
 }
 
@@ -590,9 +672,22 @@ __global__ void scale_kernel(const double2 *__restrict__ w, double scale, double
     v[i] = make_double2(a.x * scale, a.y * scale);
 }
 
+__global__ void scale_inplace_kernel(double2 *__restrict__ v, double scale, int64_t N)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double2 a = v[i];
+    v[i] = make_double2(a.x * scale, a.y * scale);
+}
+
 void launch_scale(const double2 *w, double scale, double2 *v, int64_t N, cudaStream_t s)
 {
     const int bs = 256;
+    if (w == v) {
+        scale_inplace_kernel<<<(unsigned)((N + bs - 1) / bs), bs, 0, s>>>(v, scale, N);
+        ++g_launches;
+        return;
+    }
     scale_kernel<<<(unsigned)((N + bs - 1) / bs), bs, 0, s>>>(w, scale, v, N);
     ++g_launches;
 }

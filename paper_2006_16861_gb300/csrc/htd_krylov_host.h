@@ -49,4 +49,22 @@ inline void solve_upper(const zcd *Hm, int m, const zcd *g, zcd *y, int jj)
     }
 }
 
+// Classical Gram-Schmidt with one re-orthogonalisation (CGS2).  The new vector
+// w is built in basis slot k, so one dot kernel over slots 0..k gives both
+// V_i^H w (i < k) and ||w||^2 (slot k); each pass then subtracts w -= V h.
+// With h0 (pass 1) and h1 (pass 2) the k + 1 results of the two passes, the
+// Hessenberg column is h0 + h1 and the norm after pass 2 is
+// ||w_1||^2 - |h1|^2 (Pythagoras; h1 is small against w_1, so no cancellation),
+// which saves a third pass over w for its norm.
+template <typename C2>
+inline double cgs2_column(const C2 *h0, const C2 *h1, int k, zcd *col)
+{
+    double hh = 0.0;
+    for (int i = 0; i < k; ++i) {
+        col[i] = zcd(h0[i].x + h1[i].x, h0[i].y + h1[i].y);
+        hh += h1[i].x * h1[i].x + h1[i].y * h1[i].y;
+    }
+    return h1[k].x - hh;
+}
+
 }  // namespace htd

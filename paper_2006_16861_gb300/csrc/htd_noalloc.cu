@@ -84,7 +84,7 @@ extern "C" htd_status htd_residual_norm_noalloc(htd_handle h, const void *F_dev,
 
     // every element read below is written first by this call: r by apply_H,
     // the partials by the dot kernels, the sums by the reductions
-    htd::launch_apply_H(op.L64, op.kap64, op.imH, op.S2, op.M, op.ih2,
+    htd::launch_apply_H(op.L64, op.coefP, op.imH, op.ih2,
                         static_cast<const double2 *>(U_dev), static_cast<const double2 *>(F_dev),
                         r, s);
     htd::launch_dots(r, N, 1, r, N, partial, nb, s);

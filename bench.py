@@ -55,12 +55,12 @@ WORDS_ONE_STEP, WORDS_BLOCKED = 7, 8
 # file); scaled by node count to other grid sizes.  The captures are summarised
 # under profiles/.
 NCU_TRAFFIC = {
-    "tb2d": {"file": "htd_tblock.cu", "sha16": "529e54e32fba3f34", "bytes": 25081088,
+    "tb2d": {"file": "htd_tblock.cu", "sha16": "911c4093662ebe9d", "bytes": 25086720 + 256,
              "nodes": 1001 * 1001},
     "stream3d": {"file": "htd_stream3d.cu", "sha16": "4f289c964d28aa22",
                  "bytes": 193680896 + 18157568, "nodes": 192 ** 3},
-    "stream3d_pair": {"file": "htd_stream3d_pair.cu", "sha16": "710f53e4e0917f1c",
-                      "bytes": 197462272 + 16750848, "nodes": 192 ** 3},
+    "stream3d_pair": {"file": "htd_stream3d_pair.cu", "sha16": "1c9b1035ac857f75",
+                      "bytes": 197444352 + 16969216, "nodes": 192 ** 3},
 }
 
 
@@ -106,6 +106,8 @@ def parse_args():
     ap.add_argument("--cpu-sample-s", type=float, default=10.0)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--restart", type=int, default=20)
+    ap.add_argument("--batched", type=int, default=1,
+                    help="also time the batched workload (96 systems, lockstep FGMRES)")
     ap.add_argument("--secondary-3d", type=int, default=1,
                     help="also time the FP32 recurrence on the 3-D 256^3 workload (HBM-bound)")
     return ap.parse_args()
@@ -257,6 +259,68 @@ def secondary_3d(htd, stream, flush, peaks):
                          "kernel": kern,
                          "bytes_per_launch": bytes_step, "avg_launch_us": us_step,
                          "peak_kind": f"{kind} HBM copy bandwidth"}}
+
+
+def secondary_batched(htd, stream, flush, sub_rhs=4, sub_inst=4):
+    """Batched workload: the 3-D layered model at 128^3 with 32 seeded point sources
+    as 32 right-hand sides of one handle, plus 64 2-D instances with sides uniform in
+    [200, 1000] -- 96 systems, one CUDA-graph launch per preconditioner round,
+    lockstep FGMRES(20) to 1e-6.  CUDA events on the solve stream: one warm-up solve
+    (it also builds the graph), then one timed solve.  The plain FP64 GPU form is
+    timed on a sub-batch (the 3-D handle with `sub_rhs` sources and `sub_inst` 2-D
+    instances) next to the mixed form on the same sub-batch."""
+    import torch
+    from paper_2006_16861_gb300 import workloads as W
+    setup = W.config_batched()
+
+    def dev(x):
+        return torch.from_numpy(np.ascontiguousarray(x, dtype=np.complex128)).cuda()
+
+    def run(precision, probs, Fs, reps):
+        solvers = [htd.Solver(p, precision=precision, max_rhs=F.shape[0], restart=20)
+                   for p, F in zip(probs, Fs)]
+        b = htd.Batch(solvers, [F.shape[0] for F in Fs])
+        Fd = [dev(F) for F in Fs]
+        Us = b.zeros()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        times, infos = [], None
+        for r in range(reps + 1):
+            for U in Us:
+                U.zero_()
+            flush.fill_(5)
+            e0.record(stream)
+            Us, infos = b.solve(Fd, Us, tol=TOL, max_iters=400, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            if r > 0 or reps == 0:
+                times.append(e0.elapsed_time(e1))
+        ups, k = 0, 0
+        for p, F in zip(probs, Fs):
+            for _ in range(F.shape[0]):
+                ups += p.N * infos[k]["steps"]
+                k += 1
+        b.close()
+        for sv in solvers:
+            sv.close()
+        return min(times), ups, infos
+
+    ms, ups, infos = run("mixed", setup.probs, setup.F, 1)
+    its = [i["iterations"] for i in infos]
+    sub_p = setup.probs[:1 + sub_inst]
+    sub_F = [setup.F[0][:sub_rhs]] + setup.F[1:1 + sub_inst]
+    ms_m, _, _ = run("mixed", sub_p, sub_F, 1)
+    ms_f, _, inf_f = run("fp64", sub_p, sub_F, 0)
+    return {"workload": "batched: 3d_layered_128 x 32 sources + 64 2-D instances (sides 200..1000)",
+            "systems": len(infos),
+            "unknowns": int(sum(p.N * F.shape[0] for p, F in zip(setup.probs, setup.F))),
+            "value": ups / (ms * 1e-3) / 1e9, "unit": UNIT, "time_to_tol_ms": ms,
+            "iterations_min": min(its), "iterations_max": max(its),
+            "rel_res_true_max": max(i["rel_res_true"] for i in infos),
+            "graph": "one launch per preconditioner round (65 child graphs)",
+            "fp64_sub_batch": {"systems": sub_rhs + sub_inst, "mixed_ms": ms_m, "fp64_ms": ms_f,
+                               "speedup_vs_fp64": ms_f / ms_m,
+                               "fp64_rel_res_true_max": max(i["rel_res_true"] for i in inf_f)}}
 
 
 def run_reference(args):
@@ -431,6 +495,9 @@ def run_ours(args):
     sec = None
     if args.secondary_3d and p.ndim == 2:
         sec = secondary_3d(htd, stream, flush, peaks)
+    batched = None
+    if args.batched and p.ndim == 2:
+        batched = secondary_batched(htd, stream, flush)
 
     cpu = None
     if rank == 0 and world == 1 and args.cpu_sample_s > 0:
@@ -470,6 +537,7 @@ def run_ours(args):
                          "l2_resident": l2_resident},
             "cpu_baseline": cpu,
             "secondary_3d": sec,
+            "batched": batched,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk,

@@ -80,6 +80,9 @@ def _load():
         lib.ora_window.restype = ctypes.c_double
         lib.ora_acd_step.argtypes = [P, Q, vp, vp, vp, vp]
         lib.ora_precond.argtypes = [P, Q, ctypes.c_int, vp, vp]
+        lib.ora_precond_project.argtypes = [P, Q, ctypes.c_int, vp, vp]
+        lib.ora_project_states.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_longlong,
+                                           ctypes.c_longlong, vp, vp]
         lib.ora_direct_solve.argtypes = [P, vp, vp]
         lib.ora_grad.argtypes = [P, ctypes.c_int, vp, ctypes.c_int, vp, vp, vp, vp, vp]
         lib.ora_gmres.argtypes = [P, Q, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_double,
@@ -174,13 +177,19 @@ class Oracle:
                               _ptr(un), _ptr(unm1), _ptr(fn), _ptr(out))
         return out.reshape(self.n)
 
-    def precond(self, F, mode: str = "table1") -> np.ndarray:
+    def precond(self, F, mode: str = "table1", periods: int = 1) -> np.ndarray:
+        """Table 1 ("table1"), S_T ("exact"), or the Table 1 run read out by the
+        e^{-i omega t} projection of its last `periods` periods ("project")."""
         F = self._c(F)
         out = np.empty_like(F)
-        rc = self.lib.ora_precond(ctypes.byref(self._p), ctypes.byref(self.params),
-                                  MODES[mode], _ptr(F), _ptr(out))
+        if mode == "project":
+            rc = self.lib.ora_precond_project(ctypes.byref(self._p), ctypes.byref(self.params),
+                                              int(periods), _ptr(F), _ptr(out))
+        else:
+            rc = self.lib.ora_precond(ctypes.byref(self._p), ctypes.byref(self.params),
+                                      MODES[mode], _ptr(F), _ptr(out))
         if rc:
-            raise ValueError("bad mode")
+            raise ValueError("bad mode or periods")
         return out.reshape(self.n)
 
     def direct_solve(self, F) -> np.ndarray:
@@ -220,6 +229,18 @@ class Oracle:
         d = {f: getattr(info, f) for f, _ in _Info._fields_ if f != "hist"}
         d["hist"] = list(info.hist[: info.hist_len])
         return U.reshape(self.n), d
+
+
+def project_states(states: np.ndarray, nP: int, j_first: int) -> np.ndarray:
+    """(2 / n_acc) sum_k e^{-i 2 pi (j_first + k) / nP} states[k] for real states of
+    shape (n_acc, ...)."""
+    lib = _load()
+    st = np.ascontiguousarray(states, dtype=np.float64)
+    n_acc = st.shape[0]
+    N = int(np.prod(st.shape[1:]))
+    out = np.empty(N, dtype=np.complex128)
+    lib.ora_project_states(N, int(nP), int(j_first), n_acc, _ptr(st), _ptr(out))
+    return out.reshape(st.shape[1:])
 
 
 def tables(ndim: int, stencil: str = "q1mix"):

@@ -34,6 +34,12 @@
  *   ora_precond         Table 1 (TimeDomainPreconditioner, real fields) and the
  *                       exact operator S_T^acd [Def. approx_solver] as a complex
  *                       recurrence.
+ *   ora_precond_project the windowed e^{-i omega t} projection: the real-field
+ *                       run of Table 1, read out by projecting its last whole
+ *                       periods of states onto e^{-i omega t} (not in the
+ *                       paper; it reads U off the same time-harmonic ansatz
+ *                       u(t) = Re(U e^{i omega t}) that Table 1 samples).
+ *   ora_project_states  that projection for given states (pinned directly).
  *   ora_direct_solve    banded LU with partial pivoting (exact H^{-1} F).
  *   ora_gmres           restarted GMRES, left-preconditioned [Sec. 2.4] or
  *                       flexible right-preconditioned (FGMRES), modified
@@ -516,6 +522,63 @@ static void precond_exact(const ora_problem *p, const ora_params *q, const cplx 
     cplx ph = cexp(-I * 2.0 * ORA_PI * q->T);
     for (long long i = 0; i < N; ++i) U[i] = ph * u0[i];
     free(um1); free(u0); free(u1); free(f); free(work);
+}
+
+/*
+ * Projection read-out.  The real-field run of Table 1 approaches the
+ * time-harmonic state u_j = Re(U e^{i 2 pi j / n_P}) (at j = T n_P the phase
+ * is 0, so Re U = u_{T n_P} as in Table 1).  Over whole periods
+ * sum_j e^{-i 2 pi j/n_P} Re(U e^{i 2 pi j/n_P}) = (n_acc / 2) U, because
+ * sum_j e^{-i 4 pi j/n_P} vanishes for n_P > 2, so
+ *   U = (2 / n_acc) sum_{j = j_first}^{j_first + n_acc - 1} e^{-i 2 pi j / n_P} u_j,
+ * with n_acc = (periods) n_P equal weights (a rectangular window of whole
+ * periods keeps that cancellation exact).
+ */
+static void project_add(long long N, int nP, long long j, const double *u, cplx *acc)
+{
+    double th = 2.0 * ORA_PI * (double)(j % nP) / nP;
+    cplx e = cos(th) - I * sin(th);
+    for (long long i = 0; i < N; ++i) acc[i] += e * u[i];
+}
+
+/* states: n_acc consecutive real states u_{j_first} .. u_{j_first + n_acc - 1},
+ * N values each; U = (2 / n_acc) sum e^{-i 2 pi j / n_P} u_j */
+void ora_project_states(long long N, int nP, long long j_first, long long n_acc,
+                        const double *states, cplx *U)
+{
+    for (long long i = 0; i < N; ++i) U[i] = 0.0;
+    for (long long k = 0; k < n_acc; ++k) project_add(N, nP, j_first + k, states + k * N, U);
+    for (long long i = 0; i < N; ++i) U[i] *= 2.0 / (double)n_acc;
+}
+
+/* Table 1's recurrence, read out by projecting the states u_j of the last
+ * `periods` periods (j = T n_P - periods n_P + 1 .. T n_P); 1 <= periods <= T */
+int ora_precond_project(const ora_problem *p, const ora_params *q, int periods, const cplx *F,
+                        cplx *U)
+{
+    if (periods < 1 || periods > q->T) return -1;
+    long long N = n_nodes(p);
+    long long nsteps = q->nsteps;
+    long long n_acc = (long long)periods * q->nP;
+    double *um1 = calloc(N, sizeof(double));
+    double *u0 = calloc(N, sizeof(double));
+    double *u1 = calloc(N, sizeof(double));
+    double *f = malloc(sizeof(double) * N);
+    double *work = malloc(sizeof(double) * N);
+    for (long long i = 0; i < N; ++i) U[i] = 0.0;
+    for (long long j = 0; j < nsteps; ++j) {
+        double chi = ora_window(1.0 - (double)j / (double)nsteps, q->rho);
+        double cs = cos(2.0 * ORA_PI * (double)j / q->nP);
+        double sn = sin(2.0 * ORA_PI * (double)j / q->nP);
+        for (long long i = 0; i < N; ++i)
+            f[i] = chi * (cs * creal(F[i]) - sn * cimag(F[i]));
+        acd_step_real(p, q, u0, um1, f, u1, 1, work);
+        if (j + 1 > nsteps - n_acc) project_add(N, q->nP, j + 1, u1, U);   /* state u_{j+1} */
+        double *t = um1; um1 = u0; u0 = u1; u1 = t;
+    }
+    for (long long i = 0; i < N; ++i) U[i] *= 2.0 / (double)n_acc;
+    free(um1); free(u0); free(u1); free(f); free(work);
+    return 0;
 }
 
 int ora_precond(const ora_problem *p, const ora_params *q, int mode, const cplx *F, cplx *U)

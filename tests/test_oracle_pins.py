@@ -308,7 +308,7 @@ def chi_sine_squared(s, rho):
     return math.sin(math.pi * (1 - s) / (2 * rho)) ** 2
 
 
-def scalar_preconditioner(lam, ell, q, F, mode):
+def scalar_preconditioner(lam, ell, q, F, mode, periods=1):
     """Scalar S_T (or Table 1) by the Green's-function sum of Theorem 3.
 
     k = dt^2/alpha (lam + omega^2); Lambda_+- from Eq. Lambda_pm_stability;
@@ -329,6 +329,14 @@ def scalar_preconditioner(lam, ell, q, F, mode):
         u = np.sum(G[ns - m] * c * f)
         return np.exp(-2j * math.pi * q.T) * u
     f = chi * (np.cos(2 * math.pi * m / q.nP) * F.real - np.sin(2 * math.pi * m / q.nP) * F.imag)
+    if mode == "project":
+        # u_j = sum_{m < j} G_{j-m} c f_m for the states of the last `periods` periods
+        n_acc = periods * q.nP
+        acc = 0j
+        for jj in range(ns - n_acc + 1, ns + 1):
+            uj = np.sum(G[jj - m[:jj]] * c * f[:jj]).real
+            acc += np.exp(-2j * math.pi * jj / q.nP) * uj
+        return 2.0 * acc / n_acc
     u_end = np.sum(G[ns - m] * c * f).real
     jim = ns - q.nP // 4
     mm = np.arange(jim)
@@ -353,6 +361,56 @@ def test_preconditioner_on_sine_mode_equals_greens_sum(d, stencil, R, mode):
         U = o.precond(Fs * v, mode)
         s = scalar_preconditioner(lam, ell, q, Fs, mode)
         assert np.abs(U - s * v).max() <= 1e-10 * max(abs(s), 1e-30) * np.abs(v).max()
+
+
+@pytest.mark.parametrize("d,stencil", [(2, "q1mix"), (3, "q1mix")])
+@pytest.mark.parametrize("R", ["zero", 40.0])
+@pytest.mark.parametrize("periods", [1, 2])
+def test_projection_on_sine_mode_equals_greens_sum(d, stencil, R, periods):
+    """The projection read-out on a sine mode (constant k): the grid recurrence
+    acts as a scalar, equal to the Green's-function sum of Theorem 3 projected
+    by hand over the last `periods` periods."""
+    n = (15, 13) if d == 2 else (7, 6, 5)
+    p = make_problem(d, n, c=1.0, R=R, T=3, rho=0.3)
+    o = oracle.Oracle(p, stencil)
+    q = o.params
+    kappa = (p.h * p.omega) ** 2
+    ell = q.beta * q.dt / q.alpha * (p.omega * float(p.R_node.flat[0]) / q.omega)
+    for m, Fs in [((1,) * d, 1.0 + 0.0j), ((2, 3) + (1,) * (d - 2), 0.3 - 0.7j)]:
+        v = _sine_mode(n, m)
+        lam = sine_eigenvalue(stencil, n, m, p.h, kappa)
+        U = o.precond(Fs * v, "project", periods=periods)
+        s = scalar_preconditioner(lam, ell, q, Fs, "project", periods)
+        assert np.abs(U - s * v).max() <= 1e-10 * max(abs(s), 1e-30) * np.abs(v).max()
+
+
+@pytest.mark.parametrize("nP,periods,j_first", [(4, 1, 0), (8, 2, 37), (12, 3, 1500)])
+def test_projection_recovers_time_harmonic_amplitude(nP, periods, j_first):
+    """For exactly time-harmonic states u_j = Re(U e^{i 2 pi j / n_P}) the
+    projection over whole periods returns U (the e^{-2 i theta} terms cancel);
+    over a part of a period it does not, which is why the read-out uses whole
+    periods."""
+    rng = np.random.default_rng(5)
+    U = rng.standard_normal(7) + 1j * rng.standard_normal(7)
+    j = j_first + np.arange(periods * nP)
+    states = np.real(U[None, :] * np.exp(2j * np.pi * j / nP)[:, None])
+    got = oracle.project_states(states, nP, j_first)
+    assert np.abs(got - U).max() <= 1e-13 * np.abs(U).max()
+    part = oracle.project_states(states[: nP // 2 + 1], nP, j_first)
+    assert np.abs(part - U).max() > 1e-3 * np.abs(U).max()
+
+
+def test_projection_converges_to_Hinv_with_T():
+    """The projected read-out of the damped recurrence approaches H^{-1} F as
+    T grows, like S_T (Theorem 4)."""
+    p = make_problem(2, (25, 25), c=1.0, R="layer", layer=5, ppw=8)
+    U = oracle.Oracle(p).direct_solve(p.F)
+    errs = []
+    for T in (2, 4, 8, 16, 32):
+        o = oracle.Oracle(p, T=T)
+        errs.append(np.linalg.norm(o.precond(p.F, "project") - U) / np.linalg.norm(U))
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+    assert errs[-1] < 1e-3 * errs[0]
 
 
 def test_table1_real_part_is_exact_real_part_and_linearity():

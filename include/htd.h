@@ -54,7 +54,7 @@ typedef enum {
 } htd_status;
 
 enum { HTD_FP64 = 0, HTD_MIXED = 1 };            /* recurrence precision */
-enum { HTD_MODE_TABLE1 = 0, HTD_MODE_EXACT = 1 }; /* preconditioner form */
+enum { HTD_MODE_TABLE1 = 0, HTD_MODE_EXACT = 1, HTD_MODE_PROJECT = 2 }; /* preconditioner form */
 enum { HTD_FGMRES = 0, HTD_LEFT_GMRES = 1 };     /* Krylov method */
 enum { HTD_STENCIL_Q1MIX = 0, HTD_STENCIL_FD5 = 1 };
 enum { HTD_BC_DIRICHLET = 0 };
@@ -70,7 +70,13 @@ typedef struct {
                           float, Krylov, residual and Givens in double */
     int mode;          /* HTD_MODE_TABLE1: Table 1, one real run, U = u_{T n_P} +
                           i u_{(T-1/4) n_P}.  HTD_MODE_EXACT: S_T^acd F of
-                          Def. approx_solver, two real runs (forcings F and -iF) */
+                          Def. approx_solver, two real runs (forcings F and -iF).
+                          HTD_MODE_PROJECT (not in the paper): Table 1's run read
+                          out by projection onto e^{-i omega t} over its last
+                          proj_periods whole periods, U = (2/n_acc) sum_j
+                          e^{-i 2 pi j/n_P} u_j, n_acc = proj_periods n_P, summed
+                          with compensated (Kahan) additions in the recurrence
+                          precision; like Table 1 only R-linear (use FGMRES) */
     int krylov;        /* HTD_FGMRES (flexible right preconditioning, default) or
                           HTD_LEFT_GMRES (left preconditioning, Sec. 2.4) */
     int T;             /* periods per preconditioner application, >= 1 */
@@ -84,6 +90,8 @@ typedef struct {
                           per-rhs device arrays (two states, two forcing planes,
                           and two more states for the blocked 2-D kernel) are
                           allocated max_rhs times */
+    int proj_periods;  /* HTD_MODE_PROJECT: whole periods projected, 1..T; 0
+                          means 1.  Adds four planes per right-hand side */
 } htd_options;
 
 typedef struct {
@@ -103,7 +111,7 @@ typedef struct {
 } htd_solve_info;
 
 /* Fill *opt with the defaults: FP64, TABLE1, FGMRES, T = 10, rho = 0.25,
- * nP = 0 (automatic), Q1MIX stencil, restart 20, max_rhs 1. */
+ * nP = 0 (automatic), Q1MIX stencil, restart 20, max_rhs 1, proj_periods 1. */
 void htd_default_options(htd_options *opt);
 
 /*

@@ -164,6 +164,8 @@ struct htd_ctx {
     // u3, fre, fim, slot); act_dev = active list read by the step kernels
     int rcap = 1;
     int *act_dev = nullptr;
+    // projection read-out: 4 planes of N per rhs (sums and compensations, re/im)
+    void *acc = nullptr;
     htd::RhsSet Rs{};
     int *err_dev = nullptr;     // set by a kernel whose bounded device wait gave up
     float step_us = 0.f;        // autotuned time per recurrence step (microseconds)
@@ -212,14 +214,20 @@ void free_ctx(htd_ctx *c)
         if (e) cudaEventDestroy(e);
     void *dev[] = {c->kap, c->dco, c->fre, c->fim, c->u0, c->u1, c->kap64, c->imH, c->coefP, c->V, c->Z,
                    c->w, c->t, c->r, c->partial, c->hdev, c->slot, c->Fh, c->Uh, c->u2, c->u3,
-                   c->err_dev, c->gU, c->gMu, c->gR, c->gres, c->grec, c->act_dev};
+                   c->err_dev, c->gU, c->gMu, c->gR, c->gres, c->grec, c->act_dev,
+                   c->acc};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (c->hhost) cudaFreeHost(c->hhost);
     delete c;
 }
 
-// one preconditioner run of T n_P steps; the forcing planes are already filled
+// one preconditioner run of T n_P steps; the forcing planes are already filled.
+// Table 1 / EXACT: the step kernels write the snapshot and final state into the
+// output slots (flags).  PROJECT: steps j >= j_acc (whose new states u_{j+1}
+// lie in the last proj_periods periods) run one step per launch, each
+// followed by the compensated accumulation of e^{-i theta_{j+1}} u_{j+1};
+// a finishing kernel writes (2 / n_acc) times the sums to the output slots.
 template <typename T>
 htd_status run_steps_direct(htd_ctx *c, cudaStream_t s)
 {
@@ -228,23 +236,53 @@ htd_status run_steps_direct(htd_ctx *c, cudaStream_t s)
     T *A = (T *)c->u0, *B = (T *)c->u1;
     HTD_CUDA(cudaMemsetAsync(A, 0, sizeof(T) * L.total * c->rcap, s));
     HTD_CUDA(cudaMemsetAsync(B, 0, sizeof(T) * L.total * c->rcap, s));
-    const long long jim = c->nsteps - c->nP / 4;
+    const bool project = c->opt.mode == HTD_MODE_PROJECT;
+    const long long jim = project ? -1 : c->nsteps - c->nP / 4;
+    const long long jfin = project ? -1 : c->nsteps;
+    const long long n_acc = project ? (long long)c->opt.proj_periods * c->nP : 0;
+    const long long j_acc = c->nsteps - n_acc;           // first step whose new state counts
+    const int64_t astride = 4 * L.N;
+    if (project) HTD_CUDA(cudaMemsetAsync(c->acc, 0, sizeof(T) * astride * c->rcap, s));
+    // accumulate the new state u_{j+1} (in `u`) of step j
+    auto accumulate = [&](long long j, const T *u) {
+        const double th = 2.0 * kPi * (double)((j + 1) % c->nP) / (double)c->nP;
+        htd::launch_project_accumulate<T>(L, u, (T *)c->acc, astride, (T)std::cos(th),
+                                          (T)(-std::sin(th)), c->Rs, s);
+    };
+    auto finish = [&]() {
+        htd::launch_project_finish<T>(L.N, (const T *)c->acc, astride, 2.0 / (double)n_acc,
+                                      c->slot, c->Rs, s);
+    };
+    // one-step launches for steps j0 .. nsteps-1 from (cur = u_{j0}, oth = u_{j0-1})
+    auto one_steps = [&](long long j0, T *cur, T *oth) {
+        for (long long j = j0; j < c->nsteps; ++j) {
+            int flags = 0;
+            if (j + 1 == jim) flags |= 1;
+            if (j + 1 == jfin) flags |= 2;
+            htd::launch_step<T>(L, cur, oth, (const T *)c->kap, (const T *)c->dco,
+                                (const T *)c->fre, (const T *)c->fim, C, (T)c->atab[j],
+                                (T)c->btab[j], c->slot, flags, s, c->Rs);
+            if (project && j >= j_acc) accumulate(j, oth);
+            std::swap(cur, oth);
+        }
+    };
     if constexpr (std::is_same<T, float>::value) {
       if (c->use_tb) {
         // B steps per launch; the state pair alternates between (u0,u1) and (u2,u3)
         T *pairs[2][2] = {{A, B}, {(T *)c->u2, (T *)c->u3}};
         const int map_of[2][2] = {{0, 1}, {2, 3}};
+        const long long jend = project ? j_acc : c->nsteps;   // blocked steps end here
         int from = 0;
-        for (long long j0 = 0; j0 < c->nsteps; j0 += c->tb.B) {
+        for (long long j0 = 0; j0 < jend; j0 += c->tb.B) {
             htd::TbSteps<T> S;
-            S.nsub = (int)std::min<long long>(c->tb.B, c->nsteps - j0);
+            S.nsub = (int)std::min<long long>(c->tb.B, jend - j0);
             for (int q = 0; q < htd::kTbMaxSteps; ++q) {
                 const long long j = j0 + q;
                 S.a[q] = (q < S.nsub) ? (T)c->atab[j] : T(0);
                 S.b[q] = (q < S.nsub) ? (T)c->btab[j] : T(0);
                 int flags = 0;
                 if (q < S.nsub && j + 1 == jim) flags |= 1;
-                if (q < S.nsub && j + 1 == c->nsteps) flags |= 2;
+                if (q < S.nsub && j + 1 == jfin) flags |= 2;
                 S.flags[q] = flags;
             }
             htd::launch_tb2d<T>(c->tb, c->tbmaps, map_of[from][0], map_of[from][1], L,
@@ -252,6 +290,11 @@ htd_status run_steps_direct(htd_ctx *c, cudaStream_t s)
                                 (const T *)c->fre, (const T *)c->fim, C, S, c->slot,
                                 c->err_dev, s, c->Rs);
             from = 1 - from;
+        }
+        // the blocked launches leave u_{jend} in pairs[from][0], u_{jend-1} in pairs[from][1]
+        if (project) {
+            one_steps(jend, pairs[from][0], pairs[from][1]);
+            finish();
         }
         HTD_CUDA(cudaGetLastError());
         return HTD_OK;
@@ -262,30 +305,25 @@ htd_status run_steps_direct(htd_ctx *c, cudaStream_t s)
             for (long long j = 0; j < c->nsteps; ++j) {
                 int flags = 0;
                 if (j + 1 == jim) flags |= 1;
-                if (j + 1 == c->nsteps) flags |= 2;
+                if (j + 1 == jfin) flags |= 2;
+                T *um = (j & 1) ? A : B;                    // receives u_{j+1}
                 if (c->s3_shape == kS3Pair)
-                    htd::launch_stream3d_pair(c->s3maps, (int)(j & 1), L, (j & 1) ? A : B, C,
+                    htd::launch_stream3d_pair(c->s3maps, (int)(j & 1), L, um, C,
                                               (T)c->atab[j], (T)c->btab[j], c->slot, flags,
                                               c->s3_zchunk, c->s3_stages, c->err_dev, s, c->Rs);
                 else
-                    htd::launch_stream3d(c->s3maps, (int)(j & 1), c->s3_shape, L,
-                                         (j & 1) ? A : B, C, (T)c->atab[j], (T)c->btab[j],
-                                         c->slot, flags, c->s3_zchunk, c->err_dev, s);
+                    htd::launch_stream3d(c->s3maps, (int)(j & 1), c->s3_shape, L, um, C,
+                                         (T)c->atab[j], (T)c->btab[j], c->slot, flags,
+                                         c->s3_zchunk, c->err_dev, s);
+                if (project && j >= j_acc) accumulate(j, um);
             }
+            if (project) finish();
             HTD_CUDA(cudaGetLastError());
             return HTD_OK;
         }
     }
-    for (long long j = 0; j < c->nsteps; ++j) {
-        T *cur = (j & 1) ? B : A;
-        T *oth = (j & 1) ? A : B;
-        int flags = 0;
-        if (j + 1 == jim) flags |= 1;
-        if (j + 1 == c->nsteps) flags |= 2;
-        htd::launch_step<T>(L, cur, oth, (const T *)c->kap, (const T *)c->dco, (const T *)c->fre,
-                            (const T *)c->fim, C, (T)c->atab[j], (T)c->btab[j], c->slot, flags, s,
-                            c->Rs);
-    }
+    one_steps(0, A, B);
+    if (project) finish();
     HTD_CUDA(cudaGetLastError());
     return HTD_OK;
 }
@@ -716,12 +754,15 @@ htd_status plan_impl(const htd_grid *grid, const double *c_cell, const double *R
     if (!(omega_phys > 0.0) || !std::isfinite(omega_phys)) return HTD_ERR_ARG;
     if (bc != HTD_BC_DIRICHLET) return HTD_ERR_ARG;
     if (opt.precision != HTD_FP64 && opt.precision != HTD_MIXED) return HTD_ERR_ARG;
-    if (opt.mode != HTD_MODE_TABLE1 && opt.mode != HTD_MODE_EXACT) return HTD_ERR_ARG;
+    if (opt.mode != HTD_MODE_TABLE1 && opt.mode != HTD_MODE_EXACT && opt.mode != HTD_MODE_PROJECT)
+        return HTD_ERR_ARG;
     if (opt.krylov != HTD_FGMRES && opt.krylov != HTD_LEFT_GMRES) return HTD_ERR_ARG;
     if (opt.T < 1 || !(opt.rho >= 0.0 && opt.rho <= 1.0) || opt.nP < 0) return HTD_ERR_ARG;
     if (opt.restart < 1 || opt.restart > kMaxRestart) return HTD_ERR_ARG;
     if (opt.max_rhs == 0) opt.max_rhs = 1;
     if (opt.max_rhs < 1 || opt.max_rhs > htd::kMaxRhs) return HTD_ERR_ARG;
+    if (opt.proj_periods == 0) opt.proj_periods = 1;
+    if (opt.proj_periods < 1 || opt.proj_periods > opt.T) return HTD_ERR_ARG;
     const int d = grid->ndim;
     pl->d = d;
     pl->N = 1;
@@ -860,6 +901,8 @@ htd_status create_impl(const htd_grid *grid, const double *c_cell, const double 
     HTD_CUDA(cudaMemset(c->err_dev, 0, sizeof(int)));
     HTD_CUDA(cudaMalloc((void **)&c->slot, sizeof(OutSlot) * c->rcap));
     HTD_CUDA(cudaMemset(c->slot, 0, sizeof(OutSlot) * c->rcap));
+    if (opt.mode == HTD_MODE_PROJECT)
+        HTD_CUDA(cudaMalloc(&c->acc, c->esz * 4 * (size_t)N * c->rcap));
     HTD_CUDA(cudaMalloc((void **)&c->act_dev, sizeof(int) * (1 + c->rcap)));
     HTD_CUDA(cudaMemset(c->act_dev, 0, sizeof(int) * (1 + c->rcap)));
     c->Rs.act = c->act_dev;
@@ -1075,6 +1118,7 @@ void htd_default_options(htd_options *opt)
     opt->stencil = HTD_STENCIL_Q1MIX;
     opt->restart = 20;
     opt->max_rhs = 1;
+    opt->proj_periods = 1;
 }
 
 htd_status htd_create(const htd_grid *grid, const double *c_cell_host, const double *R_node_host,

@@ -112,6 +112,18 @@ void launch_split(const Layout &L, const double2 *F, T *fre, T *fim, int flip, c
 
 void launch_set_slot(OutSlot *slot, double *final_part, double *snap_part, cudaStream_t s);
 
+// ---- projection read-out (mode HTD_MODE_PROJECT) ------------------------------
+
+// acc (per rhs, astride apart; 4 planes of N in compact order: s_re, s_im,
+// c_re, c_im) += (wc, ws) u with compensated (Kahan) additions; u padded
+template <typename T>
+void launch_project_accumulate(const Layout &L, const T *u, T *acc, int64_t astride, T wc, T ws,
+                               const RhsSet &R, cudaStream_t s);
+// U = scale (s - c) to each listed rhs's output slot (re -> final, im -> snap)
+template <typename T>
+void launch_project_finish(int64_t N, const T *acc, int64_t astride, double scale,
+                           const OutSlot *slot, const RhsSet &R, cudaStream_t s);
+
 // ---- right-hand-side batches --------------------------------------------------
 
 constexpr int kMaxRhs = 256;     // rhs per handle (act list entries)

@@ -222,6 +222,94 @@ template void launch_step<double>(const Layout &, const double *, double *, cons
                                   int, cudaStream_t, const RhsSet &);
 
 // ---------------------------------------------------------------------------
+// projection read-out: compensated sums of e^{-i theta_j} u_j
+// ---------------------------------------------------------------------------
+
+// one compensated (Kahan) addition s += x, c carrying the negated lost low part
+template <typename T>
+__device__ __forceinline__ void kahan_add(T &s, T &c, T x)
+{
+    const T y = x - c;
+    const T t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// acc planes per rhs (stride apart), compact node order: [s_re, s_im, c_re, c_im]
+// x N.  For the state u (padded layout) of every listed rhs:
+//   s_re += wc u, s_im += ws u   (wc = cos theta, ws = -sin theta), compensated.
+template <typename T>
+__global__ void __launch_bounds__(256)
+project_accumulate_kernel(Layout L, const T *__restrict__ u, T *__restrict__ acc, int64_t astride,
+                          T wc, T ws, RhsSet R, int nz)
+{
+    const int64_t ix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t iy = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
+    int rhs;
+    if (!rhs_of_slot(R, (int)blockIdx.z / nz, rhs)) return;
+    const int64_t iz = blockIdx.z % nz;
+    if (ix >= L.nx || iy >= L.ny) return;
+    const int64_t c = (iz * L.ny + iy) * L.nx + ix;
+    const T v = u[rhs * R.stride + L.node(ix, iy, iz)];
+    T *a = acc + rhs * astride;
+    T sr = a[c], si = a[L.N + c], cr = a[2 * L.N + c], ci = a[3 * L.N + c];
+    kahan_add(sr, cr, wc * v);
+    kahan_add(si, ci, ws * v);
+    a[c] = sr;
+    a[L.N + c] = si;
+    a[2 * L.N + c] = cr;
+    a[3 * L.N + c] = ci;
+}
+
+template <typename T>
+void launch_project_accumulate(const Layout &L, const T *u, T *acc, int64_t astride, T wc, T ws,
+                               const RhsSet &R, cudaStream_t s)
+{
+    const int nz = (int)L.nz;
+    dim3 blk(32, 8);
+    dim3 grd((unsigned)((L.nx + 31) / 32), (unsigned)((L.ny + 7) / 8), (unsigned)(nz * R.slots));
+    project_accumulate_kernel<T><<<grd, blk, 0, s>>>(L, u, acc, astride, wc, ws, R, nz);
+    ++g_launches;
+}
+template void launch_project_accumulate<float>(const Layout &, const float *, float *, int64_t,
+                                               float, float, const RhsSet &, cudaStream_t);
+template void launch_project_accumulate<double>(const Layout &, const double *, double *, int64_t,
+                                                double, double, const RhsSet &, cudaStream_t);
+
+// U = scale (s - c) into the output slot of every listed rhs (real part to
+// final_part, imaginary part to snap_part), in double
+template <typename T>
+__global__ void __launch_bounds__(256)
+project_finish_kernel(int64_t N, const T *__restrict__ acc, int64_t astride, double scale,
+                      const OutSlot *__restrict__ slot, RhsSet R)
+{
+    int rhs;
+    if (!rhs_of_slot(R, (int)blockIdx.y, rhs)) return;
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const T *a = acc + rhs * astride;
+    const OutSlot o = slot[rhs];
+    const double re = scale * ((double)a[c] - (double)a[2 * N + c]);
+    const double im = scale * ((double)a[N + c] - (double)a[3 * N + c]);
+    if (o.final_part) o.final_part[2 * c] = re;
+    if (o.snap_part) o.snap_part[2 * c] = im;
+}
+
+template <typename T>
+void launch_project_finish(int64_t N, const T *acc, int64_t astride, double scale,
+                           const OutSlot *slot, const RhsSet &R, cudaStream_t s)
+{
+    const int bs = 256;
+    dim3 grd((unsigned)((N + bs - 1) / bs), (unsigned)R.slots);
+    project_finish_kernel<T><<<grd, bs, 0, s>>>(N, acc, astride, scale, slot, R);
+    ++g_launches;
+}
+template void launch_project_finish<float>(int64_t, const float *, int64_t, double,
+                                           const OutSlot *, const RhsSet &, cudaStream_t);
+template void launch_project_finish<double>(int64_t, const double *, int64_t, double,
+                                            const OutSlot *, const RhsSet &, cudaStream_t);
+
+// ---------------------------------------------------------------------------
 // split / output slot
 // ---------------------------------------------------------------------------
 

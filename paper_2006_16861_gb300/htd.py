@@ -21,7 +21,7 @@ STATUS = {0: "HTD_OK", 1: "HTD_ERR_ARG", 2: "HTD_ERR_CUDA", 3: "HTD_ERR_OOM",
           7: "HTD_ERR_TIMEOUT", 8: "HTD_ERR_SIZE"}
 HTD_NOALLOC_MAX_NODES = 262144
 FP64, MIXED = 0, 1
-MODE_TABLE1, MODE_EXACT = 0, 1
+MODE_TABLE1, MODE_EXACT, MODE_PROJECT = 0, 1, 2
 FGMRES, LEFT_GMRES = 0, 1
 STENCIL_Q1MIX, STENCIL_FD5 = 0, 1
 BC_DIRICHLET = 0
@@ -47,7 +47,8 @@ class Grid(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("mode", ctypes.c_int), ("krylov", ctypes.c_int),
                 ("T", ctypes.c_int), ("rho", ctypes.c_double), ("nP", ctypes.c_int),
-                ("stencil", ctypes.c_int), ("restart", ctypes.c_int), ("max_rhs", ctypes.c_int)]
+                ("stencil", ctypes.c_int), ("restart", ctypes.c_int), ("max_rhs", ctypes.c_int),
+                ("proj_periods", ctypes.c_int)]
 
 
 class Params(ctypes.Structure):
@@ -342,12 +343,13 @@ def htd_status_string(status: int) -> str:
 def make_options(prob=None, precision: str = "fp64", mode: str = "table1",
                  krylov: str = "fgmres", stencil: str = "q1mix", restart: int = 20,
                  nP: int = 0, T: int | None = None, rho: float | None = None,
-                 max_rhs: int = 1) -> Options:
+                 max_rhs: int = 1, proj_periods: int = 1) -> Options:
     """htd_options from names; T and rho default to the problem's."""
     o = htd_default_options()
     o.max_rhs = int(max_rhs)
+    o.proj_periods = int(proj_periods)
     o.precision = {"fp64": FP64, "mixed": MIXED}[precision]
-    o.mode = {"table1": MODE_TABLE1, "exact": MODE_EXACT}[mode]
+    o.mode = {"table1": MODE_TABLE1, "exact": MODE_EXACT, "project": MODE_PROJECT}[mode]
     o.krylov = {"fgmres": FGMRES, "left": LEFT_GMRES}[krylov]
     o.stencil = {"q1mix": STENCIL_Q1MIX, "fd5": STENCIL_FD5}[stencil]
     o.restart = restart
@@ -371,8 +373,9 @@ class Solver:
     def __init__(self, prob, precision: str = "fp64", mode: str = "table1",
                  krylov: str = "fgmres", stencil: str = "q1mix", restart: int = 20,
                  nP: int = 0, T: int | None = None, rho: float | None = None,
-                 max_rhs: int = 1):
-        o = make_options(prob, precision, mode, krylov, stencil, restart, nP, T, rho, max_rhs)
+                 max_rhs: int = 1, proj_periods: int = 1):
+        o = make_options(prob, precision, mode, krylov, stencil, restart, nP, T, rho, max_rhs,
+                         proj_periods)
         self.max_rhs = int(max_rhs)
         self.prob = prob
         self.n = tuple(prob.n)

@@ -42,7 +42,7 @@ def test_struct_layouts_match_header(tmp_path):
         '#include <stdio.h>\n#include <stddef.h>\n#include "htd.h"\n'
         "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(htd_grid),"
         " sizeof(htd_options), sizeof(htd_params), sizeof(htd_solve_info),"
-        " offsetof(htd_solve_info, hist), offsetof(htd_params, nP), offsetof(htd_options, max_rhs));"
+        " offsetof(htd_solve_info, hist), offsetof(htd_params, nP), offsetof(htd_options, proj_periods));"
         "return 0;}\n")
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
@@ -51,15 +51,15 @@ def test_struct_layouts_match_header(tmp_path):
                                           check=True).stdout.split()]
     want = [ctypes.sizeof(htd.Grid), ctypes.sizeof(htd.Options), ctypes.sizeof(htd.Params),
             ctypes.sizeof(htd.SolveInfo), htd.SolveInfo.hist.offset, htd.Params.nP.offset,
-            htd.Options.max_rhs.offset]
+            htd.Options.proj_periods.offset]
     assert got == want
 
 
 def test_default_options():
     o = htd.htd_default_options()
     assert (o.precision, o.mode, o.krylov, o.T, o.rho, o.nP, o.stencil, o.restart,
-            o.max_rhs) == \
-        (htd.FP64, htd.MODE_TABLE1, htd.FGMRES, 10, 0.25, 0, htd.STENCIL_Q1MIX, 20, 1)
+            o.max_rhs, o.proj_periods) == \
+        (htd.FP64, htd.MODE_TABLE1, htd.FGMRES, 10, 0.25, 0, htd.STENCIL_Q1MIX, 20, 1, 1)
 
 
 PROBLEMS = [
@@ -108,7 +108,8 @@ def test_plan_rejects_bad_input():
         htd.htd_plan(2, p.n, p.h, p.c_cell, R, p.omega, 0, htd.make_options(p))
     assert e.value.status == 1
     for kw in ({"restart": 0}, {"restart": 65}, {"T": 0}, {"rho": 1.5}, {"max_rhs": -1},
-               {"max_rhs": 257}):
+               {"max_rhs": 257}, {"mode": "project", "proj_periods": 3},
+               {"mode": "project", "proj_periods": -1}):
         with pytest.raises(htd.HtdError) as e:
             htd.plan(p, **kw)
         assert e.value.status == 1

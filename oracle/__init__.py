@@ -85,6 +85,8 @@ def _load():
                                            ctypes.c_longlong, vp, vp]
         lib.ora_direct_solve.argtypes = [P, vp, vp]
         lib.ora_grad.argtypes = [P, ctypes.c_int, vp, ctypes.c_int, vp, vp, vp, vp, vp]
+        lib.ora_grad_td.argtypes = [P, Q, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp,
+                                    vp, vp, vp]
         lib.ora_gmres.argtypes = [P, Q, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_double,
                                   ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                   ctypes.POINTER(_Info)]
@@ -214,6 +216,32 @@ class Oracle:
                              _ptr(d), _ptr(gm), _ptr(gR), ctypes.byref(J)):
             raise ArithmeticError("singular H")
         return J.value, gm, gR
+
+    def grad_td(self, F, rec_idx, d, mode: str = "table1"):
+        """Misfit 1/2 sum_s ||P(P F_s) - d_s||^2 of the preconditioner's own
+        approximate solution (one application, mode "table1" or "exact") and its
+        gradient through the recurrence with respect to m = c^-2 per cell and R
+        per node, omega, dt and n_P held at this oracle's values.
+        Returns (J, grad_m, grad_R)."""
+        F = np.ascontiguousarray(np.asarray(F, dtype=np.complex128).reshape(-1, self.N))
+        nsrc = F.shape[0]
+        rec = np.ascontiguousarray(np.asarray(rec_idx, dtype=np.int64).reshape(-1))
+        d = np.ascontiguousarray(np.asarray(d, dtype=np.complex128).reshape(nsrc, rec.size))
+        gm = np.zeros(self.c.shape)
+        gR = np.zeros(self.n)
+        J = ctypes.c_double()
+        if self.lib.ora_grad_td(ctypes.byref(self._p), ctypes.byref(self.params), MODES[mode],
+                                nsrc, _ptr(F), int(rec.size), _ptr(rec), _ptr(d), _ptr(gm),
+                                _ptr(gR), ctypes.byref(J)):
+            raise ValueError("bad mode")
+        return J.value, gm, gR
+
+    def with_params(self, other: "Oracle") -> "Oracle":
+        """Use another oracle's recurrence parameters (omega, dt, n_P, ...) for this
+        problem: a perturbed model evaluated with the parameters held fixed."""
+        ctypes.memmove(ctypes.byref(self.params), ctypes.byref(other.params),
+                       ctypes.sizeof(_Params))
+        return self
 
     def gmres(self, F, krylov: str = "fgmres", precond: str = "table1", tol: float = 1e-6,
               restart: int = 20, maxit: int = 200, fixed: bool = False, U0=None):

@@ -40,6 +40,9 @@
  *                       paper; it reads U off the same time-harmonic ansatz
  *                       u(t) = Re(U e^{i omega t}) that Table 1 samples).
  *   ora_project_states  that projection for given states (pinned directly).
+ *   ora_grad_td         misfit of the preconditioner's own approximate solution
+ *                       and its gradient through the recurrence (discrete
+ *                       adjoint run backwards in time; not in the paper).
  *   ora_direct_solve    banded LU with partial pivoting (exact H^{-1} F).
  *   ora_gmres           restarted GMRES, left-preconditioned [Sec. 2.4] or
  *                       flexible right-preconditioned (FGMRES), modified
@@ -919,5 +922,129 @@ int ora_grad(const ora_problem *p, int nsrc, const cplx *F, int nrec, const long
     *misfit = J;
     free(U); free(r); free(mu);
     band_free(&lu);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* misfit of the time-domain approximate solution and its gradient through    */
+/* the recurrence (discrete adjoint, reverse time)                             */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * J = 1/2 sum_s sum_r |(P F_s)[rec_r] - d_{s,r}|^2 with P the preconditioner
+ * (mode Table 1 or EXACT): the approximate solution of one application, not
+ * H^{-1} F.  Each real run of P is the recurrence R_j(u) = (1 + L/2) u_{j+1}
+ * - (2 - K) u_j + (1 - L/2) u_{j-1} - g_j = 0, j = 0 .. N-1, u_0 = u_{-1} = 0
+ * (Def. of I_acd), read out at its output steps.  With multipliers lam_{j+1}
+ * for R_j, stationarity in u_k gives the same recurrence backwards in time,
+ *   (1 + L/2) lam_k = (2 - K) lam_{k+1} - (1 - L/2) lam_{k+2} - dJ/du_k,
+ * lam_{N+1} = lam_{N+2} = 0 (K and L symmetric), and
+ *   dJ/dtheta = sum_j lam_{j+1}^T dR_j/dtheta
+ *             = sum_j lam_{j+1}^T [ (dL/2 / dtheta)(u_{j+1} - u_{j-1}) + (dK/dtheta) u_j ].
+ * K depends on m = c^-2 per cell through Re H (Eq. damped Helmholtz equation,
+ * App. A cell mass M): dK/dm_alpha = -(dt^2/alpha) omega_phys^2 M on the
+ * cell's corners; L/2 = (beta dt / (2 alpha omega)) omega_phys R per node.
+ * omega, dt, n_P (chosen from c) are held fixed.  All states are kept.
+ */
+int ora_grad_td(const ora_problem *p, const ora_params *q, int mode, int nsrc, const cplx *F,
+                int nrec, const long long *rec_idx, const cplx *d, double *grad_m, double *grad_R,
+                double *misfit)
+{
+    if (mode != ORA_MODE_TABLE1 && mode != ORA_MODE_EXACT) return -1;
+    long long N = n_nodes(p), Nc = n_cells(p);
+    long long ns = q->nsteps;
+    long long jim = ns - q->nP / 4;
+    double S[4], M[4];
+    ora_tables(p->ndim, p->stencil, S, M);
+    double c = q->dt * q->dt / q->alpha;
+    double w = p->omega_phys;
+    double cm = -c * w * w;
+    double cR = q->beta * q->dt / (2.0 * q->alpha * q->omega) * w;
+    int runs = (mode == ORA_MODE_EXACT) ? 2 : 1;
+    double *u = malloc(sizeof(double) * (size_t)(ns + 2) * N);   /* u_{-1} .. u_N */
+    double *lam = malloc(sizeof(double) * (size_t)(ns + 3) * N); /* lam_0 .. lam_{N+2} */
+    double *f = malloc(sizeof(double) * N), *work = malloc(sizeof(double) * N);
+    double *dj = malloc(sizeof(double) * (size_t)2 * N);        /* dJ/du at two output steps */
+    cplx *U = malloc(sizeof(cplx) * N);
+    for (long long a = 0; a < Nc; ++a) grad_m[a] = 0.0;
+    for (long long i = 0; i < N; ++i) grad_R[i] = 0.0;
+    double J = 0.0;
+#define UST(j) (u + (size_t)((j) + 1) * N)
+#define LAM(k) (lam + (size_t)(k) * N)
+    for (int s = 0; s < nsrc; ++s) {
+        const cplx *Fs = F + (long long)s * N;
+        ora_precond(p, q, mode, Fs, U);
+        double *dre = dj, *dim = dj + N;                       /* Re / Im of U - d at receivers */
+        for (long long i = 0; i < 2 * N; ++i) dj[i] = 0.0;
+        for (int k = 0; k < nrec; ++k) {
+            cplx res = U[rec_idx[k]] - d[(long long)s * nrec + k];
+            J += 0.5 * creal(res * conj(res));
+            dre[rec_idx[k]] += creal(res);
+            dim[rec_idx[k]] += cimag(res);
+        }
+        for (int run = 0; run < runs; ++run) {
+            /* forward: the real run with forcing Re(e^{i theta_j} F) (Table 1), or
+             * Re / Im parts of the complex run of S_T (EXACT, phase e^{-i 2 pi T} = 1) */
+            for (long long i = 0; i < N; ++i) { UST(-1)[i] = 0.0; UST(0)[i] = 0.0; }
+            for (long long j = 0; j < ns; ++j) {
+                double chi = ora_window(1.0 - (double)j / (double)ns, q->rho);
+                double cs = cos(2.0 * ORA_PI * (double)j / q->nP);
+                double sn = sin(2.0 * ORA_PI * (double)j / q->nP);
+                for (long long i = 0; i < N; ++i) {
+                    double fr = creal(Fs[i]), fi = cimag(Fs[i]);
+                    if (run == 1) { double t = fr; fr = fi; fi = -t; }   /* forcing -i F */
+                    f[i] = chi * (cs * fr - sn * fi);
+                }
+                acd_step_real(p, q, UST(j), UST(j - 1), f, UST(j + 1), 1, work);
+            }
+            /* backward: lam_k for k = N .. 1 with -dJ/du_k at the output steps */
+            for (long long i = 0; i < N; ++i) { LAM(ns + 1)[i] = 0.0; LAM(ns + 2)[i] = 0.0; }
+            for (long long k = ns; k >= 1; --k) {
+                for (long long i = 0; i < N; ++i) f[i] = 0.0;
+                if (mode == ORA_MODE_TABLE1) {
+                    if (k == ns) for (long long i = 0; i < N; ++i) f[i] -= dre[i] / c;
+                    if (k == jim) for (long long i = 0; i < N; ++i) f[i] -= dim[i] / c;
+                } else if (k == ns) {
+                    const double *g = (run == 0) ? dre : dim;
+                    for (long long i = 0; i < N; ++i) f[i] = -g[i] / c;
+                }
+                acd_step_real(p, q, LAM(k + 1), LAM(k + 2), f, LAM(k), 1, work);
+                /* term of R_{k-1}: lam_k with u_k, u_{k-1}, u_{k-2} */
+                const double *lk = LAM(k), *uk = UST(k), *uk1 = UST(k - 1), *uk2 = UST(k - 2);
+                for (long long i = 0; i < N; ++i) grad_R[i] += cR * lk[i] * (uk[i] - uk2[i]);
+                long long a3[3], lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+                int d3 = p->ndim;
+                for (int t = 0; t < d3; ++t) { lo[t] = -1; hi[t] = p->n[t] - 1; }
+                int ncorner = 1 << d3;
+                for (a3[0] = lo[0]; a3[0] <= hi[0]; ++a3[0])
+                for (a3[1] = lo[1]; a3[1] <= hi[1]; ++a3[1])
+                for (a3[2] = (d3 == 3 ? lo[2] : 0); a3[2] <= (d3 == 3 ? hi[2] : 0); ++a3[2]) {
+                    long long corner[8];
+                    for (int b = 0; b < ncorner; ++b) {
+                        long long ib[3];
+                        int inside = 1;
+                        for (int t = 0; t < d3; ++t) {
+                            ib[t] = a3[t] + ((b >> (d3 - 1 - t)) & 1);
+                            if (ib[t] < 0 || ib[t] >= p->n[t]) inside = 0;
+                        }
+                        corner[b] = inside ? node_lin(p, ib) : -1;
+                    }
+                    double acc = 0.0;
+                    for (int b = 0; b < ncorner; ++b) {
+                        if (corner[b] < 0) continue;
+                        for (int g = 0; g < ncorner; ++g) {
+                            if (corner[g] < 0) continue;
+                            acc += lk[corner[b]] * M[popcount_small((unsigned)(b ^ g))] * uk1[corner[g]];
+                        }
+                    }
+                    grad_m[cell_lin(p, a3)] += cm * acc;
+                }
+            }
+        }
+    }
+#undef UST
+#undef LAM
+    *misfit = J;
+    free(u); free(lam); free(f); free(work); free(dj); free(U);
     return 0;
 }

@@ -59,3 +59,46 @@ def test_misfit_is_zero_for_exact_data_and_gradient_vanishes():
     d = U[:, rec]
     J, gm, gR = o.grad(F, rec, d)
     assert J < 1e-20 and np.abs(gm).max() < 1e-8 and np.abs(gR).max() < 1e-8
+
+
+# ---- gradient through the recurrence (the preconditioner's own solution) ------
+
+def misfit_td(p, base, F, rec, d, mode, c=None, R=None):
+    """Misfit of the perturbed model with the base model's omega, dt and n_P."""
+    q = W.Problem(p.name, p.ndim, p.n, p.h, p.c_cell if c is None else c,
+                  p.R_node if R is None else R, p.omega, p.F, p.T, p.rho)
+    return oracle.Oracle(q).with_params(base).grad_td(F, rec, d, mode)[0]
+
+
+@pytest.mark.parametrize("ndim,n,mode", [(2, (11, 9), "table1"), (2, (10, 12), "exact"),
+                                         (3, (5, 6, 4), "table1")])
+def test_recurrence_gradient_matches_central_differences(ndim, n, mode):
+    """J = 1/2 sum_s ||P(P F_s) - d_s||^2 with P the preconditioner itself: the
+    reverse-time adjoint recurrence and the K / L derivatives must agree with
+    central differences of the same misfit (recurrence parameters frozen)."""
+    p, F, rec, d = small_setup(ndim, n)
+    base = oracle.Oracle(p)
+    J, gm, gR = base.grad_td(F, rec, d, mode)
+    assert J > 0
+    m = p.c_cell ** -2.0
+    rng = np.random.default_rng(2)
+    for _ in range(3):
+        v = rng.standard_normal(m.shape) * m
+        eps = 1e-5
+        fd = (misfit_td(p, base, F, rec, d, mode, c=(m + eps * v) ** -0.5)
+              - misfit_td(p, base, F, rec, d, mode, c=(m - eps * v) ** -0.5)) / (2 * eps)
+        assert np.sum(gm * v) == pytest.approx(fd, rel=1e-6)
+        w = rng.standard_normal(p.n) * (p.R_node.max() + 1.0)
+        fd = (misfit_td(p, base, F, rec, d, mode, R=p.R_node + eps * w)
+              - misfit_td(p, base, F, rec, d, mode, R=p.R_node - eps * w)) / (2 * eps)
+        assert np.sum(gR * w) == pytest.approx(fd, rel=1e-6)
+
+
+def test_recurrence_misfit_uses_the_preconditioner_output():
+    """J of the recurrence gradient is the misfit of P F (not of H^{-1} F): zero
+    for data taken from P F itself, with a vanishing gradient."""
+    p, F, rec, _ = small_setup(2, (9, 8))
+    o = oracle.Oracle(p)
+    d = np.stack([o.precond(f, "table1").reshape(-1)[rec] for f in F])
+    J, gm, gR = o.grad_td(F, rec, d, "table1")
+    assert J < 1e-24 and np.abs(gm).max() < 1e-10 and np.abs(gR).max() < 1e-10

@@ -285,6 +285,34 @@ htd_status htd_grad(htd_handle h, int nsrc, const void *F_dev, int nrec,
                     htd_solve_info *info);
 
 /*
+ * Misfit of the preconditioner's own approximate solution and its gradient
+ * through the recurrence (reverse-time discrete adjoint with checkpoints; the
+ * paper has no gradient, this differentiates its Table 1 / S_T^acd run):
+ *   J = 1/2 sum_s sum_r |(P F_s)[rec_r] - d_{s,r}|^2,
+ * P = one application of the handle's preconditioner (mode TABLE1 or EXACT).
+ * Each real run of P is the recurrence (1 + L/2) u_{j+1} = (2 - K) u_j -
+ * (1 - L/2) u_{j-1} + g_j (Def. of I_acd); its adjoint is the same recurrence
+ * run backwards in time with -dJ/du_k injected at the read-out steps, and
+ *   dJ/dm_alpha = -(dt^2/alpha) omega_phys^2 sum_k lam_k^T M_alpha u_{k-1},
+ *   dJ/dR_i     = (beta dt omega_phys / (2 alpha omega)) sum_k lam_{k,i} (u_{k,i} - u_{k-2,i}),
+ * with m = c^{-2} per cell, M_alpha the cell mass of App. A, and omega, dt,
+ * n_P held at the handle's values (they are chosen from c at create).
+ *   nsrc, F_dev, nrec, rec_idx_host, d_dev, grad_m_dev, grad_R_dev, misfit:
+ *               as in htd_grad.
+ *   checkpoint_every  C: (u_j, u_{j-1}) are kept every C steps and each
+ *               segment is recomputed once on the way back; 0 chooses
+ *               ceil(sqrt(2 T n_P)).  Device memory 2 ceil(T n_P / C) + C + 6
+ *               state planes (the handle keeps the largest workspace asked).
+ * The states and multipliers are in the handle's recurrence precision (FP32 in
+ * mixed mode), the gradient sums in FP64.  Synchronises the stream.  Errors:
+ * HTD_ERR_ARG (bad sizes or indices, mode PROJECT), HTD_ERR_OOM, HTD_ERR_CUDA,
+ * HTD_ERR_NONFINITE, HTD_ERR_TIMEOUT.
+ */
+htd_status htd_grad_td(htd_handle h, int nsrc, const void *F_dev, int nrec,
+                       const int64_t *rec_idx_host, const void *d_dev, int checkpoint_every,
+                       void *grad_m_dev, void *grad_R_dev, double *misfit, void *stream);
+
+/*
  * Batches.  The paper solves one right-hand side of one problem at a time
  * (Sec. 5); these calls run many independent systems together: several
  * right-hand sides of one handle (sharing its coefficient arrays) and several

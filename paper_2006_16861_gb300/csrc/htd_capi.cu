@@ -173,6 +173,9 @@ struct htd_ctx {
     double2 *gU = nullptr, *gMu = nullptr, *gR = nullptr, *gres = nullptr;
     int64_t *grec = nullptr;
     int grec_cap = 0;
+    // htd_grad_td workspace (checkpoints, segment states, multipliers), grown on demand
+    void *td_ws = nullptr;
+    size_t td_ws_bytes = 0;
     // captured step sequence
     cudaGraph_t graph = nullptr;          // kept for batches (child graph nodes)
     cudaGraphExec_t exec = nullptr;
@@ -215,7 +218,7 @@ void free_ctx(htd_ctx *c)
     void *dev[] = {c->kap, c->dco, c->fre, c->fim, c->u0, c->u1, c->kap64, c->imH, c->coefP, c->V, c->Z,
                    c->w, c->t, c->r, c->partial, c->hdev, c->slot, c->Fh, c->Uh, c->u2, c->u3,
                    c->err_dev, c->gU, c->gMu, c->gR, c->gres, c->grec, c->act_dev,
-                   c->acc};
+                   c->acc, c->td_ws};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (c->hhost) cudaFreeHost(c->hhost);
@@ -731,6 +734,126 @@ htd_status autotune_s3_zchunk(htd_ctx *c)
     c->s3_zchunk = best;
     c->step_us = best_us;
     return HTD_OK;
+}
+
+// Misfit of the preconditioner's own output and its gradient through the
+// recurrence (htd_grad_td).  Per source: U = P F by the handle's fast path for
+// the misfit; then per real run a forward pass of one-step launches that keeps
+// (u_j, u_{j-1}) every C steps, and a backward sweep over the segments from the
+// last: recompute the segment's states from its checkpoint, run the adjoint
+// recurrence (the same step kernel on the multipliers, forcing -dJ/du_k at the
+// read-out steps) and add each step's gradient term.  Memory: 2 ceil(N/C) +
+// C + 6 planes.
+template <typename T>
+htd_status grad_td_impl(htd_ctx *c, int nsrc, const double2 *F, int nrec, const double2 *d,
+                        int ckpt, double *gm, double *gR, double *misfit, cudaStream_t s)
+{
+    const Layout &L = c->Lr;
+    const int64_t N = L.N;
+    const long long ns = c->nsteps;
+    const long long jim = ns - c->nP / 4;
+    const int runs = (c->opt.mode == HTD_MODE_EXACT) ? 2 : 1;
+    const long long C = ckpt > 0 ? std::min<long long>(ckpt, ns)
+                                 : std::max<long long>(1, (long long)std::ceil(std::sqrt(2.0 * ns)));
+    const long long nseg = (ns + C - 1) / C;
+    const size_t plane = sizeof(T) * (size_t)L.total;
+    const size_t nplanes = (size_t)(2 * nseg + C + 2 + 2 + 2);
+    const size_t need = plane * nplanes + sizeof(double2) * (size_t)N;
+    if (need > c->td_ws_bytes) {
+        if (c->td_ws) cudaFree(c->td_ws);
+        c->td_ws = nullptr;
+        c->td_ws_bytes = 0;
+        HTD_CUDA(cudaMalloc(&c->td_ws, need));
+        c->td_ws_bytes = need;
+    }
+    T *base = static_cast<T *>(c->td_ws);
+    auto P = [&](size_t k) { return base + k * (size_t)L.total; };
+    T *ck = P(0);                                   // checkpoint m: planes 2m (u_{mC}), 2m+1 (u_{mC-1})
+    T *seg = P(2 * nseg);                           // u_{s0-2+i} in plane i, i = 0 .. C+1
+    T *lam0 = P(2 * nseg + C + 2), *lam1 = P(2 * nseg + C + 3);
+    T *are = P(2 * nseg + C + 4), *aim = P(2 * nseg + C + 5);
+    double2 *U = reinterpret_cast<double2 *>(P(nplanes));
+    auto seg_of = [&](long long i, long long s0) { return seg + (size_t)(i - s0 + 2) * L.total; };
+    HTD_CUDA(cudaMemsetAsync(c->td_ws, 0, plane * nplanes, s));   // ghost rings stay zero
+    const StepCoef<T> Cf = cast_coef<T>(c->C);
+    const double cK = c->dt * c->dt / c->alpha;
+    const double cm = -cK * c->omega_phys * c->omega_phys;
+    const double cR = c->beta * c->dt / (2.0 * c->alpha * c->omega) * c->omega_phys;
+    const htd::RhsSet one{};
+    std::vector<double2> res(nrec > 0 ? nrec : 1);
+    double J = 0.0;
+    auto step = [&](const T *u, T *um, const T *fre, const T *fim, T a, T b) {
+        htd::launch_step<T>(L, u, um, (const T *)c->kap, (const T *)c->dco, fre, fim, Cf, a, b,
+                            c->slot, 0, s, one);
+    };
+    for (int src = 0; src < nsrc; ++src) {
+        const double2 *Fs = F + (size_t)src * N;
+        htd_status st = precond(c, Fs, U, s);
+        if (st != HTD_OK) return st;
+        HTD_CUDA(cudaMemsetAsync(are, 0, 2 * plane, s));     // are, aim adjacent
+        if (nrec > 0) {
+            htd::launch_residual_planes<T>(L, U, d + (size_t)src * nrec, c->grec, nrec, c->gres,
+                                           are, aim, s);
+            HTD_CUDA(cudaGetLastError());
+            HTD_CUDA(cudaMemcpyAsync(res.data(), c->gres, sizeof(double2) * nrec,
+                                     cudaMemcpyDeviceToHost, s));
+            HTD_CUDA(cudaStreamSynchronize(s));
+            for (int k = 0; k < nrec; ++k) J += 0.5 * (res[k].x * res[k].x + res[k].y * res[k].y);
+        }
+        if (!gm && !gR) continue;
+        for (int run = 0; run < runs; ++run) {
+            // the run's forcing planes (Table 1: F; EXACT run 1: -iF)
+            htd::launch_split<T>(L, Fs, (T *)c->fre, (T *)c->fim, run, s);
+            // forward, keeping (u_j, u_{j-1}) at j = m C
+            T *cur = seg, *oth = seg + L.total;
+            HTD_CUDA(cudaMemsetAsync(seg, 0, 2 * plane, s));
+            for (long long j = 0; j < ns; ++j) {
+                if (j % C == 0) {
+                    const long long m = j / C;
+                    HTD_CUDA(cudaMemcpyAsync(P(2 * m), cur, plane, cudaMemcpyDeviceToDevice, s));
+                    HTD_CUDA(cudaMemcpyAsync(P(2 * m + 1), oth, plane, cudaMemcpyDeviceToDevice, s));
+                }
+                step(cur, oth, (const T *)c->fre, (const T *)c->fim, (T)c->atab[j], (T)c->btab[j]);
+                std::swap(cur, oth);
+            }
+            // backward over the segments [s0, s1], s0 = 1 + m C
+            HTD_CUDA(cudaMemsetAsync(lam0, 0, 2 * plane, s));     // lam_{k+1}, lam_{k+2}
+            T *la = lam0, *lb = lam1;
+            for (long long m = nseg - 1; m >= 0; --m) {
+                const long long s0 = 1 + m * C, s1 = std::min(s0 + C - 1, ns);
+                HTD_CUDA(cudaMemcpyAsync(seg_of(s0 - 2, s0), P(2 * m + 1), plane,
+                                         cudaMemcpyDeviceToDevice, s));
+                HTD_CUDA(cudaMemcpyAsync(seg_of(s0 - 1, s0), P(2 * m), plane,
+                                         cudaMemcpyDeviceToDevice, s));
+                for (long long j = s0 - 1; j < s1; ++j) {
+                    T *dst = seg_of(j + 1, s0);
+                    HTD_CUDA(cudaMemcpyAsync(dst, seg_of(j - 1, s0), plane,
+                                             cudaMemcpyDeviceToDevice, s));
+                    step(seg_of(j, s0), dst, (const T *)c->fre, (const T *)c->fim, (T)c->atab[j],
+                         (T)c->btab[j]);
+                }
+                for (long long k = s1; k >= s0; --k) {
+                    // forcing -dJ/du_k: Table 1 reads Re U at N and Im U at jim; EXACT
+                    // reads Re U (run 0) or Im U (run 1) at N
+                    T a = T(0), b = T(0);
+                    if (runs == 1) {
+                        if (k == ns) a = T(-1);
+                        if (k == jim) b = T(1);
+                    } else if (k == ns) {
+                        if (run == 0) a = T(-1); else b = T(1);
+                    }
+                    step(la, lb, are, aim, a, b);          // lb <- lam_k
+                    std::swap(la, lb);                     // la = lam_k, lb = lam_{k+1}
+                    htd::launch_grad_td<T>(L, c->M, cm, cR, la, seg_of(k, s0), seg_of(k - 1, s0),
+                                           seg_of(k - 2, s0), gm, gR, s);
+                }
+            }
+            HTD_CUDA(cudaGetLastError());
+        }
+    }
+    HTD_CUDA(cudaStreamSynchronize(s));
+    *misfit = J;
+    return std::isfinite(J) ? HTD_OK : HTD_ERR_NONFINITE;
 }
 
 // Host-only validation and parameter selection (Sec. 2.2, App. A).
@@ -1329,6 +1452,51 @@ htd_status htd_grad(htd_handle h, int nsrc, const void *F_dev, int nrec,
     if (!std::isfinite(J) && st == HTD_OK) st = HTD_ERR_NONFINITE;
     *misfit = J;
     if (info) *info = tot;
+    return st;
+}
+
+htd_status htd_grad_td(htd_handle h, int nsrc, const void *F_dev, int nrec,
+                       const int64_t *rec_idx_host, const void *d_dev, int checkpoint_every,
+                       void *grad_m_dev, void *grad_R_dev, double *misfit, void *stream)
+{
+    if (!h || nsrc < 1 || !F_dev || nrec < 0 || !misfit || checkpoint_every < 0)
+        return HTD_ERR_ARG;
+    if (h->opt.mode != HTD_MODE_TABLE1 && h->opt.mode != HTD_MODE_EXACT) return HTD_ERR_ARG;
+    if (nrec > 0 && (!rec_idx_host || !d_dev)) return HTD_ERR_ARG;
+    const int64_t N = h->Lr.N;
+    for (int k = 0; k < nrec; ++k)
+        if (rec_idx_host[k] < 0 || rec_idx_host[k] >= N) return HTD_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (nrec > h->grec_cap) {
+        if (h->gres) cudaFree(h->gres);
+        if (h->grec) cudaFree(h->grec);
+        h->gres = nullptr;
+        h->grec = nullptr;
+        h->grec_cap = 0;
+        HTD_CUDA(cudaMalloc((void **)&h->gres, sizeof(double2) * nrec));
+        HTD_CUDA(cudaMalloc((void **)&h->grec, sizeof(int64_t) * nrec));
+        h->grec_cap = nrec;
+    }
+    if (nrec > 0)
+        HTD_CUDA(cudaMemcpyAsync(h->grec, rec_idx_host, sizeof(int64_t) * nrec,
+                                 cudaMemcpyHostToDevice, s));
+    const int64_t ncell = (h->n[0] + 1) * (h->d >= 2 ? h->n[1] + 1 : 1) * (h->d == 3 ? h->n[2] + 1 : 1);
+    if (grad_m_dev) HTD_CUDA(cudaMemsetAsync(grad_m_dev, 0, sizeof(double) * ncell, s));
+    if (grad_R_dev) HTD_CUDA(cudaMemsetAsync(grad_R_dev, 0, sizeof(double) * N, s));
+    const double2 *F = static_cast<const double2 *>(F_dev);
+    const double2 *d = static_cast<const double2 *>(d_dev);
+    double *gm = static_cast<double *>(grad_m_dev), *gR = static_cast<double *>(grad_R_dev);
+    htd_status st = (h->opt.precision == HTD_MIXED)
+                        ? grad_td_impl<float>(h, nsrc, F, nrec, d, checkpoint_every, gm, gR, misfit, s)
+                        : grad_td_impl<double>(h, nsrc, F, nrec, d, checkpoint_every, gm, gR, misfit, s);
+    if (st == HTD_OK) {
+        int flag = 0;
+        HTD_CUDA(cudaMemcpy(&flag, h->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
+        if (flag) {
+            cudaMemset(h->err_dev, 0, sizeof(int));
+            st = HTD_ERR_TIMEOUT;
+        }
+    }
     return st;
 }
 

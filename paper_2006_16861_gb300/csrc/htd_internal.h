@@ -278,6 +278,18 @@ void launch_stream3d_pair(const Stream3Maps &maps, int from, const Layout &L, fl
                           int flags, int zchunk, int stages, int *err, cudaStream_t s,
                           const RhsSet &R = RhsSet{});
 
+// Gradient through the recurrence (htd_grad_td): res = U[rec] - d and the
+// adjoint forcing planes are/aim (padded, pre-zeroed) += Re/Im res at receivers
+template <typename T>
+void launch_residual_planes(const Layout &L, const double2 *U, const double2 *d,
+                            const int64_t *rec, int nrec, double2 *res, T *are, T *aim,
+                            cudaStream_t s);
+// gm[cell] += cm sum lam_b M u_{k-1,g};  gR[node] += cR lam (u_k - u_{k-2})
+template <typename T>
+void launch_grad_td(const Layout &L, const double M[4], double cm, double cR, const T *lam,
+                    const T *uk, const T *uk1, const T *uk2, double *gm, double *gR,
+                    cudaStream_t s);
+
 // Receiver residual res = U[rec] - d, and r[rec] += conj(res) (r pre-zeroed).
 void launch_receiver_residual(const double2 *U, const double2 *d, const int64_t *rec, int nrec,
                               double2 *res, double2 *r, cudaStream_t s);

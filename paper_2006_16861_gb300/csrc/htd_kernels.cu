@@ -819,6 +819,126 @@ void launch_receiver_residual(const double2 *U, const double2 *d, const int64_t 
     ++g_launches;
 }
 
+// ---- gradient through the recurrence (htd_grad_td) --------------------------
+
+// res[k] = U[rec[k]] - d[k]; adjoint forcing planes (padded, pre-zeroed):
+// are[node(rec)] += Re res, aim[node(rec)] += Im res (receivers may repeat)
+template <typename T>
+__global__ void residual_planes_kernel(Layout L, const double2 *__restrict__ U,
+                                       const double2 *__restrict__ d,
+                                       const int64_t *__restrict__ rec, int nrec,
+                                       double2 *__restrict__ res, T *__restrict__ are,
+                                       T *__restrict__ aim)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nrec) return;
+    const int64_t c = rec[k];
+    const double2 u = U[c], dd = d[k];
+    const double2 r = make_double2(u.x - dd.x, u.y - dd.y);
+    res[k] = r;
+    const int64_t ix = c % L.nx, q = c / L.nx, iy = q % L.ny, iz = q / L.ny;
+    const int64_t i = L.node(ix, iy, iz);
+    atomicAdd(are + i, (T)r.x);
+    atomicAdd(aim + i, (T)r.y);
+}
+
+template <typename T>
+void launch_residual_planes(const Layout &L, const double2 *U, const double2 *d,
+                            const int64_t *rec, int nrec, double2 *res, T *are, T *aim,
+                            cudaStream_t s)
+{
+    if (nrec <= 0) return;
+    const int bs = 256;
+    residual_planes_kernel<T><<<(nrec + bs - 1) / bs, bs, 0, s>>>(L, U, d, rec, nrec, res, are,
+                                                                   aim);
+    ++g_launches;
+}
+template void launch_residual_planes<float>(const Layout &, const double2 *, const double2 *,
+                                            const int64_t *, int, double2 *, float *, float *,
+                                            cudaStream_t);
+template void launch_residual_planes<double>(const Layout &, const double2 *, const double2 *,
+                                             const int64_t *, int, double2 *, double *, double *,
+                                             cudaStream_t);
+
+template <typename T>
+struct TdGradCoef {
+    T M[4];
+    double cm;      // -(dt^2/alpha) omega_phys^2
+    double cR;      // beta dt omega_phys / (2 alpha omega)
+};
+
+// One term of the gradient sum, for the multiplier lam = lam_k and the states
+// u_k, u_{k-1}, u_{k-2} (all padded; the ghost ring is zero):
+//   gm[cell] += cm sum_{b,g corners} lam_b M_{|b-g|} u_{k-1,g}
+//   gR[node] += cR lam (u_k - u_{k-2})
+// One thread per cell (compact (n+1)^d order); the thread of cell a >= 0 also
+// does node a.  Products in the recurrence precision, sums in double.
+template <typename T, int D>
+__global__ void __launch_bounds__(256)
+grad_td_kernel(Layout L, TdGradCoef<T> G, const T *__restrict__ lam, const T *__restrict__ uk,
+               const T *__restrict__ uk1, const T *__restrict__ uk2, double *__restrict__ gm,
+               double *__restrict__ gR)
+{
+    const int64_t cx_n = L.nx + 1, cy_n = L.ny + 1, cz_n = (D == 3) ? L.nz + 1 : 1;
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cx_n * cy_n * cz_n) return;
+    const int64_t ax = c % cx_n - 1;
+    const int64_t rr = c / cx_n;
+    const int64_t ay = rr % cy_n - 1;
+    const int64_t az = (D == 3) ? rr / cy_n - 1 : 0;
+    constexpr int nc = (D == 3) ? 8 : 4;
+    if (gm) {
+        T l8[nc], u8[nc];
+#pragma unroll
+        for (int b = 0; b < nc; ++b) {
+            const int64_t i = L.node(ax + (b & 1), ay + ((b >> 1) & 1), az + ((b >> 2) & 1));
+            l8[b] = lam[i];
+            u8[b] = uk1[i];
+        }
+        T acc = T(0);
+#pragma unroll
+        for (int b = 0; b < nc; ++b) {
+            T row = T(0);
+#pragma unroll
+            for (int g = 0; g < nc; ++g) row += G.M[__popc(b ^ g)] * u8[g];
+            acc += l8[b] * row;
+        }
+        gm[c] += G.cm * (double)acc;
+    }
+    if (gR && ax >= 0 && ay >= 0 && (D == 2 || az >= 0) && ax < L.nx && ay < L.ny &&
+        (D == 2 || az < L.nz)) {
+        const int64_t i = L.node(ax, ay, az);
+        const int64_t n = (az * L.ny + ay) * L.nx + ax;
+        gR[n] += G.cR * (double)(lam[i] * (uk[i] - uk2[i]));
+    }
+}
+
+template <typename T>
+void launch_grad_td(const Layout &L, const double M[4], double cm, double cR, const T *lam,
+                    const T *uk, const T *uk1, const T *uk2, double *gm, double *gR,
+                    cudaStream_t s)
+{
+    TdGradCoef<T> G;
+    for (int k = 0; k < 4; ++k) G.M[k] = (T)M[k];
+    G.cm = cm;
+    G.cR = cR;
+    const int64_t ncell = (L.nx + 1) * (L.ny + 1) * ((L.d == 3) ? L.nz + 1 : 1);
+    const int bs = 256;
+    if (L.d == 3)
+        grad_td_kernel<T, 3><<<(unsigned)((ncell + bs - 1) / bs), bs, 0, s>>>(L, G, lam, uk, uk1,
+                                                                             uk2, gm, gR);
+    else
+        grad_td_kernel<T, 2><<<(unsigned)((ncell + bs - 1) / bs), bs, 0, s>>>(L, G, lam, uk, uk1,
+                                                                             uk2, gm, gR);
+    ++g_launches;
+}
+template void launch_grad_td<float>(const Layout &, const double[4], double, double, const float *,
+                                    const float *, const float *, const float *, double *,
+                                    double *, cudaStream_t);
+template void launch_grad_td<double>(const Layout &, const double[4], double, double,
+                                     const double *, const double *, const double *,
+                                     const double *, double *, double *, cudaStream_t);
+
 struct GradCoef {
     double M[4];
     double w2;      // omega_phys^2

@@ -29,7 +29,7 @@ BC_DIRICHLET = 0
 #: every function include/htd.h declares (checked by the ABI test)
 EXPORTS = ("htd_default_options", "htd_create", "htd_destroy", "htd_plan", "htd_get_params",
            "htd_apply_precond", "htd_apply_H", "htd_residual_norm", "htd_residual_norm_noalloc",
-           "htd_gmres_solve", "htd_grad",
+           "htd_gmres_solve", "htd_grad", "htd_grad_td",
            "htd_gmres_solve_host", "htd_batch_create", "htd_batch_destroy",
            "htd_batch_apply_precond", "htd_batch_gmres_solve", "htd_status_string")
 
@@ -115,6 +115,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.htd_gmres_solve_host.argtypes = [vp, vp, vp, d, i, vp, ctypes.POINTER(SolveInfo)]
     lib.htd_grad.argtypes = [vp, i, vp, i, vp, vp, d, i, vp, vp, ctypes.POINTER(d), vp,
                              ctypes.POINTER(SolveInfo)]
+    lib.htd_grad_td.argtypes = [vp, i, vp, i, vp, vp, i, vp, vp, ctypes.POINTER(d), vp]
     lib.htd_batch_create.argtypes = [i, vp, vp, ctypes.POINTER(vp)]
     lib.htd_batch_destroy.argtypes = [vp]
     lib.htd_batch_apply_precond.argtypes = [vp, vp, vp, vp]
@@ -334,6 +335,29 @@ def htd_batch_gmres_solve(batch: int, Fs, Us, tol: float, max_iters: int, nsys: 
     return out
 
 
+def htd_grad_td(handle: int, F, rec_idx: np.ndarray, d, grad_m=None, grad_R=None,
+                checkpoint_every: int = 0, stream=None) -> float:
+    """Misfit J = 1/2 sum_s ||P(P F_s) - d_s||^2 of the preconditioner's own output and
+    (into grad_m / grad_R, float64 CUDA tensors of the cell / node shapes, if given)
+    its gradient through the recurrence.  F: (nsrc, *n) complex128 CUDA tensor;
+    rec_idx: int64 node indices (host); d: (nsrc, nrec) complex128 CUDA tensor."""
+    import torch
+    nsrc = int(F.shape[0])
+    rec = np.ascontiguousarray(np.asarray(rec_idx, dtype=np.int64).reshape(-1))
+    for g in (grad_m, grad_R):
+        if g is not None and not (isinstance(g, torch.Tensor) and g.is_cuda and
+                                  g.dtype == torch.float64 and g.is_contiguous()):
+            raise TypeError("gradients must be contiguous float64 CUDA tensors")
+    J = ctypes.c_double()
+    st = load().htd_grad_td(handle, nsrc, _dev_ptr(F), int(rec.size), rec.ctypes.data,
+                            _dev_ptr(d) if rec.size else None, int(checkpoint_every),
+                            None if grad_m is None else grad_m.data_ptr(),
+                            None if grad_R is None else grad_R.data_ptr(), ctypes.byref(J),
+                            _stream_ptr(stream))
+    _check(st, "htd_grad_td")
+    return J.value
+
+
 def htd_status_string(status: int) -> str:
     return load().htd_status_string(int(status)).decode()
 
@@ -417,6 +441,17 @@ class Solver:
             gR = torch.empty(self.n, dtype=torch.float64, device="cuda")
         J, info = htd_grad(self.handle, F, rec_idx, d, tol, max_iters, gm, gR, stream)
         return J, gm, gR, info
+
+    def grad_td(self, F, rec_idx, d, checkpoint_every=0, stream=None, want_grad=True):
+        """(J, grad_m, grad_R): misfit of this preconditioner's own output and its
+        gradient through the recurrence w.r.t. c^-2 per cell and R per node."""
+        import torch
+        gm = gR = None
+        if want_grad:
+            gm = torch.empty([m + 1 for m in self.n], dtype=torch.float64, device="cuda")
+            gR = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        J = htd_grad_td(self.handle, F, rec_idx, d, gm, gR, checkpoint_every, stream)
+        return J, gm, gR
 
     def solve(self, F, U=None, tol=1e-6, max_iters=400, stream=None, allow_not_converged=False):
         U = self.zeros() if U is None else U

@@ -25,6 +25,7 @@ STENCILS = {"q1mix": 0, "fd5": 1}
 MODES = {"table1": 0, "exact": 1}
 PRECONDS = {"identity": 0, "table1": 1, "exact": 2, "direct": 3}
 KRYLOV = {"fgmres": 0, "left": 1}
+DAMPING = {"node": 0, "cell": 1}
 
 
 def build(force: bool = False) -> str:
@@ -42,7 +43,8 @@ def build(force: bool = False) -> str:
 class _Problem(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_longlong * 3), ("h", ctypes.c_double),
                 ("stencil", ctypes.c_int), ("c_cell", ctypes.c_void_p),
-                ("R_node", ctypes.c_void_p), ("omega_phys", ctypes.c_double)]
+                ("R_node", ctypes.c_void_p), ("omega_phys", ctypes.c_double),
+                ("damping", ctypes.c_int)]
 
 
 class _Params(ctypes.Structure):
@@ -50,7 +52,8 @@ class _Params(ctypes.Structure):
                 ("omega", ctypes.c_double), ("lam_max_reH", ctypes.c_double),
                 ("lam_max_A", ctypes.c_double), ("nP", ctypes.c_int),
                 ("dt", ctypes.c_double), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
-                ("T", ctypes.c_int), ("rho", ctypes.c_double), ("nsteps", ctypes.c_longlong)]
+                ("T", ctypes.c_int), ("rho", ctypes.c_double), ("nsteps", ctypes.c_longlong),
+                ("integrator", ctypes.c_int), ("lam_max_imH", ctypes.c_double)]
 
 
 class _Info(ctypes.Structure):
@@ -72,6 +75,9 @@ def _load():
         vp = ctypes.c_void_p
         lib.ora_tables.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp]
         lib.ora_setup.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_int, Q]
+        lib.ora_setup_abd.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_int, Q]
+        lib.ora_abd_step.argtypes = [P, Q, vp, vp, vp, vp]
+        lib.ora_apply_imH.argtypes = [P, vp, ctypes.c_longlong, vp]
         lib.ora_apply_reH.argtypes = [P, vp, ctypes.c_longlong, vp]
         lib.ora_apply_H.argtypes = [P, vp, vp]
         lib.ora_assemble_H.argtypes = [P, ctypes.c_longlong, vp, vp, vp, vp]
@@ -102,7 +108,7 @@ class Oracle:
     """One problem bound to the C oracle.  Keeps its input arrays alive."""
 
     def __init__(self, prob, stencil: str = "q1mix", nP: int = 0, T: int | None = None,
-                 rho: float | None = None):
+                 rho: float | None = None, integrator: str = "acd", damping: str = "node"):
         self.lib = _load()
         self.prob = prob
         self.ndim = prob.ndim
@@ -121,11 +127,12 @@ class Oracle:
         p.c_cell = _ptr(self.c)
         p.R_node = _ptr(self.R)
         p.omega_phys = prob.omega
+        p.damping = DAMPING[damping]
         self._p = p
         self.params = _Params()
-        rc = self.lib.ora_setup(ctypes.byref(p), int(prob.T if T is None else T),
-                                float(prob.rho if rho is None else rho), int(nP),
-                                ctypes.byref(self.params))
+        setup = self.lib.ora_setup_abd if integrator == "abd" else self.lib.ora_setup
+        rc = setup(ctypes.byref(p), int(prob.T if T is None else T),
+                   float(prob.rho if rho is None else rho), int(nP), ctypes.byref(self.params))
         if rc != 0:
             raise ValueError(f"oracle setup failed (rc={rc})")
 
@@ -171,6 +178,19 @@ class Oracle:
     # ---- method -----------------------------------------------------------
     def window(self, s: float, rho: float | None = None) -> float:
         return self.lib.ora_window(float(s), float(self.params.rho if rho is None else rho))
+
+    def apply_imH(self, u) -> np.ndarray:
+        u = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(-1))
+        out = np.empty_like(u)
+        self.lib.ora_apply_imH(ctypes.byref(self._p), _ptr(u), 1, _ptr(out))
+        return out.reshape(self.n)
+
+    def abd_step(self, un, unm1, fn) -> np.ndarray:
+        un, unm1, fn = self._c(un), self._c(unm1), self._c(fn)
+        out = np.empty_like(un)
+        self.lib.ora_abd_step(ctypes.byref(self._p), ctypes.byref(self.params),
+                              _ptr(un), _ptr(unm1), _ptr(fn), _ptr(out))
+        return out.reshape(self.n)
 
     def acd_step(self, un, unm1, fn) -> np.ndarray:
         un, unm1, fn = self._c(un), self._c(unm1), self._c(fn)

@@ -31,6 +31,11 @@
  *   ora_window          sine-squared window with parameter rho [Sec. 2.3].
  *   ora_acd_step        one step of I_acd [Def. of I_acd, Eq. acd_integrator,
  *                       Eq. K_L_frequency_adapted_central_differences].
+ *   ora_setup_abd /
+ *   ora_abd_step        parameters [Sec. 6.1] and one step of I_abd [Def. of
+ *                       I_abd, Eq. K_L_frequency_adapted_backward_differences],
+ *                       explicit also for non-diagonal damping (damping per
+ *                       cell with the cell mass: ORA_DAMP_CELL).
  *   ora_precond         Table 1 (TimeDomainPreconditioner, real fields) and the
  *                       exact operator S_T^acd [Def. approx_solver] as a complex
  *                       recurrence.
@@ -70,6 +75,8 @@ enum { ORA_Q1MIX = 0, ORA_FD5 = 1 };
 enum { ORA_MODE_TABLE1 = 0, ORA_MODE_EXACT = 1 };
 enum { ORA_P_IDENTITY = 0, ORA_P_TABLE1 = 1, ORA_P_EXACT = 2, ORA_P_DIRECT = 3 };
 enum { ORA_FGMRES = 0, ORA_LEFT_GMRES = 1 };
+enum { ORA_DAMP_NODE = 0, ORA_DAMP_CELL = 1 };
+enum { ORA_ACD = 0, ORA_ABD = 1 };
 
 typedef struct {
     int ndim;            /* 2 or 3 */
@@ -79,6 +86,10 @@ typedef struct {
     const double *c_cell;  /* wave speed per cell, prod(n_a + 1) */
     const double *R_node;  /* damping per node, prod(n_a), >= 0 */
     double omega_phys;   /* physical angular frequency */
+    int damping;         /* ORA_DAMP_NODE: (Im H)_ii = omega_phys R_i (diagonal);
+                            ORA_DAMP_CELL: Im H = omega_phys sum over cells of
+                            R_cell times the cell mass M (non-diagonal), R_cell
+                            the mean of R over the cell's grid corners */
 } ora_problem;
 
 typedef struct {
@@ -91,6 +102,8 @@ typedef struct {
     int T;                      /* periods */
     double rho;                 /* window parameter actually used */
     long long nsteps;           /* T * nP */
+    int integrator;             /* ORA_ACD (Def. of I_acd) or ORA_ABD (Def. of I_abd) */
+    double lam_max_imH;         /* upper bound for lambda_max(Im H) */
 } ora_params;
 
 typedef struct {
@@ -278,6 +291,59 @@ int ora_setup(const ora_problem *p, int T, double rho, int nP_req, ora_params *o
     /* rho = 0 in the paper's experiments meant a ramp over one period (Sec. 5.1) */
     out->rho = (rho <= 0.0) ? 1.0 / T : rho;
     out->nsteps = (long long)T * nP;
+    out->integrator = ORA_ACD;
+    out->lam_max_imH = 0.0;
+    for (long long i = 0; i < n_nodes(p); ++i)
+        if (p->omega_phys * p->R_node[i] > out->lam_max_imH) out->lam_max_imH = p->omega_phys * p->R_node[i];
+    return 0;
+}
+
+/*
+ * Parameters of the frequency-adapted backward-differences scheme (Sec. 6.1,
+ * Def. of I_abd).  With theta = omega dt = 2 pi / n_P:
+ *   omega^2 = -lambda_min(Re H) + (beta / theta)(1 - cos theta) lambda_max(Im H)
+ * (K positive semidefinite; -lambda_min(Re H) <= k_max^2 by the App. A bound,
+ * lambda_max(Im H) <= omega_phys max R), and n_P the smallest multiple of 4 with
+ *   (theta^2 / alpha)(lambda_max(Re H) / omega^2 + 1)
+ *     + (beta / alpha)(1 + cos theta) lambda_max(Im H) / omega^2 < 4
+ * (4 I - K - 2 L positive definite).  alpha, beta as for I_acd.
+ */
+static int abd_ok(double theta, double lam_reH, double lam_imH, double kmax2, double *omega2)
+{
+    double a = theta * theta / (4.0 * sin(0.5 * theta) * sin(0.5 * theta));
+    double b = theta / sin(theta);
+    double w2 = kmax2 + b / theta * (1.0 - cos(theta)) * lam_imH;
+    *omega2 = w2;
+    double lhs = theta * theta / a * (lam_reH / w2 + 1.0) + b / a * (1.0 + cos(theta)) * lam_imH / w2;
+    return lhs < 4.0;
+}
+
+int ora_setup_abd(const ora_problem *p, int T, double rho, int nP_req, ora_params *out)
+{
+    ora_params q;
+    int rc = ora_setup(p, T, rho, 0, &q);    /* k range, lambda bounds, window */
+    if (rc) return rc;
+    double kmax2 = q.k_max * q.k_max, w2 = 0.0;
+    int nP = 0;
+    if (nP_req > 0) {
+        if (nP_req % 4) return -2;
+        if (!abd_ok(2.0 * ORA_PI / nP_req, q.lam_max_reH, q.lam_max_imH, kmax2, &w2)) return -2;
+        nP = nP_req;
+    } else {
+        for (int c = 4; c < 1 << 20; c += 4)
+            if (abd_ok(2.0 * ORA_PI / c, q.lam_max_reH, q.lam_max_imH, kmax2, &w2)) { nP = c; break; }
+        if (!nP) return -1;
+    }
+    double theta = 2.0 * ORA_PI / nP;
+    q.omega = sqrt(w2);
+    q.lam_max_A = q.lam_max_reH + w2;
+    q.nP = nP;
+    q.dt = theta / q.omega;
+    q.alpha = theta * theta / (4.0 * sin(0.5 * theta) * sin(0.5 * theta));
+    q.beta = theta / sin(theta);
+    q.nsteps = (long long)T * nP;
+    q.integrator = ORA_ABD;
+    *out = q;
     return 0;
 }
 
@@ -336,6 +402,72 @@ void ora_apply_reH(const ora_problem *p, const double *u, long long stride, doub
 }
 
 /* out = H U = Re H U + i (omega_phys R) U, complex vectors */
+/* R of a cell for ORA_DAMP_CELL: the mean of R over the cell's corners inside
+ * the grid (every cell has at least one) */
+static double cell_R(const ora_problem *p, const long long *a3)
+{
+    int d = p->ndim;
+    double sum = 0.0;
+    int cnt = 0;
+    for (int b = 0; b < (1 << d); ++b) {
+        long long ib[3];
+        int inside = 1;
+        for (int t = 0; t < d; ++t) {
+            ib[t] = a3[t] + ((b >> (d - 1 - t)) & 1);
+            if (ib[t] < 0 || ib[t] >= p->n[t]) inside = 0;
+        }
+        if (inside) { sum += p->R_node[node_lin(p, ib)]; ++cnt; }
+    }
+    return sum / cnt;
+}
+
+/*
+ * out = Im H u (real field, element stride `stride`).  ORA_DAMP_NODE:
+ * omega_phys R_i u_i.  ORA_DAMP_CELL: the cell loop of App. A with the mass
+ * weights only, R_cell in place of kappa:
+ *   (Im H u)_beta = omega_phys sum_{cells alpha containing beta}
+ *                   R_alpha sum_{corners gamma} M_{Delta(beta,gamma)} u_gamma.
+ * The mass row sums are 1, so for constant R both forms agree on constants.
+ */
+void ora_apply_imH(const ora_problem *p, const double *u, long long stride, double *out)
+{
+    long long N = n_nodes(p);
+    if (p->damping != ORA_DAMP_CELL) {
+        for (long long i = 0; i < N; ++i) out[i * stride] = p->omega_phys * p->R_node[i] * u[i * stride];
+        return;
+    }
+    double S[4], M[4];
+    ora_tables(p->ndim, p->stencil, S, M);
+    int d = p->ndim;
+    for (long long i = 0; i < N; ++i) out[i * stride] = 0.0;
+    long long lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int a = 0; a < d; ++a) { lo[a] = -1; hi[a] = p->n[a] - 1; }
+    long long a3[3];
+    int ncorner = 1 << d;
+    for (a3[0] = lo[0]; a3[0] <= hi[0]; ++a3[0])
+    for (a3[1] = lo[1]; a3[1] <= hi[1]; ++a3[1])
+    for (a3[2] = (d == 3 ? lo[2] : 0); a3[2] <= (d == 3 ? hi[2] : 0); ++a3[2]) {
+        double r = p->omega_phys * cell_R(p, a3);
+        long long corner[8];
+        for (int b = 0; b < ncorner; ++b) {
+            long long ib[3];
+            int inside = 1;
+            for (int t = 0; t < d; ++t) {
+                ib[t] = a3[t] + ((b >> (d - 1 - t)) & 1);
+                if (ib[t] < 0 || ib[t] >= p->n[t]) inside = 0;
+            }
+            corner[b] = inside ? node_lin(p, ib) : -1;
+        }
+        for (int b = 0; b < ncorner; ++b) {
+            if (corner[b] < 0) continue;
+            double acc = 0.0;
+            for (int g = 0; g < ncorner; ++g)
+                if (corner[g] >= 0) acc += M[popcount_small((unsigned)(b ^ g))] * u[corner[g] * stride];
+            out[corner[b] * stride] += r * acc;
+        }
+    }
+}
+
 void ora_apply_H(const ora_problem *p, const cplx *U, cplx *out)
 {
     long long N = n_nodes(p);
@@ -343,8 +475,11 @@ void ora_apply_H(const ora_problem *p, const cplx *U, cplx *out)
     double *Od = (double *)out;
     ora_apply_reH(p, Ud, 2, Od);          /* real parts */
     ora_apply_reH(p, Ud + 1, 2, Od + 1);  /* imaginary parts */
-    for (long long i = 0; i < N; ++i)
-        out[i] += I * (p->omega_phys * p->R_node[i]) * U[i];
+    double *t = malloc(sizeof(double) * 2 * N);   /* interleaved: Im H Re U, Im H Im U */
+    ora_apply_imH(p, Ud, 2, t);
+    ora_apply_imH(p, Ud + 1, 2, t + 1);
+    for (long long i = 0; i < N; ++i) out[i] += -t[2 * i + 1] + I * t[2 * i];
+    free(t);
 }
 
 /*
@@ -384,12 +519,13 @@ long long ora_assemble_H(const ora_problem *p, long long cap, long long *rows,
                 rows[cnt] = node_lin(p, ib);
                 cols[cnt] = node_lin(p, ig);
                 re[cnt] = ih2 * (S[s] - kap * M[s]);
-                im[cnt] = 0.0;
+                im[cnt] = (p->damping == ORA_DAMP_CELL) ? p->omega_phys * cell_R(p, a3) * M[s] : 0.0;
             }
             ++cnt;
         }
     }
     long long N = n_nodes(p);
+    if (p->damping == ORA_DAMP_CELL) return cnt;
     for (long long i = 0; i < N; ++i) {
         if (cnt < cap) {
             rows[cnt] = i; cols[cnt] = i; re[cnt] = 0.0;
@@ -448,6 +584,55 @@ static void acd_step_real(const ora_problem *p, const ora_params *q,
     }
 }
 
+/*
+ * One step of frequency-adapted backward-differences damped leapfrog
+ * (Def. of I_abd), explicit for any symmetric B:
+ *   u_{n+1} = (2 - K - L) u_n - (I - L) u_{n-1} + g_n,
+ *   K = (dt^2/alpha) A - (dt beta (1 - cos(omega dt)) / alpha) B,
+ *   L = (beta dt / alpha) B,  A = Re H + omega^2 I,  B = omega^{-1} Im H,
+ *   g_n = (dt^2/alpha) f_n.
+ * Real fields with element stride `stride`; `work` holds 3 N stride doubles.
+ */
+static void abd_step_real(const ora_problem *p, const ora_params *q,
+                          const double *un, const double *unm1, const double *fn,
+                          double *unp1, long long stride, double *work)
+{
+    long long N = n_nodes(p);
+    double cA = q->dt * q->dt / q->alpha;
+    double cBK = q->dt * q->beta * (1.0 - cos(q->omega * q->dt)) / q->alpha / q->omega;
+    double cBL = q->beta * q->dt / q->alpha / q->omega;
+    double *reH = work, *imHu = work + N * stride, *imHp = work + 2 * N * stride;
+    ora_apply_reH(p, un, stride, reH);
+    ora_apply_imH(p, un, stride, imHu);
+    ora_apply_imH(p, unm1, stride, imHp);
+    for (long long i = 0; i < N; ++i) {
+        double u = un[i * stride], up = unm1[i * stride];
+        double Ku = cA * (reH[i * stride] + q->omega * q->omega * u) - cBK * imHu[i * stride];
+        double Lu = cBL * imHu[i * stride], Lup = cBL * imHp[i * stride];
+        unp1[i * stride] = 2.0 * u - Ku - Lu - (up - Lup) + cA * fn[i * stride];
+    }
+}
+
+void ora_abd_step(const ora_problem *p, const ora_params *q, const cplx *un,
+                  const cplx *unm1, const cplx *fn, cplx *unp1)
+{
+    long long N = n_nodes(p);
+    double *work = (double *)malloc(sizeof(double) * 6 * N);
+    for (int part = 0; part < 2; ++part)
+        abd_step_real(p, q, (const double *)un + part, (const double *)unm1 + part,
+                      (const double *)fn + part, (double *)unp1 + part, 2, work + part);
+    free(work);
+}
+
+/* the step of the parameters' integrator */
+static void any_step_real(const ora_problem *p, const ora_params *q,
+                          const double *un, const double *unm1, const double *fn,
+                          double *unp1, long long stride, double *work)
+{
+    if (q->integrator == ORA_ABD) abd_step_real(p, q, un, unm1, fn, unp1, stride, work);
+    else acd_step_real(p, q, un, unm1, fn, unp1, stride, work);
+}
+
 /* complex step: real and imaginary parts stepped separately (K, L real) */
 void ora_acd_step(const ora_problem *p, const ora_params *q, const cplx *un,
                   const cplx *unm1, const cplx *fn, cplx *unp1)
@@ -482,14 +667,14 @@ static void precond_table1(const ora_problem *p, const ora_params *q, const cplx
     double *u1 = calloc(N, sizeof(double));
     double *f = malloc(sizeof(double) * N);
     double *snap = calloc(N, sizeof(double));
-    double *work = malloc(sizeof(double) * N);
+    double *work = malloc(sizeof(double) * 3 * N);
     for (long long j = 0; j < nsteps; ++j) {
         double chi = ora_window(1.0 - (double)j / (double)nsteps, q->rho);
         double cs = cos(2.0 * ORA_PI * (double)j / q->nP);
         double sn = sin(2.0 * ORA_PI * (double)j / q->nP);
         for (long long i = 0; i < N; ++i)
             f[i] = chi * (cs * creal(F[i]) - sn * cimag(F[i]));
-        acd_step_real(p, q, u0, um1, f, u1, 1, work);
+        any_step_real(p, q, u0, um1, f, u1, 1, work);
         if (j + 1 == j_im) memcpy(snap, u1, sizeof(double) * N);
         double *t = um1; um1 = u0; u0 = u1; u1 = t;
     }
@@ -510,7 +695,7 @@ static void precond_exact(const ora_problem *p, const ora_params *q, const cplx 
     cplx *u0 = calloc(N, sizeof(cplx));
     cplx *u1 = calloc(N, sizeof(cplx));
     cplx *f = malloc(sizeof(cplx) * N);
-    double *work = malloc(sizeof(double) * 2 * N);
+    double *work = malloc(sizeof(double) * 6 * N);
     double Ttilde = 2.0 * ORA_PI * q->T / q->omega;
     for (long long n = 0; n < nsteps; ++n) {
         double t = n * q->dt;
@@ -518,7 +703,7 @@ static void precond_exact(const ora_problem *p, const ora_params *q, const cplx 
         double chi = ora_window(1.0 - t / Ttilde, q->rho);
         for (long long i = 0; i < N; ++i) f[i] = chi * e * F[i];
         for (int part = 0; part < 2; ++part)
-            acd_step_real(p, q, (const double *)u0 + part, (const double *)um1 + part,
+            any_step_real(p, q, (const double *)u0 + part, (const double *)um1 + part,
                           (const double *)f + part, (double *)u1 + part, 2, work + part);
         cplx *tmp = um1; um1 = u0; u0 = u1; u1 = tmp;
     }
@@ -560,6 +745,7 @@ int ora_precond_project(const ora_problem *p, const ora_params *q, int periods, 
                         cplx *U)
 {
     if (periods < 1 || periods > q->T) return -1;
+    if (q->integrator == ORA_ACD && p->damping == ORA_DAMP_CELL) return -1;
     long long N = n_nodes(p);
     long long nsteps = q->nsteps;
     long long n_acc = (long long)periods * q->nP;
@@ -567,7 +753,7 @@ int ora_precond_project(const ora_problem *p, const ora_params *q, int periods, 
     double *u0 = calloc(N, sizeof(double));
     double *u1 = calloc(N, sizeof(double));
     double *f = malloc(sizeof(double) * N);
-    double *work = malloc(sizeof(double) * N);
+    double *work = malloc(sizeof(double) * 3 * N);
     for (long long i = 0; i < N; ++i) U[i] = 0.0;
     for (long long j = 0; j < nsteps; ++j) {
         double chi = ora_window(1.0 - (double)j / (double)nsteps, q->rho);
@@ -575,7 +761,7 @@ int ora_precond_project(const ora_problem *p, const ora_params *q, int periods, 
         double sn = sin(2.0 * ORA_PI * (double)j / q->nP);
         for (long long i = 0; i < N; ++i)
             f[i] = chi * (cs * creal(F[i]) - sn * cimag(F[i]));
-        acd_step_real(p, q, u0, um1, f, u1, 1, work);
+        any_step_real(p, q, u0, um1, f, u1, 1, work);
         if (j + 1 > nsteps - n_acc) project_add(N, q->nP, j + 1, u1, U);   /* state u_{j+1} */
         double *t = um1; um1 = u0; u0 = u1; u1 = t;
     }
@@ -586,6 +772,8 @@ int ora_precond_project(const ora_problem *p, const ora_params *q, int periods, 
 
 int ora_precond(const ora_problem *p, const ora_params *q, int mode, const cplx *F, cplx *U)
 {
+    /* I_acd inverts I + L/2, which is only explicit for diagonal damping */
+    if (q->integrator == ORA_ACD && p->damping == ORA_DAMP_CELL) return -1;
     if (mode == ORA_MODE_TABLE1) precond_table1(p, q, F, U);
     else if (mode == ORA_MODE_EXACT) precond_exact(p, q, F, U);
     else return -1;
@@ -951,6 +1139,7 @@ int ora_grad_td(const ora_problem *p, const ora_params *q, int mode, int nsrc, c
                 double *misfit)
 {
     if (mode != ORA_MODE_TABLE1 && mode != ORA_MODE_EXACT) return -1;
+    if (q->integrator != ORA_ACD || p->damping != ORA_DAMP_NODE) return -1;
     long long N = n_nodes(p), Nc = n_cells(p);
     long long ns = q->nsteps;
     long long jim = ns - q->nP / 4;

@@ -55,6 +55,8 @@ typedef enum {
 
 enum { HTD_FP64 = 0, HTD_MIXED = 1 };            /* recurrence precision */
 enum { HTD_MODE_TABLE1 = 0, HTD_MODE_EXACT = 1, HTD_MODE_PROJECT = 2 }; /* preconditioner form */
+enum { HTD_ACD = 0, HTD_ABD = 1 };               /* time integrator */
+enum { HTD_DAMP_NODE = 0, HTD_DAMP_CELL = 1 };   /* form of Im H */
 enum { HTD_FGMRES = 0, HTD_LEFT_GMRES = 1 };     /* Krylov method */
 enum { HTD_STENCIL_Q1MIX = 0, HTD_STENCIL_FD5 = 1 };
 enum { HTD_BC_DIRICHLET = 0 };
@@ -92,6 +94,17 @@ typedef struct {
                           allocated max_rhs times */
     int proj_periods;  /* HTD_MODE_PROJECT: whole periods projected, 1..T; 0
                           means 1.  Adds four planes per right-hand side */
+    int integrator;    /* HTD_ACD: frequency-adapted central differences
+                          (Def. of I_acd, default).  HTD_ABD: frequency-adapted
+                          backward differences (Def. of I_abd, Sec. 6), explicit
+                          also for non-diagonal damping, with its omega and n_P
+                          from Sec. 6.1 (stricter: it needs lambda_max(Im H)
+                          below about 2 k_max^2) */
+    int damping;       /* HTD_DAMP_NODE: (Im H)_ii = omega_phys R_i (Eq. damped
+                          Helmholtz equation, diagonal).  HTD_DAMP_CELL: Im H =
+                          omega_phys sum over cells of R_cell times the cell mass
+                          of App. A (non-diagonal; R_cell the mean of R over the
+                          cell's grid corners); needs HTD_ABD */
 } htd_options;
 
 typedef struct {
@@ -111,7 +124,8 @@ typedef struct {
 } htd_solve_info;
 
 /* Fill *opt with the defaults: FP64, TABLE1, FGMRES, T = 10, rho = 0.25,
- * nP = 0 (automatic), Q1MIX stencil, restart 20, max_rhs 1, proj_periods 1. */
+ * nP = 0 (automatic), Q1MIX stencil, restart 20, max_rhs 1, proj_periods 1,
+ * HTD_ACD, HTD_DAMP_NODE. */
 void htd_default_options(htd_options *opt);
 
 /*
@@ -141,7 +155,8 @@ htd_status htd_destroy(htd_handle h);
 /* Parameters selected for a problem (see htd_plan). */
 typedef struct {
     double k_min, k_max;     /* min / max of omega_phys / c over cells */
-    double omega_c;          /* computational omega (= k_max, App. A bound) */
+    double omega_c;          /* computational omega (= k_max, App. A bound; with
+                                HTD_ABD the Sec. 6.1 value, above k_max) */
     double lam_max_reH;      /* upper bound for lambda_max(Re H) */
     double lam_max_A;        /* lam_max_reH + omega_c^2 */
     double dt, alpha, beta;  /* time step, Eq. define_alpha_beta */
@@ -159,7 +174,8 @@ typedef struct {
     int waves;               /* waves of CTAs per launch of that kernel */
     int step_kernel;         /* recurrence kernel in use: 0 one step per launch
                                 (gather / z-march), 1 temporally blocked 2-D
-                                (TMA tiles), 2 TMA-streamed 3-D; -1 in htd_plan */
+                                (TMA tiles), 2 TMA-streamed 3-D, 3 one-step
+                                backward differences (HTD_ABD); -1 in htd_plan */
 } htd_params;
 
 /*

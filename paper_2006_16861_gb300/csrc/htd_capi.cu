@@ -142,6 +142,7 @@ struct htd_ctx {
     // FP64 operator data
     double *kap64 = nullptr, *imH = nullptr;
     double *coefP = nullptr;    // assembled operator, h_planes(d) planes of N
+    double *coefI = nullptr;    // assembled Im H (cell damping only), same layout
     // Krylov workspace
     int m = 20;
     double2 *V = nullptr, *Z = nullptr, *w = nullptr, *t = nullptr, *r = nullptr;
@@ -215,7 +216,7 @@ void free_ctx(htd_ctx *c)
     if (c->graph) cudaGraphDestroy(c->graph);
     for (cudaEvent_t e : c->pev)
         if (e) cudaEventDestroy(e);
-    void *dev[] = {c->kap, c->dco, c->fre, c->fim, c->u0, c->u1, c->kap64, c->imH, c->coefP, c->V, c->Z,
+    void *dev[] = {c->kap, c->dco, c->fre, c->fim, c->u0, c->u1, c->kap64, c->imH, c->coefP, c->coefI, c->V, c->Z,
                    c->w, c->t, c->r, c->partial, c->hdev, c->slot, c->Fh, c->Uh, c->u2, c->u3,
                    c->err_dev, c->gU, c->gMu, c->gR, c->gres, c->grec, c->act_dev,
                    c->acc, c->td_ws};
@@ -269,6 +270,29 @@ htd_status run_steps_direct(htd_ctx *c, cudaStream_t s)
             std::swap(cur, oth);
         }
     };
+    if (c->opt.integrator == HTD_ABD) {
+        // backward differences: u_{j+1} into a third plane (the cell-damping term
+        // reads u_{j-1} at the neighbours)
+        T *cur = A, *prv = B, *nxt = (T *)c->u2;
+        const T cth = (T)std::cos(2.0 * kPi / (double)c->nP);
+        const bool cell = c->opt.damping == HTD_DAMP_CELL;
+        for (long long j = 0; j < c->nsteps; ++j) {
+            int flags = 0;
+            if (j + 1 == jim) flags |= 1;
+            if (j + 1 == jfin) flags |= 2;
+            htd::launch_abd_step<T>(L, cur, prv, nxt, (const T *)c->kap, (const T *)c->dco, cell,
+                                    (const T *)c->fre, (const T *)c->fim, C, (T)c->atab[j],
+                                    (T)c->btab[j], cth, c->slot, flags, s, c->Rs);
+            if (project && j >= j_acc) accumulate(j, nxt);
+            T *t = prv;
+            prv = cur;
+            cur = nxt;
+            nxt = t;
+        }
+        if (project) finish();
+        HTD_CUDA(cudaGetLastError());
+        return HTD_OK;
+    }
     if constexpr (std::is_same<T, float>::value) {
       if (c->use_tb) {
         // B steps per launch; the state pair alternates between (u0,u1) and (u2,u3)
@@ -428,7 +452,7 @@ htd_status precond(htd_ctx *c, const double2 *F, double2 *U, cudaStream_t s)
 
 void apply_H(htd_ctx *c, const double2 *X, const double2 *F, double2 *Y, cudaStream_t s)
 {
-    htd::launch_apply_H(c->L64, c->coefP, c->imH, 1.0 / (c->h * c->h), X, F, Y, s);
+    htd::launch_apply_H(c->L64, c->coefP, c->imH, 1.0 / (c->h * c->h), X, F, Y, s, c->coefI);
 }
 
 // dots of w with V_0..V_{k-1} into hdev + off (device); does not synchronise
@@ -886,6 +910,10 @@ htd_status plan_impl(const htd_grid *grid, const double *c_cell, const double *R
     if (opt.max_rhs < 1 || opt.max_rhs > htd::kMaxRhs) return HTD_ERR_ARG;
     if (opt.proj_periods == 0) opt.proj_periods = 1;
     if (opt.proj_periods < 1 || opt.proj_periods > opt.T) return HTD_ERR_ARG;
+    if (opt.integrator != HTD_ACD && opt.integrator != HTD_ABD) return HTD_ERR_ARG;
+    if (opt.damping != HTD_DAMP_NODE && opt.damping != HTD_DAMP_CELL) return HTD_ERR_ARG;
+    // I_acd inverts I + L/2: explicit only for diagonal damping (Sec. 6)
+    if (opt.integrator == HTD_ACD && opt.damping == HTD_DAMP_CELL) return HTD_ERR_ARG;
     const int d = grid->ndim;
     pl->d = d;
     pl->N = 1;
@@ -910,9 +938,11 @@ htd_status plan_impl(const htd_grid *grid, const double *c_cell, const double *R
         kmin = std::fmin(kmin, k);
         kmax = std::fmax(kmax, k);
     }
+    double rmax = 0.0;
     for (int64_t i = 0; i < pl->N; ++i) {
         if (!std::isfinite(R_node[i])) return HTD_ERR_NONFINITE;
         if (R_node[i] < 0.0) return HTD_ERR_ARG;
+        rmax = std::fmax(rmax, R_node[i]);
     }
     htd_params &P = pl->p;
     P.k_min = kmin;
@@ -927,7 +957,33 @@ htd_status plan_impl(const htd_grid *grid, const double *c_cell, const double *R
     P.lam_max_A = P.lam_max_reH + P.omega_c * P.omega_c;
     const double ratio = P.omega_c * P.omega_c / P.lam_max_A;
     int nP = 0;
-    if (opt.nP > 0) {
+    if (opt.integrator == HTD_ABD) {
+        // Sec. 6.1: theta = omega dt = 2 pi / n_P; omega^2 = k_max^2 + (beta/theta)
+        // (1 - cos theta) lambda_max(Im H) makes K >= 0 (App. A: -lambda_min(Re H)
+        // <= k_max^2; lambda_max(Im H) <= omega_phys max R for either damping
+        // form); n_P is the smallest multiple of 4 with 4 I - K - 2 L > 0 by
+        // the scalar bound of Eq. Deltat_bd_full_inequality.
+        const double lam_im = omega_phys * rmax;
+        auto ok = [&](int q, double *w2) {
+            const double th = 2.0 * kPi / q;
+            const double al = th * th / (2.0 - 2.0 * std::cos(th)), be = th / std::sin(th);
+            *w2 = kmax * kmax + be / th * (1.0 - std::cos(th)) * lam_im;
+            const double lhs = th * th / al * (P.lam_max_reH / *w2 + 1.0) +
+                               be / al * (1.0 + std::cos(th)) * lam_im / *w2;
+            return lhs < 4.0;
+        };
+        double w2 = 0.0;
+        if (opt.nP > 0) {
+            if (opt.nP % 4 != 0 || !ok(opt.nP, &w2)) return HTD_ERR_UNSTABLE;
+            nP = opt.nP;
+        } else {
+            for (int q = 4; q < (1 << 20) && !nP; q += 4)
+                if (ok(q, &w2)) nP = q;
+            if (!nP) return HTD_ERR_UNSTABLE;
+        }
+        P.omega_c = std::sqrt(w2);
+        P.lam_max_A = P.lam_max_reH + w2;
+    } else if (opt.nP > 0) {
         const double sv = std::sin(kPi / opt.nP);
         if (opt.nP % 4 != 0 || !(sv * sv < ratio)) return HTD_ERR_UNSTABLE;
         nP = opt.nP;
@@ -1004,6 +1060,8 @@ htd_status create_impl(const htd_grid *grid, const double *c_cell, const double 
 
     // ---- layouts and device memory ----------------------------------------
     const bool mixed = opt.precision == HTD_MIXED;
+    const bool abd = opt.integrator == HTD_ABD;
+    const bool cell_damp = opt.damping == HTD_DAMP_CELL;
     c->esz = mixed ? sizeof(float) : sizeof(double);
     c->Lr = make_layout(d, c->n, c->esz);
     c->L64 = make_layout(d, c->n, sizeof(double));
@@ -1026,6 +1084,10 @@ htd_status create_impl(const htd_grid *grid, const double *c_cell, const double 
     HTD_CUDA(cudaMemset(c->slot, 0, sizeof(OutSlot) * c->rcap));
     if (opt.mode == HTD_MODE_PROJECT)
         HTD_CUDA(cudaMalloc(&c->acc, c->esz * 4 * (size_t)N * c->rcap));
+    if (abd) {                                     // third state plane of I_abd
+        HTD_CUDA(cudaMalloc(&c->u2, bytes * c->rcap));
+        HTD_CUDA(cudaMemset(c->u2, 0, bytes * c->rcap));
+    }
     HTD_CUDA(cudaMalloc((void **)&c->act_dev, sizeof(int) * (1 + c->rcap)));
     HTD_CUDA(cudaMemset(c->act_dev, 0, sizeof(int) * (1 + c->rcap)));
     c->Rs.act = c->act_dev;
@@ -1055,8 +1117,35 @@ htd_status create_impl(const htd_grid *grid, const double *c_cell, const double 
                 const int64_t ci = (iz * ny + iy) * nx + ix;
                 const double ih = omega_phys * R_node[ci];
                 imh[ci] = ih;
-                dc[L.node(ix, iy, iz)] = 1.0 / (1.0 + 0.5 * lcoef * ih);
+                // I_acd: d = 1 / (1 + L_ii/2); I_abd with node damping: the damping
+                // coefficient beta dt omega_phys R_i / (alpha omega) (abd_step_kernel)
+                dc[L.node(ix, iy, iz)] = abd ? lcoef * ih : 1.0 / (1.0 + 0.5 * lcoef * ih);
             }
+    std::vector<double> rc64;                      // omega_phys R_cell (cell damping)
+    if (cell_damp) {
+        // R_cell = mean of R over the cell's grid corners; the coefficient goes to
+        // the cell's stored position (like q kappa), Im H is assembled from it
+        std::fill(dc.begin(), dc.end(), 0.0);
+        std::fill(imh.begin(), imh.end(), 0.0);    // no diagonal part
+        rc64.assign(c->L64.total, 0.0);
+        for (int64_t az = (d == 3 ? -1 : 0); az < (d == 3 ? nz : 1); ++az)
+            for (int64_t ay = -1; ay < ny; ++ay)
+                for (int64_t ax = -1; ax < nx; ++ax) {
+                    double sum = 0.0;
+                    int cnt = 0;
+                    for (int bz = 0; bz < (d == 3 ? 2 : 1); ++bz)
+                        for (int by = 0; by < 2; ++by)
+                            for (int bx = 0; bx < 2; ++bx) {
+                                const int64_t x = ax + bx, y = ay + by, z = (d == 3) ? az + bz : 0;
+                                if (x < 0 || x >= nx || y < 0 || y >= ny || z < 0 || z >= nz) continue;
+                                sum += R_node[(z * ny + y) * nx + x];
+                                ++cnt;
+                            }
+                    const double rcell = sum / cnt;
+                    dc[L.node(ax, ay, az)] = lcoef * omega_phys * rcell;
+                    rc64[c->L64.node(ax, ay, az)] = omega_phys * rcell;
+                }
+    }
     htd_status st = mixed ? upload_recurrence<float>(c, qk, dc) : upload_recurrence<double>(c, qk, dc);
     if (st != HTD_OK) return st;
     HTD_CUDA(cudaMemcpy(c->kap64, k64.data(), sizeof(double) * c->L64.total, cudaMemcpyHostToDevice));
@@ -1066,6 +1155,20 @@ htd_status create_impl(const htd_grid *grid, const double *c_cell, const double 
         HTD_CUDA(cudaMalloc((void **)&c->coefP, sizeof(double) * htd::h_planes(d) * (size_t)N));
         htd::launch_assemble_H(c->L64, c->kap64, S2, c->M, c->coefP, 0);
         HTD_CUDA(cudaGetLastError());
+        if (cell_damp) {
+            // Im H = sum_o M_s (sum of omega_phys R over the shared cells): the same
+            // assembly with S = 0 and -M (coefficient 0 - (-M_s) * sum)
+            double Z[4] = {0.0, 0.0, 0.0, 0.0}, Mn[4];
+            for (int k = 0; k < 4; ++k) Mn[k] = -c->M[k];
+            double *rcell = nullptr;
+            HTD_CUDA(cudaMalloc((void **)&rcell, sizeof(double) * c->L64.total));
+            HTD_CUDA(cudaMemcpy(rcell, rc64.data(), sizeof(double) * c->L64.total,
+                                cudaMemcpyHostToDevice));
+            HTD_CUDA(cudaMalloc((void **)&c->coefI, sizeof(double) * htd::h_planes(d) * (size_t)N));
+            htd::launch_assemble_H(c->L64, rcell, Z, Mn, c->coefI, 0);
+            HTD_CUDA(cudaDeviceSynchronize());
+            cudaFree(rcell);
+        }
     }
     HTD_CUDA(cudaMemcpy(c->imH, imh.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
 
@@ -1077,7 +1180,7 @@ htd_status create_impl(const htd_grid *grid, const double *c_cell, const double 
         const char *env_r = std::getenv("HTD_TB_RPT");
         const int want = env ? std::atoi(env) : 0;
         const int want_r = env_r ? std::atoi(env_r) : 0;
-        if (d == 2 && mixed && !(env && want == 0)) {
+        if (d == 2 && mixed && !abd && !(env && want == 0)) {
             htd_status ts = autotune_tb2d(c, want, want_r);
             if (ts != HTD_OK) return ts;
         }
@@ -1086,7 +1189,7 @@ htd_status create_impl(const htd_grid *grid, const double *c_cell, const double 
     // TMA-streamed 3-D FP32 step (HTD_S3=0 keeps the register z-march kernel)
     {
         const char *env = std::getenv("HTD_S3");
-        if (d == 3 && mixed && !(env && std::atoi(env) == 0)) {
+        if (d == 3 && mixed && !abd && !(env && std::atoi(env) == 0)) {
             float *planes[6] = {(float *)c->u0, (float *)c->u1, (float *)c->kap, (float *)c->dco,
                                 (float *)c->fre, (float *)c->fim};
             const char *envs = std::getenv("HTD_S3_TILE");       // tuning override
@@ -1144,6 +1247,7 @@ void operator_view(const htd_ctx *c, OperatorView *out)
     out->L64 = c->L64;
     out->kap64 = c->kap64;
     out->coefP = c->coefP;
+    out->coefI = c->coefI;
     out->imH = c->imH;
     for (int k = 0; k < 4; ++k) {
         out->S2[k] = std::ldexp(c->S[k], c->d - k);
@@ -1242,6 +1346,8 @@ void htd_default_options(htd_options *opt)
     opt->restart = 20;
     opt->max_rhs = 1;
     opt->proj_periods = 1;
+    opt->integrator = HTD_ACD;
+    opt->damping = HTD_DAMP_NODE;
 }
 
 htd_status htd_create(const htd_grid *grid, const double *c_cell_host, const double *R_node_host,
@@ -1315,7 +1421,7 @@ htd_status htd_get_params(htd_handle h, htd_params *out)
         const int64_t slots = (int64_t)P.ctas_per_sm * nsm;
         P.waves = (int)((ctas + slots - 1) / slots);
     }
-    P.step_kernel = h->use_tb ? 1 : (h->use_s3 ? 2 : 0);
+    P.step_kernel = (h->opt.integrator == HTD_ABD) ? 3 : h->use_tb ? 1 : (h->use_s3 ? 2 : 0);
     return HTD_OK;
 }
 
@@ -1379,6 +1485,7 @@ htd_status htd_grad(htd_handle h, int nsrc, const void *F_dev, int nrec,
 {
     if (!h || nsrc < 1 || !F_dev || nrec < 0 || !misfit || max_iters < 0 || !(tol > 0.0))
         return HTD_ERR_ARG;
+    if (h->opt.damping != HTD_DAMP_NODE) return HTD_ERR_ARG;   // dH/dR is diagonal here
     if (nrec > 0 && (!rec_idx_host || !d_dev)) return HTD_ERR_ARG;
     const int64_t N = h->Lr.N;
     for (int k = 0; k < nrec; ++k)
@@ -1462,6 +1569,7 @@ htd_status htd_grad_td(htd_handle h, int nsrc, const void *F_dev, int nrec,
     if (!h || nsrc < 1 || !F_dev || nrec < 0 || !misfit || checkpoint_every < 0)
         return HTD_ERR_ARG;
     if (h->opt.mode != HTD_MODE_TABLE1 && h->opt.mode != HTD_MODE_EXACT) return HTD_ERR_ARG;
+    if (h->opt.integrator != HTD_ACD) return HTD_ERR_ARG;    // the adjoint of I_acd only
     if (nrec > 0 && (!rec_idx_host || !d_dev)) return HTD_ERR_ARG;
     const int64_t N = h->Lr.N;
     for (int k = 0; k < nrec; ++k)

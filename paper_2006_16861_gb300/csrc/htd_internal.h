@@ -112,6 +112,16 @@ void launch_split(const Layout &L, const double2 *F, T *fre, T *fim, int flip, c
 
 void launch_set_slot(OutSlot *slot, double *final_part, double *snap_part, cudaStream_t s);
 
+// ---- backward-differences scheme (I_abd) ------------------------------------------
+
+// u_{n+1} -> out from u = u_n, um = u_{n-1} (see abd_step_kernel); damp: per node
+// (cell = false) or per cell (cell = true) damping coefficient plane
+template <typename T>
+void launch_abd_step(const Layout &L, const T *u, const T *um, T *out, const T *kap,
+                     const T *damp, bool cell, const T *fre, const T *fim, const StepCoef<T> &C,
+                     T a, T b, T cth, const OutSlot *slot, int flags, cudaStream_t s,
+                     const RhsSet &R = RhsSet{});
+
 // ---- projection read-out (mode HTD_MODE_PROJECT) ------------------------------
 
 // acc (per rhs, astride apart; 4 planes of N in compact order: s_re, s_im,
@@ -230,9 +240,11 @@ void launch_tb2d(const TbPlan &p, const TbMaps &maps, int in0, int in1, const La
 __host__ __device__ constexpr int h_planes(int d) { return d == 3 ? 14 : 5; }
 void launch_assemble_H(const Layout &L, const double *kap64, const double S2[4], const double M[4],
                        double *coefP, cudaStream_t s);
-// Y = H X (F == null) or Y = F - H X, complex128 compact vectors.
+// Y = H X (F == null) or Y = F - H X, complex128 compact vectors.  Im H is the
+// diagonal imH, plus the assembled planes coefI if given (cell damping).
 void launch_apply_H(const Layout &L, const double *coefP, const double *imH, double ih2,
-                    const double2 *X, const double2 *F, double2 *Y, cudaStream_t s);
+                    const double2 *X, const double2 *F, double2 *Y, cudaStream_t s,
+                    const double *coefI = nullptr);
 
 // partial[k * nb + b] = sum over block b of conj(V_k) w, k < kcount
 int dots_blocks(int64_t N);
@@ -302,6 +314,7 @@ struct OperatorView {
     Layout L64;             // layout of kap64 (compact N = L64.N)
     const double *kap64;    // (h k)^2 per cell
     const double *coefP;    // assembled operator (launch_assemble_H)
+    const double *coefI;    // assembled non-diagonal Im H, or null
     const double *imH;      // omega_phys R per node
     double S2[4], M[4], ih2;
     int device;

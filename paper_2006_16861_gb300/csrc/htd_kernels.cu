@@ -222,6 +222,122 @@ template void launch_step<double>(const Layout &, const double *, double *, cons
                                   int, cudaStream_t, const RhsSet &);
 
 // ---------------------------------------------------------------------------
+// frequency-adapted backward-differences damped leapfrog (Def. of I_abd)
+// ---------------------------------------------------------------------------
+//
+//   u_{n+1} = (2 - K - L) u_n - (I - L) u_{n-1} + g_n,
+//   K = (dt^2/alpha)(Re H + omega^2) - (dt beta (1 - cos(omega dt))/alpha) B,
+//   L = (beta dt/alpha) B,  B = Im H / omega,
+// which regroups into
+//   u_{n+1} = [2 - (dt^2/alpha)(Re H + omega^2)] u_n - u_{n-1}
+//             - (beta dt/(alpha omega)) Im H (cos(omega dt) u_n - u_{n-1}) + g_n.
+// The first bracket is the same h^2-scaled cell stencil as I_acd's (StepCoef,
+// q*kappa per cell).  Im H: node damping omega_phys R_i (damp holds
+// beta dt omega_phys R_i/(alpha omega) per node), or cell damping (damp holds
+// that coefficient with R_cell per cell; the operator is the cell-mass stencil
+// sum_o M_s (sum of damp over the shared cells) w_{beta+o}).  Reads u_{n-1} at
+// the neighbours in the cell case, so u_{n+1} goes to a third plane.
+
+template <typename T, int D, bool kCell>
+__global__ void __launch_bounds__(256)
+abd_step_kernel(const T *__restrict__ u, const T *__restrict__ um, T *__restrict__ out,
+                const T *__restrict__ kap, const T *__restrict__ damp,
+                const T *__restrict__ fre, const T *__restrict__ fim, Layout L, StepCoef<T> C,
+                T a, T b, T cth, const OutSlot *__restrict__ slot, int flags, RhsSet R, int nz)
+{
+    const int64_t ix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t iy = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
+    int rhs;
+    if (!rhs_of_slot(R, (int)blockIdx.z / nz, rhs)) return;
+    const int64_t iz = blockIdx.z % nz;
+    if (ix >= L.nx || iy >= L.ny) return;
+    const int64_t off = rhs * R.stride;
+    u += off;
+    um += off;
+    out += off;
+    fre += off;
+    fim += off;
+    slot += rhs;
+    const int64_t P = L.pitch, Q = L.plane;
+    const int64_t i = L.node(ix, iy, iz);
+    constexpr int NC = 1 << D;
+    // the node's cells, bit t of index c: upper (1) or lower (0) cell along axis t
+    // (t = 0: x, 1: y, 2: z)
+    T kc[NC], dc[NC];
+#pragma unroll
+    for (int cidx = 0; cidx < NC; ++cidx) {
+        const int ax = cidx & 1, ay = (cidx >> 1) & 1, az = (cidx >> 2) & 1;
+        const int64_t ci = i - (1 - ax) - (1 - ay) * P - (D == 3 ? (1 - az) * Q : 0);
+        kc[cidx] = kap[ci];
+        if (kCell) dc[cidx] = damp[ci];
+    }
+    T accA = T(0), accB = T(0);
+#pragma unroll
+    for (int oz = (D == 3 ? -1 : 0); oz <= (D == 3 ? 1 : 0); ++oz)
+#pragma unroll
+        for (int oy = -1; oy <= 1; ++oy)
+#pragma unroll
+            for (int ox = -1; ox <= 1; ++ox) {
+                const int sh = (ox != 0) + (oy != 0) + (oz != 0);
+                T ks = T(0), ds = T(0);
+#pragma unroll
+                for (int cidx = 0; cidx < NC; ++cidx) {
+                    const int ax = cidx & 1, ay = (cidx >> 1) & 1, az = (cidx >> 2) & 1;
+                    const bool shared = (ox == 0 || ox == 2 * ax - 1) &&
+                                        (oy == 0 || oy == 2 * ay - 1) &&
+                                        (D == 2 || oz == 0 || oz == 2 * az - 1);
+                    if (shared) {
+                        ks += kc[cidx];
+                        if (kCell) ds += dc[cidx];
+                    }
+                }
+                const int64_t j = i + ox + oy * P + (D == 3 ? oz * Q : 0);
+                const T v = u[j];
+                const T coef = (sh == 0) ? C.c0 + C.mt[0] * ks : C.mt[sh] * ks - C.cs[sh];
+                accA += coef * v;
+                if (kCell) accB += C.mt[sh] * ds * (cth * v - um[j]);
+            }
+    const T prev = um[i];
+    if (!kCell) accB = damp[i] * (cth * u[i] - prev);
+    const T unew = accA - prev - accB + (a * fre[i] - b * fim[i]);
+    out[i] = unew;
+    if (flags) {
+        const int64_t c = (iz * L.ny + iy) * L.nx + ix;
+        if ((flags & 1) && slot->snap_part) slot->snap_part[2 * c] = (double)unew;
+        if ((flags & 2) && slot->final_part) slot->final_part[2 * c] = (double)unew;
+    }
+}
+
+template <typename T>
+void launch_abd_step(const Layout &L, const T *u, const T *um, T *out, const T *kap,
+                     const T *damp, bool cell, const T *fre, const T *fim, const StepCoef<T> &C,
+                     T a, T b, T cth, const OutSlot *slot, int flags, cudaStream_t s,
+                     const RhsSet &R)
+{
+    const int nz = (int)L.nz;
+    dim3 blk(32, 8);
+    dim3 grd((unsigned)((L.nx + 31) / 32), (unsigned)((L.ny + 7) / 8), (unsigned)(nz * R.slots));
+#define HTD_ABD_LAUNCH(DD, CC)                                                                  \
+    abd_step_kernel<T, DD, CC><<<grd, blk, 0, s>>>(u, um, out, kap, damp, fre, fim, L, C, a, b, \
+                                                   cth, slot, flags, R, nz)
+    if (L.d == 3) {
+        if (cell) HTD_ABD_LAUNCH(3, true); else HTD_ABD_LAUNCH(3, false);
+    } else {
+        if (cell) HTD_ABD_LAUNCH(2, true); else HTD_ABD_LAUNCH(2, false);
+    }
+#undef HTD_ABD_LAUNCH
+    ++g_launches;
+}
+template void launch_abd_step<float>(const Layout &, const float *, const float *, float *,
+                                     const float *, const float *, bool, const float *,
+                                     const float *, const StepCoef<float> &, float, float, float,
+                                     const OutSlot *, int, cudaStream_t, const RhsSet &);
+template void launch_abd_step<double>(const Layout &, const double *, const double *, double *,
+                                      const double *, const double *, bool, const double *,
+                                      const double *, const StepCoef<double> &, double, double,
+                                      double, const OutSlot *, int, cudaStream_t, const RhsSet &);
+
+// ---------------------------------------------------------------------------
 // projection read-out: compensated sums of e^{-i theta_j} u_j
 // ---------------------------------------------------------------------------
 
@@ -505,11 +621,12 @@ void launch_assemble_H(const Layout &L, const double *kap64, const double S2[4],
 // Y = H X (or F - H X) from the assembled coefficients: per node 3^D
 // coefficient x neighbour products for the real and the imaginary part, one
 // FP64 FMA each; neighbours outside the grid are the zero Dirichlet ghosts
-template <int D>
+template <int D, bool kImH>
 __global__ void __launch_bounds__(256)
 apply_H_asm_kernel(int64_t nx, int64_t ny, int64_t nz, const double *__restrict__ coefP,
-                   const double *__restrict__ imH, double ih2, const double2 *__restrict__ X,
-                   const double2 *__restrict__ F, double2 *__restrict__ Y)
+                   const double *__restrict__ coefI, const double *__restrict__ imH, double ih2,
+                   const double2 *__restrict__ X, const double2 *__restrict__ F,
+                   double2 *__restrict__ Y)
 {
     const int64_t ix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t iy = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
@@ -517,7 +634,7 @@ apply_H_asm_kernel(int64_t nx, int64_t ny, int64_t nz, const double *__restrict_
     if (ix >= nx || iy >= ny) return;
     const int64_t N = nx * ny * nz;
     const int64_t c = (iz * ny + iy) * nx + ix;
-    double re = 0.0, im = 0.0;
+    double re = 0.0, im = 0.0, qr = 0.0, qi = 0.0;
 #pragma unroll
     for (int oz = (D == 3 ? -1 : 0); oz <= (D == 3 ? 1 : 0); ++oz)
 #pragma unroll
@@ -529,17 +646,23 @@ apply_H_asm_kernel(int64_t nx, int64_t ny, int64_t nz, const double *__restrict_
                 if (!in) continue;
                 const int64_t cn = c + ((int64_t)oz * ny + oy) * nx + ox;
                 const int lin = hlin(oz, oy, ox);
-                const double w = (lin >= 13) ? coefP[(lin - 13) * N + c]
-                                             : coefP[(13 - lin) * N + cn];
+                const int64_t ci = (lin >= 13) ? (lin - 13) * N + c : (13 - lin) * N + cn;
+                const double w = coefP[ci];
                 const double2 x = X[cn];
                 re = fma(w, x.x, re);
                 im = fma(w, x.y, im);
+                if (kImH) {                       // non-diagonal Im H (cell damping)
+                    const double wi = coefI[ci];
+                    qr = fma(wi, x.x, qr);
+                    qi = fma(wi, x.y, qi);
+                }
             }
     const double2 xc = X[c];
     const double damp = imH[c];
     double2 y;
-    y.x = ih2 * re - damp * xc.y;
-    y.y = ih2 * im + damp * xc.x;
+    // H x = (Re H x_r - Im H x_i) + i (Re H x_i + Im H x_r)
+    y.x = ih2 * re - damp * xc.y - qi;
+    y.y = ih2 * im + damp * xc.x + qr;
     if (F) {
         const double2 f = F[c];
         y.x = f.x - y.x;
@@ -549,14 +672,19 @@ apply_H_asm_kernel(int64_t nx, int64_t ny, int64_t nz, const double *__restrict_
 }
 
 void launch_apply_H(const Layout &L, const double *coefP, const double *imH, double ih2,
-                    const double2 *X, const double2 *F, double2 *Y, cudaStream_t s)
+                    const double2 *X, const double2 *F, double2 *Y, cudaStream_t s,
+                    const double *coefI)
 {
     dim3 blk(32, 8);
     dim3 grd((unsigned)((L.nx + 31) / 32), (unsigned)((L.ny + 7) / 8), (unsigned)L.nz);
-    if (L.d == 3)
-        apply_H_asm_kernel<3><<<grd, blk, 0, s>>>(L.nx, L.ny, L.nz, coefP, imH, ih2, X, F, Y);
-    else
-        apply_H_asm_kernel<2><<<grd, blk, 0, s>>>(L.nx, L.ny, L.nz, coefP, imH, ih2, X, F, Y);
+#define HTD_AH(DD, II) \
+    apply_H_asm_kernel<DD, II><<<grd, blk, 0, s>>>(L.nx, L.ny, L.nz, coefP, coefI, imH, ih2, X, F, Y)
+    if (L.d == 3) {
+        if (coefI) HTD_AH(3, true); else HTD_AH(3, false);
+    } else {
+        if (coefI) HTD_AH(2, true); else HTD_AH(2, false);
+    }
+#undef HTD_AH
     ++g_launches;
 }
 

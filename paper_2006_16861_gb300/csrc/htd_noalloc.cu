@@ -86,7 +86,7 @@ extern "C" htd_status htd_residual_norm_noalloc(htd_handle h, const void *F_dev,
     // the partials by the dot kernels, the sums by the reductions
     htd::launch_apply_H(op.L64, op.coefP, op.imH, op.ih2,
                         static_cast<const double2 *>(U_dev), static_cast<const double2 *>(F_dev),
-                        r, s);
+                        r, s, op.coefI);
     htd::launch_dots(r, N, 1, r, N, partial, nb, s);
     htd::launch_reduce(partial, nb, 1, sums, s);
     htd::launch_dots(static_cast<const double2 *>(F_dev), N, 1,

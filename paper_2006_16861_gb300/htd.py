@@ -22,6 +22,8 @@ STATUS = {0: "HTD_OK", 1: "HTD_ERR_ARG", 2: "HTD_ERR_CUDA", 3: "HTD_ERR_OOM",
 HTD_NOALLOC_MAX_NODES = 262144
 FP64, MIXED = 0, 1
 MODE_TABLE1, MODE_EXACT, MODE_PROJECT = 0, 1, 2
+ACD, ABD = 0, 1
+DAMP_NODE, DAMP_CELL = 0, 1
 FGMRES, LEFT_GMRES = 0, 1
 STENCIL_Q1MIX, STENCIL_FD5 = 0, 1
 BC_DIRICHLET = 0
@@ -48,7 +50,8 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("mode", ctypes.c_int), ("krylov", ctypes.c_int),
                 ("T", ctypes.c_int), ("rho", ctypes.c_double), ("nP", ctypes.c_int),
                 ("stencil", ctypes.c_int), ("restart", ctypes.c_int), ("max_rhs", ctypes.c_int),
-                ("proj_periods", ctypes.c_int)]
+                ("proj_periods", ctypes.c_int), ("integrator", ctypes.c_int),
+                ("damping", ctypes.c_int)]
 
 
 class Params(ctypes.Structure):
@@ -367,9 +370,12 @@ def htd_status_string(status: int) -> str:
 def make_options(prob=None, precision: str = "fp64", mode: str = "table1",
                  krylov: str = "fgmres", stencil: str = "q1mix", restart: int = 20,
                  nP: int = 0, T: int | None = None, rho: float | None = None,
-                 max_rhs: int = 1, proj_periods: int = 1) -> Options:
+                 max_rhs: int = 1, proj_periods: int = 1, integrator: str = "acd",
+                 damping: str = "node") -> Options:
     """htd_options from names; T and rho default to the problem's."""
     o = htd_default_options()
+    o.integrator = {"acd": ACD, "abd": ABD}[integrator]
+    o.damping = {"node": DAMP_NODE, "cell": DAMP_CELL}[damping]
     o.max_rhs = int(max_rhs)
     o.proj_periods = int(proj_periods)
     o.precision = {"fp64": FP64, "mixed": MIXED}[precision]
@@ -397,9 +403,10 @@ class Solver:
     def __init__(self, prob, precision: str = "fp64", mode: str = "table1",
                  krylov: str = "fgmres", stencil: str = "q1mix", restart: int = 20,
                  nP: int = 0, T: int | None = None, rho: float | None = None,
-                 max_rhs: int = 1, proj_periods: int = 1):
+                 max_rhs: int = 1, proj_periods: int = 1, integrator: str = "acd",
+                 damping: str = "node"):
         o = make_options(prob, precision, mode, krylov, stencil, restart, nP, T, rho, max_rhs,
-                         proj_periods)
+                         proj_periods, integrator, damping)
         self.max_rhs = int(max_rhs)
         self.prob = prob
         self.n = tuple(prob.n)

@@ -42,7 +42,7 @@ def test_struct_layouts_match_header(tmp_path):
         '#include <stdio.h>\n#include <stddef.h>\n#include "htd.h"\n'
         "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(htd_grid),"
         " sizeof(htd_options), sizeof(htd_params), sizeof(htd_solve_info),"
-        " offsetof(htd_solve_info, hist), offsetof(htd_params, nP), offsetof(htd_options, proj_periods));"
+        " offsetof(htd_solve_info, hist), offsetof(htd_params, nP), offsetof(htd_options, damping));"
         "return 0;}\n")
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
@@ -51,15 +51,16 @@ def test_struct_layouts_match_header(tmp_path):
                                           check=True).stdout.split()]
     want = [ctypes.sizeof(htd.Grid), ctypes.sizeof(htd.Options), ctypes.sizeof(htd.Params),
             ctypes.sizeof(htd.SolveInfo), htd.SolveInfo.hist.offset, htd.Params.nP.offset,
-            htd.Options.proj_periods.offset]
+            htd.Options.damping.offset]
     assert got == want
 
 
 def test_default_options():
     o = htd.htd_default_options()
     assert (o.precision, o.mode, o.krylov, o.T, o.rho, o.nP, o.stencil, o.restart,
-            o.max_rhs, o.proj_periods) == \
-        (htd.FP64, htd.MODE_TABLE1, htd.FGMRES, 10, 0.25, 0, htd.STENCIL_Q1MIX, 20, 1, 1)
+            o.max_rhs, o.proj_periods, o.integrator, o.damping) == \
+        (htd.FP64, htd.MODE_TABLE1, htd.FGMRES, 10, 0.25, 0, htd.STENCIL_Q1MIX, 20, 1, 1,
+         htd.ACD, htd.DAMP_NODE)
 
 
 PROBLEMS = [
@@ -109,7 +110,7 @@ def test_plan_rejects_bad_input():
     assert e.value.status == 1
     for kw in ({"restart": 0}, {"restart": 65}, {"T": 0}, {"rho": 1.5}, {"max_rhs": -1},
                {"max_rhs": 257}, {"mode": "project", "proj_periods": 3},
-               {"mode": "project", "proj_periods": -1}):
+               {"mode": "project", "proj_periods": -1}, {"damping": "cell"}):
         with pytest.raises(htd.HtdError) as e:
             htd.plan(p, **kw)
         assert e.value.status == 1
@@ -124,3 +125,22 @@ def test_plan_rejects_bad_input():
 def test_status_strings():
     for s in range(9):
         assert htd.htd_status_string(s)
+
+
+@pytest.mark.parametrize("damping", ["node", "cell"])
+def test_plan_abd_matches_oracle(damping):
+    """The backward-differences parameters of Sec. 6.1 (omega above k_max, n_P, dt)
+    agree with the oracle's; the admissible damping is weaker than for I_acd."""
+    p = W.config_2d_constant(41, ppw=8.0, layer=6, T=3)
+    p = W.Problem(p.name, p.ndim, p.n, p.h, p.c_cell, 0.5 * p.R_node, p.omega, p.F, p.T, p.rho)
+    got = htd.plan(p, integrator="abd", damping=damping)
+    o = oracle.Oracle(p, integrator="abd", damping=damping)
+    assert got["nP"] == o.params.nP
+    assert got["omega_c"] == pytest.approx(o.params.omega, rel=1e-14)
+    assert got["dt"] == pytest.approx(o.params.dt, rel=1e-14)
+    assert got["omega_c"] > got["k_max"]
+    # R0 = 2 omega at c_min = 1 sits at the limit 2 lambda_max(Im H) / k_max^2 -> 4
+    q = W.config_2d_constant(41, ppw=8.0, layer=6, T=3)
+    with pytest.raises(htd.HtdError) as e:
+        htd.plan(q, integrator="abd")
+    assert e.value.status == 4

@@ -68,6 +68,8 @@ def step_kernel_name(prm, ndim):
     """(name, traffic key) of the recurrence kernel a context uses."""
     sk = prm.get("step_kernel")
     if sk == 1:
+        if prm["tile"][2] == 2:
+            return f"tb2d_pair_kernel<{prm['steps_per_launch']}>", "tb2d_pair"
         return f"tb2d_kernel<float,{prm['steps_per_launch']}>", "tb2d"
     if sk == 2:
         if list(prm["tile"][:2]) == [64, 8]:

@@ -167,9 +167,10 @@ typedef struct {
     int steps_per_launch;    /* recurrence steps per kernel launch (temporal
                                 blocking; 1 = one step per launch; 0 in htd_plan,
                                 which does not look at the device) */
-    int tile[3];             /* owned tile (x, y, z) of the blocked 2-D step kernel, or
-                                column tile and z chunk of the streamed 3-D one; 0 if
-                                unused */
+    int tile[3];             /* owned tile (x, y) of the blocked 2-D step kernel and
+                                its columns per thread (1, or 2: node pairs in paired
+                                FP32 instructions), or column tile and z chunk of the
+                                streamed 3-D one; 0 if unused */
     int ctas_per_sm;         /* resident CTAs per SM of that kernel */
     int waves;               /* waves of CTAs per launch of that kernel */
     int step_kernel;         /* recurrence kernel in use: 0 one step per launch

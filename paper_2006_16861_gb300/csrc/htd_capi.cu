@@ -621,8 +621,11 @@ htd_status autotune_tb2d(htd_ctx *c, int want_B, int want_RPT)
     const Layout &L = c->Lr;
     std::vector<htd::TbPlan> all = htd::tb2d_candidates<float>(L, want_B);
     std::vector<htd::TbPlan> cands;
+    const char *env_pair = std::getenv("HTD_TB_PAIR");     // tuning override: 0 scalar, 1 pairs
     for (const htd::TbPlan &p : all)
-        if (want_RPT == 0 || p.RPT == want_RPT) cands.push_back(p);
+        if ((want_RPT == 0 || p.RPT == want_RPT) &&
+            (!env_pair || (int)p.pair == std::atoi(env_pair)))
+            cands.push_back(p);
     if (cands.empty()) return HTD_OK;
     const size_t bytes = sizeof(float) * (size_t)L.total * c->rcap;
     HTD_CUDA(cudaMalloc(&c->u2, bytes));
@@ -1402,7 +1405,7 @@ htd_status htd_get_params(htd_handle h, htd_params *out)
     P.steps_per_launch = h->use_tb ? h->tb.B : 1;
     P.tile[0] = h->use_tb ? h->tb.TX : 0;
     P.tile[1] = h->use_tb ? h->tb.TY : 0;
-    P.tile[2] = 0;
+    P.tile[2] = h->use_tb ? (h->tb.pair ? 2 : 1) : 0;
     P.ctas_per_sm = h->use_tb ? h->tb.occ : 0;
     P.waves = h->use_tb ? h->tb.waves : 0;
     if (h->use_s3) {

@@ -43,24 +43,60 @@ struct StepCoef {
     T mt[4];    // M_s (mass weights per Hamming distance)
 };
 
+// Rounded arithmetic with no contraction left to the compiler, for float,
+// double and float2 (paired FP32: each lane rounds like the scalar op), so
+// that kernels evaluating the same expression on scalars or on node pairs
+// produce bit-identical results.
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double vadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double vmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double vfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// StepCoef as the operand type V of stencil2d (V = T, or float2 broadcasts)
+template <typename V>
+struct Stencil2dCoef {
+    V c0, mt0, mt1, mt2, ncs1, ncs2;     // ncs = -cs
+};
+
+template <typename T>
+__device__ __forceinline__ Stencil2dCoef<T> stencil2d_coef(const StepCoef<T> &C)
+{
+    return {C.c0, C.mt[0], C.mt[1], C.mt[2], -C.cs[1], -C.cs[2]};
+}
+
+__device__ __forceinline__ Stencil2dCoef<float2> stencil2d_coef2(const StepCoef<float> &C)
+{
+    auto b = [](float x) { return make_float2(x, x); };
+    return {b(C.c0), b(C.mt[0]), b(C.mt[1]), b(C.mt[2]), b(-C.cs[1]), b(-C.cs[2])};
+}
+
 // (2 - K) u at one node of the 2-D cell-form operator (App. A), h^2-scaled
 // coefficients as in StepCoef.  u<r><c>: u_j at row offset r, column offset c
 // (m = -1, 0, p = +1); k<ay><ax>: q*kappa of the node's four cells; pm, p0, pp:
 // u_{-1,-1} + u_{-1,+1}, u_{0,-1} + u_{0,+1}, u_{+1,-1} + u_{+1,+1}; hk0 = k00 + k01,
-// hk1 = k10 + k11.  Written as a shallow tree of independent partial sums so
-// that the one-step and the temporally blocked kernels (which share it) give
-// identical results and have short dependency chains.
-template <typename T>
-__device__ __forceinline__ T stencil2d(const StepCoef<T> &C, T umm, T um0, T ump, T u0m, T u00,
-                                       T u0p, T upm, T up0, T upp, T k00, T k01, T k10, T k11,
-                                       T pm, T p0, T pp, T hk0, T hk1)
+// hk1 = k10 + k11.  A shallow tree of independent partial sums (short
+// dependency chains) with every rounding spelled out: the one-step kernel, the
+// temporally blocked kernel and its node-pair form (V = float2) all give
+// identical results.
+template <typename V>
+__device__ __forceinline__ V stencil2d(const Stencil2dCoef<V> &C, V umm, V um0, V ump, V u0m, V u00,
+                                       V u0p, V upm, V up0, V upp, V k00, V k01, V k10, V k11,
+                                       V pm, V p0, V pp, V hk0, V hk1)
 {
-    const T center = C.c0 + C.mt[0] * (hk0 + hk1);
-    const T edge = (um0 + up0) + p0;
-    const T corner = pm + pp;
-    const T m1 = (hk0 * um0 + hk1 * up0) + ((k00 + k10) * u0m + (k01 + k11) * u0p);
-    const T m2 = (k00 * umm + k01 * ump) + (k10 * upm + k11 * upp);
-    return (center * u00 - C.cs[1] * edge) + (C.mt[1] * m1 + (C.mt[2] * m2 - C.cs[2] * corner));
+    const V center = vfma(C.mt0, vadd(hk0, hk1), C.c0);
+    const V edge = vadd(vadd(um0, up0), p0);
+    const V corner = vadd(pm, pp);
+    const V m1 = vadd(vfma(hk0, um0, vmul(hk1, up0)),
+                      vfma(vadd(k00, k10), u0m, vmul(vadd(k01, k11), u0p)));
+    const V m2 = vadd(vfma(k00, umm, vmul(k01, ump)), vfma(k10, upm, vmul(k11, upp)));
+    const V r1 = vfma(center, u00, vmul(C.ncs1, edge));
+    const V r2 = vfma(C.mt1, m1, vfma(C.mt2, m2, vmul(C.ncs2, corner)));
+    return vadd(r1, r2);
 }
 
 // Output targets of a preconditioner run, read by the step kernels from device
@@ -200,7 +236,9 @@ struct TbSteps {
 struct TbPlan {
     int B = 0;          // steps per launch (halo width)
     int RPT = 0;        // rows per thread
-    int RG = 0;         // row groups: threads = 64 * RG, tile rows H = RG * RPT
+    int RG = 0;         // row groups: tile rows H = RG * RPT, threads 64 * RG (32 * RG
+                        // for node pairs)
+    bool pair = false;  // two adjacent columns per thread in paired FP32 instructions
     int TX = 0, TY = 0; // owned tile
     int H = 0;          // tile rows including the halo
     size_t smem = 0;    // dynamic shared memory per CTA

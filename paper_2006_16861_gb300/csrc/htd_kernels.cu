@@ -64,12 +64,13 @@ step2d_kernel(const T *__restrict__ u, T *__restrict__ um, const T *__restrict__
     // pair sums shared with the temporally blocked kernel (same order, same result)
     const T pm = umm + ump, p0 = u0m + u0p, pp = upm + upp;
     const T hk0 = k00 + k01, hk1 = k10 + k11;
-    const T acc = stencil2d(C, umm, um0, ump, u0m, u00, u0p, upm, up0, upp, k00, k01, k10, k11,
+    const Stencil2dCoef<T> SC = stencil2d_coef(C);
+    const T acc = stencil2d(SC, umm, um0, ump, u0m, u00, u0p, upm, up0, upp, k00, k01, k10, k11,
                             pm, p0, pp, hk0, hk1);
-    const T g = a * fre[i] - b * fim[i];
+    const T g = vfma(a, fre[i], vmul(-b, fim[i]));
     const T d = dco[i];
     const T uprev = um[i];
-    const T unew = d * (acc + g - T(2) * uprev) + uprev;
+    const T unew = vfma(d, vfma(T(-2), uprev, vadd(acc, g)), uprev);
     um[i] = unew;
     if (flags) {
         const int64_t c = iy * L.nx + ix;

@@ -203,6 +203,7 @@ tb2d_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, T *__restrict
     const int dom_lo = (int)max((int64_t)0, -y0);
     const int dom_hi = (int)min((int64_t)H, (int64_t)L.ny - y0);
 
+    const Stencil2dCoef<T> SC = stencil2d_coef(C);
     // per-step forcing coefficients and flags, staged in shared memory so that
     // the step loop does not index the parameter block dynamically
     __shared__ T s_a[kTbMaxSteps], s_b[kTbMaxSteps];
@@ -244,14 +245,14 @@ tb2d_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, T *__restrict
             const T k10 = sk[(ly + 1) * BW + cc], k11 = sk[(ly + 1) * BW + cc + 1];
             const T pp = upm + upp;
             const T hk1 = k10 + k11;
-            const T acc = stencil2d(C, umm, um0, ump, u0m, u00, u0p, upm, up0, upp, k00, k01, k10,
+            const T acc = stencil2d(SC, umm, um0, ump, u0m, u00, u0p, upm, up0, upp, k00, k01, k10,
                                     k11, pm, p0, pp, hk0, hk1);
             // every thread stores; outside the updated region it stores u_{j+s-1}
             // back unchanged, so no per-row branch is needed
             const int ni = (ly + 1) * BW + cc + 1;
-            const T g = a * rfr[i] - b * rfi[i];
+            const T g = vfma(a, rfr[i], vmul(-b, rfi[i]));
             const T uprev = prv[ni];
-            const T unew = rd[i] * (acc + g - T(2) * uprev) + uprev;
+            const T unew = vfma(rd[i], vfma(T(-2), uprev, vadd(acc, g)), uprev);
             const bool upd = col_ok && ly >= lo && ly < hi;
             prv[ni] = upd ? unew : uprev;
             if (kOut && upd && col_owned && ly >= B && ly < B + TY) {
@@ -283,6 +284,231 @@ tb2d_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, T *__restrict
             uD[g] = prev[si];
         }
     }
+}
+
+// Node-pair form of tb2d_kernel (FP32): thread (p, g) owns the columns
+// lx = 2p, 2p+1 of rows g RPT .. g RPT + RPT - 1, and every operation of the
+// per-node update runs on the pair with the paired FP32 instructions (each
+// lane rounds like the scalar instruction, so the results are those of
+// tb2d_kernel and step2d_kernel).  The columns of a pair sit at an even shared
+// memory column (the box starts one column left of a 16-byte boundary and
+// tiles start at even x), so (lx, lx+1) is one 64-bit access; lx - 1 and
+// lx + 2 are single loads.
+__device__ __forceinline__ float2 pr(float a, float b) { return make_float2(a, b); }
+
+template <int B, int RPT, int RG>
+__global__ void __launch_bounds__(32 * RG, 1)
+tb2d_pair_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, float *__restrict__ uC,
+                 float *__restrict__ uD, const float *__restrict__ dco,
+                 const float *__restrict__ fre, const float *__restrict__ fim, Layout L,
+                 StepCoef<float> C, TbSteps<float> S, const OutSlot *__restrict__ slot,
+                 int *__restrict__ err, RhsSet R)
+{
+    typedef float T;
+    constexpr int W = kW, TX = W - 2 * B, BW = kBoxW;
+    constexpr int H = RG * RPT, TY = H - 2 * B;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    constexpr int ae = (int)(tb2d_array_bytes<T>(H) / sizeof(T));
+    T *smem_t = reinterpret_cast<T *>(smem_raw);
+    T *su0 = smem_t;
+    T *su1 = smem_t + ae;
+    T *sk = smem_t + 2 * ae;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_t + 3 * ae);
+
+    const int tid = threadIdx.x;
+    int rhs;
+    if (!rhs_of_slot(R, (int)blockIdx.z, rhs)) return;
+    const int64_t x0 = (int64_t)blockIdx.x * TX - B;
+    const int64_t y0 = (int64_t)blockIdx.y * TY - B;
+    const int64_t c0 = L.xl + x0 - 1;
+    const int xs = (int)(c0 - (c0 % 4));
+    const int off = (int)(c0 - xs);
+    // TMA destinations 128-byte aligned and node pairs at even columns; refuse otherwise
+    if ((smem_u32(smem_raw) & 127u) || !(off & 1)) {
+        if (tid == 0) atomicExch(err, 1);
+        return;
+    }
+    uC += rhs * R.stride;
+    uD += rhs * R.stride;
+    fre += rhs * R.stride;
+    fim += rhs * R.stride;
+    slot += rhs;
+
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        mbar_expect_tx(bar, (unsigned)(3 * (size_t)(H + 2) * BW * sizeof(T)));
+        const int ys = (int)y0;
+        tma_load_3d(su0, &maps.m[in0], xs, ys, rhs, bar);
+        tma_load_3d(su1, &maps.m[in1], xs, ys, rhs, bar);
+        tma_load_2d(sk, &maps.m[4], xs, ys, bar);
+    }
+
+    const int lx = 2 * (tid & 31);                        // first column of the pair
+    const int row0 = (tid >> 5) * RPT;
+    const int64_t gx = x0 + lx;
+    const bool inA = gx >= 0 && gx < L.nx, inB = gx + 1 >= 0 && gx + 1 < L.nx;
+    float2 rd[RPT], rfr[RPT], rfi[RPT];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+        const int64_t gy = y0 + row0 + i;
+        const bool rin = gy >= 0 && gy < L.ny;
+        const int64_t g = rin ? (gy + 1) * L.pitch + L.xl + gx : 0;
+        const bool a = rin && inA, b = rin && inB;
+        rd[i] = pr(a ? dco[g] : 0.f, b ? dco[g + 1] : 0.f);
+        rfr[i] = pr(a ? fre[g] : 0.f, b ? fre[g + 1] : 0.f);
+        rfi[i] = pr(a ? fim[g] : 0.f, b ? fim[g + 1] : 0.f);
+    }
+
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(bar);
+    if (__syncthreads_or(!ok)) {
+        if (tid == 0) {
+            atomicExch(err, 1);
+            mbar_wait_bounded(bar);
+        }
+        __syncthreads();
+        return;
+    }
+
+    const bool ownA = lx >= B && lx < B + TX;              // lx and lx+1 are owned together
+    const int cc = lx + off;                               // smem column of lx - 1 (odd)
+    const int dom_lo = (int)max((int64_t)0, -y0);
+    const int dom_hi = (int)min((int64_t)H, (int64_t)L.ny - y0);
+    const Stencil2dCoef<float2> SC = stencil2d_coef2(C);
+    const float2 n2 = pr(-2.f, -2.f);
+
+    __shared__ T s_a[kTbMaxSteps], s_b[kTbMaxSteps];
+    __shared__ int s_flags[kTbMaxSteps];
+    if (tid == 0) {
+#pragma unroll
+        for (int q = 0; q < kTbMaxSteps; ++q) {
+            s_a[q] = S.a[q];
+            s_b[q] = S.b[q];
+            s_flags[q] = S.flags[q];
+        }
+    }
+    __syncthreads();
+
+    // u row r of the plane as the pairs (m, 0, p) = (u(lx-1+o), u(lx+o)), o = 0, 1, 2
+    auto urow = [&](const T *pl, int r, float2 &m, float2 &z, float2 &p) {
+        const T *q = pl + r * BW + cc;
+        const float l = q[0];
+        z = *reinterpret_cast<const float2 *>(q + 1);
+        const float rr = q[3];
+        m = pr(l, z.x);
+        p = pr(z.y, rr);
+    };
+    // cell row r: k0 = cells left of the nodes, k1 = cells right of them
+    auto krow = [&](int r, float2 &k0, float2 &k1) {
+        const T *q = sk + r * BW + cc;
+        k1 = *reinterpret_cast<const float2 *>(q + 1);
+        k0 = pr(q[0], k1.x);
+    };
+
+    auto step = [&](int s, auto with_out) {
+        constexpr bool kOut = decltype(with_out)::value;
+        const T *__restrict__ cur = (s & 1) ? su1 : su0;
+        T *__restrict__ prv = (s & 1) ? su0 : su1;
+        const float2 a2 = pr(s_a[s], s_a[s]), nb2 = pr(-s_b[s], -s_b[s]);
+        const int flags = s_flags[s];
+        const bool okA = inA && lx >= s + 1 && lx < W - s - 1;
+        const bool okB = inB && lx + 1 >= s + 1 && lx + 1 < W - s - 1;
+        const int lo = max(s + 1, dom_lo), hi = min(H - s - 1, dom_hi);
+        float2 umm, um0, ump, u0m, u00, u0p;
+        urow(cur, row0, umm, um0, ump);
+        urow(cur, row0 + 1, u0m, u00, u0p);
+        float2 pm = vadd(umm, ump), p0 = vadd(u0m, u0p);
+        float2 k00, k01;
+        krow(row0, k00, k01);
+        float2 hk0 = vadd(k00, k01);
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+            const int ly = row0 + i;
+            float2 upm, up0, upp, k10, k11;
+            urow(cur, ly + 2, upm, up0, upp);
+            krow(ly + 1, k10, k11);
+            const float2 pp = vadd(upm, upp);
+            const float2 hk1 = vadd(k10, k11);
+            const float2 acc = stencil2d(SC, umm, um0, ump, u0m, u00, u0p, upm, up0, upp, k00, k01,
+                                         k10, k11, pm, p0, pp, hk0, hk1);
+            const int ni = (ly + 1) * BW + cc + 1;
+            const float2 g = vfma(a2, rfr[i], vmul(nb2, rfi[i]));
+            const float2 uprev = *reinterpret_cast<const float2 *>(prv + ni);
+            const float2 unew = vfma(rd[i], vfma(n2, uprev, vadd(acc, g)), uprev);
+            const bool rowupd = ly >= lo && ly < hi;
+            const bool uA = okA && rowupd, uB = okB && rowupd;
+            *reinterpret_cast<float2 *>(prv + ni) = pr(uA ? unew.x : uprev.x, uB ? unew.y : uprev.y);
+            if (kOut && ownA && ly >= B && ly < B + TY) {
+                const int64_t c = (y0 + ly) * L.nx + gx;
+                if ((flags & 1) && slot->snap_part) {
+                    if (uA) slot->snap_part[2 * c] = (double)unew.x;
+                    if (uB) slot->snap_part[2 * c + 2] = (double)unew.y;
+                }
+                if ((flags & 2) && slot->final_part) {
+                    if (uA) slot->final_part[2 * c] = (double)unew.x;
+                    if (uB) slot->final_part[2 * c + 2] = (double)unew.y;
+                }
+            }
+            umm = u0m; um0 = u00; ump = u0p; pm = p0;
+            u0m = upm; u00 = up0; u0p = upp; p0 = pp;
+            k00 = k10; k01 = k11; hk0 = hk1;
+        }
+        __syncthreads();
+    };
+    for (int s = 0; s < S.nsub; ++s) {
+        if (s_flags[s]) step(s, std::true_type{});
+        else step(s, std::false_type{});
+    }
+
+    const T *last = (S.nsub & 1) ? su1 : su0;
+    const T *prev = (S.nsub & 1) ? su0 : su1;
+    if (ownA && (inA || inB)) {
+        for (int ly = max(row0, B); ly < min(row0 + RPT, B + TY); ++ly) {
+            const int64_t gy = y0 + ly;
+            if (gy >= L.ny) break;
+            const int64_t g = (gy + 1) * L.pitch + L.xl + gx;
+            const int si = (ly + 1) * BW + cc + 1;
+            if (inA) { uC[g] = last[si]; uD[g] = prev[si]; }
+            if (inB) { uC[g + 1] = last[si + 1]; uD[g + 1] = prev[si + 1]; }
+        }
+    }
+}
+
+template <int B, int RPT, int RG>
+void add_pair_candidate(const Layout &L, std::vector<TbPlan> &out)
+{
+    constexpr int H = RG * RPT, TY = H - 2 * B, TX = kW - 2 * B, kThreads = 32 * RG;
+    const size_t smem = tb2d_smem_bytes<float>(H);
+    if (H + 2 > 256 || smem > 220 * 1024) return;
+    if (cudaFuncSetAttribute(tb2d_pair_kernel<B, RPT, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return;
+    }
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tb2d_pair_kernel<B, RPT, RG>, kThreads,
+                                                      smem) != cudaSuccess || occ < 1) {
+        (void)cudaGetLastError();
+        return;
+    }
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    TbPlan p;
+    p.B = B;
+    p.RPT = RPT;
+    p.RG = RG;
+    p.pair = true;
+    p.TX = TX;
+    p.TY = TY;
+    p.H = H;
+    p.smem = smem;
+    p.grid_x = (int)((L.nx + TX - 1) / TX);
+    p.grid_y = (int)((L.ny + TY - 1) / TY);
+    p.occ = occ;
+    const int64_t slots = (int64_t)nsm * occ;
+    p.waves = (int)(((int64_t)p.grid_x * p.grid_y + slots - 1) / slots);
+    out.push_back(p);
 }
 
 template <typename T, int B, int RPT, int RG>
@@ -340,6 +566,19 @@ std::vector<TbPlan> tb2d_candidates(const Layout &L, int want_B)
         add_candidate<T, 8, 6, 16>(L, v);
         add_candidate<T, 8, 10, 16>(L, v);
     }
+    if constexpr (std::is_same<T, float>::value) {
+        if (want_B == 0 || want_B == 4) {
+            add_pair_candidate<4, 10, 16>(L, v);
+            add_pair_candidate<4, 6, 16>(L, v);
+            add_pair_candidate<4, 12, 8>(L, v);
+        }
+        if (want_B == 0 || want_B == 8) {
+            add_pair_candidate<8, 10, 16>(L, v);
+            add_pair_candidate<8, 6, 16>(L, v);
+            add_pair_candidate<8, 12, 8>(L, v);
+            add_pair_candidate<8, 12, 16>(L, v);
+        }
+    }
     return v;
 }
 
@@ -387,6 +626,25 @@ void launch_tb2d(const TbPlan &p, const TbMaps &maps, int in0, int in1, const La
                  const RhsSet &R)
 {
     dim3 grd((unsigned)p.grid_x, (unsigned)p.grid_y, (unsigned)R.slots);
+    if constexpr (std::is_same<T, float>::value) {
+#define HTD_TB2D_PAIR_CASE(BB, RR, GG)                                                          \
+        if (p.pair && p.B == BB && p.RPT == RR && p.RG == GG) {                                 \
+            tb2d_pair_kernel<BB, RR, GG><<<grd, 32 * GG, p.smem, s>>>(maps, in0, in1, uC, uD,   \
+                                                                      dco, fre, fim, L, C, S,   \
+                                                                      slot, err, R);            \
+            ++g_launches;                                                                       \
+            return;                                                                             \
+        }
+        HTD_TB2D_PAIR_CASE(4, 10, 16)
+        HTD_TB2D_PAIR_CASE(4, 6, 16)
+        HTD_TB2D_PAIR_CASE(4, 12, 8)
+        HTD_TB2D_PAIR_CASE(8, 10, 16)
+        HTD_TB2D_PAIR_CASE(8, 6, 16)
+        HTD_TB2D_PAIR_CASE(8, 12, 8)
+        HTD_TB2D_PAIR_CASE(8, 12, 16)
+#undef HTD_TB2D_PAIR_CASE
+    }
+    if (p.pair) return;
 #define HTD_TB2D_CASE(BB, RR, GG)                                                              \
     if (p.B == BB && p.RPT == RR && p.RG == GG) {                                              \
         tb2d_kernel<T, BB, RR, GG><<<grd, kW * GG, p.smem, s>>>(maps, in0, in1, uC, uD, dco,   \

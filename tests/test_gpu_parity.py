@@ -128,17 +128,22 @@ def test_gmres_fp64_config1_converges_to_direct_solution():
 
 
 TB_CASES = [(37, 45), (1, 7), (3, 2), (130, 67), (101, 101), (64, 300)]
-TB_CONFIGS = [("4", "12"), ("4", "10"), ("8", "6"), ("8", "20"), (None, None)]
+TB_CONFIGS = [("4", "12", "0"), ("4", "10", "0"), ("8", "6", "0"), ("8", "20", "0"),
+              ("4", "10", "1"), ("4", "12", "1"), ("8", "6", "1"), ("8", "12", "1"),
+              (None, None, None)]
 
 
 @pytest.mark.parametrize("n", TB_CASES, ids=[f"{a}x{b}" for a, b in TB_CASES])
-@pytest.mark.parametrize("B,rpt", TB_CONFIGS, ids=[f"B{b}_r{r}" for b, r in TB_CONFIGS])
+@pytest.mark.parametrize("B,rpt,pair", TB_CONFIGS,
+                         ids=[f"B{b}_r{r}_p{q}" for b, r, q in TB_CONFIGS])
 @pytest.mark.parametrize("mode", ["table1", "exact"])
-def test_temporal_blocking_matches_one_step(n, B, rpt, mode, monkeypatch):
+def test_temporal_blocking_matches_one_step(n, B, rpt, pair, mode, monkeypatch):
     """The 2-D FP32 recurrence with B steps per launch (shared-memory tiles with a
-    halo of B, rows per thread rpt) against the one-step-per-launch kernel and the
-    FP64 oracle; None = the autotuner's own choice.  Step counts that are not
-    multiples of B and snapshots inside a launch included."""
+    halo of B, rows per thread rpt, one column per thread or node pairs in
+    paired FP32 instructions) against the one-step-per-launch kernel, bit for
+    bit (the same roundings in the same order), and the FP64 oracle; None = the
+    autotuner's own choice.  Step counts that are not multiples of B and
+    snapshots inside a launch included."""
     p = het_problem(2, n, T=3) if min(n) > 1 else het_problem(2, n, T=2)
     monkeypatch.setenv("HTD_TB", "0")
     s0 = htd.Solver(p, precision="mixed", mode=mode)
@@ -147,16 +152,17 @@ def test_temporal_blocking_matches_one_step(n, B, rpt, mode, monkeypatch):
     if B is not None:
         monkeypatch.setenv("HTD_TB", B)
         monkeypatch.setenv("HTD_TB_RPT", rpt)
+        monkeypatch.setenv("HTD_TB_PAIR", pair)
     s1 = htd.Solver(p, precision="mixed", mode=mode)
     if B is not None:
         assert s1.params["steps_per_launch"] == int(B)
-        row_groups = 16 if int(rpt) in (6, 10) else 8
-        assert s1.params["tile"][1] == row_groups * int(rpt) - 2 * int(B)
+        groups = (16, 8) if pair == "1" else ((16,) if int(rpt) in (6, 10) else (8,))
+        assert s1.params["tile"][1] in [g * int(rpt) - 2 * int(B) for g in groups]
     o = oracle.Oracle(p)
     for F in (p.F, W.random_rhs(6, p.n)):
         a = host(s0.precond(dev(F))).reshape(-1)
         b = host(s1.precond(dev(F))).reshape(-1)
-        assert rel_l2(b, a) <= 1e-6, rel_l2(b, a)
+        assert np.array_equal(b, a), rel_l2(b, a)
         assert rel_l2(b, o.precond(F, mode).reshape(-1)) <= 2e-5
 
 

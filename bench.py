@@ -57,6 +57,8 @@ WORDS_ONE_STEP, WORDS_BLOCKED = 7, 8
 NCU_TRAFFIC = {
     "tb2d": {"file": "htd_tblock.cu", "sha16": "911c4093662ebe9d", "bytes": 25086720 + 256,
              "nodes": 1001 * 1001},
+    "tb2d_pair": {"file": "htd_tblock.cu", "sha16": "36845b87e2bac8d7", "bytes": 25059328 + 512,
+                  "nodes": 1001 * 1001},
     "stream3d": {"file": "htd_stream3d.cu", "sha16": "4f289c964d28aa22",
                  "bytes": 193680896 + 18157568, "nodes": 192 ** 3},
     "stream3d_pair": {"file": "htd_stream3d_pair.cu", "sha16": "1c9b1035ac857f75",
@@ -103,7 +105,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="2d_grf_1001",
-                    choices=["2d_grf_1001", "3d_layered_256", "3d_layered_192", "2d_const_101"])
+                    choices=["2d_grf_1001", "3d_layered_256", "3d_layered_192", "2d_const_101",
+                             "3d_paper_shape"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--cpu-sample-s", type=float, default=10.0)
     ap.add_argument("--e2e-steps", type=int, default=5)
@@ -129,6 +132,10 @@ def make_workload(name, rank=0):
         p = W.config_3d_layered(192, layer=18)
         desc = ("3-D 192^3 (profiling size) 4-layer c [1.5..4.5] x (1+0.1 GRF), h=1/191, "
                 "8 ppw at min c, 18-cell layer R0=2w, point source, T=24, rho=0.25")
+    elif name == "3d_paper_shape":
+        p = W.config_3d_paper_shape()
+        desc = ("3-D 200x200x106 (the paper's smallest 3-D example size), 4-layer model in place "
+                "of SEG/EAGE salt, 6 ppw at min c, 16-cell layer R0=2w, point source, T=25")
     else:
         p = W.config_2d_constant(101)
         desc = "2-D 101x101 constant c=1, h=0.01, 10 ppw, 20-cell layer, point source, T=10"

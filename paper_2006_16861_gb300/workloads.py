@@ -309,3 +309,26 @@ def config_batched(n3: int = 128, nsrc: int = 32, ninst: int = 64, side_lo: int 
         probs.append(p)
         Fs.append(p.F[None].astype(np.complex128))
     return BatchSetup(probs, Fs)
+
+
+def config_3d_paper_shape(shape=(106, 200, 200), ppw: float = 6.0, T: int = 25, layer: int = 16,
+                          seed: int = 2006168616, corr_len: float = 0.05,
+                          rho: float = 0.25) -> Problem:
+    """The size of the paper's smallest 3-D example (200 x 200 x 106 nodes, depth
+    along axis 0) at 6 points per wavelength and T = 25, with the 4-layer model of
+    config_3d_layered standing in for the unavailable SEG/EAGE salt model (h from
+    the longest side, layers by depth, 10 % Gaussian perturbation);
+    ``layer``-cell absorbing layer (R0 = 2 omega) and a centre point source."""
+    n = tuple(int(m) for m in shape)
+    h = 1.0 / (max(n) - 1)
+    cells = tuple(m + 1 for m in n)
+    depth = (np.arange(cells[0]) - 0.5) / (n[0] - 1)
+    layers = np.asarray((1.5, 2.5, 3.5, 4.5))
+    q = np.clip(np.floor(depth * len(layers)).astype(int), 0, len(layers) - 1)
+    g = gaussian_random_field(seed, cells, corr_len / h)
+    c = layers[q][:, None, None] * (1.0 + 0.1 * g)
+    cmin = float(c.min())
+    omega = 2.0 * math.pi * cmin / (ppw * h)
+    R = damping_profile(3, n, layer, 2.0 * omega)
+    F = point_source(3, n, h)
+    return Problem("3d_paper_shape", 3, n, h, c, R, omega, F, T, rho)

@@ -227,6 +227,17 @@ void free_ctx(htd_ctx *c)
 }
 
 // one preconditioner run of T n_P steps; the forcing planes are already filled.
+// Consecutive blocked launches overlap (programmatic dependent launch) unless
+// HTD_TB_OVERLAP=0 (a tuning override).
+bool tb_overlap()
+{
+    static const bool on = [] {
+        const char *e = std::getenv("HTD_TB_OVERLAP");
+        return !(e && std::atoi(e) == 0);
+    }();
+    return on;
+}
+
 // Table 1 / EXACT: the step kernels write the snapshot and final state into the
 // output slots (flags).  PROJECT: steps j >= j_acc (whose new states u_{j+1}
 // lie in the last proj_periods periods) run one step per launch, each
@@ -315,7 +326,7 @@ htd_status run_steps_direct(htd_ctx *c, cudaStream_t s)
             htd::launch_tb2d<T>(c->tb, c->tbmaps, map_of[from][0], map_of[from][1], L,
                                 pairs[1 - from][0], pairs[1 - from][1], (const T *)c->dco,
                                 (const T *)c->fre, (const T *)c->fim, C, S, c->slot,
-                                c->err_dev, s, c->Rs);
+                                c->err_dev, s, c->Rs, j0 > 0 && tb_overlap());
             from = 1 - from;
         }
         // the blocked launches leave u_{jend} in pairs[from][0], u_{jend-1} in pairs[from][1]
@@ -670,7 +681,8 @@ htd_status autotune_tb2d(htd_ctx *c, int want_B, int want_RPT)
             if (r == 2) HTD_CUDA(cudaEventRecord(e0, s));
             htd::launch_tb2d<float>(cands[k], maps, 0, 1, L, (float *)c->u2, (float *)c->u3,
                                     (const float *)c->dco, (const float *)c->fre,
-                                    (const float *)c->fim, C, S, c->slot, c->err_dev, s);
+                                    (const float *)c->fim, C, S, c->slot, c->err_dev, s,
+                                    htd::RhsSet{}, r > 0 && tb_overlap());
         }
         HTD_CUDA(cudaEventRecord(e1, s));
         HTD_CUDA(cudaEventSynchronize(e1));

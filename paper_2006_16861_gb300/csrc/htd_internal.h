@@ -265,12 +265,16 @@ bool make_tb2d_maps(const Layout &L, const TbPlan &p, T *const planes[5], TbMaps
                     int nrhs = 1);
 
 // nsub <= B steps from the state pair (maps in0, in1) into the planes uC, uD;
-// a timed-out TMA wait sets *err = 1.
+// a timed-out TMA wait sets *err = 1.  overlap: the previous kernel on the
+// stream is a blocked launch of the same sequence, so this launch may start
+// while it drains (programmatic dependent launch): its prologue reads only
+// q*kappa, d and the forcing, which no launch of the sequence writes, and it
+// waits for the previous grid before it touches a state plane.
 template <typename T>
 void launch_tb2d(const TbPlan &p, const TbMaps &maps, int in0, int in1, const Layout &L, T *uC,
                  T *uD, const T *dco, const T *fre, const T *fim, const StepCoef<T> &C,
                  const TbSteps<T> &S, const OutSlot *slot, int *err, cudaStream_t s,
-                 const RhsSet &R = RhsSet{});
+                 const RhsSet &R = RhsSet{}, bool overlap = false);
 
 // Assembled FP64 operator: coefficient planes (N doubles each) of the centre
 // and of the positive offsets (the other half follows from symmetry):

@@ -3,12 +3,15 @@
 //
 // Each CTA owns a TX x TY tile of nodes (TX = 64 - 2B) and needs it with a halo
 // of B nodes (64 columns, H = TY + 2B rows), plus one more ring for the
-// neighbour reads, the q*kappa of the cells touching those nodes, the per-node
-// d and the two forcing planes.  All six come from the padded device layout,
-// where a cell sits at the position of its lower-corner node, so one TMA box
-// of kBoxW x (H + 2) elements per array covers everything: one thread issues
-// six cp.async.bulk.tensor.2d copies (zero fill outside the array) that
-// complete on one mbarrier; the box starts at a 16-byte aligned column.
+// neighbour reads, and the q*kappa of the cells touching those nodes.  All
+// three come from the padded device layout, where a cell sits at the position
+// of its lower-corner node, so one TMA box of kBoxW x (H + 2) elements per
+// array covers everything: one thread issues three cp.async.bulk.tensor copies
+// (zero fill outside the array) that complete on one mbarrier; the box starts
+// at a 16-byte aligned column.  The per-node d and the two forcing planes are
+// read into registers.  Consecutive launches of a step sequence overlap
+// (programmatic dependent launch): a launch reads q*kappa, d and the forcing
+// while the previous one drains and loads the state planes after it.
 //
 // Step s (s = 0 .. nsub-1) updates the nodes of the ring-shrunk region
 // [s+1, 63-s) x [s+1, H-s-1); after nsub <= B steps the owned core
@@ -17,13 +20,14 @@
 // a half-updated halo).  Per node the arithmetic is exactly that of
 // step2d_kernel (same expression, same order).
 //
-// Threads: 256 = 64 columns x 4 row groups; a thread walks down its rows with
-// a 3x3 register window of u_j and a 2x2 window of cells.
+// Threads: 64 columns x RG row groups; a thread walks down its rows with a 3x3
+// register window of u_j and a 2x2 window of cells.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "htd_internal.h"
@@ -118,6 +122,21 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
+// Programmatic dependent launch.  Code before grid_dep_wait() may run while
+// the previous kernel of the stream drains (when the launch allows it); after
+// it, everything that kernel wrote is visible.  grid_dep_launch() lets the
+// next launch of the stream be scheduled onto SMs as this grid's CTAs retire.
+// Both are no-ops for an ordinary launch.
+__device__ __forceinline__ void grid_dep_wait()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+__device__ __forceinline__ void grid_dep_launch()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 template <typename T, int B, int RPT, int RG>
 __global__ void __launch_bounds__(kW * RG, 1)
 tb2d_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, T *__restrict__ uC,
@@ -157,12 +176,12 @@ tb2d_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, T *__restrict
     const int xs = (int)(c0 - (c0 % kAlign));
     const int off = (int)(c0 - xs);                        // 0 .. kAlign-1
 
+    // q*kappa, d and the forcing: no launch of the step sequence writes them, so
+    // they are read before the wait for the previous launch
+    const int ys = (int)y0;
     if (tid == 0) {
         mbar_init(bar, 1);
         mbar_expect_tx(bar, (unsigned)(3 * (size_t)(H + 2) * BW * sizeof(T)));
-        const int ys = (int)y0;
-        tma_load_3d(su0, &maps.m[in0], xs, ys, rhs, bar);
-        tma_load_3d(su1, &maps.m[in1], xs, ys, rhs, bar);
         tma_load_2d(sk, &maps.m[4], xs, ys, bar);
     }
 
@@ -182,28 +201,6 @@ tb2d_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, T *__restrict
         rfr[i] = in ? fre[g] : T(0);
         rfi[i] = in ? fim[g] : T(0);
     }
-
-    __syncthreads();                                      // barrier initialised before anyone waits
-    const bool ok = mbar_wait_bounded(bar);
-    if (__syncthreads_or(!ok)) {
-        // give up: record it, wait (bounded) once more for the copies in flight, return
-        if (tid == 0) {
-            atomicExch(err, 1);
-            mbar_wait_bounded(bar);
-        }
-        __syncthreads();
-        return;
-    }
-
-    // smem positions: node (ly, lx) at row ly + 1, column lx + 1 + off; its
-    // cells (ly + ay, lx + ax) at row ly + ay, column lx + ax + off
-    const bool col_owned = lx >= B && lx < B + TX;
-    const int cc = lx + off;                               // smem column of (lx - 1)
-    // rows of this tile inside the domain: y0 + ly in [0, ny)
-    const int dom_lo = (int)max((int64_t)0, -y0);
-    const int dom_hi = (int)min((int64_t)H, (int64_t)L.ny - y0);
-
-    const Stencil2dCoef<T> SC = stencil2d_coef(C);
     // per-step forcing coefficients and flags, staged in shared memory so that
     // the step loop does not index the parameter block dynamically
     __shared__ T s_a[kTbMaxSteps], s_b[kTbMaxSteps];
@@ -216,7 +213,34 @@ tb2d_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, T *__restrict
             s_flags[q] = S.flags[q];
         }
     }
-    __syncthreads();
+
+    grid_dep_wait();                                      // the state planes are final from here
+    if (tid == 0) {
+        tma_load_3d(su0, &maps.m[in0], xs, ys, rhs, bar);
+        tma_load_3d(su1, &maps.m[in1], xs, ys, rhs, bar);
+    }
+    __syncthreads();                                      // barrier initialised before anyone waits
+    const bool ok = mbar_wait_bounded(bar);
+    if (__syncthreads_or(!ok)) {
+        // give up: record it, wait (bounded) once more for the copies in flight, return
+        if (tid == 0) {
+            atomicExch(err, 1);
+            mbar_wait_bounded(bar);
+        }
+        __syncthreads();
+        return;
+    }
+    grid_dep_launch();
+
+    // smem positions: node (ly, lx) at row ly + 1, column lx + 1 + off; its
+    // cells (ly + ay, lx + ax) at row ly + ay, column lx + ax + off
+    const bool col_owned = lx >= B && lx < B + TX;
+    const int cc = lx + off;                               // smem column of (lx - 1)
+    // rows of this tile inside the domain: y0 + ly in [0, ny)
+    const int dom_lo = (int)max((int64_t)0, -y0);
+    const int dom_hi = (int)min((int64_t)H, (int64_t)L.ny - y0);
+
+    const Stencil2dCoef<T> SC = stencil2d_coef(C);
 
     // one step over this thread's rows; WITH_OUT: also write the owned nodes to
     // the output vector (the snapshot / final steps only)
@@ -334,12 +358,12 @@ tb2d_pair_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, float *_
     fim += rhs * R.stride;
     slot += rhs;
 
+    // q*kappa, d and the forcing before the wait for the previous launch (as in
+    // tb2d_kernel)
+    const int ys = (int)y0;
     if (tid == 0) {
         mbar_init(bar, 1);
         mbar_expect_tx(bar, (unsigned)(3 * (size_t)(H + 2) * BW * sizeof(T)));
-        const int ys = (int)y0;
-        tma_load_3d(su0, &maps.m[in0], xs, ys, rhs, bar);
-        tma_load_3d(su1, &maps.m[in1], xs, ys, rhs, bar);
         tma_load_2d(sk, &maps.m[4], xs, ys, bar);
     }
 
@@ -358,25 +382,6 @@ tb2d_pair_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, float *_
         rfr[i] = pr(a ? fre[g] : 0.f, b ? fre[g + 1] : 0.f);
         rfi[i] = pr(a ? fim[g] : 0.f, b ? fim[g + 1] : 0.f);
     }
-
-    __syncthreads();
-    const bool ok = mbar_wait_bounded(bar);
-    if (__syncthreads_or(!ok)) {
-        if (tid == 0) {
-            atomicExch(err, 1);
-            mbar_wait_bounded(bar);
-        }
-        __syncthreads();
-        return;
-    }
-
-    const bool ownA = lx >= B && lx < B + TX;              // lx and lx+1 are owned together
-    const int cc = lx + off;                               // smem column of lx - 1 (odd)
-    const int dom_lo = (int)max((int64_t)0, -y0);
-    const int dom_hi = (int)min((int64_t)H, (int64_t)L.ny - y0);
-    const Stencil2dCoef<float2> SC = stencil2d_coef2(C);
-    const float2 n2 = pr(-2.f, -2.f);
-
     __shared__ T s_a[kTbMaxSteps], s_b[kTbMaxSteps];
     __shared__ int s_flags[kTbMaxSteps];
     if (tid == 0) {
@@ -387,7 +392,30 @@ tb2d_pair_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, float *_
             s_flags[q] = S.flags[q];
         }
     }
+
+    grid_dep_wait();
+    if (tid == 0) {
+        tma_load_3d(su0, &maps.m[in0], xs, ys, rhs, bar);
+        tma_load_3d(su1, &maps.m[in1], xs, ys, rhs, bar);
+    }
     __syncthreads();
+    const bool ok = mbar_wait_bounded(bar);
+    if (__syncthreads_or(!ok)) {
+        if (tid == 0) {
+            atomicExch(err, 1);
+            mbar_wait_bounded(bar);
+        }
+        __syncthreads();
+        return;
+    }
+    grid_dep_launch();
+
+    const bool ownA = lx >= B && lx < B + TX;              // lx and lx+1 are owned together
+    const int cc = lx + off;                               // smem column of lx - 1 (odd)
+    const int dom_lo = (int)max((int64_t)0, -y0);
+    const int dom_hi = (int)min((int64_t)H, (int64_t)L.ny - y0);
+    const Stencil2dCoef<float2> SC = stencil2d_coef2(C);
+    const float2 n2 = pr(-2.f, -2.f);
 
     // u row r of the plane as the pairs (m, 0, p) = (u(lx-1+o), u(lx+o)), o = 0, 1, 2
     auto urow = [&](const T *pl, int r, float2 &m, float2 &z, float2 &p) {
@@ -619,19 +647,37 @@ bool make_tb2d_maps(const Layout &L, const TbPlan &p, T *const planes[5], TbMaps
     return true;
 }
 
+// launch through cudaLaunchKernelEx, with programmatic stream serialisation
+// when `overlap` is set
+template <typename... KArgs, typename... Args>
+void launch_ex(void (*kern)(KArgs...), dim3 grd, unsigned threads, size_t smem, cudaStream_t s,
+               bool overlap, Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grd;
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = overlap ? 1 : 0;
+    (void)cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);   // errors: cudaGetLastError
+}
+
 template <typename T>
 void launch_tb2d(const TbPlan &p, const TbMaps &maps, int in0, int in1, const Layout &L, T *uC,
                  T *uD, const T *dco, const T *fre, const T *fim, const StepCoef<T> &C,
                  const TbSteps<T> &S, const OutSlot *slot, int *err, cudaStream_t s,
-                 const RhsSet &R)
+                 const RhsSet &R, bool overlap)
 {
     dim3 grd((unsigned)p.grid_x, (unsigned)p.grid_y, (unsigned)R.slots);
     if constexpr (std::is_same<T, float>::value) {
 #define HTD_TB2D_PAIR_CASE(BB, RR, GG)                                                          \
         if (p.pair && p.B == BB && p.RPT == RR && p.RG == GG) {                                 \
-            tb2d_pair_kernel<BB, RR, GG><<<grd, 32 * GG, p.smem, s>>>(maps, in0, in1, uC, uD,   \
-                                                                      dco, fre, fim, L, C, S,   \
-                                                                      slot, err, R);            \
+            launch_ex(tb2d_pair_kernel<BB, RR, GG>, grd, 32 * GG, p.smem, s, overlap, maps, in0, \
+                      in1, uC, uD, dco, fre, fim, L, C, S, slot, err, R);                       \
             ++g_launches;                                                                       \
             return;                                                                             \
         }
@@ -647,8 +693,8 @@ void launch_tb2d(const TbPlan &p, const TbMaps &maps, int in0, int in1, const La
     if (p.pair) return;
 #define HTD_TB2D_CASE(BB, RR, GG)                                                              \
     if (p.B == BB && p.RPT == RR && p.RG == GG) {                                              \
-        tb2d_kernel<T, BB, RR, GG><<<grd, kW * GG, p.smem, s>>>(maps, in0, in1, uC, uD, dco,   \
-                                                               fre, fim, L, C, S, slot, err, R); \
+        launch_ex(tb2d_kernel<T, BB, RR, GG>, grd, kW * GG, p.smem, s, overlap, maps, in0, in1,   \
+                  uC, uD, dco, fre, fim, L, C, S, slot, err, R);                               \
         ++g_launches;                                                                          \
         return;                                                                                \
     }
@@ -668,6 +714,6 @@ template bool make_tb2d_maps<float>(const Layout &, const TbPlan &, float *const
 template void launch_tb2d<float>(const TbPlan &, const TbMaps &, int, int, const Layout &, float *,
                                  float *, const float *, const float *, const float *,
                                  const StepCoef<float> &, const TbSteps<float> &, const OutSlot *,
-                                 int *, cudaStream_t, const RhsSet &);
+                                 int *, cudaStream_t, const RhsSet &, bool);
 
 }  // namespace htd

@@ -227,12 +227,12 @@ void free_ctx(htd_ctx *c)
 }
 
 // one preconditioner run of T n_P steps; the forcing planes are already filled.
-// Consecutive blocked launches overlap (programmatic dependent launch) unless
-// HTD_TB_OVERLAP=0 (a tuning override).
-bool tb_overlap()
+// Consecutive launches of the blocked 2-D and the streamed 3-D step overlap
+// (programmatic dependent launch) unless HTD_OVERLAP=0 (a tuning override).
+bool step_overlap()
 {
     static const bool on = [] {
-        const char *e = std::getenv("HTD_TB_OVERLAP");
+        const char *e = std::getenv("HTD_OVERLAP");
         return !(e && std::atoi(e) == 0);
     }();
     return on;
@@ -326,7 +326,7 @@ htd_status run_steps_direct(htd_ctx *c, cudaStream_t s)
             htd::launch_tb2d<T>(c->tb, c->tbmaps, map_of[from][0], map_of[from][1], L,
                                 pairs[1 - from][0], pairs[1 - from][1], (const T *)c->dco,
                                 (const T *)c->fre, (const T *)c->fim, C, S, c->slot,
-                                c->err_dev, s, c->Rs, j0 > 0 && tb_overlap());
+                                c->err_dev, s, c->Rs, j0 > 0 && step_overlap());
             from = 1 - from;
         }
         // the blocked launches leave u_{jend} in pairs[from][0], u_{jend-1} in pairs[from][1]
@@ -348,7 +348,8 @@ htd_status run_steps_direct(htd_ctx *c, cudaStream_t s)
                 if (c->s3_shape == kS3Pair)
                     htd::launch_stream3d_pair(c->s3maps, (int)(j & 1), L, um, C,
                                               (T)c->atab[j], (T)c->btab[j], c->slot, flags,
-                                              c->s3_zchunk, c->s3_stages, c->err_dev, s, c->Rs);
+                                              c->s3_zchunk, c->s3_stages, c->err_dev, s, c->Rs,
+                                              j > 0 && step_overlap());
                 else
                     htd::launch_stream3d(c->s3maps, (int)(j & 1), c->s3_shape, L, um, C,
                                          (T)c->atab[j], (T)c->btab[j], c->slot, flags,
@@ -682,7 +683,7 @@ htd_status autotune_tb2d(htd_ctx *c, int want_B, int want_RPT)
             htd::launch_tb2d<float>(cands[k], maps, 0, 1, L, (float *)c->u2, (float *)c->u3,
                                     (const float *)c->dco, (const float *)c->fre,
                                     (const float *)c->fim, C, S, c->slot, c->err_dev, s,
-                                    htd::RhsSet{}, r > 0 && tb_overlap());
+                                    htd::RhsSet{}, r > 0 && step_overlap());
         }
         HTD_CUDA(cudaEventRecord(e1, s));
         HTD_CUDA(cudaEventSynchronize(e1));
@@ -747,7 +748,8 @@ htd_status autotune_s3_zchunk(htd_ctx *c)
             if (c->s3_shape == kS3Pair)
                 htd::launch_stream3d_pair(c->s3maps, r & 1, L, (r & 1) ? (float *)c->u0
                                                                         : (float *)c->u1,
-                                          C, 0.f, 0.f, c->slot, 0, zc, c->s3_stages, c->err_dev, s);
+                                          C, 0.f, 0.f, c->slot, 0, zc, c->s3_stages, c->err_dev, s,
+                                          htd::RhsSet{}, r > 0 && step_overlap());
             else
                 htd::launch_stream3d(c->s3maps, r & 1, c->s3_shape, L,
                                      (r & 1) ? (float *)c->u0 : (float *)c->u1, C, 0.f, 0.f,

@@ -138,6 +138,28 @@ __device__ __forceinline__ bool rhs_of_slot(const RhsSet &R, int k, int &rhs)
 // across handles used concurrently; used for statistics only).
 extern long long g_launches;
 
+// Launch through cudaLaunchKernelEx; with `overlap`, programmatic stream
+// serialisation: the kernel may start while the previous kernel of the stream
+// drains, and must call griddepcontrol.wait before it reads anything that
+// kernel writes or writes anything that kernel reads.  Launch errors are left
+// for cudaGetLastError.
+template <typename... KArgs, typename... Args>
+void launch_ex(void (*kern)(KArgs...), dim3 grd, unsigned threads, size_t smem, cudaStream_t s,
+               bool overlap, Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grd;
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = overlap ? 1 : 0;
+    (void)cudaLaunchKernelEx(&cfg, kern, static_cast<Args &&>(args)...);
+}
+
 template <typename T>
 void launch_step(const Layout &L, const T *u, T *um, const T *kap, const T *dco,
                  const T *fre, const T *fim, const StepCoef<T> &C, T a, T b,
@@ -327,10 +349,13 @@ bool make_stream3d_pair_maps(const Layout &L, float *const planes[6], Stream3Map
                              int nrhs = 1);
 // stages: 6 (2 CTAs per SM) or 4 (3 CTAs per SM)
 int stream3d_pair_zchunk(const Layout &L, int stages);
+// overlap: the launch may start while the previous kernel of the stream drains
+// (its prologue loads q*kappa, d and the forcing, which no step writes; the
+// state planes are loaded after the wait for that kernel)
 void launch_stream3d_pair(const Stream3Maps &maps, int from, const Layout &L, float *um,
                           const StepCoef<float> &C, float a, float b, const OutSlot *slot,
                           int flags, int zchunk, int stages, int *err, cudaStream_t s,
-                          const RhsSet &R = RhsSet{});
+                          const RhsSet &R = RhsSet{}, bool overlap = false);
 
 // Gradient through the recurrence (htd_grad_td): res = U[rec] - d and the
 // adjoint forcing planes are/aim (padded, pre-zeroed) += Re/Im res at receivers

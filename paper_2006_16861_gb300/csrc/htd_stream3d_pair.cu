@@ -103,19 +103,41 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
-// stored plane p of rhs r: u_j and q*kappa with the halo, d, Re F, Im F, u_{j-1}
-__device__ __forceinline__ void load_stage(const Stream3Maps &maps, int iu, int ium, float *stage,
-                                           uint64_t *bar, int xs, int xn, int y0, int p, int r)
+// Stored plane p of rhs r into one stage: u_j and q*kappa with the halo, d,
+// Re F, Im F, u_{j-1}.  The stage's byte count is announced first; the
+// coefficient part (q*kappa, d, forcing: no step writes them) and the state
+// part (u_j, u_{j-1}) may be issued separately.
+__device__ __forceinline__ void load_stage_coef(const Stream3Maps &maps, float *stage, uint64_t *bar,
+                                                int xs, int xn, int y0, int p, int r)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                  "r"(kStageTxBytes)
                  : "memory");
-    tma_load_4d(stage, &maps.m[iu], xs, y0, p, r, bar);
     tma_load_3d(stage + kHaloStride, &maps.m[2], xs, y0, p, bar);
     tma_load_3d(stage + 2 * kHaloStride, &maps.m[3], xn, y0 + 1, p, bar);
     tma_load_4d(stage + 2 * kHaloStride + kNodeElems, &maps.m[4], xn, y0 + 1, p, r, bar);
     tma_load_4d(stage + 2 * kHaloStride + 2 * kNodeElems, &maps.m[5], xn, y0 + 1, p, r, bar);
+}
+
+__device__ __forceinline__ void load_stage_state(const Stream3Maps &maps, int iu, int ium,
+                                                 float *stage, uint64_t *bar, int xs, int xn,
+                                                 int y0, int p, int r)
+{
+    tma_load_4d(stage, &maps.m[iu], xs, y0, p, r, bar);
     tma_load_4d(stage + 2 * kHaloStride + 3 * kNodeElems, &maps.m[ium], xn, y0 + 1, p, r, bar);
+}
+
+// programmatic dependent launch (no-ops for an ordinary launch): code before
+// grid_dep_wait() may overlap the previous kernel of the stream; after it,
+// everything that kernel wrote is visible
+__device__ __forceinline__ void grid_dep_wait()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+__device__ __forceinline__ void grid_dep_launch()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // pair helpers
@@ -171,17 +193,28 @@ stream3d_pair_kernel(const __grid_constant__ Stream3Maps maps, int iu, int ium,
         abort_flag = 0;
     }
     __syncthreads();
+    grid_dep_launch();       // the next step may be scheduled as this grid's CTAs retire
 
     // ---- producer warp ----------------------------------------------------
     if (tid >= kThreads) {
         if (tid == kThreads) {
-            for (int p = 0; p < nplanes; ++p) {
+            // the first NS stages: coefficients before the wait for the previous
+            // step, states after it
+            const int npre = min(NS, nplanes);
+            for (int p = 0; p < npre; ++p)
+                load_stage_coef(maps, ring + p * kStageElems, &full[p], xs, xn, (int)y0,
+                                (int)(zb + p), rhs);
+            grid_dep_wait();
+            for (int p = 0; p < npre; ++p)
+                load_stage_state(maps, iu, ium, ring + p * kStageElems, &full[p], xs, xn, (int)y0,
+                                 (int)(zb + p), rhs);
+            for (int p = NS; p < nplanes; ++p) {
                 const int st = p % NS;
-                if (p >= NS && !wait_bounded(&empty[st], (unsigned)(((p / NS) - 1) & 1),
-                                                  &abort_flag))
-                    break;
-                load_stage(maps, iu, ium, ring + st * kStageElems, &full[st], xs, xn, (int)y0,
-                           (int)(zb + p), rhs);
+                if (!wait_bounded(&empty[st], (unsigned)(((p / NS) - 1) & 1), &abort_flag)) break;
+                float *stage = ring + st * kStageElems;
+                load_stage_coef(maps, stage, &full[st], xs, xn, (int)y0, (int)(zb + p), rhs);
+                load_stage_state(maps, iu, ium, stage, &full[st], xs, xn, (int)y0, (int)(zb + p),
+                                 rhs);
             }
             if (abort_flag) {
                 atomicExch(err, 1);
@@ -198,6 +231,7 @@ stream3d_pair_kernel(const __grid_constant__ Stream3Maps maps, int iu, int ium,
     }
 
     // ---- consumer warps: nodes (x, x+1), x = x0 + 2 tx, row y = y0 + ty ----
+    grid_dep_wait();         // before any write of a plane the previous step reads
     const int tx = tid & 31, ty = tid >> 5;
     const int lane = tid & 31;
     const int64_t gx = x0 + 2 * tx, gy = y0 + ty;
@@ -389,17 +423,17 @@ int stream3d_pair_zchunk(const Layout &L, int stages)
 void launch_stream3d_pair(const Stream3Maps &maps, int from, const Layout &L, float *um,
                           const StepCoef<float> &C, float a, float b, const OutSlot *slot,
                           int flags, int zchunk, int stages, int *err, cudaStream_t s,
-                          const RhsSet &R)
+                          const RhsSet &R, bool overlap)
 {
     const int iu = from ? 1 : 0, ium = from ? 6 : 7;
     dim3 grd((unsigned)(((L.nx + kTX - 1) / kTX) * R.slots), (unsigned)((L.ny + kTY - 1) / kTY),
              (unsigned)((L.nz + zchunk - 1) / zchunk));
     if (stages == 4)
-        stream3d_pair_kernel<4><<<grd, kThreads + 32, stream3d_pair_smem_bytes(4), s>>>(
-            maps, iu, ium, um, L, C, a, b, slot, flags, zchunk, err, R);
+        launch_ex(stream3d_pair_kernel<4>, grd, kThreads + 32, stream3d_pair_smem_bytes(4), s,
+                  overlap, maps, iu, ium, um, L, C, a, b, slot, flags, zchunk, err, R);
     else
-        stream3d_pair_kernel<6><<<grd, kThreads + 32, stream3d_pair_smem_bytes(6), s>>>(
-            maps, iu, ium, um, L, C, a, b, slot, flags, zchunk, err, R);
+        launch_ex(stream3d_pair_kernel<6>, grd, kThreads + 32, stream3d_pair_smem_bytes(6), s,
+                  overlap, maps, iu, ium, um, L, C, a, b, slot, flags, zchunk, err, R);
     ++g_launches;
 }
 

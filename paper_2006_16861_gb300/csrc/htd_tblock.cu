@@ -27,7 +27,6 @@
 
 #include <algorithm>
 #include <type_traits>
-#include <utility>
 #include <vector>
 
 #include "htd_internal.h"
@@ -645,25 +644,6 @@ bool make_tb2d_maps(const Layout &L, const TbPlan &p, T *const planes[5], TbMaps
             return false;
     }
     return true;
-}
-
-// launch through cudaLaunchKernelEx, with programmatic stream serialisation
-// when `overlap` is set
-template <typename... KArgs, typename... Args>
-void launch_ex(void (*kern)(KArgs...), dim3 grd, unsigned threads, size_t smem, cudaStream_t s,
-               bool overlap, Args &&...args)
-{
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grd;
-    cfg.blockDim = dim3(threads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = overlap ? 1 : 0;
-    (void)cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);   // errors: cudaGetLastError
 }
 
 template <typename T>

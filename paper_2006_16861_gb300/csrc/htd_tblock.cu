@@ -13,11 +13,15 @@
 // (programmatic dependent launch): a launch reads q*kappa, d and the forcing
 // while the previous one drains and loads the state planes after it.
 //
-// Step s (s = 0 .. nsub-1) updates the nodes of the ring-shrunk region
-// [s+1, 63-s) x [s+1, H-s-1); after nsub <= B steps the owned core
-// [B, B+TX) x [B, B+TY) holds u_{j+nsub} and u_{j+nsub-1}, which are stored to
-// the other pair of global state planes (so that neighbouring CTAs never read
-// a half-updated halo).  Per node the arithmetic is exactly that of
+// Step s (s = 0 .. nsub-1) gives correct values on the ring-shrunk region
+// R_s = [s+1, 63-s) x [s+1, H-s-1), whose stencil reads only R_{s-1}; after
+// nsub <= B steps the owned core [B, B+TX) x [B, B+TY) holds u_{j+nsub} and
+// u_{j+nsub-1}, which are stored to the other pair of global state planes (so
+// that neighbouring CTAs never read a half-updated halo).  Every node of the
+// tile is written in every step, without a per-node test: outside R_s the
+// value is never read by a node of R_{s+1}, and outside the domain d = 0 (and
+// the forcing is zero), so the update returns u_{j+s-1} = 0 there exactly and
+// the zero Dirichlet ring stays zero.  Per node the arithmetic is exactly that of
 // step2d_kernel (same expression, same order).
 //
 // Threads: 64 columns x RG row groups; a thread walks down its rows with a 3x3
@@ -249,9 +253,6 @@ tb2d_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, T *__restrict
         T *__restrict__ prv = (s & 1) ? su0 : su1;         // u_{j+s-1}, overwritten by u_{j+s+1}
         const T a = s_a[s], b = s_b[s];
         const int flags = s_flags[s];
-        const bool col_ok = col_in_domain && lx >= s + 1 && lx < W - s - 1;
-        // rows updated in this step: ring-shrunk region and the domain
-        const int lo = max(s + 1, dom_lo), hi = min(H - s - 1, dom_hi);
         // window: rows row0 - 1 (m) and row0 (0); outer-pair sums of u rows and
         // horizontal sums of cell rows carried from row to row
         const T *cp = cur + row0 * BW + cc;
@@ -270,15 +271,14 @@ tb2d_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, T *__restrict
             const T hk1 = k10 + k11;
             const T acc = stencil2d(SC, umm, um0, ump, u0m, u00, u0p, upm, up0, upp, k00, k01, k10,
                                     k11, pm, p0, pp, hk0, hk1);
-            // every thread stores; outside the updated region it stores u_{j+s-1}
-            // back unchanged, so no per-row branch is needed
+            // every node stores (see the header: no per-node test is needed)
             const int ni = (ly + 1) * BW + cc + 1;
             const T g = vfma(a, rfr[i], vmul(-b, rfi[i]));
             const T uprev = prv[ni];
             const T unew = vfma(rd[i], vfma(T(-2), uprev, vadd(acc, g)), uprev);
-            const bool upd = col_ok && ly >= lo && ly < hi;
-            prv[ni] = upd ? unew : uprev;
-            if (kOut && upd && col_owned && ly >= B && ly < B + TY) {
+            prv[ni] = unew;
+            if (kOut && col_in_domain && col_owned && ly >= B && ly < B + TY && ly >= dom_lo &&
+                ly < dom_hi) {
                 const int64_t c = (y0 + ly) * L.nx + gx;
                 if ((flags & 1) && slot->snap_part) slot->snap_part[2 * c] = (double)unew;
                 if ((flags & 2) && slot->final_part) slot->final_part[2 * c] = (double)unew;
@@ -438,9 +438,6 @@ tb2d_pair_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, float *_
         T *__restrict__ prv = (s & 1) ? su0 : su1;
         const float2 a2 = pr(s_a[s], s_a[s]), nb2 = pr(-s_b[s], -s_b[s]);
         const int flags = s_flags[s];
-        const bool okA = inA && lx >= s + 1 && lx < W - s - 1;
-        const bool okB = inB && lx + 1 >= s + 1 && lx + 1 < W - s - 1;
-        const int lo = max(s + 1, dom_lo), hi = min(H - s - 1, dom_hi);
         float2 umm, um0, ump, u0m, u00, u0p;
         urow(cur, row0, umm, um0, ump);
         urow(cur, row0 + 1, u0m, u00, u0p);
@@ -462,18 +459,16 @@ tb2d_pair_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, float *_
             const float2 g = vfma(a2, rfr[i], vmul(nb2, rfi[i]));
             const float2 uprev = *reinterpret_cast<const float2 *>(prv + ni);
             const float2 unew = vfma(rd[i], vfma(n2, uprev, vadd(acc, g)), uprev);
-            const bool rowupd = ly >= lo && ly < hi;
-            const bool uA = okA && rowupd, uB = okB && rowupd;
-            *reinterpret_cast<float2 *>(prv + ni) = pr(uA ? unew.x : uprev.x, uB ? unew.y : uprev.y);
-            if (kOut && ownA && ly >= B && ly < B + TY) {
+            *reinterpret_cast<float2 *>(prv + ni) = unew;   // no per-node test (header)
+            if (kOut && ownA && ly >= B && ly < B + TY && ly >= dom_lo && ly < dom_hi) {
                 const int64_t c = (y0 + ly) * L.nx + gx;
                 if ((flags & 1) && slot->snap_part) {
-                    if (uA) slot->snap_part[2 * c] = (double)unew.x;
-                    if (uB) slot->snap_part[2 * c + 2] = (double)unew.y;
+                    if (inA) slot->snap_part[2 * c] = (double)unew.x;
+                    if (inB) slot->snap_part[2 * c + 2] = (double)unew.y;
                 }
                 if ((flags & 2) && slot->final_part) {
-                    if (uA) slot->final_part[2 * c] = (double)unew.x;
-                    if (uB) slot->final_part[2 * c + 2] = (double)unew.y;
+                    if (inA) slot->final_part[2 * c] = (double)unew.x;
+                    if (inB) slot->final_part[2 * c + 2] = (double)unew.y;
                 }
             }
             umm = u0m; um0 = u00; ump = u0p; pm = p0;

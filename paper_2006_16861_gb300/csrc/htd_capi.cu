@@ -634,9 +634,11 @@ htd_status autotune_tb2d(htd_ctx *c, int want_B, int want_RPT)
     std::vector<htd::TbPlan> all = htd::tb2d_candidates<float>(L, want_B);
     std::vector<htd::TbPlan> cands;
     const char *env_pair = std::getenv("HTD_TB_PAIR");     // tuning override: 0 scalar, 1 pairs
+    const char *env_sd = std::getenv("HTD_TB_SD");         // tuning override: d in smem 0/1
     for (const htd::TbPlan &p : all)
         if ((want_RPT == 0 || p.RPT == want_RPT) &&
-            (!env_pair || (int)p.pair == std::atoi(env_pair)))
+            (!env_pair || (int)p.pair == std::atoi(env_pair)) &&
+            (!env_sd || (int)p.sd == std::atoi(env_sd)))
             cands.push_back(p);
     if (cands.empty()) return HTD_OK;
     const size_t bytes = sizeof(float) * (size_t)L.total * c->rcap;
@@ -650,8 +652,8 @@ htd_status autotune_tb2d(htd_ctx *c, int want_B, int want_RPT)
     HTD_CUDA(cudaEventCreate(&e0));
     HTD_CUDA(cudaEventCreate(&e1));
     const StepCoef<float> C = cast_coef<float>(c->C);
-    float *planes[5] = {(float *)c->u0, (float *)c->u1, (float *)c->u2, (float *)c->u3,
-                        (float *)c->kap};
+    float *planes[6] = {(float *)c->u0, (float *)c->u1, (float *)c->u2, (float *)c->u3,
+                        (float *)c->kap, (float *)c->dco};
     const int reps = 4;
     // the one-step kernel
     float best_us = INFINITY;
@@ -1190,8 +1192,9 @@ htd_status create_impl(const htd_grid *grid, const double *c_cell, const double 
     HTD_CUDA(cudaMemcpy(c->imH, imh.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
 
     // temporal blocking for the 2-D FP32 recurrence, picked by timing against the
-    // one-step kernel.  HTD_TB=0 disables it; HTD_TB=4/8 (and HTD_TB_RPT=8/12/16/20)
-    // force a blocked configuration of that depth (and rows per thread).
+    // one-step kernel.  HTD_TB=0 disables it; HTD_TB=4/8 (and HTD_TB_RPT=6/8/10/12/20,
+    // HTD_TB_PAIR=0/1, HTD_TB_SD=0/1) force a blocked configuration of that depth
+    // (rows per thread, pair form, d in shared memory); tuning overrides.
     {
         const char *env = std::getenv("HTD_TB");
         const char *env_r = std::getenv("HTD_TB_RPT");

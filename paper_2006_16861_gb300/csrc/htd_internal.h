@@ -261,6 +261,7 @@ struct TbPlan {
     int RG = 0;         // row groups: tile rows H = RG * RPT, threads 64 * RG (32 * RG
                         // for node pairs)
     bool pair = false;  // two adjacent columns per thread in paired FP32 instructions
+    bool sd = false;    // (pair form) d staged in shared memory instead of registers
     int TX = 0, TY = 0; // owned tile
     int H = 0;          // tile rows including the halo
     size_t smem = 0;    // dynamic shared memory per CTA
@@ -270,9 +271,9 @@ struct TbPlan {
     float us_per_step = 0.f;   // measured by the autotuner
 };
 
-// TMA descriptors of the planes u0, u1, u2, u3 and q*kappa.
+// TMA descriptors of the planes u0, u1, u2, u3, q*kappa and d.
 struct TbMaps {
-    CUtensorMap m[5];
+    CUtensorMap m[6];
 };
 
 // The blocked-kernel configurations (B = 4 or 8 steps per launch, want_B = 0:
@@ -283,7 +284,7 @@ std::vector<TbPlan> tb2d_candidates(const Layout &L, int want_B);
 // The four state planes are nrhs stacks of planes L.total elements apart (one
 // per rhs, 3-D maps with the rhs as the outer coordinate); q*kappa is shared.
 template <typename T>
-bool make_tb2d_maps(const Layout &L, const TbPlan &p, T *const planes[5], TbMaps *maps,
+bool make_tb2d_maps(const Layout &L, const TbPlan &p, T *const planes[6], TbMaps *maps,
                     int nrhs = 1);
 
 // nsub <= B steps from the state pair (maps in0, in1) into the planes uC, uD;

@@ -50,10 +50,12 @@ __host__ __device__ constexpr size_t tb2d_array_bytes(int H)
     return (((size_t)(H + 2) * kBoxW * sizeof(T)) + 127) & ~(size_t)127;
 }
 
+// `arrays` boxes (u_j, u_{j-1}, q*kappa and, for the pair form with d staged,
+// d) and the mbarrier
 template <typename T>
-size_t tb2d_smem_bytes(int H)
+size_t tb2d_smem_bytes(int H, int arrays = 3)
 {
-    return 3 * tb2d_array_bytes<T>(H) + 16;   // three boxes and the mbarrier
+    return arrays * tb2d_array_bytes<T>(H) + 16;
 }
 
 __device__ __forceinline__ unsigned smem_u32(const void *p)
@@ -316,10 +318,12 @@ tb2d_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, T *__restrict
 // tb2d_kernel and step2d_kernel).  The columns of a pair sit at an even shared
 // memory column (the box starts one column left of a 16-byte boundary and
 // tiles start at even x), so (lx, lx+1) is one 64-bit access; lx - 1 and
-// lx + 2 are single loads.
+// lx + 2 are single loads.  SD: d comes from a fourth TMA box in shared memory
+// (zero outside the domain, like the register copy) instead of registers,
+// which frees 2 RPT registers per thread for more resident warps.
 __device__ __forceinline__ float2 pr(float a, float b) { return make_float2(a, b); }
 
-template <int B, int RPT, int RG>
+template <int B, int RPT, int RG, bool SD>
 __global__ void __launch_bounds__(32 * RG, 1)
 tb2d_pair_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, float *__restrict__ uC,
                  float *__restrict__ uD, const float *__restrict__ dco,
@@ -336,7 +340,9 @@ tb2d_pair_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, float *_
     T *su0 = smem_t;
     T *su1 = smem_t + ae;
     T *sk = smem_t + 2 * ae;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_t + 3 * ae);
+    T *sd = smem_t + 3 * ae;                               // SD only
+    constexpr int kArrays = SD ? 4 : 3;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_t + kArrays * ae);
 
     const int tid = threadIdx.x;
     int rhs;
@@ -362,22 +368,23 @@ tb2d_pair_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, float *_
     const int ys = (int)y0;
     if (tid == 0) {
         mbar_init(bar, 1);
-        mbar_expect_tx(bar, (unsigned)(3 * (size_t)(H + 2) * BW * sizeof(T)));
+        mbar_expect_tx(bar, (unsigned)(kArrays * (size_t)(H + 2) * BW * sizeof(T)));
         tma_load_2d(sk, &maps.m[4], xs, ys, bar);
+        if (SD) tma_load_2d(sd, &maps.m[5], xs, ys, bar);
     }
 
     const int lx = 2 * (tid & 31);                        // first column of the pair
     const int row0 = (tid >> 5) * RPT;
     const int64_t gx = x0 + lx;
     const bool inA = gx >= 0 && gx < L.nx, inB = gx + 1 >= 0 && gx + 1 < L.nx;
-    float2 rd[RPT], rfr[RPT], rfi[RPT];
+    float2 rd[SD ? 1 : RPT], rfr[RPT], rfi[RPT];
 #pragma unroll
     for (int i = 0; i < RPT; ++i) {
         const int64_t gy = y0 + row0 + i;
         const bool rin = gy >= 0 && gy < L.ny;
         const int64_t g = rin ? (gy + 1) * L.pitch + L.xl + gx : 0;
         const bool a = rin && inA, b = rin && inB;
-        rd[i] = pr(a ? dco[g] : 0.f, b ? dco[g + 1] : 0.f);
+        if (!SD) rd[i] = pr(a ? dco[g] : 0.f, b ? dco[g + 1] : 0.f);
         rfr[i] = pr(a ? fre[g] : 0.f, b ? fre[g + 1] : 0.f);
         rfi[i] = pr(a ? fim[g] : 0.f, b ? fim[g + 1] : 0.f);
     }
@@ -458,7 +465,8 @@ tb2d_pair_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, float *_
             const int ni = (ly + 1) * BW + cc + 1;
             const float2 g = vfma(a2, rfr[i], vmul(nb2, rfi[i]));
             const float2 uprev = *reinterpret_cast<const float2 *>(prv + ni);
-            const float2 unew = vfma(rd[i], vfma(n2, uprev, vadd(acc, g)), uprev);
+            const float2 dn = SD ? *reinterpret_cast<const float2 *>(sd + ni) : rd[SD ? 0 : i];
+            const float2 unew = vfma(dn, vfma(n2, uprev, vadd(acc, g)), uprev);
             *reinterpret_cast<float2 *>(prv + ni) = unew;   // no per-node test (header)
             if (kOut && ownA && ly >= B && ly < B + TY && ly >= dom_lo && ly < dom_hi) {
                 const int64_t c = (y0 + ly) * L.nx + gx;
@@ -496,20 +504,20 @@ tb2d_pair_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, float *_
     }
 }
 
-template <int B, int RPT, int RG>
+template <int B, int RPT, int RG, bool SD>
 void add_pair_candidate(const Layout &L, std::vector<TbPlan> &out)
 {
     constexpr int H = RG * RPT, TY = H - 2 * B, TX = kW - 2 * B, kThreads = 32 * RG;
-    const size_t smem = tb2d_smem_bytes<float>(H);
+    const size_t smem = tb2d_smem_bytes<float>(H, SD ? 4 : 3);
     if (H + 2 > 256 || smem > 220 * 1024) return;
-    if (cudaFuncSetAttribute(tb2d_pair_kernel<B, RPT, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess) {
+    if (cudaFuncSetAttribute(tb2d_pair_kernel<B, RPT, RG, SD>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         (void)cudaGetLastError();
         return;
     }
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tb2d_pair_kernel<B, RPT, RG>, kThreads,
-                                                      smem) != cudaSuccess || occ < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tb2d_pair_kernel<B, RPT, RG, SD>,
+                                                      kThreads, smem) != cudaSuccess || occ < 1) {
         (void)cudaGetLastError();
         return;
     }
@@ -521,6 +529,7 @@ void add_pair_candidate(const Layout &L, std::vector<TbPlan> &out)
     p.RPT = RPT;
     p.RG = RG;
     p.pair = true;
+    p.sd = SD;
     p.TX = TX;
     p.TY = TY;
     p.H = H;
@@ -590,24 +599,26 @@ std::vector<TbPlan> tb2d_candidates(const Layout &L, int want_B)
     }
     if constexpr (std::is_same<T, float>::value) {
         if (want_B == 0 || want_B == 4) {
-            add_pair_candidate<4, 10, 16>(L, v);
-            add_pair_candidate<4, 6, 16>(L, v);
-            add_pair_candidate<4, 12, 8>(L, v);
+            add_pair_candidate<4, 10, 16, false>(L, v);
+            add_pair_candidate<4, 6, 16, false>(L, v);
+            add_pair_candidate<4, 12, 8, false>(L, v);
+            add_pair_candidate<4, 8, 20, true>(L, v);
         }
         if (want_B == 0 || want_B == 8) {
-            add_pair_candidate<8, 10, 16>(L, v);
-            add_pair_candidate<8, 6, 16>(L, v);
-            add_pair_candidate<8, 12, 8>(L, v);
-            add_pair_candidate<8, 12, 16>(L, v);
+            add_pair_candidate<8, 10, 16, false>(L, v);
+            add_pair_candidate<8, 6, 16, false>(L, v);
+            add_pair_candidate<8, 12, 8, false>(L, v);
+            add_pair_candidate<8, 8, 20, true>(L, v);
+            add_pair_candidate<8, 10, 16, true>(L, v);
         }
     }
     return v;
 }
 
-// Tensor maps of the planes u0, u1, u2, u3 (3-D: pitch x rows x nrhs) and
-// q*kappa (2-D: pitch x rows) with a kBoxW x (H + 2) box.
+// Tensor maps of the planes u0, u1, u2, u3 (3-D: pitch x rows x nrhs), q*kappa
+// and d (2-D: pitch x rows) with a kBoxW x (H + 2) box.
 template <typename T>
-bool make_tb2d_maps(const Layout &L, const TbPlan &p, T *const planes[5], TbMaps *maps, int nrhs)
+bool make_tb2d_maps(const Layout &L, const TbPlan &p, T *const planes[6], TbMaps *maps, int nrhs)
 {
     typedef CUresult (*EncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
@@ -630,7 +641,7 @@ bool make_tb2d_maps(const Layout &L, const TbPlan &p, T *const planes[5], TbMaps
     const cuuint32_t estr[3] = {1, 1, 1};
     const CUtensorMapDataType dt =
         sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
-    for (int i = 0; i < 5; ++i) {
+    for (int i = 0; i < 6; ++i) {
         const cuuint32_t rank = (i < 4) ? 3 : 2;
         if (encode(&maps->m[i], dt, rank, (void *)planes[i], dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -649,20 +660,22 @@ void launch_tb2d(const TbPlan &p, const TbMaps &maps, int in0, int in1, const La
 {
     dim3 grd((unsigned)p.grid_x, (unsigned)p.grid_y, (unsigned)R.slots);
     if constexpr (std::is_same<T, float>::value) {
-#define HTD_TB2D_PAIR_CASE(BB, RR, GG)                                                          \
-        if (p.pair && p.B == BB && p.RPT == RR && p.RG == GG) {                                 \
-            launch_ex(tb2d_pair_kernel<BB, RR, GG>, grd, 32 * GG, p.smem, s, overlap, maps, in0, \
-                      in1, uC, uD, dco, fre, fim, L, C, S, slot, err, R);                       \
+#define HTD_TB2D_PAIR_CASE(BB, RR, GG, SS)                                                      \
+        if (p.pair && p.B == BB && p.RPT == RR && p.RG == GG && p.sd == SS) {                   \
+            launch_ex(tb2d_pair_kernel<BB, RR, GG, SS>, grd, 32 * GG, p.smem, s, overlap, maps,  \
+                      in0, in1, uC, uD, dco, fre, fim, L, C, S, slot, err, R);                  \
             ++g_launches;                                                                       \
             return;                                                                             \
         }
-        HTD_TB2D_PAIR_CASE(4, 10, 16)
-        HTD_TB2D_PAIR_CASE(4, 6, 16)
-        HTD_TB2D_PAIR_CASE(4, 12, 8)
-        HTD_TB2D_PAIR_CASE(8, 10, 16)
-        HTD_TB2D_PAIR_CASE(8, 6, 16)
-        HTD_TB2D_PAIR_CASE(8, 12, 8)
-        HTD_TB2D_PAIR_CASE(8, 12, 16)
+        HTD_TB2D_PAIR_CASE(4, 10, 16, false)
+        HTD_TB2D_PAIR_CASE(4, 6, 16, false)
+        HTD_TB2D_PAIR_CASE(4, 12, 8, false)
+        HTD_TB2D_PAIR_CASE(4, 8, 20, true)
+        HTD_TB2D_PAIR_CASE(8, 10, 16, false)
+        HTD_TB2D_PAIR_CASE(8, 6, 16, false)
+        HTD_TB2D_PAIR_CASE(8, 12, 8, false)
+        HTD_TB2D_PAIR_CASE(8, 8, 20, true)
+        HTD_TB2D_PAIR_CASE(8, 10, 16, true)
 #undef HTD_TB2D_PAIR_CASE
     }
     if (p.pair) return;
@@ -685,7 +698,7 @@ void launch_tb2d(const TbPlan &p, const TbMaps &maps, int in0, int in1, const La
 }
 
 template std::vector<TbPlan> tb2d_candidates<float>(const Layout &, int);
-template bool make_tb2d_maps<float>(const Layout &, const TbPlan &, float *const[5], TbMaps *, int);
+template bool make_tb2d_maps<float>(const Layout &, const TbPlan &, float *const[6], TbMaps *, int);
 template void launch_tb2d<float>(const TbPlan &, const TbMaps &, int, int, const Layout &, float *,
                                  float *, const float *, const float *, const float *,
                                  const StepCoef<float> &, const TbSteps<float> &, const OutSlot *,

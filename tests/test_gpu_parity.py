@@ -128,22 +128,24 @@ def test_gmres_fp64_config1_converges_to_direct_solution():
 
 
 TB_CASES = [(37, 45), (1, 7), (3, 2), (130, 67), (101, 101), (64, 300)]
-TB_CONFIGS = [("4", "12", "0"), ("4", "10", "0"), ("8", "6", "0"), ("8", "20", "0"),
-              ("4", "10", "1"), ("4", "12", "1"), ("8", "6", "1"), ("8", "12", "1"),
-              (None, None, None)]
+TB_CONFIGS = [("4", "12", "0", "0"), ("4", "10", "0", "0"), ("8", "6", "0", "0"),
+              ("8", "20", "0", "0"), ("4", "10", "1", "0"), ("4", "12", "1", "0"),
+              ("8", "6", "1", "0"), ("8", "12", "1", "0"), ("4", "8", "1", "1"),
+              ("8", "8", "1", "1"), ("8", "10", "1", "1"), (None, None, None, None)]
 
 
 @pytest.mark.parametrize("n", TB_CASES, ids=[f"{a}x{b}" for a, b in TB_CASES])
-@pytest.mark.parametrize("B,rpt,pair", TB_CONFIGS,
-                         ids=[f"B{b}_r{r}_p{q}" for b, r, q in TB_CONFIGS])
+@pytest.mark.parametrize("B,rpt,pair,sd", TB_CONFIGS,
+                         ids=[f"B{b}_r{r}_p{q}_d{d}" for b, r, q, d in TB_CONFIGS])
 @pytest.mark.parametrize("mode", ["table1", "exact"])
-def test_temporal_blocking_matches_one_step(n, B, rpt, pair, mode, monkeypatch):
+def test_temporal_blocking_matches_one_step(n, B, rpt, pair, sd, mode, monkeypatch):
     """The 2-D FP32 recurrence with B steps per launch (shared-memory tiles with a
     halo of B, rows per thread rpt, one column per thread or node pairs in
-    paired FP32 instructions) against the one-step-per-launch kernel, bit for
-    bit (the same roundings in the same order), and the FP64 oracle; None = the
-    autotuner's own choice.  Step counts that are not multiples of B and
-    snapshots inside a launch included."""
+    paired FP32 instructions, d in registers or staged in shared memory)
+    against the one-step-per-launch kernel, bit for bit (the same roundings in
+    the same order), and the FP64 oracle; None = the autotuner's own choice.
+    Step counts that are not multiples of B and snapshots inside a launch
+    included."""
     p = het_problem(2, n, T=3) if min(n) > 1 else het_problem(2, n, T=2)
     monkeypatch.setenv("HTD_TB", "0")
     s0 = htd.Solver(p, precision="mixed", mode=mode)
@@ -153,10 +155,11 @@ def test_temporal_blocking_matches_one_step(n, B, rpt, pair, mode, monkeypatch):
         monkeypatch.setenv("HTD_TB", B)
         monkeypatch.setenv("HTD_TB_RPT", rpt)
         monkeypatch.setenv("HTD_TB_PAIR", pair)
+        monkeypatch.setenv("HTD_TB_SD", sd)
     s1 = htd.Solver(p, precision="mixed", mode=mode)
     if B is not None:
         assert s1.params["steps_per_launch"] == int(B)
-        groups = (16, 8) if pair == "1" else ((16,) if int(rpt) in (6, 10) else (8,))
+        groups = (20, 16, 8) if pair == "1" else ((16,) if int(rpt) in (6, 10) else (8,))
         assert s1.params["tile"][1] in [g * int(rpt) - 2 * int(B) for g in groups]
     o = oracle.Oracle(p)
     for F in (p.F, W.random_rhs(6, p.n)):

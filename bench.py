@@ -538,6 +538,7 @@ def run_ours(args):
                          "frac": achieved / peak,
                          "traffic": ncu_traffic(tkey, N) if tkey else None,
                          "effective_single_step_gbs": N * 4 * WORDS_ONE_STEP * spl / avg_launch_s / 1e9,
+                         "effective_frac": N * 4 * WORDS_ONE_STEP * spl / avg_launch_s / 1e9 / peak,
                          "kernel": kern,
                          "steps_per_launch": spl,
                          "bytes_per_launch": bytes_per_launch,

@@ -55,14 +55,12 @@ WORDS_ONE_STEP, WORDS_BLOCKED = 7, 8
 # file); scaled by node count to other grid sizes.  The captures are summarised
 # under profiles/.
 NCU_TRAFFIC = {
-    "tb2d": {"file": "htd_tblock.cu", "sha16": "911c4093662ebe9d", "bytes": 25086720 + 256,
-             "nodes": 1001 * 1001},
-    "tb2d_pair": {"file": "htd_tblock.cu", "sha16": "36845b87e2bac8d7", "bytes": 25059328 + 512,
+    "tb2d_pair": {"file": "htd_tblock.cu", "sha16": "817cd9e86c007b19", "bytes": 25186304 + 0,
                   "nodes": 1001 * 1001},
     "stream3d": {"file": "htd_stream3d.cu", "sha16": "4f289c964d28aa22",
                  "bytes": 193680896 + 18157568, "nodes": 192 ** 3},
-    "stream3d_pair": {"file": "htd_stream3d_pair.cu", "sha16": "1c9b1035ac857f75",
-                      "bytes": 197444352 + 16969216, "nodes": 192 ** 3},
+    "stream3d_pair": {"file": "htd_stream3d_pair.cu", "sha16": "1dfa3c101a78a408",
+                      "bytes": 197457920 + 17060096, "nodes": 192 ** 3},
 }
 
 

@@ -58,7 +58,7 @@ enum { HTD_MODE_TABLE1 = 0, HTD_MODE_EXACT = 1, HTD_MODE_PROJECT = 2 }; /* preco
 enum { HTD_ACD = 0, HTD_ABD = 1 };               /* time integrator */
 enum { HTD_DAMP_NODE = 0, HTD_DAMP_CELL = 1 };   /* form of Im H */
 enum { HTD_FGMRES = 0, HTD_LEFT_GMRES = 1 };     /* Krylov method */
-enum { HTD_STENCIL_Q1MIX = 0, HTD_STENCIL_FD5 = 1 };
+enum { HTD_STENCIL_Q1MIX = 0, HTD_STENCIL_FD5 = 1, HTD_STENCIL_FAMILY = 2 };
 enum { HTD_BC_DIRICHLET = 0 };
 
 typedef struct {
@@ -85,7 +85,19 @@ typedef struct {
     double rho;        /* window parameter in [0, 1]; 0 means a ramp over one
                           period (rho = 1/T), as in Sec. 5.1 */
     int nP;            /* time steps per period; 0 = smallest stable multiple of 4 */
-    int stencil;       /* HTD_STENCIL_Q1MIX or HTD_STENCIL_FD5 */
+    int stencil;       /* cell kernel of App. A (per Hamming distance s between two
+                          corners of a cell: h^2 H_cell = S_s - (h k)^2 M_s).
+                          HTD_STENCIL_Q1MIX: Q1 element stiffness, half consistent
+                          Q1 mass + half lumped mass (the stand-in for the paper's
+                          optimized coefficients, which it does not print).
+                          HTD_STENCIL_FD5: edge stiffness and lumped mass (the
+                          5-/7-point operator of Sec. 3.1 for constant k).
+                          HTD_STENCIL_FAMILY: S = stencil_gamma S(Q1) +
+                          (1 - stencil_gamma) S(FD5), M = stencil_a M(consistent Q1)
+                          + (1 - stencil_a) M(lumped); (a, gamma) = (0.5, 1) is
+                          Q1MIX and (0, 0) is FD5.  Every member has a PSD cell
+                          stiffness and 0 <= cell mass <= 2^-d I, the properties
+                          the bounds of App. A use */
     int restart;       /* Krylov restart length m for htd_gmres_solve, 1..64 */
     int max_rhs;       /* right-hand sides one batched application may carry for
                           this handle (htd_batch_*), 1..256; 0 means 1.  The
@@ -105,6 +117,15 @@ typedef struct {
                           omega_phys sum over cells of R_cell times the cell mass
                           of App. A (non-diagonal; R_cell the mean of R over the
                           cell's grid corners); needs HTD_ABD */
+    double stencil_a;  /* HTD_STENCIL_FAMILY: weight of the consistent Q1 mass, in
+                          [0, 1] (default 0.5) */
+    double stencil_gamma; /* HTD_STENCIL_FAMILY: weight of the Q1 element stiffness,
+                          in [0, 1] (default 1) */
+    int tblock;        /* recurrence steps per launch of the 2-D FP32 kernel:
+                          0 = chosen at create by timing the one-step kernel and
+                          the blocked configurations (default), 1 = one step per
+                          launch, 4 or 8 = temporally blocked with that depth.
+                          Ignored for other precisions, dimensions and I_abd */
 } htd_options;
 
 typedef struct {
@@ -125,7 +146,7 @@ typedef struct {
 
 /* Fill *opt with the defaults: FP64, TABLE1, FGMRES, T = 10, rho = 0.25,
  * nP = 0 (automatic), Q1MIX stencil, restart 20, max_rhs 1, proj_periods 1,
- * HTD_ACD, HTD_DAMP_NODE. */
+ * HTD_ACD, HTD_DAMP_NODE, stencil_a 0.5, stencil_gamma 1, tblock 0. */
 void htd_default_options(htd_options *opt);
 
 /*

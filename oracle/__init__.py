@@ -6,7 +6,8 @@ check and the benchmark's CPU-baseline / reference leg may import it.  It wraps
 the CUDA library.
 
 Functions take a ``workloads.Problem`` (grid, c per cell, R per node, physical
-omega, T, rho) and a stencil name ("q1mix" or "fd5").
+omega, T, rho) and a stencil name ("q1mix", "fd5", or "family" with the mass
+and stiffness weights stencil_a, stencil_gamma).
 """
 from __future__ import annotations
 
@@ -21,7 +22,7 @@ _SRC = os.path.join(_HERE, "htd_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 
-STENCILS = {"q1mix": 0, "fd5": 1}
+STENCILS = {"q1mix": 0, "fd5": 1, "family": 2}
 MODES = {"table1": 0, "exact": 1}
 PRECONDS = {"identity": 0, "table1": 1, "exact": 2, "direct": 3}
 KRYLOV = {"fgmres": 0, "left": 1}
@@ -44,7 +45,8 @@ class _Problem(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_longlong * 3), ("h", ctypes.c_double),
                 ("stencil", ctypes.c_int), ("c_cell", ctypes.c_void_p),
                 ("R_node", ctypes.c_void_p), ("omega_phys", ctypes.c_double),
-                ("damping", ctypes.c_int)]
+                ("damping", ctypes.c_int), ("stencil_a", ctypes.c_double),
+                ("stencil_gamma", ctypes.c_double)]
 
 
 class _Params(ctypes.Structure):
@@ -74,6 +76,7 @@ def _load():
         Q = ctypes.POINTER(_Params)
         vp = ctypes.c_void_p
         lib.ora_tables.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp]
+        lib.ora_tables_family.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, vp, vp]
         lib.ora_setup.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_int, Q]
         lib.ora_setup_abd.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_int, Q]
         lib.ora_abd_step.argtypes = [P, Q, vp, vp, vp, vp]
@@ -108,7 +111,8 @@ class Oracle:
     """One problem bound to the C oracle.  Keeps its input arrays alive."""
 
     def __init__(self, prob, stencil: str = "q1mix", nP: int = 0, T: int | None = None,
-                 rho: float | None = None, integrator: str = "acd", damping: str = "node"):
+                 rho: float | None = None, integrator: str = "acd", damping: str = "node",
+                 stencil_a: float = 0.5, stencil_gamma: float = 1.0):
         self.lib = _load()
         self.prob = prob
         self.ndim = prob.ndim
@@ -128,6 +132,8 @@ class Oracle:
         p.R_node = _ptr(self.R)
         p.omega_phys = prob.omega
         p.damping = DAMPING[damping]
+        p.stencil_a = float(stencil_a)
+        p.stencil_gamma = float(stencil_gamma)
         self._p = p
         self.params = _Params()
         setup = self.lib.ora_setup_abd if integrator == "abd" else self.lib.ora_setup
@@ -291,11 +297,16 @@ def project_states(states: np.ndarray, nP: int, j_first: int) -> np.ndarray:
     return out.reshape(st.shape[1:])
 
 
-def tables(ndim: int, stencil: str = "q1mix"):
+def tables(ndim: int, stencil: str = "q1mix", stencil_a: float = 0.5,
+           stencil_gamma: float = 1.0):
     """(S, M) Hamming-distance tables used by the oracle (length ndim + 1)."""
     lib = _load()
     S = np.zeros(4)
     M = np.zeros(4)
-    if lib.ora_tables(ndim, STENCILS[stencil], _ptr(S), _ptr(M)):
+    if stencil == "family":
+        rc = lib.ora_tables_family(ndim, float(stencil_a), float(stencil_gamma), _ptr(S), _ptr(M))
+    else:
+        rc = lib.ora_tables(ndim, STENCILS[stencil], _ptr(S), _ptr(M))
+    if rc:
         raise ValueError("bad stencil")
     return S[: ndim + 1].copy(), M[: ndim + 1].copy()

@@ -19,6 +19,8 @@
  *                       paper's optimized f_s are not printed in the paper;
  *                       the stencil "Q1MIX" is the stated stand-in (textbook Q1
  *                       stiffness, half consistent plus half lumped Q1 mass).
+ *   ora_tables_family   the two-parameter family between FD5 and Q1MIX
+ *                       (stiffness and mass weights a, gamma).
  *   ora_setup           omega = sqrt(-lambda_min(Re H)) via the per-cell bound
  *                       (App. A), lambda_max bound (Sec. 3.2, generalised to the
  *                       maximum of the constant-coefficient symbol), the CFL
@@ -71,7 +73,7 @@ typedef double complex cplx;
 
 #define ORA_PI 3.14159265358979323846
 
-enum { ORA_Q1MIX = 0, ORA_FD5 = 1 };
+enum { ORA_Q1MIX = 0, ORA_FD5 = 1, ORA_FAMILY = 2 };
 enum { ORA_MODE_TABLE1 = 0, ORA_MODE_EXACT = 1 };
 enum { ORA_P_IDENTITY = 0, ORA_P_TABLE1 = 1, ORA_P_EXACT = 2, ORA_P_DIRECT = 3 };
 enum { ORA_FGMRES = 0, ORA_LEFT_GMRES = 1 };
@@ -82,7 +84,7 @@ typedef struct {
     int ndim;            /* 2 or 3 */
     long long n[3];      /* unknown nodes per axis (n[2] ignored for ndim 2) */
     double h;            /* grid spacing */
-    int stencil;         /* ORA_Q1MIX or ORA_FD5 */
+    int stencil;         /* ORA_Q1MIX, ORA_FD5 or ORA_FAMILY */
     const double *c_cell;  /* wave speed per cell, prod(n_a + 1) */
     const double *R_node;  /* damping per node, prod(n_a), >= 0 */
     double omega_phys;   /* physical angular frequency */
@@ -90,6 +92,8 @@ typedef struct {
                             ORA_DAMP_CELL: Im H = omega_phys sum over cells of
                             R_cell times the cell mass M (non-diagonal), R_cell
                             the mean of R over the cell's grid corners */
+    double stencil_a;    /* ORA_FAMILY: weight of the consistent Q1 mass */
+    double stencil_gamma;  /* ORA_FAMILY: weight of the Q1 element stiffness */
 } ora_problem;
 
 typedef struct {
@@ -205,6 +209,44 @@ int ora_tables(int ndim, int stencil, double S[4], double M[4])
     return -1;
 }
 
+/*
+ * FAMILY(a, gamma): the cell stiffness gamma S(Q1) + (1 - gamma) S(FD5) and the
+ * cell mass a M(consistent Q1) + (1 - a) M(lumped), both per Hamming distance
+ * with the tables written out above; a, gamma in [0, 1].  Convex combinations
+ * of PSD kernels stay PSD and of masses within [0, 2^-d] stay within it, so
+ * App. A's bounds hold for every member.
+ */
+int ora_tables_family(int ndim, double a, double gamma, double S[4], double M[4])
+{
+    for (int s = 0; s < 4; ++s) { S[s] = 0.0; M[s] = 0.0; }
+    if (ndim != 2 && ndim != 3) return -1;
+    if (!(a >= 0.0 && a <= 1.0) || !(gamma >= 0.0 && gamma <= 1.0)) return -1;
+    double sq1[4] = {0, 0, 0, 0}, sfd[4] = {0, 0, 0, 0}, mc[4] = {0, 0, 0, 0};
+    if (ndim == 2) {
+        sq1[0] = 2.0 / 3.0; sq1[1] = -1.0 / 6.0; sq1[2] = -1.0 / 3.0;
+        mc[0] = 4.0 / 36.0; mc[1] = 2.0 / 36.0; mc[2] = 1.0 / 36.0;
+        sfd[0] = 1.0; sfd[1] = -0.5;
+    } else {
+        sq1[0] = 1.0 / 3.0; sq1[1] = 0.0; sq1[2] = -1.0 / 12.0; sq1[3] = -1.0 / 12.0;
+        mc[0] = 8.0 / 216.0; mc[1] = 4.0 / 216.0; mc[2] = 2.0 / 216.0; mc[3] = 1.0 / 216.0;
+        sfd[0] = 0.75; sfd[1] = -0.25;
+    }
+    double lumped = (ndim == 2) ? 0.25 : 0.125;
+    for (int s = 0; s <= ndim; ++s) {
+        S[s] = gamma * sq1[s] + (1.0 - gamma) * sfd[s];
+        M[s] = a * mc[s] + (1.0 - a) * (s == 0 ? lumped : 0.0);
+    }
+    return 0;
+}
+
+/* the tables of a problem's stencil */
+static int problem_tables(const ora_problem *p, double S[4], double M[4])
+{
+    if (p->stencil == ORA_FAMILY)
+        return ora_tables_family(p->ndim, p->stencil_a, p->stencil_gamma, S, M);
+    return ora_tables(p->ndim, p->stencil, S, M);
+}
+
 /* ------------------------------------------------------------------------- */
 /* parameters                                                                 */
 /* ------------------------------------------------------------------------- */
@@ -228,7 +270,7 @@ int ora_setup(const ora_problem *p, int T, double rho, int nP_req, ora_params *o
     if (p->ndim != 2 && p->ndim != 3) return -1;
     if (T <= 0 || rho > 1.0 || p->h <= 0.0 || p->omega_phys <= 0.0) return -1;
     double S[4], M[4];
-    if (ora_tables(p->ndim, p->stencil, S, M)) return -1;
+    if (problem_tables(p, S, M)) return -1;
     long long Nc = n_cells(p);
     double kmin = INFINITY, kmax = 0.0;
     for (long long c = 0; c < Nc; ++c) {
@@ -363,7 +405,7 @@ int ora_setup_abd(const ora_problem *p, int T, double rho, int nP_req, ora_param
 void ora_apply_reH(const ora_problem *p, const double *u, long long stride, double *out)
 {
     double S[4], M[4];
-    ora_tables(p->ndim, p->stencil, S, M);
+    problem_tables(p, S, M);
     int d = p->ndim;
     long long N = n_nodes(p);
     for (long long i = 0; i < N; ++i) out[i * stride] = 0.0;
@@ -437,7 +479,7 @@ void ora_apply_imH(const ora_problem *p, const double *u, long long stride, doub
         return;
     }
     double S[4], M[4];
-    ora_tables(p->ndim, p->stencil, S, M);
+    problem_tables(p, S, M);
     int d = p->ndim;
     for (long long i = 0; i < N; ++i) out[i * stride] = 0.0;
     long long lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
@@ -491,7 +533,7 @@ long long ora_assemble_H(const ora_problem *p, long long cap, long long *rows,
                          long long *cols, double *re, double *im)
 {
     double S[4], M[4];
-    ora_tables(p->ndim, p->stencil, S, M);
+    problem_tables(p, S, M);
     int d = p->ndim;
     long long cnt = 0;
     double ih2 = 1.0 / (p->h * p->h);
@@ -1062,7 +1104,7 @@ int ora_grad(const ora_problem *p, int nsrc, const cplx *F, int nrec, const long
     band_lu lu;
     if (band_factor(p, &lu)) { band_free(&lu); return -1; }
     double S[4], M[4];
-    ora_tables(p->ndim, p->stencil, S, M);
+    problem_tables(p, S, M);
     cplx *U = malloc(sizeof(cplx) * N), *r = malloc(sizeof(cplx) * N), *mu = malloc(sizeof(cplx) * N);
     for (long long c = 0; c < Nc; ++c) grad_m[c] = 0.0;
     for (long long i = 0; i < N; ++i) grad_R[i] = 0.0;
@@ -1144,7 +1186,7 @@ int ora_grad_td(const ora_problem *p, const ora_params *q, int mode, int nsrc, c
     long long ns = q->nsteps;
     long long jim = ns - q->nP / 4;
     double S[4], M[4];
-    ora_tables(p->ndim, p->stencil, S, M);
+    problem_tables(p, S, M);
     double c = q->dt * q->dt / q->alpha;
     double w = p->omega_phys;
     double cm = -c * w * w;

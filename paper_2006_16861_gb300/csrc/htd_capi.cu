@@ -44,31 +44,35 @@ constexpr int kS3Default = kS3Pair;
 // Q1MIX mass = half consistent + half lumped (2^-d on the diagonal).
 // FD5: each grid edge shared by 2^{d-1} cells carries weight w = 2^{1-d}, so a
 // corner has stiffness d w and its edge neighbours -w; lumped mass 2^-d.
-bool cell_weights(int d, int stencil, double S[4], double M[4])
+// FAMILY(a, gamma): gamma Q1 stiffness + (1 - gamma) FD5 stiffness, a
+// consistent mass + (1 - a) lumped mass (Q1MIX = (0.5, 1), FD5 = (0, 0)).
+bool cell_weights(int d, int stencil, double a, double gamma, double S[4], double M[4])
 {
     for (int s = 0; s < 4; ++s) { S[s] = 0.0; M[s] = 0.0; }
-    const double m_same = 1.0 / 3.0, m_diff = 1.0 / 6.0;
     if (stencil == HTD_STENCIL_Q1MIX) {
-        for (int s = 0; s <= d; ++s) {
-            // axes that differ contribute k1 = -1 (and m1 = 1/6 when not differentiated)
-            double st = 0.0;
-            st += s * (-1.0) * std::pow(m_diff, s - 1) * std::pow(m_same, d - s);
-            st += (d - s) * (1.0) * std::pow(m_diff, s) * std::pow(m_same, d - s - 1);
-            S[s] = st;
-            double cons = std::pow(m_diff, s) * std::pow(m_same, d - s);
-            double lump = (s == 0) ? std::ldexp(1.0, -d) : 0.0;
-            M[s] = 0.5 * cons + 0.5 * lump;
-        }
-        return true;
+        a = 0.5;
+        gamma = 1.0;
+    } else if (stencil == HTD_STENCIL_FD5) {
+        a = 0.0;
+        gamma = 0.0;
+    } else if (stencil != HTD_STENCIL_FAMILY || !(a >= 0.0 && a <= 1.0) ||
+               !(gamma >= 0.0 && gamma <= 1.0)) {
+        return false;
     }
-    if (stencil == HTD_STENCIL_FD5) {
-        double w = std::ldexp(1.0, 1 - d);
-        S[0] = d * w;
-        S[1] = -w;
-        M[0] = std::ldexp(1.0, -d);
-        return true;
+    const double m_same = 1.0 / 3.0, m_diff = 1.0 / 6.0;
+    const double w = std::ldexp(1.0, 1 - d);
+    for (int s = 0; s <= d; ++s) {
+        // Q1: axes that differ contribute k1 = -1 (and m1 = 1/6 when not differentiated)
+        double q1 = 0.0;
+        q1 += s * (-1.0) * std::pow(m_diff, s - 1) * std::pow(m_same, d - s);
+        q1 += (d - s) * (1.0) * std::pow(m_diff, s) * std::pow(m_same, d - s - 1);
+        const double fd = (s == 0) ? d * w : (s == 1) ? -w : 0.0;
+        S[s] = (gamma == 1.0) ? q1 : (gamma == 0.0) ? fd : gamma * q1 + (1.0 - gamma) * fd;
+        const double cons = std::pow(m_diff, s) * std::pow(m_same, d - s);
+        const double lump = (s == 0) ? std::ldexp(1.0, -d) : 0.0;
+        M[s] = (a == 0.0) ? lump : a * cons + (1.0 - a) * lump;
     }
-    return false;
+    return true;
 }
 
 double binom(int n, int k)
@@ -945,7 +949,10 @@ htd_status plan_impl(const htd_grid *grid, const double *c_cell, const double *R
         pl->Nc *= grid->n[a] + 1;
     }
     if (pl->N > ((int64_t)1 << 34)) return HTD_ERR_ARG;
-    if (!cell_weights(d, opt.stencil, pl->S, pl->M)) return HTD_ERR_ARG;
+    if (!cell_weights(d, opt.stencil, opt.stencil_a, opt.stencil_gamma, pl->S, pl->M))
+        return HTD_ERR_ARG;
+    if (opt.tblock != 0 && opt.tblock != 1 && opt.tblock != 4 && opt.tblock != 8)
+        return HTD_ERR_ARG;
     pl->opt = opt;
 
     double kmin = INFINITY, kmax = 0.0;
@@ -1192,15 +1199,17 @@ htd_status create_impl(const htd_grid *grid, const double *c_cell, const double 
     HTD_CUDA(cudaMemcpy(c->imH, imh.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
 
     // temporal blocking for the 2-D FP32 recurrence, picked by timing against the
-    // one-step kernel.  HTD_TB=0 disables it; HTD_TB=4/8 (and HTD_TB_RPT=6/8/10/12/20,
-    // HTD_TB_PAIR=0/1, HTD_TB_SD=0/1) force a blocked configuration of that depth
-    // (rows per thread, pair form, d in shared memory); tuning overrides.
+    // one-step kernel, or as options.tblock asks (1: one step per launch, 4/8:
+    // that depth).  Tuning overrides: HTD_TB=0 disables it; HTD_TB=4/8 (and
+    // HTD_TB_RPT=6/8/10/12/20, HTD_TB_PAIR=0/1, HTD_TB_SD=0/1) force a blocked
+    // configuration of that depth (rows per thread, pair form, d in shared memory).
     {
         const char *env = std::getenv("HTD_TB");
         const char *env_r = std::getenv("HTD_TB_RPT");
-        const int want = env ? std::atoi(env) : 0;
+        const int want = env ? std::atoi(env) : (opt.tblock == 1 ? 0 : opt.tblock);
         const int want_r = env_r ? std::atoi(env_r) : 0;
-        if (d == 2 && mixed && !abd && !(env && want == 0)) {
+        const bool off = env ? want == 0 : opt.tblock == 1;
+        if (d == 2 && mixed && !abd && !off) {
             htd_status ts = autotune_tb2d(c, want, want_r);
             if (ts != HTD_OK) return ts;
         }
@@ -1368,6 +1377,9 @@ void htd_default_options(htd_options *opt)
     opt->proj_periods = 1;
     opt->integrator = HTD_ACD;
     opt->damping = HTD_DAMP_NODE;
+    opt->stencil_a = 0.5;
+    opt->stencil_gamma = 1.0;
+    opt->tblock = 0;
 }
 
 htd_status htd_create(const htd_grid *grid, const double *c_cell_host, const double *R_node_host,

@@ -25,7 +25,7 @@ MODE_TABLE1, MODE_EXACT, MODE_PROJECT = 0, 1, 2
 ACD, ABD = 0, 1
 DAMP_NODE, DAMP_CELL = 0, 1
 FGMRES, LEFT_GMRES = 0, 1
-STENCIL_Q1MIX, STENCIL_FD5 = 0, 1
+STENCIL_Q1MIX, STENCIL_FD5, STENCIL_FAMILY = 0, 1, 2
 BC_DIRICHLET = 0
 
 #: every function include/htd.h declares (checked by the ABI test)
@@ -51,7 +51,8 @@ class Options(ctypes.Structure):
                 ("T", ctypes.c_int), ("rho", ctypes.c_double), ("nP", ctypes.c_int),
                 ("stencil", ctypes.c_int), ("restart", ctypes.c_int), ("max_rhs", ctypes.c_int),
                 ("proj_periods", ctypes.c_int), ("integrator", ctypes.c_int),
-                ("damping", ctypes.c_int)]
+                ("damping", ctypes.c_int), ("stencil_a", ctypes.c_double),
+                ("stencil_gamma", ctypes.c_double), ("tblock", ctypes.c_int)]
 
 
 class Params(ctypes.Structure):
@@ -371,9 +372,17 @@ def make_options(prob=None, precision: str = "fp64", mode: str = "table1",
                  krylov: str = "fgmres", stencil: str = "q1mix", restart: int = 20,
                  nP: int = 0, T: int | None = None, rho: float | None = None,
                  max_rhs: int = 1, proj_periods: int = 1, integrator: str = "acd",
-                 damping: str = "node") -> Options:
-    """htd_options from names; T and rho default to the problem's."""
+                 damping: str = "node", stencil_a: float | None = None,
+                 stencil_gamma: float | None = None, tblock: int = 0) -> Options:
+    """htd_options from names; T and rho default to the problem's.  stencil
+    "family" takes stencil_a (consistent-mass weight) and stencil_gamma (Q1
+    stiffness weight)."""
     o = htd_default_options()
+    if stencil_a is not None:
+        o.stencil_a = float(stencil_a)
+    if stencil_gamma is not None:
+        o.stencil_gamma = float(stencil_gamma)
+    o.tblock = int(tblock)
     o.integrator = {"acd": ACD, "abd": ABD}[integrator]
     o.damping = {"node": DAMP_NODE, "cell": DAMP_CELL}[damping]
     o.max_rhs = int(max_rhs)
@@ -381,7 +390,7 @@ def make_options(prob=None, precision: str = "fp64", mode: str = "table1",
     o.precision = {"fp64": FP64, "mixed": MIXED}[precision]
     o.mode = {"table1": MODE_TABLE1, "exact": MODE_EXACT, "project": MODE_PROJECT}[mode]
     o.krylov = {"fgmres": FGMRES, "left": LEFT_GMRES}[krylov]
-    o.stencil = {"q1mix": STENCIL_Q1MIX, "fd5": STENCIL_FD5}[stencil]
+    o.stencil = {"q1mix": STENCIL_Q1MIX, "fd5": STENCIL_FD5, "family": STENCIL_FAMILY}[stencil]
     o.restart = restart
     o.nP = nP
     if T is not None or prob is not None:
@@ -404,9 +413,10 @@ class Solver:
                  krylov: str = "fgmres", stencil: str = "q1mix", restart: int = 20,
                  nP: int = 0, T: int | None = None, rho: float | None = None,
                  max_rhs: int = 1, proj_periods: int = 1, integrator: str = "acd",
-                 damping: str = "node"):
+                 damping: str = "node", stencil_a: float | None = None,
+                 stencil_gamma: float | None = None, tblock: int = 0):
         o = make_options(prob, precision, mode, krylov, stencil, restart, nP, T, rho, max_rhs,
-                         proj_periods, integrator, damping)
+                         proj_periods, integrator, damping, stencil_a, stencil_gamma, tblock)
         self.max_rhs = int(max_rhs)
         self.prob = prob
         self.n = tuple(prob.n)

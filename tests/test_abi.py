@@ -40,9 +40,11 @@ def test_struct_layouts_match_header(tmp_path):
     src = tmp_path / "sz.c"
     src.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "htd.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(htd_grid),"
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(htd_grid),"
         " sizeof(htd_options), sizeof(htd_params), sizeof(htd_solve_info),"
-        " offsetof(htd_solve_info, hist), offsetof(htd_params, nP), offsetof(htd_options, damping));"
+        " offsetof(htd_solve_info, hist), offsetof(htd_params, nP), offsetof(htd_options, damping),"
+        " offsetof(htd_options, stencil_a), offsetof(htd_options, stencil_gamma),"
+        " offsetof(htd_options, tblock));"
         "return 0;}\n")
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
@@ -51,16 +53,18 @@ def test_struct_layouts_match_header(tmp_path):
                                           check=True).stdout.split()]
     want = [ctypes.sizeof(htd.Grid), ctypes.sizeof(htd.Options), ctypes.sizeof(htd.Params),
             ctypes.sizeof(htd.SolveInfo), htd.SolveInfo.hist.offset, htd.Params.nP.offset,
-            htd.Options.damping.offset]
+            htd.Options.damping.offset, htd.Options.stencil_a.offset,
+            htd.Options.stencil_gamma.offset, htd.Options.tblock.offset]
     assert got == want
 
 
 def test_default_options():
     o = htd.htd_default_options()
     assert (o.precision, o.mode, o.krylov, o.T, o.rho, o.nP, o.stencil, o.restart,
-            o.max_rhs, o.proj_periods, o.integrator, o.damping) == \
+            o.max_rhs, o.proj_periods, o.integrator, o.damping, o.stencil_a, o.stencil_gamma,
+            o.tblock) == \
         (htd.FP64, htd.MODE_TABLE1, htd.FGMRES, 10, 0.25, 0, htd.STENCIL_Q1MIX, 20, 1, 1,
-         htd.ACD, htd.DAMP_NODE)
+         htd.ACD, htd.DAMP_NODE, 0.5, 1.0, 0)
 
 
 PROBLEMS = [
@@ -71,12 +75,16 @@ PROBLEMS = [
 ]
 
 
+STENCILS = [("q1mix", {}), ("fd5", {}), ("family", {"stencil_a": 0.3, "stencil_gamma": 0.6}),
+            ("family", {"stencil_a": 1.0, "stencil_gamma": 0.0})]
+
+
 @pytest.mark.parametrize("mk", PROBLEMS)
-@pytest.mark.parametrize("stencil", ["q1mix", "fd5"])
-def test_plan_matches_oracle_parameters(mk, stencil):
+@pytest.mark.parametrize("stencil,kw", STENCILS, ids=["q1mix", "fd5", "family", "family_a1g0"])
+def test_plan_matches_oracle_parameters(mk, stencil, kw):
     p = mk()
-    mine = htd.plan(p, stencil=stencil)
-    ref = oracle.Oracle(p, stencil).param_dict()
+    mine = htd.plan(p, stencil=stencil, **kw)
+    ref = oracle.Oracle(p, stencil, **kw).param_dict()
     assert mine["nP"] == ref["nP"]
     assert mine["T"] == ref["T"] and mine["steps"] == ref["nsteps"]
     for a, b in [("omega_c", "omega"), ("k_min", "k_min"), ("k_max", "k_max"),
@@ -110,7 +118,10 @@ def test_plan_rejects_bad_input():
     assert e.value.status == 1
     for kw in ({"restart": 0}, {"restart": 65}, {"T": 0}, {"rho": 1.5}, {"max_rhs": -1},
                {"max_rhs": 257}, {"mode": "project", "proj_periods": 3},
-               {"mode": "project", "proj_periods": -1}, {"damping": "cell"}):
+               {"mode": "project", "proj_periods": -1}, {"damping": "cell"},
+               {"stencil": "family", "stencil_a": -0.1}, {"stencil": "family", "stencil_a": 1.5},
+               {"stencil": "family", "stencil_gamma": float("nan")},
+               {"stencil": "family", "stencil_gamma": 2.0}, {"tblock": 2}, {"tblock": -1}):
         with pytest.raises(htd.HtdError) as e:
             htd.plan(p, **kw)
         assert e.value.status == 1
@@ -120,6 +131,21 @@ def test_plan_rejects_bad_input():
         htd.htd_plan(4, p.n, p.h, p.c_cell, p.R_node, p.omega, 0, htd.make_options(p))
     with pytest.raises(htd.HtdError):
         htd.htd_plan(2, p.n, p.h, p.c_cell, p.R_node, p.omega, 1, htd.make_options(p))
+    o = htd.make_options(p)
+    o.stencil = 3
+    with pytest.raises(htd.HtdError) as e:
+        htd.htd_plan(2, p.n, p.h, p.c_cell, p.R_node, p.omega, 0, o)
+    assert e.value.status == 1
+    # the family's weights are read only for HTD_STENCIL_FAMILY
+    assert htd.plan(p, stencil="q1mix", stencil_a=7.0)["nP"] == ok["nP"]
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_family_corners_are_q1mix_and_fd5(d):
+    """FAMILY(0.5, 1) plans exactly like Q1MIX and FAMILY(0, 0) like FD5."""
+    p = W.config_2d_constant(41, T=2) if d == 2 else W.config_3d_layered(12, layer=3, T=2)
+    for st, a, g in (("q1mix", 0.5, 1.0), ("fd5", 0.0, 0.0)):
+        assert htd.plan(p, stencil="family", stencil_a=a, stencil_gamma=g) == htd.plan(p, stencil=st)
 
 
 def test_status_strings():

@@ -93,6 +93,45 @@ def test_q1mix_tables_are_q1_element_matrices(d):
     assert np.linalg.eigvalsh(Sk).min() >= -1e-14
 
 
+FAMILY = [(0.3, 0.6), (1.0, 0.0), (0.0, 1.0), (0.8, 0.25)]
+
+
+@pytest.mark.parametrize("d", [2, 3])
+@pytest.mark.parametrize("a,g", FAMILY)
+def test_family_tables_mix_q1_element_matrices_and_edge_stiffness(d, a, g):
+    """FAMILY(a, gamma): gamma x (Q1 element stiffness, Gauss quadrature) +
+    (1 - gamma) x (edge stiffness: weight 2^{1-d} per cell edge), a x (consistent
+    Q1 mass) + (1 - a) x (row-sum lumped mass); each entry depends only on the
+    Hamming distance, the stiffness kernel is PSD and 0 <= mass <= 2^-d."""
+    K, Mc, ham = q1_element_matrices(d)
+    w = 2.0 ** (1 - d)
+    Kfd = np.where(ham == 1, -w, 0.0)
+    Kfd[np.diag_indices_from(Kfd)] = -Kfd.sum(axis=1)              # edge graph Laplacian
+    Ml = np.diag(Mc.sum(axis=1))
+    Kf = g * K + (1 - g) * Kfd
+    Mf = a * Mc + (1 - a) * Ml
+    S, M = oracle.tables(d, "family", a, g)
+    for s in range(d + 1):
+        sel = ham == s
+        assert np.allclose(Kf[sel], Kf[sel][0]) and np.allclose(Mf[sel], Mf[sel][0])
+        assert Kf[sel][0] == pytest.approx(S[s], abs=1e-14)
+        assert Mf[sel][0] == pytest.approx(M[s], abs=1e-14)
+    assert np.linalg.eigvalsh(S[ham]).min() >= -1e-14
+    ev_m = np.linalg.eigvalsh(M[ham])
+    assert ev_m.min() >= -1e-14 and ev_m.max() <= 2.0 ** -d + 1e-14
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_family_corners_are_q1mix_and_fd5(d):
+    for st, a, g in (("q1mix", 0.5, 1.0), ("fd5", 0.0, 0.0)):
+        S0, M0 = oracle.tables(d, st)
+        S1, M1 = oracle.tables(d, "family", a, g)
+        assert np.array_equal(S0, S1) and np.array_equal(M0, M1)
+    for a, g in ((-0.1, 0.5), (0.5, 1.2), (np.nan, 0.5)):
+        with pytest.raises(ValueError):
+            oracle.tables(d, "family", a, g)
+
+
 @pytest.mark.parametrize("d", [2, 3])
 def test_fd5_constant_k_is_the_papers_5_point_operator(d):
     """Sec. 3.1: (HU) = h^-2 (2d U - sum of axis neighbours) - k^2 U + i Im H U."""
@@ -124,12 +163,14 @@ def _sine_mode(n, m):
     return v
 
 
-def sine_eigenvalue(stencil, n, m, h, kappa):
+def sine_eigenvalue(stencil, n, m, h, kappa, a=0.5, g=1.0):
     """Eigenvalue of Re H (constant kappa = (hk)^2, zero Dirichlet) on sine mode m.
 
     Q1 finite elements assemble to tensor products of the 1-D stiffness
     tridiag(-1, 2, -1) and 1-D consistent mass tridiag(1, 4, 1)/6; lumped mass
-    assembles to the identity.  FD5 is the textbook Laplacian minus k^2.
+    assembles to the identity.  FD5 is the textbook Laplacian minus k^2.  The
+    family mixes the two stiffnesses with weights g, 1 - g and the two masses
+    with weights a, 1 - a (Q1MIX: a = 1/2, g = 1).
     """
     th = [math.pi * ma / (na + 1) for na, ma in zip(n, m)]
     k1 = [2 - 2 * math.cos(t) for t in th]
@@ -137,8 +178,9 @@ def sine_eigenvalue(stencil, n, m, h, kappa):
     d = len(n)
     if stencil == "fd5":
         return (sum(k1) - kappa) / h ** 2
-    stiff = sum(k1[a] * np.prod([m1[b] for b in range(d) if b != a]) for a in range(d))
-    mass = 0.5 * np.prod(m1) + 0.5
+    stiff = sum(k1[a_] * np.prod([m1[b] for b in range(d) if b != a_]) for a_ in range(d))
+    stiff = g * stiff + (1 - g) * sum(k1)
+    mass = a * np.prod(m1) + (1 - a)
     return (stiff - kappa * mass) / h ** 2
 
 
@@ -155,6 +197,39 @@ def test_sine_modes_diagonalise_constant_coefficient_operator(d, stencil):
         lam = sine_eigenvalue(stencil, n, m, p.h, kappa)
         Hv = o.apply_reH(v)
         assert np.abs(Hv - lam * v).max() <= 1e-10 * abs(lam) * np.abs(v).max() + 1e-9
+
+
+@pytest.mark.parametrize("d", [2, 3])
+@pytest.mark.parametrize("a,g", FAMILY)
+def test_sine_modes_diagonalise_family_operator(d, a, g):
+    n = (8, 7) if d == 2 else (5, 4, 6)
+    p = make_problem(d, n, c=0.9, R="zero")
+    o = oracle.Oracle(p, "family", stencil_a=a, stencil_gamma=g)
+    kappa = (p.h * p.omega / 0.9) ** 2
+    rng = np.random.default_rng(2)
+    for _ in range(6):
+        m = tuple(int(rng.integers(1, na + 1)) for na in n)
+        v = _sine_mode(n, m)
+        lam = sine_eigenvalue("family", n, m, p.h, kappa, a, g)
+        Hv = o.apply_reH(v)
+        assert np.abs(Hv - lam * v).max() <= 1e-10 * abs(lam) * np.abs(v).max() + 1e-9
+
+
+@pytest.mark.parametrize("d,n", [(2, (9, 8)), (3, (5, 4, 5))])
+@pytest.mark.parametrize("a,g", FAMILY)
+def test_family_required_properties_and_bounds(d, n, a, g):
+    """Re H symmetric with lambda_min >= -k_max^2 and lambda_max below the
+    symbol-vertex bound; K >= 0 and 4 I - K > 0 at the chosen time step."""
+    p = make_problem(d, n, het=True, R="layer", layer=2)
+    o = oracle.Oracle(p, "family", stencil_a=a, stencil_gamma=g)
+    reH = o.H_sparse().toarray().real
+    assert np.allclose(reH, reH.T, atol=1e-9)
+    ev = np.linalg.eigvalsh(reH)
+    q = o.params
+    assert ev.min() >= -q.k_max ** 2 * (1 + 1e-12)
+    assert ev.max() <= q.lam_max_reH * (1 + 1e-12)
+    evK = np.linalg.eigvalsh(q.dt ** 2 / q.alpha * (reH + q.omega ** 2 * np.eye(o.N)))
+    assert evK.min() >= -1e-12 and evK.max() < 4.0
 
 
 # ----------------------------------------------------------------------------

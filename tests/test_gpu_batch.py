@@ -133,3 +133,29 @@ def test_batch_rejects_bad_arguments():
         htd.htd_batch_gmres_solve(b.handle, [F], [F], 1e-6, 10, 2)     # F aliases U
     assert e.value.status == 1
     b.close()
+
+
+def test_config_batched_full_size():
+    """The full batched configuration (3-D 128^3 layered model with 32 seeded
+    point sources as right-hand sides of one handle, plus 64 2-D instances with
+    sides in [200, 1000]) in the launch configuration the benchmark times: one
+    lockstep FGMRES(20) solve of all 96 systems; every solution reaches a true
+    relative residual <= 1e-6 by the oracle's FP64 operator."""
+    setup = W.config_batched()
+    solvers = [htd.Solver(p, precision="mixed", max_rhs=F.shape[0], restart=20)
+               for p, F in zip(setup.probs, setup.F)]
+    b = htd.Batch(solvers, [F.shape[0] for F in setup.F])
+    Us, infos = b.solve([dev(F) for F in setup.F], tol=1e-6, max_iters=400)
+    assert len(infos) == 96
+    k = 0
+    for p, F, U in zip(setup.probs, setup.F, Us):
+        Ub = host(U)
+        o = oracle.Oracle(p)
+        for r in range(F.shape[0]):
+            assert infos[k]["converged"], (k, infos[k])
+            res = np.linalg.norm(F[r] - o.apply_H(Ub[r])) / np.linalg.norm(F[r])
+            assert res <= 1e-6, (k, res)
+            k += 1
+    b.close()
+    for s in solvers:
+        s.close()

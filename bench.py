@@ -73,7 +73,7 @@ def step_kernel_name(prm, ndim):
         return f"tb2d_kernel<float,{prm['steps_per_launch']}>", "tb2d"
     if sk == 2:
         if list(prm["tile"][:2]) == [64, 8]:
-            return "stream3d_pair_kernel<6>", "stream3d_pair"
+            return "stream3d_pair_kernel", "stream3d_pair"
         return "stream3d_kernel", "stream3d"
     return ("step2d_kernel<float>" if ndim == 2 else "step3d_kernel<float>"), None
 

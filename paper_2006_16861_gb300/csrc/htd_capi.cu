@@ -164,7 +164,7 @@ struct htd_ctx {
     bool use_s3 = false;
     int s3_zchunk = 0;
     int s3_shape = 0;
-    int s3_stages = 6;
+    int s3_stages = 7;
     // right-hand-side batch: rcap rhs slots in every per-rhs array (u0, u1, u2,
     // u3, fre, fim, slot); act_dev = active list read by the step kernels
     int rcap = 1;
@@ -1235,7 +1235,8 @@ htd_status create_impl(const htd_grid *grid, const double *c_cell, const double 
                 c->use_s3 = htd::make_stream3d_maps(L, c->s3_shape, planes, &c->s3maps);
             if (c->use_s3) {
                 const char *envst = std::getenv("HTD_S3_STAGES");  // tuning override
-                c->s3_stages = (envst && std::atoi(envst) == 4) ? 4 : 6;
+                const int want_st = envst ? std::atoi(envst) : 7;
+                c->s3_stages = (want_st == 4 || want_st == 6) ? want_st : 7;
                 c->s3_zchunk = c->s3_shape == kS3Pair ? htd::stream3d_pair_zchunk(L, c->s3_stages)
                                                       : htd::stream3d_zchunk(L, c->s3_shape);
                 const char *envz = std::getenv("HTD_S3_ZCHUNK");   // tuning override

@@ -148,7 +148,7 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
 // NS shared-memory stages: a node plane holds three of them, the rest is the
-// producer's lead; 6 stages (86 KB) fit 2 CTAs per SM, 4 stages (57 KB) fit 3
+// producer's lead; 6 or 7 stages (86 / 100 KB) fit 2 CTAs per SM, 4 stages (57 KB) fit 3
 template <int NS>
 __global__ void __launch_bounds__(kThreads + 32, NS >= 6 ? 2 : 3)
 stream3d_pair_kernel(const __grid_constant__ Stream3Maps maps, int iu, int ium,
@@ -401,7 +401,9 @@ bool make_stream3d_pair_maps(const Layout &L, float *const planes[6], Stream3Map
             CUDA_SUCCESS)
             return false;
     }
-    return cudaFuncSetAttribute(stream3d_pair_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(stream3d_pair_kernel<7>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)stream3d_pair_smem_bytes(7)) == cudaSuccess &&
+           cudaFuncSetAttribute(stream3d_pair_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)stream3d_pair_smem_bytes(6)) == cudaSuccess &&
            cudaFuncSetAttribute(stream3d_pair_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)stream3d_pair_smem_bytes(4)) == cudaSuccess;
@@ -428,7 +430,10 @@ void launch_stream3d_pair(const Stream3Maps &maps, int from, const Layout &L, fl
     const int iu = from ? 1 : 0, ium = from ? 6 : 7;
     dim3 grd((unsigned)(((L.nx + kTX - 1) / kTX) * R.slots), (unsigned)((L.ny + kTY - 1) / kTY),
              (unsigned)((L.nz + zchunk - 1) / zchunk));
-    if (stages == 4)
+    if (stages == 7)
+        launch_ex(stream3d_pair_kernel<7>, grd, kThreads + 32, stream3d_pair_smem_bytes(7), s,
+                  overlap, maps, iu, ium, um, L, C, a, b, slot, flags, zchunk, err, R);
+    else if (stages == 4)
         launch_ex(stream3d_pair_kernel<4>, grd, kThreads + 32, stream3d_pair_smem_bytes(4), s,
                   overlap, maps, iu, ium, um, L, C, a, b, slot, flags, zchunk, err, R);
     else

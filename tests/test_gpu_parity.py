@@ -174,14 +174,15 @@ S3_CASES = [(13, 17, 19), (40, 9, 70), (1, 3, 1), (2, 2, 2), (64, 16, 33), (5, 3
 
 @pytest.mark.parametrize("n", S3_CASES, ids=["x".join(map(str, c)) for c in S3_CASES])
 @pytest.mark.parametrize("mode", ["table1", "exact"])
-@pytest.mark.parametrize("tile", ["0", "1", "2", "3", "3:4"])
+@pytest.mark.parametrize("tile", ["0", "1", "2", "3", "3:4", "3:6"])
 def test_streamed_3d_step_matches_register_kernel(n, mode, tile, monkeypatch):
     """The TMA-streamed 3-D FP32 step (one node per thread on 32 x 8, 64 x 4 or
     128 x 2 column tiles, or node pairs in paired FP32 instructions on 64 x 8
     tiles; z chunks, a ring of shared-memory stages fed by a producer warp)
     against the register z-march kernel and the FP64 oracle, on ragged grids
     (odd nx leaves the last pair half-used) and several z chunks (16 planes per
-    chunk at these sizes); "3:4" runs the pair kernel with 4 ring stages."""
+    chunk at these sizes); "3:4" and "3:6" run the pair kernel with 4 or 6 ring
+    stages instead of the default 7."""
     p = het_problem(3, n, T=2)
     monkeypatch.setenv("HTD_S3", "0")
     s0 = htd.Solver(p, precision="mixed", mode=mode)

@@ -67,10 +67,11 @@ step2d_kernel(const T *__restrict__ u, T *__restrict__ um, const T *__restrict__
     const Stencil2dCoef<T> SC = stencil2d_coef(C);
     const T acc = stencil2d(SC, umm, um0, ump, u0m, u00, u0p, upm, up0, upp, k00, k01, k10, k11,
                             pm, p0, pp, hk0, hk1);
-    const T g = vfma(a, fre[i], vmul(-b, fim[i]));
+    // acc + a Re F - b Im F as two FMAs (the blocked kernels round the same way)
+    const T ag = vfma(a, fre[i], vfma(-b, fim[i], acc));
     const T d = dco[i];
     const T uprev = um[i];
-    const T unew = vfma(d, vfma(T(-2), uprev, vadd(acc, g)), uprev);
+    const T unew = vfma(d, vfma(T(-2), uprev, ag), uprev);
     um[i] = unew;
     if (flags) {
         const int64_t c = iy * L.nx + ix;

@@ -275,9 +275,9 @@ tb2d_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, T *__restrict
                                     k11, pm, p0, pp, hk0, hk1);
             // every node stores (see the header: no per-node test is needed)
             const int ni = (ly + 1) * BW + cc + 1;
-            const T g = vfma(a, rfr[i], vmul(-b, rfi[i]));
+            const T ag = vfma(a, rfr[i], vfma(-b, rfi[i], acc));
             const T uprev = prv[ni];
-            const T unew = vfma(rd[i], vfma(T(-2), uprev, vadd(acc, g)), uprev);
+            const T unew = vfma(rd[i], vfma(T(-2), uprev, ag), uprev);
             prv[ni] = unew;
             if (kOut && col_in_domain && col_owned && ly >= B && ly < B + TY && ly >= dom_lo &&
                 ly < dom_hi) {
@@ -463,10 +463,10 @@ tb2d_pair_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, float *_
             const float2 acc = stencil2d(SC, umm, um0, ump, u0m, u00, u0p, upm, up0, upp, k00, k01,
                                          k10, k11, pm, p0, pp, hk0, hk1);
             const int ni = (ly + 1) * BW + cc + 1;
-            const float2 g = vfma(a2, rfr[i], vmul(nb2, rfi[i]));
+            const float2 ag = vfma(a2, rfr[i], vfma(nb2, rfi[i], acc));
             const float2 uprev = *reinterpret_cast<const float2 *>(prv + ni);
             const float2 dn = SD ? *reinterpret_cast<const float2 *>(sd + ni) : rd[SD ? 0 : i];
-            const float2 unew = vfma(dn, vfma(n2, uprev, vadd(acc, g)), uprev);
+            const float2 unew = vfma(dn, vfma(n2, uprev, ag), uprev);
             *reinterpret_cast<float2 *>(prv + ni) = unew;   // no per-node test (header)
             if (kOut && ownA && ly >= B && ly < B + TY && ly >= dom_lo && ly < dom_hi) {
                 const int64_t c = (y0 + ly) * L.nx + gx;

@@ -96,7 +96,7 @@ def ncu_traffic(key, nodes):
     return rec["bytes"] * nodes / rec["nodes"]
 
 
-def parse_args():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -113,7 +113,7 @@ def parse_args():
                     help="also time the batched workload (96 systems, lockstep FGMRES)")
     ap.add_argument("--secondary-3d", type=int, default=1,
                     help="also time the FP32 recurrence on the 3-D 256^3 workload (HBM-bound)")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def make_workload(name, rank=0):
@@ -363,6 +363,19 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def all_reduce_scalar(x, op, world, device):
+    """One float reduced over the ranks (op: a torch.distributed.ReduceOp); the
+    value itself when there is one rank.  device: "cuda" under NCCL, "cpu" under
+    gloo."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=op)
+    return float(t.item())
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -381,18 +394,10 @@ def run_ours(args):
             dist.barrier()
 
     def allmax(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return all_reduce_scalar(x, dist.ReduceOp.MAX, world, "cuda")
 
     def allsum(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+        return all_reduce_scalar(x, dist.ReduceOp.SUM, world, "cuda")
 
     p, desc = make_workload(args.workload, rank)
     N = math.prod(p.n)

@@ -232,14 +232,12 @@ void free_ctx(htd_ctx *c)
 
 // one preconditioner run of T n_P steps; the forcing planes are already filled.
 // Consecutive launches of the blocked 2-D and the streamed 3-D step overlap
-// (programmatic dependent launch) unless HTD_OVERLAP=0 (a tuning override).
+// (programmatic dependent launch) unless HTD_OVERLAP=0 (a tuning override, read
+// whenever a step sequence is built or captured).
 bool step_overlap()
 {
-    static const bool on = [] {
-        const char *e = std::getenv("HTD_OVERLAP");
-        return !(e && std::atoi(e) == 0);
-    }();
-    return on;
+    const char *e = std::getenv("HTD_OVERLAP");
+    return !(e && std::atoi(e) == 0);
 }
 
 // Table 1 / EXACT: the step kernels write the snapshot and final state into the
@@ -373,8 +371,7 @@ htd_status run_steps_direct(htd_ctx *c, cudaStream_t s)
 
 bool graphs_disabled()
 {
-    static const bool no_graph = std::getenv("HTD_NO_GRAPH") != nullptr;
-    return no_graph;
+    return std::getenv("HTD_NO_GRAPH") != nullptr;   // read at every use (cheap)
 }
 
 // Capture the whole step sequence of one run into a graph (once per handle):

@@ -314,3 +314,28 @@ def test_config_3d_256_full_size():
     Ug = host(U)
     rel = np.linalg.norm(p.F - o.apply_H(Ug)) / np.linalg.norm(p.F)
     assert info["converged"] and rel <= 1e-6
+
+
+@pytest.mark.parametrize("ndim,n", [(2, (130, 67)), (2, (1001, 1001)), (3, (37, 70, 41))],
+                         ids=["2d-130x67", "2d-1001", "3d-37x70x41"])
+def test_overlapped_launches_change_nothing(ndim, n, monkeypatch):
+    """Consecutive step launches overlap (programmatic dependent launch: the next
+    launch reads the coefficients while the previous one drains, and waits for
+    it before touching a state plane).  The outputs equal those of plain
+    stream-ordered launches bit for bit, captured graph and direct launches."""
+    p = het_problem(ndim, n, T=2)
+    monkeypatch.setenv("HTD_OVERLAP", "0")
+    s0 = htd.Solver(p, precision="mixed")
+    F2 = W.random_rhs(5, p.n)
+    ref = [host(s0.precond(dev(F))) for F in (p.F, F2)]
+    monkeypatch.delenv("HTD_OVERLAP")
+    s1 = htd.Solver(p, precision="mixed")
+    assert s1.params["step_kernel"] in (1, 2)           # blocked 2-D or streamed 3-D
+    for r in range(3):
+        for F, want in zip((p.F, F2), ref):
+            assert np.array_equal(host(s1.precond(dev(F))), want)
+    monkeypatch.setenv("HTD_NO_GRAPH", "1")
+    s2 = htd.Solver(p, precision="mixed")
+    assert np.array_equal(host(s2.precond(dev(p.F))), ref[0])
+    for s in (s0, s1, s2):
+        s.close()

@@ -49,6 +49,12 @@ TOL = 1e-6
 # B-step temporally blocked launch reads the same 6 planes once and writes the
 # last two states (8 words)
 WORDS_ONE_STEP, WORDS_BLOCKED = 7, 8
+# FP64 recurrence: FLOPs per point update as the step kernels compute it (FMA =
+# 2): 2-D 12 FMA + 20 add/mul; 3-D 57 FMA + 21 add/mul (27 coefficients and 27
+# products of the stencil sum, 19 cell sums, forcing and update); FP64 pipe
+# peak 2 DFMA per clock per SM x 152 SMs x 2 x 2.07e9
+FP64_FLOPS_PER_UPDATE = {2: 44, 3: 135}
+FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
 # capture, valid only for the kernel source it was taken on (sha256 prefix of the
@@ -485,6 +491,7 @@ def run_ours(args):
     # plain FP64 GPU form on the same workload: time to 1e-6
     fp64_ms = None
     fp64_info = None
+    fp64_roof = None
     if args.fp64_steps > 0:
         s64 = htd.Solver(p, precision="fp64", mode="table1", krylov="fgmres",
                          restart=args.restart)
@@ -501,6 +508,15 @@ def run_ours(args):
             t.append(e0.elapsed_time(e1))
         fp64_ms = allmax(statistics.mean(t))
         s64.close()
+        # the FP64 step kernel against the FP64 pipe (it is ALU-bound on GB300):
+        # FLOPs per point update of step2d/step3d as written (FMA = 2)
+        fp_upd = FP64_FLOPS_PER_UPDATE[p.ndim]
+        upd = N * fp64_info["steps"]
+        achieved = fp_upd * upd / (fp64_info["ms_precond"] * 1e-3) / 1e12
+        fp64_roof = {"bound": "alu", "kernel": f"step{p.ndim}d_kernel<double>",
+                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS, "flops_per_update": fp_upd,
+                     "peak_kind": "FP64 pipe: 2 DFMA per clock per SM x 152 SMs x 2.07 GHz"}
 
     # secondary: the recurrence alone on the 3-D 256^3 layered workload, whose
     # working set (470 MB per step) is far larger than L2
@@ -537,6 +553,7 @@ def run_ours(args):
             "speedup_vs_fp64": (fp64_ms / ms_per_step) if fp64_ms else None,
             "iterations": its[-1], "rel_res_true": max(rels),
             "fp64_iterations": fp64_info["iterations"] if fp64_info else None,
+            "fp64_roofline": fp64_roof,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
                          "traffic": ncu_traffic(tkey, N) if tkey else None,

@@ -110,7 +110,7 @@ def parse_args(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="2d_grf_1001",
                     choices=["2d_grf_1001", "3d_layered_256", "3d_layered_192", "2d_const_101",
-                             "3d_paper_shape"])
+                             "3d_paper_shape", "3d_paper_shape_4hz", "3d_paper_shape_6hz"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--cpu-sample-s", type=float, default=10.0)
     ap.add_argument("--e2e-steps", type=int, default=5)
@@ -140,6 +140,14 @@ def make_workload(name, rank=0):
         p = W.config_3d_paper_shape()
         desc = ("3-D 200x200x106 (the paper's smallest 3-D example size), 4-layer model in place "
                 "of SEG/EAGE salt, 6 ppw at min c, 16-cell layer R0=2w, point source, T=25")
+    elif name == "3d_paper_shape_4hz":
+        p = W.config_3d_paper_shape(shape=(130, 280, 280), T=40)
+        desc = ("3-D 280x280x130 (the paper's second 3-D example size), 4-layer model in place "
+                "of SEG/EAGE salt, 6 ppw at min c, 16-cell layer R0=2w, point source, T=40")
+    elif name == "3d_paper_shape_6hz":
+        p = W.config_3d_paper_shape(shape=(165, 392, 392), T=60)
+        desc = ("3-D 392x392x165 (the paper's largest 3-D example size), 4-layer model in place "
+                "of SEG/EAGE salt, 6 ppw at min c, 16-cell layer R0=2w, point source, T=60")
     else:
         p = W.config_2d_constant(101)
         desc = "2-D 101x101 constant c=1, h=0.01, 10 ppw, 20-cell layer, point source, T=10"

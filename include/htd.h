@@ -10,6 +10,10 @@
  * (TimeDomainPreconditioner): T n_P steps of the frequency-adapted leapfrog
  * recurrence I_acd (Def. of I_acd) driven by the windowed time-harmonic
  * forcing (Def. approx_solver), used inside restarted GMRES (Sec. 2.4).
+ * Options (htd_options) select the exact operator S_T instead of Table 1's
+ * read-out, a windowed projection read-out, the backward-differences scheme
+ * I_abd of Sec. 6, FP32 or FP64 recurrence, the stencil, and right-hand-side
+ * batching; htd_grad and htd_grad_td return misfit gradients.
  *
  * Conventions (all entry points):
  *  - Plain C types only.  Pointers named *_dev are CUDA device pointers on the

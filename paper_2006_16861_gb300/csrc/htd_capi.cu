@@ -164,7 +164,7 @@ struct htd_ctx {
     bool use_s3 = false;
     int s3_zchunk = 0;
     int s3_shape = 0;
-    int s3_stages = 7;
+    int s3_stages = 5;
     // right-hand-side batch: rcap rhs slots in every per-rhs array (u0, u1, u2,
     // u3, fre, fim, slot); act_dev = active list read by the step kernels
     int rcap = 1;
@@ -745,6 +745,9 @@ htd_status autotune_s3_zchunk(htd_ctx *c)
     const int reps = 4;
     float best_us = INFINITY;
     int best = c->s3_zchunk;
+    // two passes over the candidates, each candidate's best kept: neighbouring
+    // chunk lengths differ by 1-2 %, about the spread of a single timing
+    for (int pass = 0; pass < 2; ++pass)
     for (int zc : cands) {
         for (int r = 0; r < 2 + reps; ++r) {
             if (r == 2) HTD_CUDA(cudaEventRecord(e0, s));
@@ -1232,8 +1235,8 @@ htd_status create_impl(const htd_grid *grid, const double *c_cell, const double 
                 c->use_s3 = htd::make_stream3d_maps(L, c->s3_shape, planes, &c->s3maps);
             if (c->use_s3) {
                 const char *envst = std::getenv("HTD_S3_STAGES");  // tuning override
-                const int want_st = envst ? std::atoi(envst) : 7;
-                c->s3_stages = (want_st == 4 || want_st == 6) ? want_st : 7;
+                const int want_st = envst ? std::atoi(envst) : 5;
+                c->s3_stages = (want_st == 4 || want_st == 6 || want_st == 7) ? want_st : 5;
                 c->s3_zchunk = c->s3_shape == kS3Pair ? htd::stream3d_pair_zchunk(L, c->s3_stages)
                                                       : htd::stream3d_zchunk(L, c->s3_shape);
                 const char *envz = std::getenv("HTD_S3_ZCHUNK");   // tuning override
@@ -1442,7 +1445,7 @@ htd_status htd_get_params(htd_handle h, htd_params *out)
         P.tile[0] = tx[sh];
         P.tile[1] = ty[sh];
         P.tile[2] = h->s3_zchunk;
-        P.ctas_per_sm = (sh == kS3Pair && h->s3_stages == 4) ? 3 : 2;
+        P.ctas_per_sm = (sh == kS3Pair && h->s3_stages <= 5) ? 3 : 2;
         int dev = 0, nsm = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);

@@ -22,6 +22,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "htd_internal.h"
 
 namespace htd {
@@ -147,8 +149,10 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// NS shared-memory stages: a node plane holds three of them, the rest is the
-// producer's lead; 6 or 7 stages (86 / 100 KB) fit 2 CTAs per SM, 4 stages (57 KB) fit 3
+// NS shared-memory stages: the consumers hold one or two of them (the stage
+// being read and the previous one, whose node data the finished node plane
+// needs), the rest is the producer's lead; 4 or 5 stages (57 / 72 KB) fit 3
+// CTAs per SM (the default, 5), 6 or 7 stages (86 / 100 KB) fit 2
 template <int NS>
 __global__ void __launch_bounds__(kThreads + 32, NS >= 6 ? 2 : 3)
 stream3d_pair_kernel(const __grid_constant__ Stream3Maps maps, int iu, int ium,
@@ -181,7 +185,6 @@ stream3d_pair_kernel(const __grid_constant__ Stream3Maps maps, int iu, int ium,
     const int xs = (int)(c0 & ~(int64_t)3);
     const int xn = (int)(L.xl + x0);
     const int nplanes = (int)(ze - zb) + 2;
-    const int nq = nplanes - 2;
 
     if (tid == 0) {
         for (int st = 0; st < NS; ++st) {
@@ -243,8 +246,10 @@ stream3d_pair_kernel(const __grid_constant__ Stream3Maps maps, int iu, int ium,
     const float2 a2 = bc(a), nb2 = bc(-b), ntwo = bc(-2.f);
     int wst = 0;
     unsigned wph = 0;
+    // the outcome is made warp-uniform, so that a warp never splits between
+    // giving up and going on to the warp-wide release
     auto full_wait_next = [&]() -> bool {
-        const bool r = wait_bounded(&full[wst], wph, &abort_flag);
+        const bool r = __all_sync(0xffffffffu, wait_bounded(&full[wst], wph, &abort_flag));
         if (++wst == NS) { wst = 0; wph ^= 1u; }
         return r;
     };
@@ -293,31 +298,42 @@ stream3d_pair_kernel(const __grid_constant__ Stream3Maps maps, int iu, int ium,
             kk[2][ox] = kx[1][ox];
         }
     };
-    // node plane iz: u of stored iz, iz+1, iz+2 (stages s0, s1, s2), cells of stored
-    // iz and iz+1, node data of stored iz+1; every operand is read from the ring,
-    // so a thread keeps no plane windows in registers
-    auto update = [&](const float *s0, const float *s1, const float *s2) {
-        float2 kl[3][3], kh[3][3];
-        load_k(kl, s0);
-        load_k(kh, s1);
-        const float *sp[3] = {s0, s1, s2};
-        float2 acc = bc(0.f);
+    // Each stored plane P is read from the ring once: its u_j rows are pushed
+    // into the stencil sums of the three node planes it touches -- P + 1 (as
+    // its lower plane, with the cell sums of c(P)), P (middle plane, c(P-1) +
+    // c(P)) and P - 1 (upper plane, c(P-1)) -- where c(P) is the cell plane
+    // stored with P.  A node plane receives its lower, middle and upper terms in
+    // that order, each in (oy, ox) order, so the sums are those of the one-node
+    // kernel bit for bit.  accL, accM, accU: node planes P + 1, P, P - 1.
+    float2 kprev[3][3], kcur[3][3];
 #pragma unroll
-        for (int oz = 0; oz < 3; ++oz)
+    for (int oy = 0; oy < 3; ++oy)
 #pragma unroll
-            for (int oy = 0; oy < 3; ++oy) {
-                float2 uv[3];
-                load_u(uv, sp[oz], oy);
+        for (int ox = 0; ox < 3; ++ox) kprev[oy][ox] = bc(0.f);
+    float2 accL = bc(0.f), accM = bc(0.f), accU = bc(0.f);
+    auto coef = [&](int oz, int oy, int ox, float2 ks) -> float2 {
+        const int sh = (oz != 1) + (oy != 1) + (ox != 1);
+        return (sh == 0) ? fma2(m0, ks, cc0) : fma2(mf[sh], ks, ncf[sh]);
+    };
+    // the terms of stored plane `st` for the node planes flagged
+    auto push = [&](const float *st, auto doL, auto doM, auto doU) {
+        constexpr bool kL = decltype(doL)::value, kM = decltype(doM)::value,
+                       kU = decltype(doU)::value;
 #pragma unroll
-                for (int ox = 0; ox < 3; ++ox) {
-                    const int sh = (oz != 1) + (oy != 1) + (ox != 1);
-                    const float2 ks = (oz == 0) ? kl[oy][ox] : (oz == 2) ? kh[oy][ox]
-                                                                       : add2(kl[oy][ox], kh[oy][ox]);
-                    const float2 coef = (sh == 0) ? fma2(m0, ks, cc0) : fma2(mf[sh], ks, ncf[sh]);
-                    acc = fma2(coef, uv[ox], acc);
-                }
+        for (int oy = 0; oy < 3; ++oy) {
+            float2 uv[3];
+            load_u(uv, st, oy);
+#pragma unroll
+            for (int ox = 0; ox < 3; ++ox) {
+                if (kL) accL = fma2(coef(0, oy, ox, kcur[oy][ox]), uv[ox], accL);
+                if (kM) accM = fma2(coef(1, oy, ox, add2(kprev[oy][ox], kcur[oy][ox])), uv[ox], accM);
+                if (kU) accU = fma2(coef(2, oy, ox, kprev[oy][ox]), uv[ox], accU);
             }
-        const float *nd = s1 + 2 * kHaloStride + no;
+        }
+    };
+    // node plane of stored plane `sn` complete: update, store, outputs
+    auto finish = [&](const float *sn, float2 acc) {
+        const float *nd = sn + 2 * kHaloStride + no;
         const float2 d = *reinterpret_cast<const float2 *>(nd);
         const float2 fr = *reinterpret_cast<const float2 *>(nd + kNodeElems);
         const float2 fi = *reinterpret_cast<const float2 *>(nd + 2 * kNodeElems);
@@ -344,17 +360,34 @@ stream3d_pair_kernel(const __grid_constant__ Stream3Maps maps, int iu, int ium,
         cidx += cstride;
     };
 
-    // stored planes zb, zb + 1 first; node plane q then waits for stored q + 2 and
-    // frees stored q when it is done
-    bool ok = full_wait_next() && full_wait_next();
-    int s0 = 0, s1 = 1, s2 = 2;
-    for (int q = 0; ok && q < nq; ++q) {
+    // stored planes zb + p, p = 0 .. nplanes - 1; node planes are stored planes
+    // 1 .. nplanes - 2.  Plane p feeds node p + 1 if p <= nplanes - 3, node p if
+    // 1 <= p <= nplanes - 2, node p - 1 if p >= 2 (which it completes); after
+    // plane p the stage of plane p - 1 is no longer needed.
+    using T_ = std::true_type;
+    using F_ = std::false_type;
+    bool ok = true;
+    for (int p = 0; p < nplanes; ++p) {
         if (!(ok = full_wait_next())) break;
-        update(ring + s0 * kStageElems, ring + s1 * kStageElems, ring + s2 * kStageElems);
-        release_next();
-        s0 = s1;
-        s1 = s2;
-        if (++s2 == NS) s2 = 0;
+        const float *st = ring + (p % NS) * kStageElems;
+        if (p < nplanes - 1) load_k(kcur, st);
+        const bool hL = p <= nplanes - 3, hM = p >= 1 && p <= nplanes - 2, hU = p >= 2;
+        if (hL && hM && hU) push(st, T_{}, T_{}, T_{});
+        else if (hL && hM) push(st, T_{}, T_{}, F_{});
+        else if (hL && hU) push(st, T_{}, F_{}, T_{});
+        else if (hM && hU) push(st, F_{}, T_{}, T_{});
+        else if (hL) push(st, T_{}, F_{}, F_{});
+        else if (hM) push(st, F_{}, T_{}, F_{});
+        else push(st, F_{}, F_{}, T_{});
+        if (hU) finish(ring + ((p - 1) % NS) * kStageElems, accU);
+        if (p >= 1) release_next();
+        accU = accM;
+        accM = accL;
+        accL = bc(0.f);
+#pragma unroll
+        for (int oy = 0; oy < 3; ++oy)
+#pragma unroll
+            for (int ox = 0; ox < 3; ++ox) kprev[oy][ox] = kcur[oy][ox];
     }
 }
 
@@ -405,6 +438,8 @@ bool make_stream3d_pair_maps(const Layout &L, float *const planes[6], Stream3Map
                                 (int)stream3d_pair_smem_bytes(7)) == cudaSuccess &&
            cudaFuncSetAttribute(stream3d_pair_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)stream3d_pair_smem_bytes(6)) == cudaSuccess &&
+           cudaFuncSetAttribute(stream3d_pair_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)stream3d_pair_smem_bytes(5)) == cudaSuccess &&
            cudaFuncSetAttribute(stream3d_pair_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)stream3d_pair_smem_bytes(4)) == cudaSuccess;
 }
@@ -416,7 +451,7 @@ int stream3d_pair_zchunk(const Layout &L, int stages)
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int64_t tiles = ((L.nx + kTX - 1) / kTX) * ((L.ny + kTY - 1) / kTY);
     int64_t zc = 64;
-    const int per_sm = stages == 4 ? 3 : 2;
+    const int per_sm = stages <= 5 ? 3 : 2;
     while (zc > 16 && tiles * ((L.nz + zc - 1) / zc) < per_sm * nsm) zc /= 2;
     if (zc > L.nz) zc = L.nz;
     return (int)zc;
@@ -432,6 +467,9 @@ void launch_stream3d_pair(const Stream3Maps &maps, int from, const Layout &L, fl
              (unsigned)((L.nz + zchunk - 1) / zchunk));
     if (stages == 7)
         launch_ex(stream3d_pair_kernel<7>, grd, kThreads + 32, stream3d_pair_smem_bytes(7), s,
+                  overlap, maps, iu, ium, um, L, C, a, b, slot, flags, zchunk, err, R);
+    else if (stages == 5)
+        launch_ex(stream3d_pair_kernel<5>, grd, kThreads + 32, stream3d_pair_smem_bytes(5), s,
                   overlap, maps, iu, ium, um, L, C, a, b, slot, flags, zchunk, err, R);
     else if (stages == 4)
         launch_ex(stream3d_pair_kernel<4>, grd, kThreads + 32, stream3d_pair_smem_bytes(4), s,

@@ -174,15 +174,15 @@ S3_CASES = [(13, 17, 19), (40, 9, 70), (1, 3, 1), (2, 2, 2), (64, 16, 33), (5, 3
 
 @pytest.mark.parametrize("n", S3_CASES, ids=["x".join(map(str, c)) for c in S3_CASES])
 @pytest.mark.parametrize("mode", ["table1", "exact"])
-@pytest.mark.parametrize("tile", ["0", "1", "2", "3", "3:4", "3:6"])
+@pytest.mark.parametrize("tile", ["0", "1", "2", "3", "3:4", "3:6", "3:7"])
 def test_streamed_3d_step_matches_register_kernel(n, mode, tile, monkeypatch):
     """The TMA-streamed 3-D FP32 step (one node per thread on 32 x 8, 64 x 4 or
     128 x 2 column tiles, or node pairs in paired FP32 instructions on 64 x 8
     tiles; z chunks, a ring of shared-memory stages fed by a producer warp)
     against the register z-march kernel and the FP64 oracle, on ragged grids
     (odd nx leaves the last pair half-used) and several z chunks (16 planes per
-    chunk at these sizes); "3:4" and "3:6" run the pair kernel with 4 or 6 ring
-    stages instead of the default 7."""
+    chunk at these sizes); "3:4", "3:6" and "3:7" run the pair kernel with 4, 6
+    or 7 ring stages instead of the default 5."""
     p = het_problem(3, n, T=2)
     monkeypatch.setenv("HTD_S3", "0")
     s0 = htd.Solver(p, precision="mixed", mode=mode)
@@ -339,3 +339,24 @@ def test_overlapped_launches_change_nothing(ndim, n, monkeypatch):
     assert np.array_equal(host(s2.precond(dev(p.F))), ref[0])
     for s in (s0, s1, s2):
         s.close()
+
+
+@pytest.mark.parametrize("stages", ["5", "7"])
+def test_pair_streamed_kernel_matches_one_node_kernel_bitwise(stages, monkeypatch):
+    """The node-pair streamed 3-D kernel reads each stored plane once and pushes
+    it into the sums of the three node planes it touches; the terms reach each
+    sum in the order of the one-node streamed kernel, and paired instructions
+    round each lane like scalar ones, so the outputs agree bit for bit (ragged
+    x: the last pair half-used)."""
+    p = het_problem(3, (29, 45, 37), T=2)
+    monkeypatch.setenv("HTD_S3_TILE", "0")
+    s0 = htd.Solver(p, precision="mixed")
+    monkeypatch.setenv("HTD_S3_TILE", "3")
+    monkeypatch.setenv("HTD_S3_STAGES", stages)
+    s1 = htd.Solver(p, precision="mixed")
+    assert s0.params["step_kernel"] == s1.params["step_kernel"] == 2
+    assert s1.params["tile"][:2] == [64, 8] and s0.params["tile"][:2] != [64, 8]
+    for F in (p.F, W.random_rhs(9, p.n)):
+        assert np.array_equal(host(s0.precond(dev(F))), host(s1.precond(dev(F))))
+    s0.close()
+    s1.close()

@@ -65,8 +65,8 @@ NCU_TRAFFIC = {
                   "nodes": 1001 * 1001},
     "stream3d": {"file": "htd_stream3d.cu", "sha16": "4f289c964d28aa22",
                  "bytes": 193680896 + 18157568, "nodes": 192 ** 3},
-    "stream3d_pair": {"file": "htd_stream3d_pair.cu", "sha16": "20c9153a76edcafb",
-                      "bytes": 197324544 + 16010240, "nodes": 192 ** 3},
+    "stream3d_pair": {"file": "htd_stream3d_pair.cu", "sha16": "8c6bdafcd9f39e71",
+                      "bytes": 201089536 + 15837696, "nodes": 192 ** 3},
 }
 
 

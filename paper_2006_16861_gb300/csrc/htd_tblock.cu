@@ -83,6 +83,13 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
                  : "memory");
 }
 
+// plain arrive (release at CTA scope: the arriving warp's shared-memory writes,
+// ordered before it by __syncwarp, are visible to the thread whose wait completes)
+__device__ __forceinline__ void mbar_arrive_cta(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase)
 {
     unsigned ok;
@@ -399,6 +406,21 @@ tb2d_pair_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, float *_
         }
     }
 
+    // Step-to-step order between row groups: warp g reads one halo row of its
+    // neighbours g - 1 and g + 1 and overwrites rows they read one step earlier,
+    // so before step s it waits only for those two to finish step s - 1 (one
+    // mbarrier per warp and step parity, arrived on by the neighbours' lane 0),
+    // instead of a barrier over the whole CTA.  Waits are bounded; a timeout
+    // sets *err and the abort word, and later waits are skipped.
+    __shared__ uint64_t nbar[2][RG];
+    __shared__ int nabort;
+    const int wg = tid >> 5, wl = tid & 31;
+    if (tid == 0) {
+        for (int q = 0; q < 2; ++q)
+            for (int g = 0; g < RG; ++g)
+                mbar_init(&nbar[q][g], (unsigned)((g > 0) + (g < RG - 1)));
+        nabort = 0;
+    }
     grid_dep_wait();
     if (tid == 0) {
         tma_load_3d(su0, &maps.m[in0], xs, ys, rhs, bar);
@@ -483,12 +505,35 @@ tb2d_pair_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, float *_
             u0m = upm; u00 = up0; u0p = upp; p0 = pp;
             k00 = k10; k01 = k11; hk0 = hk1;
         }
-        __syncthreads();
     };
+    const bool has_nb = RG > 1;
     for (int s = 0; s < S.nsub; ++s) {
+        if (s > 0 && has_nb) {
+            // the neighbours have finished step s - 1
+            uint64_t *b = &nbar[(s - 1) & 1][wg];
+            const unsigned par = (unsigned)(((s - 1) >> 1) & 1);
+            if (!mbar_try_wait(b, par)) {
+                const unsigned long long t0 = global_ns();
+                while (!*(volatile int *)&nabort && !mbar_try_wait(b, par)) {
+                    if (global_ns() - t0 > kWaitLimitNs) {
+                        *(volatile int *)&nabort = 1;
+                        atomicExch(err, 1);
+                    }
+                }
+            }
+            __syncwarp();
+        }
         if (s_flags[s]) step(s, std::true_type{});
         else step(s, std::false_type{});
+        if (s + 1 < S.nsub && has_nb) {
+            __syncwarp();                                // the warp's rows of step s written
+            if (wl == 0) {
+                if (wg > 0) mbar_arrive_cta(&nbar[s & 1][wg - 1]);
+                if (wg < RG - 1) mbar_arrive_cta(&nbar[s & 1][wg + 1]);
+            }
+        }
     }
+    __syncwarp();
 
     const T *last = (S.nsub & 1) ? su1 : su0;
     const T *prev = (S.nsub & 1) ? su0 : su1;

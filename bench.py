@@ -61,7 +61,7 @@ FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12
 # file); scaled by node count to other grid sizes.  The captures are summarised
 # under profiles/.
 NCU_TRAFFIC = {
-    "tb2d_pair": {"file": "htd_tblock.cu", "sha16": "153cab2185c8a1a9", "bytes": 25192448 + 1792,
+    "tb2d_pair": {"file": "htd_tblock.cu", "sha16": "b9afe2271fc20c85", "bytes": 25192448 + 1792,
                   "nodes": 1001 * 1001},
     "stream3d": {"file": "htd_stream3d.cu", "sha16": "4f289c964d28aa22",
                  "bytes": 193680896 + 18157568, "nodes": 192 ** 3},

@@ -9,7 +9,7 @@
 // array covers everything: one thread issues three cp.async.bulk.tensor copies
 // (zero fill outside the array) that complete on one mbarrier; the box starts
 // at a 16-byte aligned column.  The per-node d and the two forcing planes are
-// read into registers.  Consecutive launches of a step sequence overlap
+// read into registers (the pair form can stage d by a fourth box instead).  Consecutive launches of a step sequence overlap
 // (programmatic dependent launch): a launch reads q*kappa, d and the forcing
 // while the previous one drains and loads the state planes after it.
 //

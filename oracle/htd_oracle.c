@@ -47,6 +47,11 @@
  *                       paper; it reads U off the same time-harmonic ansatz
  *                       u(t) = Re(U e^{i omega t}) that Table 1 samples).
  *   ora_project_states  that projection for given states (pinned directly).
+ *   ora_grad            receiver misfit 0.5 sum_s |P U_s - d_s|^2 of exact
+ *                       solutions and its gradient with respect to c^-2 per cell
+ *                       and R per node, by one adjoint solve per source (H is
+ *                       complex symmetric; not in the paper).
+ *   ora_apply_imH       Im H alone (diagonal, or the cell-mass form).
  *   ora_grad_td         misfit of the preconditioner's own approximate solution
  *                       and its gradient through the recurrence (discrete
  *                       adjoint run backwards in time; not in the paper).

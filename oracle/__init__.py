@@ -11,6 +11,7 @@ and stiffness weights stencil_a, stencil_gamma).
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -71,36 +72,64 @@ _lib = None
 def _load():
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
-        P = ctypes.POINTER(_Problem)
-        Q = ctypes.POINTER(_Params)
-        vp = ctypes.c_void_p
-        lib.ora_tables.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp]
-        lib.ora_tables_family.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, vp, vp]
-        lib.ora_setup.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_int, Q]
-        lib.ora_setup_abd.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_int, Q]
-        lib.ora_abd_step.argtypes = [P, Q, vp, vp, vp, vp]
-        lib.ora_apply_imH.argtypes = [P, vp, ctypes.c_longlong, vp]
-        lib.ora_apply_reH.argtypes = [P, vp, ctypes.c_longlong, vp]
-        lib.ora_apply_H.argtypes = [P, vp, vp]
-        lib.ora_assemble_H.argtypes = [P, ctypes.c_longlong, vp, vp, vp, vp]
-        lib.ora_assemble_H.restype = ctypes.c_longlong
-        lib.ora_window.argtypes = [ctypes.c_double, ctypes.c_double]
-        lib.ora_window.restype = ctypes.c_double
-        lib.ora_acd_step.argtypes = [P, Q, vp, vp, vp, vp]
-        lib.ora_precond.argtypes = [P, Q, ctypes.c_int, vp, vp]
-        lib.ora_precond_project.argtypes = [P, Q, ctypes.c_int, vp, vp]
-        lib.ora_project_states.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_longlong,
-                                           ctypes.c_longlong, vp, vp]
-        lib.ora_direct_solve.argtypes = [P, vp, vp]
-        lib.ora_grad.argtypes = [P, ctypes.c_int, vp, ctypes.c_int, vp, vp, vp, vp, vp]
-        lib.ora_grad_td.argtypes = [P, Q, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp,
-                                    vp, vp, vp]
-        lib.ora_gmres.argtypes = [P, Q, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_double,
-                                  ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                  ctypes.POINTER(_Info)]
-        _lib = lib
+        _lib = _configure(ctypes.CDLL(build()))
     return _lib
+
+
+def _configure(lib):
+    """Declare the argument types of the C entry points on a loaded library."""
+    P = ctypes.POINTER(_Problem)
+    Q = ctypes.POINTER(_Params)
+    vp = ctypes.c_void_p
+    lib.ora_tables.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp]
+    lib.ora_tables_family.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, vp, vp]
+    lib.ora_setup.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_int, Q]
+    lib.ora_setup_abd.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_int, Q]
+    lib.ora_abd_step.argtypes = [P, Q, vp, vp, vp, vp]
+    lib.ora_apply_imH.argtypes = [P, vp, ctypes.c_longlong, vp]
+    lib.ora_apply_reH.argtypes = [P, vp, ctypes.c_longlong, vp]
+    lib.ora_apply_H.argtypes = [P, vp, vp]
+    lib.ora_assemble_H.argtypes = [P, ctypes.c_longlong, vp, vp, vp, vp]
+    lib.ora_assemble_H.restype = ctypes.c_longlong
+    lib.ora_window.argtypes = [ctypes.c_double, ctypes.c_double]
+    lib.ora_window.restype = ctypes.c_double
+    lib.ora_acd_step.argtypes = [P, Q, vp, vp, vp, vp]
+    lib.ora_precond.argtypes = [P, Q, ctypes.c_int, vp, vp]
+    lib.ora_precond_project.argtypes = [P, Q, ctypes.c_int, vp, vp]
+    lib.ora_project_states.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_longlong,
+                                       ctypes.c_longlong, vp, vp]
+    lib.ora_direct_solve.argtypes = [P, vp, vp]
+    lib.ora_grad.argtypes = [P, ctypes.c_int, vp, ctypes.c_int, vp, vp, vp, vp, vp]
+    lib.ora_grad_td.argtypes = [P, Q, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp,
+                                vp, vp, vp]
+    lib.ora_gmres.argtypes = [P, Q, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_double,
+                              ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                              ctypes.POINTER(_Info)]
+    return lib
+
+
+@contextlib.contextmanager
+def use_library(path: str):
+    """Run the oracle from another build of its source (tests that plant a
+    mistake in a copy of htd_oracle.c and check that the pins catch it)."""
+    global _lib
+    saved = _load()
+    _lib = _configure(ctypes.CDLL(path))
+    try:
+        yield _lib
+    finally:
+        _lib = saved
+
+
+def compile_library(src_path: str, out_path: str) -> str:
+    """Compile a copy of the oracle source with the flags build() uses."""
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math",
+                           "-ffp-contract=off", "-o", out_path, src_path, "-lm"])
+    return out_path
+
+
+def source_path() -> str:
+    return _SRC
 
 
 def _ptr(a: np.ndarray) -> int:

@@ -1,0 +1,85 @@
+"""The pins must catch plausible mistakes in the oracle.
+
+Each case plants one mistake in a copy of the oracle's C source (the parameter
+beta, the snapshot index, a mass weight, the Hamming distance, the damping
+factor, the window argument, a forcing sign, a Givens conjugate, the sign of
+the damping term), builds it, runs a battery of the pins of
+test_oracle_pins.py against it, and requires that at least one pin fails.  The
+unmodified source passes the same battery.  Everything runs on the CPU.
+"""
+import os
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+# (name, original text, planted text): each original occurs in the source; the
+# first occurrence is replaced
+MUTANTS = [
+    ("beta", "out->beta = x / sin(x);", "out->beta = x / tan(x);"),
+    ("snapshot index", "long long j_im = nsteps - q->nP / 4;",
+     "long long j_im = nsteps - q->nP / 2;"),
+    ("mass weight", "M[1] = 0.5 * (2.0 / 36.0);", "M[1] = 0.5 * (1.0 / 36.0);"),
+    ("Hamming distance", "int s = popcount_small((unsigned)(b ^ g));",
+     "int s = popcount_small((unsigned)(b & g));"),
+    ("damping factor", "/ (1.0 + 0.5 * L);", "/ (1.0 + L);"),
+    ("window argument", "ora_window(1.0 - (double)j / (double)nsteps, q->rho)",
+     "ora_window((double)j / (double)nsteps, q->rho)"),
+    ("forcing sign", "f[i] = chi * (cs * creal(F[i]) - sn * cimag(F[i]));",
+     "f[i] = chi * (cs * creal(F[i]) + sn * cimag(F[i]));"),
+    ("Givens conjugate", "col[j] = conj(cs[j]) * a + sn[j] * b;",
+     "col[j] = cs[j] * a + sn[j] * b;"),
+    ("damping sign", "out[i] += -t[2 * i + 1] + I * t[2 * i];",
+     "out[i] += t[2 * i + 1] - I * t[2 * i];"),
+]
+
+BATTERY = [
+    lambda: pins.test_q1mix_tables_are_q1_element_matrices(2),
+    lambda: pins.test_q1mix_tables_are_q1_element_matrices(3),
+    lambda: pins.test_fd5_constant_k_is_the_papers_5_point_operator(2),
+    lambda: pins.test_sine_modes_diagonalise_constant_coefficient_operator(2, "q1mix"),
+    lambda: pins.test_sine_modes_diagonalise_constant_coefficient_operator(3, "q1mix"),
+    lambda: pins.test_parameter_formulas(),
+    lambda: pins.test_window_is_admissible(),
+    lambda: pins.test_prop1_time_harmonic_solutions_are_reproduced_exactly(2, (13, 11)),
+    lambda: pins.test_theorem1_energy_identity(),
+    lambda: pins.test_preconditioner_on_sine_mode_equals_greens_sum(2, "q1mix", "zero", "table1"),
+    lambda: pins.test_preconditioner_on_sine_mode_equals_greens_sum(2, "q1mix", 40.0, "table1"),
+    lambda: pins.test_preconditioner_on_sine_mode_equals_greens_sum(2, "q1mix", 40.0, "exact"),
+    lambda: pins.test_direct_solve_matches_scipy(2, (23, 19)),
+    lambda: pins.test_gmres_unpreconditioned_matches_scipy_residual_history(),
+    lambda: pins.test_gmres_recovers_manufactured_solution("fgmres", "table1"),
+    lambda: pins.test_gmres_recovers_manufactured_solution("left", "exact"),
+]
+
+
+def failing_pins(lib_path):
+    failed = []
+    with oracle.use_library(lib_path):
+        for k, pin in enumerate(BATTERY):
+            try:
+                pin()
+            except (AssertionError, ValueError, FloatingPointError):
+                failed.append(k)
+    return failed
+
+
+def build_variant(tmp_path, name, old, new):
+    src = open(oracle.source_path()).read()
+    assert old in src, name
+    path = os.path.join(str(tmp_path), "ora_" + name.replace(" ", "_"))
+    with open(path + ".c", "w") as f:
+        f.write(src.replace(old, new, 1))
+    return oracle.compile_library(path + ".c", path + ".so")
+
+
+def test_unmodified_oracle_passes_the_battery(tmp_path):
+    lib = build_variant(tmp_path, "same", "#include <math.h>", "#include <math.h>")
+    assert failing_pins(lib) == []
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_planted_mistake_fails_a_pin(tmp_path, name, old, new):
+    lib = build_variant(tmp_path, name, old, new)
+    assert failing_pins(lib), f"no pin catches: {name}"

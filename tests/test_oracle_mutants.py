@@ -3,8 +3,11 @@
 Each case plants one mistake in a copy of the oracle's C source (the parameter
 beta, the snapshot index, a mass weight, the Hamming distance, the damping
 factor, the window argument, a forcing sign, a Givens conjugate, the sign of
-the damping term), builds it, runs a battery of the pins of
-test_oracle_pins.py against it, and requires that at least one pin fails.  The
+the damping term, the projection phase, the I_abd damping weight, the stencil
+family's mass mix, the adjoint source of the misfit gradient, a term of the
+recurrence adjoint), builds it, runs a battery of the pins of
+test_oracle_pins.py, test_oracle_abd.py and test_oracle_gradient.py against
+it, and requires that at least one pin fails.  The
 unmodified source passes the same battery.  Everything runs on the CPU.
 """
 import os
@@ -12,6 +15,8 @@ import os
 import pytest
 
 import oracle
+import test_oracle_abd as abd
+import test_oracle_gradient as grad
 import test_oracle_pins as pins
 
 # (name, original text, planted text): each original occurs in the source; the
@@ -32,6 +37,14 @@ MUTANTS = [
      "col[j] = cs[j] * a + sn[j] * b;"),
     ("damping sign", "out[i] += -t[2 * i + 1] + I * t[2 * i];",
      "out[i] += t[2 * i + 1] - I * t[2 * i];"),
+    ("projection phase", "cplx e = cos(th) - I * sin(th);", "cplx e = cos(th) + I * sin(th);"),
+    ("I_abd damping weight", "(1.0 - cos(q->omega * q->dt)) / q->alpha / q->omega;",
+     "(1.0 + cos(q->omega * q->dt)) / q->alpha / q->omega;"),
+    ("family mass mix", "M[s] = a * mc[s] + (1.0 - a) * (s == 0 ? lumped : 0.0);",
+     "M[s] = (1.0 - a) * mc[s] + a * (s == 0 ? lumped : 0.0);"),
+    ("adjoint source", "r[rec_idx[k]] += conj(res);", "r[rec_idx[k]] += res;"),
+    ("recurrence adjoint R term", "grad_R[i] += cR * lk[i] * (uk[i] - uk2[i]);",
+     "grad_R[i] += cR * lk[i] * (uk[i] + uk2[i]);"),
 ]
 
 BATTERY = [
@@ -51,6 +64,13 @@ BATTERY = [
     lambda: pins.test_gmres_unpreconditioned_matches_scipy_residual_history(),
     lambda: pins.test_gmres_recovers_manufactured_solution("fgmres", "table1"),
     lambda: pins.test_gmres_recovers_manufactured_solution("left", "exact"),
+    lambda: pins.test_projection_recovers_time_harmonic_amplitude(8, 2, 37),
+    lambda: pins.test_projection_on_sine_mode_equals_greens_sum(2, "q1mix", "zero", 1),
+    lambda: pins.test_family_tables_mix_q1_element_matrices_and_edge_stiffness(2, 0.3, 0.6),
+    lambda: abd.test_abd_reproduces_time_harmonic_solutions_exactly(2, (9, 8), "node"),
+    lambda: abd.test_abd_energy("layer"),
+    lambda: grad.test_gradient_matches_central_differences(2, (11, 9)),
+    lambda: grad.test_recurrence_gradient_matches_central_differences(2, (11, 9), "table1"),
 ]
 
 

@@ -4,8 +4,9 @@ Each case plants one mistake in a copy of the oracle's C source (the parameter
 beta, the snapshot index, a mass weight, the Hamming distance, the damping
 factor, the window argument, a forcing sign, a Givens conjugate, the sign of
 the damping term, the projection phase, the I_abd damping weight, the stencil
-family's mass mix, the adjoint source of the misfit gradient, a term of the
-recurrence adjoint), builds it, runs a battery of the pins of
+family's mass and stiffness mixes, the adjoint source of the misfit gradient,
+a term of the recurrence adjoint, the phase of the exact run's forcing),
+builds it, runs a battery of the pins of
 test_oracle_pins.py, test_oracle_abd.py and test_oracle_gradient.py against
 it, and requires that at least one pin fails.  The
 unmodified source passes the same battery.  Everything runs on the CPU.
@@ -45,6 +46,10 @@ MUTANTS = [
     ("adjoint source", "r[rec_idx[k]] += conj(res);", "r[rec_idx[k]] += res;"),
     ("recurrence adjoint R term", "grad_R[i] += cR * lk[i] * (uk[i] - uk2[i]);",
      "grad_R[i] += cR * lk[i] * (uk[i] + uk2[i]);"),
+    ("exact-run forcing phase", "cplx e = cexp(I * q->omega * t);",
+     "cplx e = cexp(-I * q->omega * t);"),
+    ("family stiffness mix", "S[s] = gamma * sq1[s] + (1.0 - gamma) * sfd[s];",
+     "S[s] = gamma * sq1[s] + (1.0 - gamma) * sq1[s];"),
 ]
 
 BATTERY = [
@@ -69,6 +74,8 @@ BATTERY = [
     lambda: pins.test_family_tables_mix_q1_element_matrices_and_edge_stiffness(2, 0.3, 0.6),
     lambda: abd.test_abd_reproduces_time_harmonic_solutions_exactly(2, (9, 8), "node"),
     lambda: abd.test_abd_energy("layer"),
+    lambda: abd.test_cell_damping_operator("q1mix"),
+    lambda: pins.test_sine_modes_diagonalise_family_operator(2, 0.3, 0.6),
     lambda: grad.test_gradient_matches_central_differences(2, (11, 9)),
     lambda: grad.test_recurrence_gradient_matches_central_differences(2, (11, 9), "table1"),
 ]

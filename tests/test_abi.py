@@ -170,3 +170,18 @@ def test_plan_abd_matches_oracle(damping):
     with pytest.raises(htd.HtdError) as e:
         htd.plan(q, integrator="abd")
     assert e.value.status == 4
+
+
+@pytest.mark.parametrize("damping", ["node", "cell"])
+@pytest.mark.parametrize("a,g", [(0.3, 0.6), (1.0, 0.0)])
+def test_plan_abd_family_matches_oracle(damping, a, g):
+    """I_abd's parameters with a stencil-family member agree with the oracle's."""
+    p = W.config_2d_constant(41, ppw=8.0, layer=6, T=3)
+    p = W.Problem(p.name, p.ndim, p.n, p.h, p.c_cell, 0.5 * p.R_node, p.omega, p.F, p.T, p.rho)
+    got = htd.plan(p, integrator="abd", damping=damping, stencil="family", stencil_a=a,
+                   stencil_gamma=g)
+    o = oracle.Oracle(p, integrator="abd", damping=damping, stencil="family", stencil_a=a,
+                      stencil_gamma=g)
+    assert got["nP"] == o.params.nP
+    assert got["omega_c"] == pytest.approx(o.params.omega, rel=1e-14)
+    assert got["lam_max_reH"] == pytest.approx(o.params.lam_max_reH, rel=1e-12)

@@ -230,7 +230,6 @@ void free_ctx(htd_ctx *c)
     delete c;
 }
 
-// one preconditioner run of T n_P steps; the forcing planes are already filled.
 // Consecutive launches of the blocked 2-D and the streamed 3-D step overlap
 // (programmatic dependent launch) unless HTD_OVERLAP=0 (a tuning override, read
 // whenever a step sequence is built or captured).
@@ -240,6 +239,7 @@ bool step_overlap()
     return !(e && std::atoi(e) == 0);
 }
 
+// One preconditioner run of T n_P steps; the forcing planes are already filled.
 // Table 1 / EXACT: the step kernels write the snapshot and final state into the
 // output slots (flags).  PROJECT: steps j >= j_acc (whose new states u_{j+1}
 // lie in the last proj_periods periods) run one step per launch, each

@@ -16,15 +16,23 @@ Printed (one JSON line on rank 0):
               L2 flushed (256 MiB write) between timed steps;
   roofline    the step kernel: algorithmic bytes per launch / average launch
               time, measured live (events around every preconditioner
-              application), against the measured HBM copy bandwidth;
+              application), against the measured HBM copy bandwidth; with the
+              ncu DRAM bytes per launch (`traffic`, null once the kernel source
+              differs from the captured one) and, for the blocked kernel, the
+              one-step-equivalent bandwidth and its fraction (`effective_*`);
+  fp64_roofline the FP64 step kernel of the plain form against the FP64 pipe;
   e2e         the same metric through htd_gmres_solve_host with pinned host
               buffers, host<->device copies inside the timed region;
   time_to_tol_ms / fp64_time_to_tol_ms / speedup_vs_fp64
               the solve time in mixed and in plain FP64 mode on the same GPU;
-  cpu_baseline the FP64 CPU oracle on a bounded sample of the same workload.
+  secondary_3d the FP32 recurrence on the 3-D 256^3 layered workload and its
+              HBM roofline (the HBM-bound case);
+  batched     the 96-system batched workload solved in lockstep;
+  cpu_baseline the FP64 CPU oracle on a bounded sample of the same workload;
+  clocks, gpu_launches  SM clocks sampled during the timed region; kernels
+              launched by the library in it.
 
---impl reference times the oracle (the CPU reference of this build) on the
-same workload and metric.
+--impl reference times the oracle on the same workload and metric.
 """
 import argparse
 import json

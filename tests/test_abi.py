@@ -185,3 +185,15 @@ def test_plan_abd_family_matches_oracle(damping, a, g):
     assert got["nP"] == o.params.nP
     assert got["omega_c"] == pytest.approx(o.params.omega, rel=1e-14)
     assert got["lam_max_reH"] == pytest.approx(o.params.lam_max_reH, rel=1e-12)
+
+
+def test_plan_rejects_empty_and_oversized_grids():
+    """n[a] = 0 (an empty grid) and more than 2^24 nodes on an axis are refused
+    before any array is read; a 1 x 1 grid is accepted."""
+    c = np.ones((2, 2))
+    R = np.zeros((1, 1))
+    assert htd.htd_plan(2, (1, 1), 0.1, c, R, 5.0, 0, htd.make_options(T=2, rho=0.25))["nP"] > 0
+    for n in ((0, 5), (5, 0), (1 << 25, 1)):
+        with pytest.raises(htd.HtdError) as e:
+            htd.htd_plan(2, n, 0.1, np.ones(1), np.ones(1), 5.0, 0, htd.make_options(T=2, rho=0.25))
+        assert e.value.status == 1

@@ -130,7 +130,38 @@ typedef struct {
                           the blocked configurations (default), 1 = one step per
                           launch, 4 or 8 = temporally blocked with that depth.
                           Ignored for other precisions, dimensions and I_abd */
+    /* Kernel selection.  The defaults (all 0) let htd_create pick by timing;
+       the other values restrict or force a kernel variant, for tuning and for
+       tests that compare variants.  Every variant computes the same recurrence;
+       the tests hold them to bit-identity or to the FP32 tolerance. */
+    int tb_rows;       /* blocked 2-D kernel: rows per thread the create-time
+                          tuner may pick (6, 8, 10, 12 or 20); 0 = any */
+    int tb_form;       /* blocked 2-D kernel: HTD_TB_ANY (tuned), HTD_TB_COLUMN
+                          (one column per thread), HTD_TB_PAIR (two columns per
+                          thread in paired FP32 instructions, d in registers),
+                          HTD_TB_PAIR_SD (pairs, d staged in shared memory) */
+    int s3_kernel;     /* 3-D FP32 step kernel: HTD_S3_PAIR (TMA-streamed z
+                          planes, node pairs; default), HTD_S3_ZMARCH (one step
+                          per launch, register z-march), HTD_S3_NODE_32x8,
+                          HTD_S3_NODE_64x4, HTD_S3_NODE_128x2 (TMA-streamed, one
+                          node per thread on that column tile) */
+    int s3_stages;     /* ring stages of the streamed 3-D kernels: 0 = 5, or 4, 6, 7 */
+    int s3_zchunk;     /* z planes per CTA of the streamed 3-D kernels: 0 = chosen
+                          at create by timing, else that many */
+    int launch;        /* bit flags: HTD_LAUNCH_NO_OVERLAP (consecutive step
+                          launches do not overlap by programmatic dependent
+                          launch), HTD_LAUNCH_NO_GRAPH (steps launched one by one
+                          instead of replaying a captured CUDA graph) */
+    long long wait_limit_ns; /* bound of the device-side waits between the row
+                          groups of the blocked 2-D kernel; 0 = 1 s.  A wait that
+                          runs out makes the call return HTD_ERR_TIMEOUT (see
+                          htd_set_wait_limit) */
 } htd_options;
+
+enum { HTD_TB_ANY = 0, HTD_TB_COLUMN = 1, HTD_TB_PAIR = 2, HTD_TB_PAIR_SD = 3 };
+enum { HTD_S3_PAIR = 0, HTD_S3_ZMARCH = 1, HTD_S3_NODE_32x8 = 2, HTD_S3_NODE_64x4 = 3,
+       HTD_S3_NODE_128x2 = 4 };
+enum { HTD_LAUNCH_NO_OVERLAP = 1, HTD_LAUNCH_NO_GRAPH = 2 };
 
 typedef struct {
     int iterations;           /* Arnoldi steps taken */
@@ -150,7 +181,8 @@ typedef struct {
 
 /* Fill *opt with the defaults: FP64, TABLE1, FGMRES, T = 10, rho = 0.25,
  * nP = 0 (automatic), Q1MIX stencil, restart 20, max_rhs 1, proj_periods 1,
- * HTD_ACD, HTD_DAMP_NODE, stencil_a 0.5, stencil_gamma 1, tblock 0. */
+ * HTD_ACD, HTD_DAMP_NODE, stencil_a 0.5, stencil_gamma 1, tblock 0, and 0 for
+ * every kernel-selection field. */
 void htd_default_options(htd_options *opt);
 
 /*
@@ -243,11 +275,12 @@ htd_status htd_residual_norm(htd_handle h, const void *F_dev, const void *U_dev,
  * Allocation-free variant of htd_residual_norm: *rel = ||F - H U|| / ||F||
  * (0 if F = 0), with the residual vector and the reduction partial sums kept
  * in a fixed buffer inside the library instead of the handle's workspace.
- * The paper has no counterpart; this exists for callers that must not
- * allocate device memory at call time -- code that runs while a CUDA stream
- * capture is active (cudaMalloc is not permitted during a global-mode
- * capture), or an application whose device memory belongs to its own pool
- * and which forbids libraries to call cudaMalloc/cudaFree in its solve loop.
+ * The paper has no counterpart.  It is for callers that cannot let a library
+ * allocate device memory when they call it: applications whose device memory
+ * is handed out by their own pool (a framework's caching allocator that has
+ * reserved most of the GPU, so that a library's cudaMalloc would fail or
+ * fragment it), and solve loops that cannot afford the device-wide
+ * synchronisation that cudaMalloc/cudaFree may imply while other streams run.
  * The call makes no cudaMalloc, cudaFree or other allocating call.
  *   Limit: N = prod(n) <= HTD_NOALLOC_MAX_NODES; larger problems return
  *   HTD_ERR_SIZE and compute nothing.
@@ -259,10 +292,16 @@ htd_status htd_residual_norm(htd_handle h, const void *F_dev, const void *U_dev,
  *   clearing is needed.  Calls whose GPU work overlaps (several streams or
  *   host threads at once) race on the buffer: serialise them.
  *   The first call on each device looks up the buffer's device address
- *   (cudaGetSymbolAddress, which may load the module); make that first call
- *   before any stream capture.  The handle's device must be current.
- * Synchronises the stream.  Errors: HTD_ERR_ARG, HTD_ERR_SIZE,
- * HTD_ERR_NONFINITE, HTD_ERR_CUDA.
+ *   (cudaGetSymbolAddress, which may load the module); the address is cached
+ *   per device and looked up again after a call that returned HTD_ERR_CUDA
+ *   (after cudaDeviceReset, make such a call or expect stale addresses until
+ *   one fails).  The handle's device must be current.
+ *   The call returns a host value, so it copies the two sums to the host and
+ *   synchronises `stream`: it cannot be recorded into a CUDA graph, and
+ *   `stream` must not be capturing.
+ *   A CUDA error already pending when the call starts is reported as
+ *   HTD_ERR_CUDA and left pending; nothing is launched then.
+ * Errors: HTD_ERR_ARG, HTD_ERR_SIZE, HTD_ERR_NONFINITE, HTD_ERR_CUDA.
  */
 #define HTD_NOALLOC_MAX_NODES 262144
 htd_status htd_residual_norm_noalloc(htd_handle h, const void *F_dev, const void *U_dev,
@@ -396,6 +435,30 @@ htd_status htd_batch_apply_precond(htd_batch b, const void *const *F_dev, void *
  */
 htd_status htd_batch_gmres_solve(htd_batch b, const void *const *F_dev, void *const *U_dev,
                                  double tol, int max_iters, void *stream, htd_solve_info *info);
+
+/*
+ * Test and tuning hooks.
+ *
+ * htd_set_wait_limit: bound (ns) of the device-side waits between the row
+ * groups of the blocked 2-D kernel for this handle's later launches (0 = 1 s,
+ * the default); the copy-completion waits keep their fixed 1 s bound so that
+ * no CTA exits with a copy in flight.  stall_test != 0 makes the first such
+ * wait of every CTA wait on a barrier that nothing arrives on, so it runs out
+ * after limit_ns: the kernel records the timeout, skips its remaining waits,
+ * finishes, and the call that ran it returns HTD_ERR_TIMEOUT (its outputs are
+ * then unspecified).  This exercises the timeout path without a fault or a
+ * hang.  Synchronous.  Errors: HTD_ERR_ARG (limit_ns < 0), HTD_ERR_CUDA.
+ */
+htd_status htd_set_wait_limit(htd_handle h, long long limit_ns, int stall_test);
+
+/*
+ * Host-side allocation-failure injection for tests: the library's device
+ * allocations numbered 0 .. after-1 from this call on succeed, allocation
+ * number `after` fails as if the device were out of memory (the calling entry
+ * point returns HTD_ERR_OOM after releasing what it took), later ones succeed.
+ * after < 0 switches it off.  Process-wide, not thread-safe.
+ */
+void htd_test_fail_alloc(long long after);
 
 /* Static string for a status code. */
 const char *htd_status_string(htd_status s);

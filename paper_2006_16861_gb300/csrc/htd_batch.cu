@@ -434,7 +434,7 @@ htd_status create_batch(int ninst, const htd_handle *handles, const int *nrhs, h
         tab += 2 * ci.rcap;
         b->tab_off.push_back(tab);
     }
-    HTD_CUDA(cudaMalloc((void **)&b->ws, sizeof(double2) * ws));
+    HTD_CUDA(htd::dev_malloc((void **)&b->ws, sizeof(double2) * ws));
     size_t off = 0;
     for (Sys &y : b->sys) {
         y.V = b->ws + off;
@@ -445,12 +445,12 @@ htd_status create_batch(int ninst, const htd_handle *handles, const int *nrhs, h
         off += (size_t)y.N;
     }
     const size_t hb = sizeof(double2) * kHBlock * b->sys.size();
-    HTD_CUDA(cudaMalloc((void **)&b->hdev, hb));
+    HTD_CUDA(htd::dev_malloc((void **)&b->hdev, hb));
     HTD_CUDA(cudaMemset(b->hdev, 0, hb));
-    HTD_CUDA(cudaMallocHost((void **)&b->hhost, hb));
-    HTD_CUDA(cudaMalloc((void **)&b->tab_dev, sizeof(double2 *) * tab));
+    HTD_CUDA(htd::host_malloc((void **)&b->hhost, hb));
+    HTD_CUDA(htd::dev_malloc((void **)&b->tab_dev, sizeof(double2 *) * tab));
     HTD_CUDA(cudaMemset(b->tab_dev, 0, sizeof(double2 *) * tab));
-    HTD_CUDA(cudaMallocHost((void **)&b->tab_host, sizeof(double2 *) * tab));
+    HTD_CUDA(htd::host_malloc((void **)&b->tab_host, sizeof(double2 *) * tab));
     std::memset(b->tab_host, 0, sizeof(double2 *) * tab);
     HTD_CUDA(cudaEventCreateWithFlags(&b->tab_ev, cudaEventDisableTiming));
     HTD_CUDA(cudaEventCreate(&b->ev[0]));

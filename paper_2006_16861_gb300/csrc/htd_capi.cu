@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <complex>
@@ -231,12 +232,11 @@ void free_ctx(htd_ctx *c)
 }
 
 // Consecutive launches of the blocked 2-D and the streamed 3-D step overlap
-// (programmatic dependent launch) unless HTD_OVERLAP=0 (a tuning override, read
-// whenever a step sequence is built or captured).
-bool step_overlap()
+// (programmatic dependent launch) unless the handle's options say
+// HTD_LAUNCH_NO_OVERLAP.
+bool step_overlap(const htd_ctx *c)
 {
-    const char *e = std::getenv("HTD_OVERLAP");
-    return !(e && std::atoi(e) == 0);
+    return !(c->opt.launch & HTD_LAUNCH_NO_OVERLAP);
 }
 
 // One preconditioner run of T n_P steps; the forcing planes are already filled.
@@ -328,7 +328,7 @@ htd_status run_steps_direct(htd_ctx *c, cudaStream_t s)
             htd::launch_tb2d<T>(c->tb, c->tbmaps, map_of[from][0], map_of[from][1], L,
                                 pairs[1 - from][0], pairs[1 - from][1], (const T *)c->dco,
                                 (const T *)c->fre, (const T *)c->fim, C, S, c->slot,
-                                c->err_dev, s, c->Rs, j0 > 0 && step_overlap());
+                                c->err_dev, s, c->Rs, j0 > 0 && step_overlap(c));
             from = 1 - from;
         }
         // the blocked launches leave u_{jend} in pairs[from][0], u_{jend-1} in pairs[from][1]
@@ -351,7 +351,7 @@ htd_status run_steps_direct(htd_ctx *c, cudaStream_t s)
                     htd::launch_stream3d_pair(c->s3maps, (int)(j & 1), L, um, C,
                                               (T)c->atab[j], (T)c->btab[j], c->slot, flags,
                                               c->s3_zchunk, c->s3_stages, c->err_dev, s, c->Rs,
-                                              j > 0 && step_overlap());
+                                              j > 0 && step_overlap(c));
                 else
                     htd::launch_stream3d(c->s3maps, (int)(j & 1), c->s3_shape, L, um, C,
                                          (T)c->atab[j], (T)c->btab[j], c->slot, flags,
@@ -369,9 +369,11 @@ htd_status run_steps_direct(htd_ctx *c, cudaStream_t s)
     return HTD_OK;
 }
 
-bool graphs_disabled()
+// HTD_LAUNCH_NO_GRAPH: the steps are launched one by one instead of replaying
+// a captured graph
+bool graphs_disabled(const htd_ctx *c)
 {
-    return std::getenv("HTD_NO_GRAPH") != nullptr;   // read at every use (cheap)
+    return (c->opt.launch & HTD_LAUNCH_NO_GRAPH) != 0;
 }
 
 // Capture the whole step sequence of one run into a graph (once per handle):
@@ -410,7 +412,7 @@ void capture_steps(htd_ctx *c)
 template <typename T>
 htd_status run_steps(htd_ctx *c, cudaStream_t s)
 {
-    if (!graphs_disabled()) capture_steps<T>(c);
+    if (!graphs_disabled(c)) capture_steps<T>(c);
     if (c->exec) {
         HTD_CUDA(cudaGraphLaunch(c->exec, s));
         htd::g_launches += c->nsteps;            // one step kernel per graph node
@@ -634,18 +636,17 @@ htd_status autotune_tb2d(htd_ctx *c, int want_B, int want_RPT)
     const Layout &L = c->Lr;
     std::vector<htd::TbPlan> all = htd::tb2d_candidates<float>(L, want_B);
     std::vector<htd::TbPlan> cands;
-    const char *env_pair = std::getenv("HTD_TB_PAIR");     // tuning override: 0 scalar, 1 pairs
-    const char *env_sd = std::getenv("HTD_TB_SD");         // tuning override: d in smem 0/1
-    for (const htd::TbPlan &p : all)
-        if ((want_RPT == 0 || p.RPT == want_RPT) &&
-            (!env_pair || (int)p.pair == std::atoi(env_pair)) &&
-            (!env_sd || (int)p.sd == std::atoi(env_sd)))
+    const int form = c->opt.tb_form;                       // HTD_TB_ANY: every form
+    for (const htd::TbPlan &p : all) {
+        const int pf = !p.pair ? HTD_TB_COLUMN : (p.sd ? HTD_TB_PAIR_SD : HTD_TB_PAIR);
+        if ((want_RPT == 0 || p.RPT == want_RPT) && (form == HTD_TB_ANY || form == pf))
             cands.push_back(p);
+    }
     if (cands.empty()) return HTD_OK;
     const size_t bytes = sizeof(float) * (size_t)L.total * c->rcap;
-    HTD_CUDA(cudaMalloc(&c->u2, bytes));
+    HTD_CUDA(htd::dev_malloc(&c->u2, bytes));
     HTD_CUDA(cudaMemset(c->u2, 0, bytes));
-    HTD_CUDA(cudaMalloc(&c->u3, bytes));
+    HTD_CUDA(htd::dev_malloc(&c->u3, bytes));
     HTD_CUDA(cudaMemset(c->u3, 0, bytes));
     cudaStream_t s;
     HTD_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
@@ -686,7 +687,7 @@ htd_status autotune_tb2d(htd_ctx *c, int want_B, int want_RPT)
             htd::launch_tb2d<float>(cands[k], maps, 0, 1, L, (float *)c->u2, (float *)c->u3,
                                     (const float *)c->dco, (const float *)c->fre,
                                     (const float *)c->fim, C, S, c->slot, c->err_dev, s,
-                                    htd::RhsSet{}, r > 0 && step_overlap());
+                                    htd::RhsSet{}, r > 0 && step_overlap(c));
         }
         HTD_CUDA(cudaEventRecord(e1, s));
         HTD_CUDA(cudaEventSynchronize(e1));
@@ -755,7 +756,7 @@ htd_status autotune_s3_zchunk(htd_ctx *c)
                 htd::launch_stream3d_pair(c->s3maps, r & 1, L, (r & 1) ? (float *)c->u0
                                                                         : (float *)c->u1,
                                           C, 0.f, 0.f, c->slot, 0, zc, c->s3_stages, c->err_dev, s,
-                                          htd::RhsSet{}, r > 0 && step_overlap());
+                                          htd::RhsSet{}, r > 0 && step_overlap(c));
             else
                 htd::launch_stream3d(c->s3maps, r & 1, c->s3_shape, L,
                                      (r & 1) ? (float *)c->u0 : (float *)c->u1, C, 0.f, 0.f,
@@ -810,7 +811,7 @@ htd_status grad_td_impl(htd_ctx *c, int nsrc, const double2 *F, int nrec, const 
         if (c->td_ws) cudaFree(c->td_ws);
         c->td_ws = nullptr;
         c->td_ws_bytes = 0;
-        HTD_CUDA(cudaMalloc(&c->td_ws, need));
+        HTD_CUDA(htd::dev_malloc(&c->td_ws, need));
         c->td_ws_bytes = need;
     }
     T *base = static_cast<T *>(c->td_ws);
@@ -942,17 +943,30 @@ htd_status plan_impl(const htd_grid *grid, const double *c_cell, const double *R
     pl->N = 1;
     pl->Nc = 1;
     for (int a = 0; a < 3; ++a) pl->n[a] = 1;
+    // every product is checked against the node limit before it is formed, so
+    // no int64 product can overflow (N <= 2^34 and each factor <= 2^24 + 1)
+    constexpr int64_t kMaxNodes = (int64_t)1 << 34;
     for (int a = 0; a < d; ++a) {
         if (grid->n[a] < 1 || grid->n[a] > ((int64_t)1 << 24)) return HTD_ERR_ARG;
+        if (pl->N > kMaxNodes / grid->n[a]) return HTD_ERR_ARG;
+        if (pl->Nc > (2 * kMaxNodes) / (grid->n[a] + 1)) return HTD_ERR_ARG;
         pl->n[a] = grid->n[a];
         pl->N *= grid->n[a];
         pl->Nc *= grid->n[a] + 1;
     }
-    if (pl->N > ((int64_t)1 << 34)) return HTD_ERR_ARG;
     if (!cell_weights(d, opt.stencil, opt.stencil_a, opt.stencil_gamma, pl->S, pl->M))
         return HTD_ERR_ARG;
     if (opt.tblock != 0 && opt.tblock != 1 && opt.tblock != 4 && opt.tblock != 8)
         return HTD_ERR_ARG;
+    if (opt.tb_rows != 0 && opt.tb_rows != 6 && opt.tb_rows != 8 && opt.tb_rows != 10 &&
+        opt.tb_rows != 12 && opt.tb_rows != 20)
+        return HTD_ERR_ARG;
+    if (opt.tb_form < HTD_TB_ANY || opt.tb_form > HTD_TB_PAIR_SD) return HTD_ERR_ARG;
+    if (opt.s3_kernel < HTD_S3_PAIR || opt.s3_kernel > HTD_S3_NODE_128x2) return HTD_ERR_ARG;
+    if (opt.s3_stages != 0 && (opt.s3_stages < 4 || opt.s3_stages > 7)) return HTD_ERR_ARG;
+    if (opt.s3_zchunk < 0 || opt.s3_zchunk > (1 << 24)) return HTD_ERR_ARG;
+    if (opt.launch & ~(HTD_LAUNCH_NO_OVERLAP | HTD_LAUNCH_NO_GRAPH)) return HTD_ERR_ARG;
+    if (opt.wait_limit_ns < 0) return HTD_ERR_ARG;
     pl->opt = opt;
 
     double kmin = INFINITY, kmax = 0.0;
@@ -1096,31 +1110,36 @@ htd_status create_impl(const htd_grid *grid, const double *c_cell, const double 
     c->rcap = opt.max_rhs;
     void **shared_arrs[] = {&c->kap, &c->dco};
     for (void **pp : shared_arrs) {
-        HTD_CUDA(cudaMalloc(pp, bytes));
+        HTD_CUDA(htd::dev_malloc(pp, bytes));
         HTD_CUDA(cudaMemset(*pp, 0, bytes));
     }
     void **rhs_arrs[] = {&c->fre, &c->fim, &c->u0, &c->u1};
     for (void **pp : rhs_arrs) {
-        HTD_CUDA(cudaMalloc(pp, bytes * c->rcap));
+        HTD_CUDA(htd::dev_malloc(pp, bytes * c->rcap));
         HTD_CUDA(cudaMemset(*pp, 0, bytes * c->rcap));
     }
-    HTD_CUDA(cudaMalloc((void **)&c->err_dev, sizeof(int)));
-    HTD_CUDA(cudaMemset(c->err_dev, 0, sizeof(int)));
-    HTD_CUDA(cudaMalloc((void **)&c->slot, sizeof(OutSlot) * c->rcap));
+    HTD_CUDA(htd::dev_malloc((void **)&c->err_dev, sizeof(int) * htd::kStatusWords));
+    {
+        int words[htd::kStatusWords] = {0, 0, 0, 0};
+        const unsigned long long lim = (unsigned long long)opt.wait_limit_ns;
+        std::memcpy(&words[2], &lim, sizeof(lim));
+        HTD_CUDA(cudaMemcpy(c->err_dev, words, sizeof(words), cudaMemcpyHostToDevice));
+    }
+    HTD_CUDA(htd::dev_malloc((void **)&c->slot, sizeof(OutSlot) * c->rcap));
     HTD_CUDA(cudaMemset(c->slot, 0, sizeof(OutSlot) * c->rcap));
     if (opt.mode == HTD_MODE_PROJECT)
-        HTD_CUDA(cudaMalloc(&c->acc, c->esz * 4 * (size_t)N * c->rcap));
+        HTD_CUDA(htd::dev_malloc(&c->acc, c->esz * 4 * (size_t)N * c->rcap));
     if (abd) {                                     // third state plane of I_abd
-        HTD_CUDA(cudaMalloc(&c->u2, bytes * c->rcap));
+        HTD_CUDA(htd::dev_malloc(&c->u2, bytes * c->rcap));
         HTD_CUDA(cudaMemset(c->u2, 0, bytes * c->rcap));
     }
-    HTD_CUDA(cudaMalloc((void **)&c->act_dev, sizeof(int) * (1 + c->rcap)));
+    HTD_CUDA(htd::dev_malloc((void **)&c->act_dev, sizeof(int) * (1 + c->rcap)));
     HTD_CUDA(cudaMemset(c->act_dev, 0, sizeof(int) * (1 + c->rcap)));
     c->Rs.act = c->act_dev;
     c->Rs.slots = c->rcap;
     c->Rs.stride = L.total;
-    HTD_CUDA(cudaMalloc((void **)&c->kap64, sizeof(double) * c->L64.total));
-    HTD_CUDA(cudaMalloc((void **)&c->imH, sizeof(double) * N));
+    HTD_CUDA(htd::dev_malloc((void **)&c->kap64, sizeof(double) * c->L64.total));
+    HTD_CUDA(htd::dev_malloc((void **)&c->imH, sizeof(double) * N));
 
     // per-cell kappa = (h omega_phys / c)^2 at the cell's stored position;
     // per-node d = 1 / (1 + L_ii / 2), L = (beta dt / alpha) Im H / omega
@@ -1178,7 +1197,7 @@ htd_status create_impl(const htd_grid *grid, const double *c_cell, const double 
     {
         double S2[4];
         for (int k = 0; k < 4; ++k) S2[k] = std::ldexp(c->S[k], d - k);
-        HTD_CUDA(cudaMalloc((void **)&c->coefP, sizeof(double) * htd::h_planes(d) * (size_t)N));
+        HTD_CUDA(htd::dev_malloc((void **)&c->coefP, sizeof(double) * htd::h_planes(d) * (size_t)N));
         htd::launch_assemble_H(c->L64, c->kap64, S2, c->M, c->coefP, 0);
         HTD_CUDA(cudaGetLastError());
         if (cell_damp) {
@@ -1187,10 +1206,10 @@ htd_status create_impl(const htd_grid *grid, const double *c_cell, const double 
             double Z[4] = {0.0, 0.0, 0.0, 0.0}, Mn[4];
             for (int k = 0; k < 4; ++k) Mn[k] = -c->M[k];
             double *rcell = nullptr;
-            HTD_CUDA(cudaMalloc((void **)&rcell, sizeof(double) * c->L64.total));
+            HTD_CUDA(htd::dev_malloc((void **)&rcell, sizeof(double) * c->L64.total));
             HTD_CUDA(cudaMemcpy(rcell, rc64.data(), sizeof(double) * c->L64.total,
                                 cudaMemcpyHostToDevice));
-            HTD_CUDA(cudaMalloc((void **)&c->coefI, sizeof(double) * htd::h_planes(d) * (size_t)N));
+            HTD_CUDA(htd::dev_malloc((void **)&c->coefI, sizeof(double) * htd::h_planes(d) * (size_t)N));
             htd::launch_assemble_H(c->L64, rcell, Z, Mn, c->coefI, 0);
             HTD_CUDA(cudaDeviceSynchronize());
             cudaFree(rcell);
@@ -1200,29 +1219,22 @@ htd_status create_impl(const htd_grid *grid, const double *c_cell, const double 
 
     // temporal blocking for the 2-D FP32 recurrence, picked by timing against the
     // one-step kernel, or as options.tblock asks (1: one step per launch, 4/8:
-    // that depth).  Tuning overrides: HTD_TB=0 disables it; HTD_TB=4/8 (and
-    // HTD_TB_RPT=6/8/10/12/20, HTD_TB_PAIR=0/1, HTD_TB_SD=0/1) force a blocked
-    // configuration of that depth (rows per thread, pair form, d in shared memory).
+    // that depth); tb_rows and tb_form restrict the configurations tried
     {
-        const char *env = std::getenv("HTD_TB");
-        const char *env_r = std::getenv("HTD_TB_RPT");
-        const int want = env ? std::atoi(env) : (opt.tblock == 1 ? 0 : opt.tblock);
-        const int want_r = env_r ? std::atoi(env_r) : 0;
-        const bool off = env ? want == 0 : opt.tblock == 1;
-        if (d == 2 && mixed && !abd && !off) {
-            htd_status ts = autotune_tb2d(c, want, want_r);
+        const int want = (opt.tblock == 1) ? 0 : opt.tblock;
+        if (d == 2 && mixed && !abd && opt.tblock != 1) {
+            htd_status ts = autotune_tb2d(c, want, opt.tb_rows);
             if (ts != HTD_OK) return ts;
         }
     }
 
-    // TMA-streamed 3-D FP32 step (HTD_S3=0 keeps the register z-march kernel)
+    // TMA-streamed 3-D FP32 step (HTD_S3_ZMARCH keeps the register z-march kernel)
     {
-        const char *env = std::getenv("HTD_S3");
-        if (d == 3 && mixed && !abd && !(env && std::atoi(env) == 0)) {
+        if (d == 3 && mixed && !abd && opt.s3_kernel != HTD_S3_ZMARCH) {
             float *planes[6] = {(float *)c->u0, (float *)c->u1, (float *)c->kap, (float *)c->dco,
                                 (float *)c->fre, (float *)c->fim};
-            const char *envs = std::getenv("HTD_S3_TILE");       // tuning override
-            c->s3_shape = envs ? std::atoi(envs) : kS3Default;
+            // option value -> kernel shape (0..2 one node per thread, kS3Pair pairs)
+            c->s3_shape = (opt.s3_kernel == HTD_S3_PAIR) ? kS3Default : opt.s3_kernel - HTD_S3_NODE_32x8;
             if (c->s3_shape != kS3Pair && c->rcap > 1) c->s3_shape = kS3Pair;   // rhs batches
             if (c->s3_shape == kS3Pair) {
                 c->use_s3 = htd::make_stream3d_pair_maps(L, planes, &c->s3maps, c->rcap);
@@ -1234,14 +1246,11 @@ htd_status create_impl(const htd_grid *grid, const double *c_cell, const double 
             if (c->s3_shape != kS3Pair && c->rcap == 1)
                 c->use_s3 = htd::make_stream3d_maps(L, c->s3_shape, planes, &c->s3maps);
             if (c->use_s3) {
-                const char *envst = std::getenv("HTD_S3_STAGES");  // tuning override
-                const int want_st = envst ? std::atoi(envst) : 5;
-                c->s3_stages = (want_st == 4 || want_st == 6 || want_st == 7) ? want_st : 5;
+                c->s3_stages = (opt.s3_stages == 0) ? 5 : opt.s3_stages;
                 c->s3_zchunk = c->s3_shape == kS3Pair ? htd::stream3d_pair_zchunk(L, c->s3_stages)
                                                       : htd::stream3d_zchunk(L, c->s3_shape);
-                const char *envz = std::getenv("HTD_S3_ZCHUNK");   // tuning override
-                if (envz && std::atoi(envz) > 0) {
-                    c->s3_zchunk = std::atoi(envz);
+                if (opt.s3_zchunk > 0) {
+                    c->s3_zchunk = opt.s3_zchunk;
                 } else {
                     htd_status ts = autotune_s3_zchunk(c);
                     if (ts != HTD_OK) return ts;
@@ -1253,15 +1262,15 @@ htd_status create_impl(const htd_grid *grid, const double *c_cell, const double 
 
     // Krylov workspace
     const size_t vb = sizeof(double2) * (size_t)N;
-    HTD_CUDA(cudaMalloc((void **)&c->V, vb * (c->m + 1)));
-    if (opt.krylov == HTD_FGMRES) HTD_CUDA(cudaMalloc((void **)&c->Z, vb * c->m));
-    HTD_CUDA(cudaMalloc((void **)&c->w, vb));
-    HTD_CUDA(cudaMalloc((void **)&c->t, vb));
-    HTD_CUDA(cudaMalloc((void **)&c->r, vb));
+    HTD_CUDA(htd::dev_malloc((void **)&c->V, vb * (c->m + 1)));
+    if (opt.krylov == HTD_FGMRES) HTD_CUDA(htd::dev_malloc((void **)&c->Z, vb * c->m));
+    HTD_CUDA(htd::dev_malloc((void **)&c->w, vb));
+    HTD_CUDA(htd::dev_malloc((void **)&c->t, vb));
+    HTD_CUDA(htd::dev_malloc((void **)&c->r, vb));
     c->nb = htd::dots_blocks(N);
-    HTD_CUDA(cudaMalloc((void **)&c->partial, sizeof(double2) * (size_t)c->nb * (kMaxRestart + 1)));
-    HTD_CUDA(cudaMalloc((void **)&c->hdev, sizeof(double2) * 3 * 72));
-    HTD_CUDA(cudaMallocHost((void **)&c->hhost, sizeof(double2) * 3 * 72));
+    HTD_CUDA(htd::dev_malloc((void **)&c->partial, sizeof(double2) * (size_t)c->nb * (kMaxRestart + 1)));
+    HTD_CUDA(htd::dev_malloc((void **)&c->hdev, sizeof(double2) * 3 * 72));
+    HTD_CUDA(htd::host_malloc((void **)&c->hhost, sizeof(double2) * 3 * 72));
     HTD_CUDA(cudaEventCreate(&c->pev[0]));
     HTD_CUDA(cudaEventCreate(&c->pev[1]));
     HTD_CUDA(cudaDeviceSynchronize());
@@ -1319,7 +1328,7 @@ htd_status ctx_stage_run(htd_ctx *c, int run, int n, const int *idx, const doubl
 
 cudaGraph_t ctx_step_graph(htd_ctx *c)
 {
-    if (graphs_disabled()) return nullptr;
+    if (graphs_disabled(c)) return nullptr;
     if (c->opt.precision == HTD_MIXED) capture_steps<float>(c);
     else capture_steps<double>(c);
     return c->exec ? c->graph : nullptr;
@@ -1359,9 +1368,56 @@ htd_status ctx_take_error(htd_ctx *c)
     return HTD_OK;
 }
 
+// ---- allocation (every device or pinned allocation of the library) --------
+
+namespace {
+std::atomic<long long> g_fail_after{-1};    // htd_test_fail_alloc: allocations left before a failure
+
+bool fail_this_allocation()
+{
+    long long k = g_fail_after.load();
+    while (k >= 0 && !g_fail_after.compare_exchange_weak(k, k - 1)) {
+    }
+    return k == 0;
+}
+}  // namespace
+
+cudaError_t dev_malloc_raw(void **p, size_t bytes)
+{
+    if (fail_this_allocation()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t host_malloc_raw(void **p, size_t bytes)
+{
+    if (fail_this_allocation()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocHost(p, bytes);
+}
+
 }  // namespace htd
 
 extern "C" {
+
+void htd_test_fail_alloc(long long after)
+{
+    htd::g_fail_after.store(after < 0 ? -1 : after);
+}
+
+htd_status htd_set_wait_limit(htd_handle h, long long limit_ns, int stall_test)
+{
+    if (!h || limit_ns < 0) return HTD_ERR_ARG;
+    int words[3] = {stall_test ? 1 : 0, 0, 0};
+    const unsigned long long lim = (unsigned long long)limit_ns;
+    std::memcpy(&words[1], &lim, sizeof(lim));
+    HTD_CUDA(cudaMemcpy(h->err_dev + 1, words, sizeof(words), cudaMemcpyHostToDevice));
+    return HTD_OK;
+}
 
 void htd_default_options(htd_options *opt)
 {
@@ -1381,6 +1437,13 @@ void htd_default_options(htd_options *opt)
     opt->stencil_a = 0.5;
     opt->stencil_gamma = 1.0;
     opt->tblock = 0;
+    opt->tb_rows = 0;
+    opt->tb_form = HTD_TB_ANY;
+    opt->s3_kernel = HTD_S3_PAIR;
+    opt->s3_stages = 0;
+    opt->s3_zchunk = 0;
+    opt->launch = 0;
+    opt->wait_limit_ns = 0;
 }
 
 htd_status htd_create(const htd_grid *grid, const double *c_cell_host, const double *R_node_host,
@@ -1500,8 +1563,8 @@ htd_status htd_gmres_solve_host(htd_handle h, const void *F_host, void *U_host, 
     if (!h || !F_host || !U_host || max_iters < 0) return HTD_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t vb = sizeof(double2) * (size_t)h->Lr.N;
-    if (!h->Fh) HTD_CUDA(cudaMalloc((void **)&h->Fh, vb));
-    if (!h->Uh) HTD_CUDA(cudaMalloc((void **)&h->Uh, vb));
+    if (!h->Fh) HTD_CUDA(htd::dev_malloc((void **)&h->Fh, vb));
+    if (!h->Uh) HTD_CUDA(htd::dev_malloc((void **)&h->Uh, vb));
     HTD_CUDA(cudaMemcpyAsync(h->Fh, F_host, vb, cudaMemcpyHostToDevice, s));
     HTD_CUDA(cudaMemcpyAsync(h->Uh, U_host, vb, cudaMemcpyHostToDevice, s));
     htd_status st = gmres(h, h->Fh, h->Uh, tol, max_iters, s, info);
@@ -1525,17 +1588,17 @@ htd_status htd_grad(htd_handle h, int nsrc, const void *F_dev, int nrec,
         if (rec_idx_host[k] < 0 || rec_idx_host[k] >= N) return HTD_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t vb = sizeof(double2) * (size_t)N;
-    if (!h->gU) HTD_CUDA(cudaMalloc((void **)&h->gU, vb));
-    if (!h->gMu) HTD_CUDA(cudaMalloc((void **)&h->gMu, vb));
-    if (!h->gR) HTD_CUDA(cudaMalloc((void **)&h->gR, vb));
+    if (!h->gU) HTD_CUDA(htd::dev_malloc((void **)&h->gU, vb));
+    if (!h->gMu) HTD_CUDA(htd::dev_malloc((void **)&h->gMu, vb));
+    if (!h->gR) HTD_CUDA(htd::dev_malloc((void **)&h->gR, vb));
     if (nrec > h->grec_cap) {
         if (h->gres) cudaFree(h->gres);
         if (h->grec) cudaFree(h->grec);
         h->gres = nullptr;
         h->grec = nullptr;
         h->grec_cap = 0;
-        HTD_CUDA(cudaMalloc((void **)&h->gres, sizeof(double2) * nrec));
-        HTD_CUDA(cudaMalloc((void **)&h->grec, sizeof(int64_t) * nrec));
+        HTD_CUDA(htd::dev_malloc((void **)&h->gres, sizeof(double2) * nrec));
+        HTD_CUDA(htd::dev_malloc((void **)&h->grec, sizeof(int64_t) * nrec));
         h->grec_cap = nrec;
     }
     if (nrec > 0)
@@ -1614,8 +1677,8 @@ htd_status htd_grad_td(htd_handle h, int nsrc, const void *F_dev, int nrec,
         h->gres = nullptr;
         h->grec = nullptr;
         h->grec_cap = 0;
-        HTD_CUDA(cudaMalloc((void **)&h->gres, sizeof(double2) * nrec));
-        HTD_CUDA(cudaMalloc((void **)&h->grec, sizeof(int64_t) * nrec));
+        HTD_CUDA(htd::dev_malloc((void **)&h->gres, sizeof(double2) * nrec));
+        HTD_CUDA(htd::dev_malloc((void **)&h->grec, sizeof(int64_t) * nrec));
         h->grec_cap = nrec;
     }
     if (nrec > 0)

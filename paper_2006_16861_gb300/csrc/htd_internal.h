@@ -132,6 +132,31 @@ __device__ __forceinline__ bool rhs_of_slot(const RhsSet &R, int k, int &rhs)
     return true;
 }
 
+// ---- device allocation (htd_capi.cu) ---------------------------------------
+
+// Every allocation the library makes goes through these: cudaMalloc /
+// cudaMallocHost, unless the test hook htd_test_fail_alloc has armed a failure
+// for this allocation (then cudaErrorMemoryAllocation, nothing allocated).
+cudaError_t dev_malloc_raw(void **p, size_t bytes);
+cudaError_t host_malloc_raw(void **p, size_t bytes);
+template <typename T>
+cudaError_t dev_malloc(T **p, size_t bytes)
+{
+    return dev_malloc_raw(reinterpret_cast<void **>(p), bytes);
+}
+template <typename T>
+cudaError_t host_malloc(T **p, size_t bytes)
+{
+    return host_malloc_raw(reinterpret_cast<void **>(p), bytes);
+}
+
+// Per-handle status words on the device (the `err` pointer the kernels get):
+// err[0] error flag (a bounded wait gave up), err[1] stall test (the first
+// neighbour wait of each CTA waits on a barrier nothing arrives on), err[2..3]
+// the neighbour-wait bound in ns as one 64-bit word (0 = kDefaultWaitNs).
+constexpr int kStatusWords = 4;
+constexpr unsigned long long kDefaultWaitNs = 1000000000ull;
+
 // ---- kernel launchers (htd_kernels.cu) --------------------------------------
 
 // Number of kernels enqueued by this library (host counter, not thread-safe
@@ -311,7 +336,10 @@ void launch_apply_H(const Layout &L, const double *coefP, const double *imH, dou
                     const double2 *X, const double2 *F, double2 *Y, cudaStream_t s,
                     const double *coefI = nullptr);
 
-// partial[k * nb + b] = sum over block b of conj(V_k) w, k < kcount
+// partial[k * nb + b] = sum over block b of conj(V_k) w, k < kcount.
+// dots_blocks: blocks per dot pass, 4 per SM of the current device (queried
+// once per device), at most kMaxDotBlocks.
+constexpr int kMaxDotBlocks = 1216;
 int dots_blocks(int64_t N);
 void launch_dots(const double2 *V, int64_t ldv, int kcount, const double2 *w, int64_t N,
                  double2 *partial, int nb, cudaStream_t s);

@@ -25,6 +25,7 @@
 // q = dt^2 / (alpha h^2), c0 = 2 - (dt^2/alpha) omega^2 - q 2^d S_0,
 // cs_s = q 2^{d-s} S_s; the stored per-cell coefficient is q * kappa.
 #include <cuda_runtime.h>
+#include <algorithm>
 
 #include "htd_internal.h"
 
@@ -792,8 +793,26 @@ dots_kernel(const double2 *__restrict__ V, int64_t ldv, int kcount, const double
 
 int dots_blocks(int64_t N)
 {
+    // 4 blocks per SM of the current device, looked up once per device
+    static int sm_count[64] = {0};
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        (void)cudaGetLastError();
+        dev = -1;
+    }
+    if (dev >= 0 && sm_count[dev] > 0) {
+        nsm = sm_count[dev];
+    } else if (dev >= 0 &&
+               cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+               nsm > 0) {
+        sm_count[dev] = nsm;
+    } else {
+        (void)cudaGetLastError();
+        nsm = 1;
+    }
+    const int64_t cap = std::min<int64_t>(4 * (int64_t)nsm, kMaxDotBlocks);
     int64_t nb = (N + 8 * kRedThreads - 1) / (8 * kRedThreads);
-    if (nb > 608) nb = 608;     // 4 blocks per SM on 152 SMs
+    if (nb > cap) nb = cap;
     if (nb < 1) nb = 1;
     return (int)nb;
 }

@@ -42,7 +42,7 @@ namespace {
 constexpr int kW = 64;           // tile width including the halo
 constexpr int kBoxW = 72;        // TMA box width: 64 + 2 pad columns + up to 3 for alignment, rounded
 // threads = 64 columns x RG row groups (RG = 8 or 16)
-constexpr unsigned long long kWaitLimitNs = 1000000000ull;   // 1 s bound on the mbarrier wait
+constexpr unsigned long long kWaitLimitNs = kDefaultWaitNs;  // 1 s bound on the TMA-completion wait
 
 template <typename T>
 __host__ __device__ constexpr size_t tb2d_array_bytes(int H)
@@ -410,16 +410,22 @@ tb2d_pair_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, float *_
     // neighbours g - 1 and g + 1 and overwrites rows they read one step earlier,
     // so before step s it waits only for those two to finish step s - 1 (one
     // mbarrier per warp and step parity, arrived on by the neighbours' lane 0),
-    // instead of a barrier over the whole CTA.  Waits are bounded; a timeout
-    // sets *err and the abort word, and later waits are skipped.
+    // instead of a barrier over the whole CTA.  Waits are bounded by the
+    // handle's limit (err[2..3], read only when a wait does not complete at
+    // once); a timeout sets *err and the abort word, and later waits are
+    // skipped.  With the stall test (err[1]) warp 0's first wait is on `never`,
+    // which nothing arrives on, so it runs out.
     __shared__ uint64_t nbar[2][RG];
-    __shared__ int nabort;
+    __shared__ uint64_t never;
+    __shared__ int nabort, nstall;
     const int wg = tid >> 5, wl = tid & 31;
     if (tid == 0) {
         for (int q = 0; q < 2; ++q)
             for (int g = 0; g < RG; ++g)
                 mbar_init(&nbar[q][g], (unsigned)((g > 0) + (g < RG - 1)));
+        mbar_init(&never, 1u);
         nabort = 0;
+        nstall = *(volatile const int *)(err + 1);
     }
     grid_dep_wait();
     if (tid == 0) {
@@ -511,11 +517,18 @@ tb2d_pair_kernel(const __grid_constant__ TbMaps maps, int in0, int in1, float *_
         if (s > 0 && has_nb) {
             // the neighbours have finished step s - 1
             uint64_t *b = &nbar[(s - 1) & 1][wg];
-            const unsigned par = (unsigned)(((s - 1) >> 1) & 1);
+            unsigned par = (unsigned)(((s - 1) >> 1) & 1);
+            if (s == 1 && wg == 0 && nstall) {
+                b = &never;
+                par = 0;
+            }
             if (!mbar_try_wait(b, par)) {
                 const unsigned long long t0 = global_ns();
+                unsigned long long lim =
+                    *reinterpret_cast<volatile const unsigned long long *>(err + 2);
+                if (lim == 0) lim = kDefaultWaitNs;
                 while (!*(volatile int *)&nabort && !mbar_try_wait(b, par)) {
-                    if (global_ns() - t0 > kWaitLimitNs) {
+                    if (global_ns() - t0 > lim) {
                         *(volatile int *)&nabort = 1;
                         atomicExch(err, 1);
                     }

@@ -27,13 +27,17 @@ DAMP_NODE, DAMP_CELL = 0, 1
 FGMRES, LEFT_GMRES = 0, 1
 STENCIL_Q1MIX, STENCIL_FD5, STENCIL_FAMILY = 0, 1, 2
 BC_DIRICHLET = 0
+TB_ANY, TB_COLUMN, TB_PAIR, TB_PAIR_SD = 0, 1, 2, 3
+S3_PAIR, S3_ZMARCH, S3_NODE_32x8, S3_NODE_64x4, S3_NODE_128x2 = 0, 1, 2, 3, 4
+LAUNCH_NO_OVERLAP, LAUNCH_NO_GRAPH = 1, 2
 
 #: every function include/htd.h declares (checked by the ABI test)
 EXPORTS = ("htd_default_options", "htd_create", "htd_destroy", "htd_plan", "htd_get_params",
            "htd_apply_precond", "htd_apply_H", "htd_residual_norm", "htd_residual_norm_noalloc",
            "htd_gmres_solve", "htd_grad", "htd_grad_td",
            "htd_gmres_solve_host", "htd_batch_create", "htd_batch_destroy",
-           "htd_batch_apply_precond", "htd_batch_gmres_solve", "htd_status_string")
+           "htd_batch_apply_precond", "htd_batch_gmres_solve", "htd_set_wait_limit",
+           "htd_test_fail_alloc", "htd_status_string")
 
 
 class HtdError(RuntimeError):
@@ -52,7 +56,11 @@ class Options(ctypes.Structure):
                 ("stencil", ctypes.c_int), ("restart", ctypes.c_int), ("max_rhs", ctypes.c_int),
                 ("proj_periods", ctypes.c_int), ("integrator", ctypes.c_int),
                 ("damping", ctypes.c_int), ("stencil_a", ctypes.c_double),
-                ("stencil_gamma", ctypes.c_double), ("tblock", ctypes.c_int)]
+                ("stencil_gamma", ctypes.c_double), ("tblock", ctypes.c_int),
+                ("tb_rows", ctypes.c_int), ("tb_form", ctypes.c_int),
+                ("s3_kernel", ctypes.c_int), ("s3_stages", ctypes.c_int),
+                ("s3_zchunk", ctypes.c_int), ("launch", ctypes.c_int),
+                ("wait_limit_ns", ctypes.c_longlong)]
 
 
 class Params(ctypes.Structure):
@@ -124,10 +132,13 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.htd_batch_destroy.argtypes = [vp]
     lib.htd_batch_apply_precond.argtypes = [vp, vp, vp, vp]
     lib.htd_batch_gmres_solve.argtypes = [vp, vp, vp, d, i, vp, vp]
+    lib.htd_set_wait_limit.argtypes = [vp, ctypes.c_longlong, i]
+    lib.htd_test_fail_alloc.argtypes = [ctypes.c_longlong]
+    lib.htd_test_fail_alloc.restype = None
     lib.htd_status_string.argtypes = [i]
     lib.htd_status_string.restype = ctypes.c_char_p
     for f in EXPORTS:
-        if f not in ("htd_default_options", "htd_status_string"):
+        if f not in ("htd_default_options", "htd_status_string", "htd_test_fail_alloc"):
             getattr(lib, f).restype = i
     _lib = lib
     return lib
@@ -362,22 +373,46 @@ def htd_grad_td(handle: int, F, rec_idx: np.ndarray, d, grad_m=None, grad_R=None
     return J.value
 
 
+def htd_set_wait_limit(handle: int, limit_ns: int, stall_test: bool = False) -> None:
+    """Bound of the blocked 2-D kernel's neighbour waits (0 = 1 s); with
+    stall_test the first such wait of every CTA runs out (test hook)."""
+    _check(load().htd_set_wait_limit(handle, int(limit_ns), int(bool(stall_test))),
+           "htd_set_wait_limit")
+
+
+def htd_test_fail_alloc(after: int) -> None:
+    """Test hook: the library's allocation number `after` (counted from now)
+    fails as if the device were out of memory; negative switches it off."""
+    load().htd_test_fail_alloc(int(after))
+
+
 def htd_status_string(status: int) -> str:
     return load().htd_status_string(int(status)).decode()
 
 
 # ---- convenience object ------------------------------------------------------
 
+KERNEL_FIELDS = ("tb_rows", "tb_form", "s3_kernel", "s3_stages", "s3_zchunk", "launch",
+                 "wait_limit_ns")
+
+
 def make_options(prob=None, precision: str = "fp64", mode: str = "table1",
                  krylov: str = "fgmres", stencil: str = "q1mix", restart: int = 20,
                  nP: int = 0, T: int | None = None, rho: float | None = None,
                  max_rhs: int = 1, proj_periods: int = 1, integrator: str = "acd",
                  damping: str = "node", stencil_a: float | None = None,
-                 stencil_gamma: float | None = None, tblock: int = 0) -> Options:
+                 stencil_gamma: float | None = None, tblock: int = 0,
+                 **kernel) -> Options:
     """htd_options from names; T and rho default to the problem's.  stencil
     "family" takes stencil_a (consistent-mass weight) and stencil_gamma (Q1
-    stiffness weight)."""
+    stiffness weight).  Keyword arguments named like the kernel-selection
+    fields (tb_rows, tb_form, s3_kernel, s3_stages, s3_zchunk, launch,
+    wait_limit_ns) set those fields."""
     o = htd_default_options()
+    for k, v in kernel.items():
+        if k not in KERNEL_FIELDS:
+            raise TypeError(f"unknown option {k!r}")
+        setattr(o, k, int(v))
     if stencil_a is not None:
         o.stencil_a = float(stencil_a)
     if stencil_gamma is not None:
@@ -414,9 +449,10 @@ class Solver:
                  nP: int = 0, T: int | None = None, rho: float | None = None,
                  max_rhs: int = 1, proj_periods: int = 1, integrator: str = "acd",
                  damping: str = "node", stencil_a: float | None = None,
-                 stencil_gamma: float | None = None, tblock: int = 0):
+                 stencil_gamma: float | None = None, tblock: int = 0, **kernel):
         o = make_options(prob, precision, mode, krylov, stencil, restart, nP, T, rho, max_rhs,
-                         proj_periods, integrator, damping, stencil_a, stencil_gamma, tblock)
+                         proj_periods, integrator, damping, stencil_a, stencil_gamma, tblock,
+                         **kernel)
         self.max_rhs = int(max_rhs)
         self.prob = prob
         self.n = tuple(prob.n)

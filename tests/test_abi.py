@@ -45,6 +45,8 @@ def test_struct_layouts_match_header(tmp_path):
         " offsetof(htd_solve_info, hist), offsetof(htd_params, nP), offsetof(htd_options, damping),"
         " offsetof(htd_options, stencil_a), offsetof(htd_options, stencil_gamma),"
         " offsetof(htd_options, tblock));"
+        "printf(\"%zu %zu %zu\\n\", offsetof(htd_options, s3_kernel),"
+        " offsetof(htd_options, launch), offsetof(htd_options, wait_limit_ns));"
         "return 0;}\n")
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
@@ -54,8 +56,34 @@ def test_struct_layouts_match_header(tmp_path):
     want = [ctypes.sizeof(htd.Grid), ctypes.sizeof(htd.Options), ctypes.sizeof(htd.Params),
             ctypes.sizeof(htd.SolveInfo), htd.SolveInfo.hist.offset, htd.Params.nP.offset,
             htd.Options.damping.offset, htd.Options.stencil_a.offset,
-            htd.Options.stencil_gamma.offset, htd.Options.tblock.offset]
+            htd.Options.stencil_gamma.offset, htd.Options.tblock.offset,
+            htd.Options.s3_kernel.offset, htd.Options.launch.offset,
+            htd.Options.wait_limit_ns.offset]
     assert got == want
+
+
+@pytest.mark.parametrize("field,value", [("tb_rows", 7), ("tb_rows", -1), ("tb_form", 4),
+                                         ("tb_form", -1), ("s3_kernel", 5), ("s3_kernel", -1),
+                                         ("s3_stages", 3), ("s3_stages", 8), ("s3_zchunk", -1),
+                                         ("launch", 4), ("wait_limit_ns", -1)])
+def test_plan_rejects_bad_kernel_selection(field, value):
+    """The kernel-selection fields of htd_options are validated on the host,
+    like every other option (HTD_ERR_ARG)."""
+    p = W.config_2d_constant(21)
+    htd.plan(p)                                       # the defaults are accepted
+    with pytest.raises(htd.HtdError) as e:
+        htd.plan(p, **{field: value})
+    assert e.value.status == 1
+
+
+def test_plan_accepts_every_documented_kernel_selection():
+    p = W.config_2d_constant(21)
+    for kw in (dict(tb_rows=8, tb_form=htd.TB_PAIR_SD), dict(tb_form=htd.TB_COLUMN),
+               dict(s3_kernel=htd.S3_NODE_128x2, s3_stages=7, s3_zchunk=16),
+               dict(s3_kernel=htd.S3_ZMARCH),
+               dict(launch=htd.LAUNCH_NO_OVERLAP | htd.LAUNCH_NO_GRAPH),
+               dict(wait_limit_ns=1000)):
+        assert htd.plan(p, **kw)["nP"] > 0
 
 
 def test_default_options():
@@ -196,4 +224,11 @@ def test_plan_rejects_empty_and_oversized_grids():
     for n in ((0, 5), (5, 0), (1 << 25, 1)):
         with pytest.raises(htd.HtdError) as e:
             htd.htd_plan(2, n, 0.1, np.ones(1), np.ones(1), 5.0, 0, htd.make_options(T=2, rho=0.25))
+        assert e.value.status == 1
+    # each axis within 2^24 but the product beyond the 2^34-node limit: refused
+    # before the product is formed (2^72 would wrap an int64 to 0) and before
+    # the one-element arrays are read
+    for n in ((1 << 24, 1 << 24, 1 << 24), (1 << 24, 1 << 24, 1 << 16), (1 << 24, 1 << 11, 1)):
+        with pytest.raises(htd.HtdError) as e:
+            htd.htd_plan(3, n, 0.1, np.ones(1), np.ones(1), 5.0, 0, htd.make_options(T=2, rho=0.25))
         assert e.value.status == 1

@@ -128,17 +128,24 @@ def test_gmres_fp64_config1_converges_to_direct_solution():
 
 
 TB_CASES = [(37, 45), (1, 7), (3, 2), (130, 67), (101, 101), (64, 300)]
-TB_CONFIGS = [("4", "12", "0", "0"), ("4", "10", "0", "0"), ("8", "6", "0", "0"),
-              ("8", "20", "0", "0"), ("4", "10", "1", "0"), ("4", "12", "1", "0"),
-              ("8", "6", "1", "0"), ("8", "12", "1", "0"), ("4", "8", "1", "1"),
-              ("8", "8", "1", "1"), ("8", "10", "1", "1"), (None, None, None, None)]
+TB_CONFIGS = [(4, 12, 0, 0), (4, 10, 0, 0), (8, 6, 0, 0), (8, 20, 0, 0), (4, 10, 1, 0),
+              (4, 12, 1, 0), (8, 6, 1, 0), (8, 12, 1, 0), (4, 8, 1, 1), (8, 8, 1, 1),
+              (8, 10, 1, 1), (None, None, None, None)]
+
+
+def tb_options(B, rpt, pair, sd):
+    """Options forcing one blocked 2-D configuration (depth, rows per thread, form)."""
+    if B is None:
+        return {}
+    form = htd.TB_COLUMN if not pair else (htd.TB_PAIR_SD if sd else htd.TB_PAIR)
+    return dict(tblock=B, tb_rows=rpt, tb_form=form)
 
 
 @pytest.mark.parametrize("n", TB_CASES, ids=[f"{a}x{b}" for a, b in TB_CASES])
 @pytest.mark.parametrize("B,rpt,pair,sd", TB_CONFIGS,
                          ids=[f"B{b}_r{r}_p{q}_d{d}" for b, r, q, d in TB_CONFIGS])
 @pytest.mark.parametrize("mode", ["table1", "exact"])
-def test_temporal_blocking_matches_one_step(n, B, rpt, pair, sd, mode, monkeypatch):
+def test_temporal_blocking_matches_one_step(n, B, rpt, pair, sd, mode):
     """The 2-D FP32 recurrence with B steps per launch (shared-memory tiles with a
     halo of B, rows per thread rpt, one column per thread or node pairs in
     paired FP32 instructions, d in registers or staged in shared memory)
@@ -147,20 +154,14 @@ def test_temporal_blocking_matches_one_step(n, B, rpt, pair, sd, mode, monkeypat
     Step counts that are not multiples of B and snapshots inside a launch
     included."""
     p = het_problem(2, n, T=3) if min(n) > 1 else het_problem(2, n, T=2)
-    monkeypatch.setenv("HTD_TB", "0")
-    s0 = htd.Solver(p, precision="mixed", mode=mode)
+    s0 = htd.Solver(p, precision="mixed", mode=mode, tblock=1)
     assert s0.params["steps_per_launch"] == 1
-    monkeypatch.delenv("HTD_TB")
+    s1 = htd.Solver(p, precision="mixed", mode=mode, **tb_options(B, rpt, pair, sd))
     if B is not None:
-        monkeypatch.setenv("HTD_TB", B)
-        monkeypatch.setenv("HTD_TB_RPT", rpt)
-        monkeypatch.setenv("HTD_TB_PAIR", pair)
-        monkeypatch.setenv("HTD_TB_SD", sd)
-    s1 = htd.Solver(p, precision="mixed", mode=mode)
-    if B is not None:
-        assert s1.params["steps_per_launch"] == int(B)
-        groups = (20, 16, 8) if pair == "1" else ((16,) if int(rpt) in (6, 10) else (8,))
-        assert s1.params["tile"][1] in [g * int(rpt) - 2 * int(B) for g in groups]
+        assert s1.params["steps_per_launch"] == B
+        assert s1.params["tile"][2] == (2 if pair else 1)
+        groups = (20, 16, 8) if pair else ((16,) if rpt in (6, 10) else (8,))
+        assert s1.params["tile"][1] in [g * rpt - 2 * B for g in groups]
     o = oracle.Oracle(p)
     for F in (p.F, W.random_rhs(6, p.n)):
         a = host(s0.precond(dev(F))).reshape(-1)
@@ -172,10 +173,23 @@ def test_temporal_blocking_matches_one_step(n, B, rpt, pair, sd, mode, monkeypat
 S3_CASES = [(13, 17, 19), (40, 9, 70), (1, 3, 1), (2, 2, 2), (64, 16, 33), (5, 33, 65)]
 
 
+S3_KERNELS = {"0": htd.S3_NODE_32x8, "1": htd.S3_NODE_64x4, "2": htd.S3_NODE_128x2,
+              "3": htd.S3_PAIR}
+
+
+def s3_options(tile):
+    """Options forcing a streamed 3-D kernel ("0".."2" one node per thread on
+    32 x 8, 64 x 4, 128 x 2 tiles; "3" node pairs), ":k" = k ring stages."""
+    o = dict(s3_kernel=S3_KERNELS[tile.split(":")[0]])
+    if ":" in tile:
+        o["s3_stages"] = int(tile.split(":")[1])
+    return o
+
+
 @pytest.mark.parametrize("n", S3_CASES, ids=["x".join(map(str, c)) for c in S3_CASES])
 @pytest.mark.parametrize("mode", ["table1", "exact"])
 @pytest.mark.parametrize("tile", ["0", "1", "2", "3", "3:4", "3:6", "3:7"])
-def test_streamed_3d_step_matches_register_kernel(n, mode, tile, monkeypatch):
+def test_streamed_3d_step_matches_register_kernel(n, mode, tile):
     """The TMA-streamed 3-D FP32 step (one node per thread on 32 x 8, 64 x 4 or
     128 x 2 column tiles, or node pairs in paired FP32 instructions on 64 x 8
     tiles; z chunks, a ring of shared-memory stages fed by a producer warp)
@@ -184,14 +198,9 @@ def test_streamed_3d_step_matches_register_kernel(n, mode, tile, monkeypatch):
     chunk at these sizes); "3:4", "3:6" and "3:7" run the pair kernel with 4, 6
     or 7 ring stages instead of the default 5."""
     p = het_problem(3, n, T=2)
-    monkeypatch.setenv("HTD_S3", "0")
-    s0 = htd.Solver(p, precision="mixed", mode=mode)
+    s0 = htd.Solver(p, precision="mixed", mode=mode, s3_kernel=htd.S3_ZMARCH)
     assert s0.params["step_kernel"] == 0
-    monkeypatch.delenv("HTD_S3")
-    monkeypatch.setenv("HTD_S3_TILE", tile.split(":")[0])
-    if ":" in tile:                                     # shared-memory stages of the pair kernel
-        monkeypatch.setenv("HTD_S3_STAGES", tile.split(":")[1])
-    s1 = htd.Solver(p, precision="mixed", mode=mode)
+    s1 = htd.Solver(p, precision="mixed", mode=mode, **s3_options(tile))
     assert s1.params["step_kernel"] == 2
     o = oracle.Oracle(p)
     for F in (p.F, W.random_rhs(7, p.n)):
@@ -201,20 +210,17 @@ def test_streamed_3d_step_matches_register_kernel(n, mode, tile, monkeypatch):
         assert rel_l2(b, o.precond(F, mode).reshape(-1)) <= 2e-5
 
 
-@pytest.mark.parametrize("zchunk", ["1", "5", "7"])
+@pytest.mark.parametrize("zchunk", [1, 5, 7])
 @pytest.mark.parametrize("tile", ["0", "3"])
-def test_streamed_3d_forced_z_chunks(zchunk, tile, monkeypatch):
+def test_streamed_3d_forced_z_chunks(zchunk, tile):
     """Short and ragged z chunks (19 planes as 19 x 1, 5+5+5+4, 7+7+5): every
     chunk boundary re-reads its two halo planes, and the result is the same as
     one-chunk streaming and the register z-march kernel, to rounding."""
     p = het_problem(3, (37, 21, 19), T=2)
-    monkeypatch.setenv("HTD_S3", "0")
-    s0 = htd.Solver(p, precision="mixed")
-    monkeypatch.delenv("HTD_S3")
-    monkeypatch.setenv("HTD_S3_TILE", tile)
-    monkeypatch.setenv("HTD_S3_ZCHUNK", zchunk)
-    s1 = htd.Solver(p, precision="mixed")
+    s0 = htd.Solver(p, precision="mixed", s3_kernel=htd.S3_ZMARCH)
+    s1 = htd.Solver(p, precision="mixed", s3_zchunk=zchunk, **s3_options(tile))
     assert s1.params["step_kernel"] == 2
+    assert s1.params["tile"][2] == zchunk
     F = W.random_rhs(8, p.n)
     a = host(s0.precond(dev(F))).reshape(-1)
     b = host(s1.precond(dev(F))).reshape(-1)
@@ -318,42 +324,36 @@ def test_config_3d_256_full_size():
 
 @pytest.mark.parametrize("ndim,n", [(2, (130, 67)), (2, (1001, 1001)), (3, (37, 70, 41))],
                          ids=["2d-130x67", "2d-1001", "3d-37x70x41"])
-def test_overlapped_launches_change_nothing(ndim, n, monkeypatch):
+def test_overlapped_launches_change_nothing(ndim, n):
     """Consecutive step launches overlap (programmatic dependent launch: the next
     launch reads the coefficients while the previous one drains, and waits for
     it before touching a state plane).  The outputs equal those of plain
     stream-ordered launches bit for bit, captured graph and direct launches."""
     p = het_problem(ndim, n, T=2)
-    monkeypatch.setenv("HTD_OVERLAP", "0")
-    s0 = htd.Solver(p, precision="mixed")
+    s0 = htd.Solver(p, precision="mixed", launch=htd.LAUNCH_NO_OVERLAP)
     F2 = W.random_rhs(5, p.n)
     ref = [host(s0.precond(dev(F))) for F in (p.F, F2)]
-    monkeypatch.delenv("HTD_OVERLAP")
     s1 = htd.Solver(p, precision="mixed")
     assert s1.params["step_kernel"] in (1, 2)           # blocked 2-D or streamed 3-D
     for r in range(3):
         for F, want in zip((p.F, F2), ref):
             assert np.array_equal(host(s1.precond(dev(F))), want)
-    monkeypatch.setenv("HTD_NO_GRAPH", "1")
-    s2 = htd.Solver(p, precision="mixed")
+    s2 = htd.Solver(p, precision="mixed", launch=htd.LAUNCH_NO_GRAPH)
     assert np.array_equal(host(s2.precond(dev(p.F))), ref[0])
     for s in (s0, s1, s2):
         s.close()
 
 
 @pytest.mark.parametrize("stages", ["5", "7"])
-def test_pair_streamed_kernel_matches_one_node_kernel_bitwise(stages, monkeypatch):
+def test_pair_streamed_kernel_matches_one_node_kernel_bitwise(stages):
     """The node-pair streamed 3-D kernel reads each stored plane once and pushes
     it into the sums of the three node planes it touches; the terms reach each
     sum in the order of the one-node streamed kernel, and paired instructions
     round each lane like scalar ones, so the outputs agree bit for bit (ragged
     x: the last pair half-used)."""
     p = het_problem(3, (29, 45, 37), T=2)
-    monkeypatch.setenv("HTD_S3_TILE", "0")
-    s0 = htd.Solver(p, precision="mixed")
-    monkeypatch.setenv("HTD_S3_TILE", "3")
-    monkeypatch.setenv("HTD_S3_STAGES", stages)
-    s1 = htd.Solver(p, precision="mixed")
+    s0 = htd.Solver(p, precision="mixed", s3_kernel=htd.S3_NODE_32x8)
+    s1 = htd.Solver(p, precision="mixed", **s3_options("3:" + stages))
     assert s0.params["step_kernel"] == s1.params["step_kernel"] == 2
     assert s1.params["tile"][:2] == [64, 8] and s0.params["tile"][:2] != [64, 8]
     for F in (p.F, W.random_rhs(9, p.n)):

@@ -34,12 +34,12 @@ CASES = [  # (ndim, n, T, periods, precision)
 
 @pytest.mark.parametrize("case", CASES, ids=[f"{c[0]}d-{'x'.join(map(str, c[1]))}-T{c[2]}-p{c[3]}-{c[4]}"
                                              for c in CASES])
-def test_projection_matches_oracle(case, monkeypatch):
+def test_projection_matches_oracle(case):
     ndim, n, T, periods, precision = case
     p = het_problem(ndim, n, T=T)
-    if precision == "mixed" and ndim == 2:
-        monkeypatch.setenv("HTD_TB", "4")            # the blocked kernel carries the bulk
-    s = htd.Solver(p, precision=precision, mode="project", proj_periods=periods)
+    # 2-D mixed: the blocked kernel (depth 4) carries the bulk
+    kw = dict(tblock=4) if precision == "mixed" and ndim == 2 else {}
+    s = htd.Solver(p, precision=precision, mode="project", proj_periods=periods, **kw)
     if precision == "mixed" and ndim == 2:
         assert s.params["step_kernel"] == 1
     if precision == "mixed" and ndim == 3:

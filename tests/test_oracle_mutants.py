@@ -50,6 +50,7 @@ MUTANTS = [
      "cplx e = cexp(-I * q->omega * t);"),
     ("family stiffness mix", "S[s] = gamma * sq1[s] + (1.0 - gamma) * sfd[s];",
      "S[s] = gamma * sq1[s] + (1.0 - gamma) * sq1[s];"),
+    ("window kinked at its ends", "    return v * v;\n}", "    return v;\n}"),
 ]
 
 BATTERY = [
@@ -78,6 +79,7 @@ BATTERY = [
     lambda: pins.test_sine_modes_diagonalise_family_operator(2, 0.3, 0.6),
     lambda: grad.test_gradient_matches_central_differences(2, (11, 9)),
     lambda: grad.test_recurrence_gradient_matches_central_differences(2, (11, 9), "table1"),
+    lambda: pins.test_theorem5_rate_of_ST_on_sine_modes((8, 1)),
 ]
 
 
@@ -110,3 +112,14 @@ def test_unmodified_oracle_passes_the_battery(tmp_path):
 def test_planted_mistake_fails_a_pin(tmp_path, name, old, new):
     lib = build_variant(tmp_path, name, old, new)
     assert failing_pins(lib), f"no pin catches: {name}"
+
+
+def test_rate_pin_alone_catches_a_kinked_window(tmp_path):
+    """The Theorem 5 rate pin by itself catches a window that keeps the limit
+    S_T -> H^-1 but is only continuous (sin instead of sin^2 on the taper: a
+    kink where the taper meets 0 and 1), whose error decays like T^-1."""
+    name, old, new = next(m for m in MUTANTS if m[0] == "window kinked at its ends")
+    lib = build_variant(tmp_path, name, old, new)
+    with oracle.use_library(lib):
+        with pytest.raises(AssertionError):
+            pins.test_theorem5_rate_of_ST_on_sine_modes((8, 1))

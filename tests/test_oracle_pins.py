@@ -505,6 +505,50 @@ def test_table1_real_part_is_exact_real_part_and_linearity():
     assert np.abs(Ut_i - 1j * Ut).max() > 1e-6 * scale
 
 
+RATE_T = (12, 16, 20, 24, 32, 40, 48, 64, 80, 96, 128)
+
+
+def st_error_envelope_slope(stencil_mode, Ts=RATE_T):
+    """Least-squares slope of log(envelope of |s_T(lambda) lambda - 1|) against
+    log T, with s_T(lambda) read off the oracle's S_T applied to a sine mode of
+    a constant-k grid without damping (an eigenvector of Re H), and the last
+    error.  The envelope max_{T' >= T} err(T') removes the oscillation that the
+    aliasing and pole terms of the convolution formula put on the error."""
+    n, m = stencil_mode
+    p = make_problem(2, n, c=1.0, R="zero", T=4, rho=0.25, ppw=6)
+    kappa = (p.h * p.omega) ** 2
+    lam = sine_eigenvalue("q1mix", n, m, p.h, kappa)
+    v = _sine_mode(n, m)
+    errs = []
+    for T in Ts:
+        U = oracle.Oracle(p, T=int(T)).precond(v, "exact")
+        s = (U * v).sum() / (v * v).sum()
+        errs.append(abs(s * lam - 1.0))
+    env = [max(errs[i:]) for i in range(len(errs))]
+    return np.polyfit(np.log(Ts), np.log(env), 1)[0], errs[-1], lam
+
+
+@pytest.mark.parametrize("m", [(2, 1), (8, 1), (18, 1), (24, 1)],
+                         ids=["caseI-near-minus-omega2", "caseI", "caseII", "caseII-large"])
+def test_theorem5_rate_of_ST_on_sine_modes(m):
+    """Theorem 5 (speed of convergence, Im H = 0): S_T acts on an eigenvector of
+    Re H as the scalar s_T(lambda), and |s_T(lambda) - 1/lambda| decays like a
+    power of T fixed by the smoothness of the window chi.  The sin^2 window of
+    Sec. 2.3 is piecewise smooth with jumps in its second derivative, so chi-hat
+    decays like |sigma|^-3 (N_1 = 3 in the theorem's decay assumption, by the
+    rule that jumps in the k-th derivative give N_1 = k + 1); chi = 1 near 0
+    makes every moment of chi-hat vanish, and the integrability half of the
+    moment condition then allows N_2 = 1, so the theorem guarantees at least
+    T^-1 in both of its cases (lambda < 0 and lambda > 0, away from 0).  The
+    |sigma|^-3 tails of chi-hat give an error envelope of order T^-2; a window
+    that is only continuous (a kink at its ends, N_1 = 2) gives T^-1 (planted in
+    test_oracle_mutants.py).  Modes in case I (lambda in [-omega^2, gamma],
+    gamma < 0) and in case II (lambda > 0)."""
+    slope, last, lam = st_error_envelope_slope(((31, 31), m))
+    assert slope <= -1.8, (lam, slope)
+    assert last <= 3e-3, (lam, last)
+
+
 def test_theorem4_ST_converges_to_Hinv():
     p = make_problem(2, (25, 25), c=1.0, R="layer", layer=5, ppw=8)
     o0 = oracle.Oracle(p)

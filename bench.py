@@ -28,7 +28,9 @@ Printed (one JSON line on rank 0):
   fp64_roofline the FP64 step kernel of the plain form against the FP64 pipe;
   secondary_2d the 2-D 1001^2 heterogeneous solve (L2-resident; its blocked
               step kernel is reported against the FP32 pipe, `bound` "alu");
-  batched     the 96-system batched workload solved in lockstep;
+  batched     the 96-system batched workload solved in lockstep, and the same
+              systems solved one at a time;
+  adjoint     the two gradients of the 512^2, 8-source adjoint configuration;
   cpu_baseline the FP64 CPU oracle on a bounded sample of the same workload,
               on one core and on all host cores (independent copies);
   clocks, gpu_launches  SM clocks sampled during the timed region; kernels
@@ -132,6 +134,8 @@ def parse_args(argv=None):
     ap.add_argument("--restart", type=int, default=20)
     ap.add_argument("--batched", type=int, default=1,
                     help="also time the batched workload (96 systems, lockstep FGMRES)")
+    ap.add_argument("--adjoint", type=int, default=1,
+                    help="also time the gradients of the adjoint configuration (512^2, 8 sources)")
     ap.add_argument("--secondary-2d", type=int, default=1,
                     help="also time the 2-D 1001^2 solve (L2-resident, ALU roofline)")
     ap.add_argument("--option", action="append", default=[], metavar="KEY=VALUE",
@@ -460,8 +464,33 @@ def secondary_batched(htd, stream, flush, sub_rhs=4, sub_inst=4):
             sv.close()
         return min(times), ups, infos
 
+    def sequential(probs, Fs):
+        """The same systems solved one at a time (one handle per instance, one
+        right-hand side per solve), device time summed."""
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        total, ups = 0.0, 0
+        for p, F in zip(probs, Fs):
+            sv = htd.Solver(p, precision="mixed", restart=20)
+            for r in range(F.shape[0]):
+                Fd = dev(F[r])
+                U = torch.zeros_like(Fd)
+                if r == 0:                                   # graph capture, untimed
+                    htd.htd_gmres_solve(sv.handle, Fd, U, TOL, 400, stream)
+                    U.zero_()
+                flush.fill_(7)
+                e0.record(stream)
+                info = htd.htd_gmres_solve(sv.handle, Fd, U, TOL, 400, stream)
+                e1.record(stream)
+                e1.synchronize()
+                total += e0.elapsed_time(e1)
+                ups += p.N * info["steps"]
+            sv.close()
+        return total, ups
+
     ms, ups, infos = run("mixed", setup.probs, setup.F, 1)
     its = [i["iterations"] for i in infos]
+    seq_ms, seq_ups = sequential(setup.probs, setup.F)
     sub_p = setup.probs[:1 + sub_inst]
     sub_F = [setup.F[0][:sub_rhs]] + setup.F[1:1 + sub_inst]
     ms_m, _, _ = run("mixed", sub_p, sub_F, 1)
@@ -473,9 +502,47 @@ def secondary_batched(htd, stream, flush, sub_rhs=4, sub_inst=4):
             "iterations_min": min(its), "iterations_max": max(its),
             "rel_res_true_max": max(i["rel_res_true"] for i in infos),
             "graph": "one launch per preconditioner round (65 child graphs)",
+            "sequential": {"time_ms": seq_ms, "value": seq_ups / (seq_ms * 1e-3) / 1e9,
+                           "what": "the same 96 systems solved one at a time, device time "
+                                   "summed (first solve of each handle untimed)"},
+            "speedup_vs_sequential": seq_ms / ms,
             "fp64_sub_batch": {"systems": sub_rhs + sub_inst, "mixed_ms": ms_m, "fp64_ms": ms_f,
                                "speedup_vs_fp64": ms_f / ms_m,
                                "fp64_rel_res_true_max": max(i["rel_res_true"] for i in inf_f)}}
+
+
+def secondary_adjoint(htd, stream):
+    """The adjoint configuration (2-D 512^2, smooth random c, 8 seeded sources,
+    receivers in the top absorbing layer): the receiver-misfit gradient by
+    adjoint FGMRES solves (htd_grad, tol 1e-6) and the gradient of the
+    preconditioner's own misfit through the recurrence by the checkpointed
+    reverse-time adjoint (htd_grad_td), mixed precision, CUDA events."""
+    import torch
+    from paper_2006_16861_gb300 import workloads as W
+    st = W.config_adjoint(512)
+    p = st.prob
+    F = torch.from_numpy(np.ascontiguousarray(st.F)).cuda()
+    rec = torch.from_numpy(st.rec_idx).cuda()
+    pt = W.Problem(p.name, 2, p.n, p.h, st.c_true, p.R_node, p.omega, p.F, p.T, p.rho)
+    strue = htd.Solver(pt, precision="mixed")
+    d = torch.stack([strue.solve(F[k].contiguous(), tol=1e-8, max_iters=600)[0].reshape(-1)[rec]
+                     for k in range(F.shape[0])]).contiguous()
+    strue.close()
+    s = htd.Solver(p, precision="mixed")
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    out = {"workload": "adjoint: 2-D 512^2, 8 sources, receivers in the top layer",
+           "steps_per_apply": s.params["steps"]}
+    for name, call in (("grad_adjoint_solves", lambda: s.grad(F, st.rec_idx, d, tol=1e-6)),
+                       ("grad_through_recurrence", lambda: s.grad_td(F, st.rec_idx, d))):
+        call()                                              # warm-up (workspace, graphs)
+        e0.record(stream)
+        call()
+        e1.record(stream)
+        e1.synchronize()
+        out[name + "_ms"] = e0.elapsed_time(e1)
+    s.close()
+    return out
 
 
 # ---- the reference arm: the oracle ------------------------------------------------
@@ -695,6 +762,9 @@ def run_ours(args):
     batched = None
     if args.batched:
         batched = secondary_batched(htd, stream, flush)
+    adjoint = None
+    if args.adjoint:
+        adjoint = secondary_adjoint(htd, stream)
 
     cpu = None
     if rank == 0 and world == 1 and args.cpu_sample_s > 0:
@@ -726,6 +796,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "secondary_2d": sec2d,
             "batched": batched,
+            "adjoint": adjoint,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk,

@@ -1205,14 +1205,18 @@ htd_status create_impl(const htd_grid *grid, const double *c_cell, const double 
             // assembly with S = 0 and -M (coefficient 0 - (-M_s) * sum)
             double Z[4] = {0.0, 0.0, 0.0, 0.0}, Mn[4];
             for (int k = 0; k < 4; ++k) Mn[k] = -c->M[k];
+            // coefI first: the handle owns it, so a failure below leaks nothing
+            HTD_CUDA(htd::dev_malloc((void **)&c->coefI, sizeof(double) * htd::h_planes(d) * (size_t)N));
             double *rcell = nullptr;
             HTD_CUDA(htd::dev_malloc((void **)&rcell, sizeof(double) * c->L64.total));
-            HTD_CUDA(cudaMemcpy(rcell, rc64.data(), sizeof(double) * c->L64.total,
-                                cudaMemcpyHostToDevice));
-            HTD_CUDA(htd::dev_malloc((void **)&c->coefI, sizeof(double) * htd::h_planes(d) * (size_t)N));
-            htd::launch_assemble_H(c->L64, rcell, Z, Mn, c->coefI, 0);
-            HTD_CUDA(cudaDeviceSynchronize());
+            cudaError_t e = cudaMemcpy(rcell, rc64.data(), sizeof(double) * c->L64.total,
+                                       cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) {
+                htd::launch_assemble_H(c->L64, rcell, Z, Mn, c->coefI, 0);
+                e = cudaDeviceSynchronize();
+            }
             cudaFree(rcell);
+            HTD_CUDA(e);
         }
     }
     HTD_CUDA(cudaMemcpy(c->imH, imh.data(), sizeof(double) * N, cudaMemcpyHostToDevice));

@@ -14,7 +14,10 @@
 // y0-1 .. y0+8) and exact 64 x 8 boxes of d, Re F, Im F, u_{j-1}.  In the halo
 // boxes node column x sits at box column x - x0 + 1 + off with off = 3 (the
 // padded layout puts column x0 - 1 at 3 mod 4), so (x, x+1) for even x - x0
-// is an aligned 64-bit pair and x - 1, x + 2 are single loads.
+// is an aligned 64-bit pair and x - 1, x + 2 are single loads.  The two halo
+// planes of a z chunk (below and above its node planes) load only u_j, plus
+// q*kappa for the lower one: their node boxes would never be read, and as the
+// neighbouring chunk runs in another wave they would come from DRAM.
 //
 // Per node the arithmetic is the one-node kernel's, in the same order, with
 // each scalar operation replaced by the same operation on a pair; paired
@@ -38,6 +41,10 @@ constexpr int kHaloStride = 768;                // padded to 3072 bytes (128-byt
 constexpr int kNodeElems = kTX * kTY;           // 512 floats
 constexpr int kStageElems = 2 * kHaloStride + 4 * kNodeElems;
 constexpr unsigned kStageTxBytes = (2 * kHaloElems + 4 * kNodeElems) * 4;
+// the two halo planes of a z chunk carry only what the stencil reads from them:
+// u_j and q*kappa on the lower one, u_j on the upper one
+constexpr unsigned kFirstTxBytes = 2 * kHaloElems * 4;
+constexpr unsigned kLastTxBytes = kHaloElems * 4;
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;
 
 __device__ __forceinline__ unsigned smem_u32(const void *p)
@@ -108,14 +115,19 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, i
 // Stored plane p of rhs r into one stage: u_j and q*kappa with the halo, d,
 // Re F, Im F, u_{j-1}.  The stage's byte count is announced first; the
 // coefficient part (q*kappa, d, forcing: no step writes them) and the state
-// part (u_j, u_{j-1}) may be issued separately.
+// part (u_j, u_{j-1}) may be issued separately.  `kind` 0: a node plane of the
+// chunk (everything); 1: the lower halo plane (u_j, q*kappa); 2: the upper
+// halo plane (u_j only).  The node boxes of a halo plane are never read.
 __device__ __forceinline__ void load_stage_coef(const Stream3Maps &maps, float *stage, uint64_t *bar,
-                                                int xs, int xn, int y0, int p, int r)
+                                                int xs, int xn, int y0, int p, int r, int kind)
 {
+    const unsigned bytes = kind == 0 ? kStageTxBytes : kind == 1 ? kFirstTxBytes : kLastTxBytes;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(kStageTxBytes)
+                 "r"(bytes)
                  : "memory");
+    if (kind == 2) return;
     tma_load_3d(stage + kHaloStride, &maps.m[2], xs, y0, p, bar);
+    if (kind == 1) return;
     tma_load_3d(stage + 2 * kHaloStride, &maps.m[3], xn, y0 + 1, p, bar);
     tma_load_4d(stage + 2 * kHaloStride + kNodeElems, &maps.m[4], xn, y0 + 1, p, r, bar);
     tma_load_4d(stage + 2 * kHaloStride + 2 * kNodeElems, &maps.m[5], xn, y0 + 1, p, r, bar);
@@ -123,10 +135,11 @@ __device__ __forceinline__ void load_stage_coef(const Stream3Maps &maps, float *
 
 __device__ __forceinline__ void load_stage_state(const Stream3Maps &maps, int iu, int ium,
                                                  float *stage, uint64_t *bar, int xs, int xn,
-                                                 int y0, int p, int r)
+                                                 int y0, int p, int r, int kind)
 {
     tma_load_4d(stage, &maps.m[iu], xs, y0, p, r, bar);
-    tma_load_4d(stage + 2 * kHaloStride + 3 * kNodeElems, &maps.m[ium], xn, y0 + 1, p, r, bar);
+    if (kind == 0)
+        tma_load_4d(stage + 2 * kHaloStride + 3 * kNodeElems, &maps.m[ium], xn, y0 + 1, p, r, bar);
 }
 
 // programmatic dependent launch (no-ops for an ordinary launch): code before
@@ -204,20 +217,22 @@ stream3d_pair_kernel(const __grid_constant__ Stream3Maps maps, int iu, int ium,
             // the first NS stages: coefficients before the wait for the previous
             // step, states after it
             const int npre = min(NS, nplanes);
+            auto kind_of = [&](int p) { return p == 0 ? 1 : (p == nplanes - 1 ? 2 : 0); };
             for (int p = 0; p < npre; ++p)
                 load_stage_coef(maps, ring + p * kStageElems, &full[p], xs, xn, (int)y0,
-                                (int)(zb + p), rhs);
+                                (int)(zb + p), rhs, kind_of(p));
             grid_dep_wait();
             for (int p = 0; p < npre; ++p)
                 load_stage_state(maps, iu, ium, ring + p * kStageElems, &full[p], xs, xn, (int)y0,
-                                 (int)(zb + p), rhs);
+                                 (int)(zb + p), rhs, kind_of(p));
             for (int p = NS; p < nplanes; ++p) {
                 const int st = p % NS;
                 if (!wait_bounded(&empty[st], (unsigned)(((p / NS) - 1) & 1), &abort_flag)) break;
                 float *stage = ring + st * kStageElems;
-                load_stage_coef(maps, stage, &full[st], xs, xn, (int)y0, (int)(zb + p), rhs);
+                load_stage_coef(maps, stage, &full[st], xs, xn, (int)y0, (int)(zb + p), rhs,
+                                kind_of(p));
                 load_stage_state(maps, iu, ium, stage, &full[st], xs, xn, (int)y0, (int)(zb + p),
-                                 rhs);
+                                 rhs, kind_of(p));
             }
             if (abort_flag) {
                 atomicExch(err, 1);

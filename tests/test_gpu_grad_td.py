@@ -120,3 +120,93 @@ def test_recurrence_gradient_rejects_bad_arguments():
     with pytest.raises(htd.HtdError) as e:
         s.grad_td(dev(F), bad, dev(d))
     assert e.value.status == 1
+
+
+def _config5_data(st, precision="fp64"):
+    """Receiver data of the adjoint configuration for the recurrence misfit: the
+    preconditioner's own output for the 'true' model (c with the 5 % blob),
+    sampled at the receivers (computed with the library; the comparisons below
+    use GPU misfits or the oracle on the same data)."""
+    p = st.prob
+    pt = W.Problem(p.name, 2, p.n, p.h, st.c_true, p.R_node, p.omega, p.F, p.T, p.rho)
+    s = htd.Solver(pt, precision=precision)
+    rec = torch.from_numpy(st.rec_idx).cuda()
+    d = torch.stack([s.precond(dev(st.F[k])).reshape(-1)[rec] for k in range(st.F.shape[0])])
+    s.close()
+    return d.contiguous()
+
+
+def test_recurrence_gradient_at_the_adjoint_configuration_size():
+    """The checkpointed reverse-time adjoint on the full adjoint configuration:
+    2-D 512^2, smooth random c, 8 seeded point sources, receivers on the first
+    row inside the top absorbing layer.  FP64: the gradient along localized
+    directions (which leave the recurrence parameters, chosen from min / max c,
+    unchanged) against central differences of the GPU misfit, relative error
+    < 1e-4; the mixed-precision gradient against the FP64 one within 2e-4."""
+    st = W.config_adjoint(512)
+    p = st.prob
+    F = dev(st.F)
+    d = _config5_data(st)
+    s = htd.Solver(p, precision="fp64")
+    prm0 = s.params
+    J, gm, gR = s.grad_td(F, st.rec_idx, d)
+    s.close()
+    gm, gR = gm.cpu().numpy(), gR.cpu().numpy()
+    assert J > 0 and np.isfinite(gm).all() and np.isfinite(gR).all()
+    sm = htd.Solver(p, precision="mixed")
+    Jm, gmm, gRm = sm.grad_td(F, st.rec_idx, d)
+    sm.close()
+    assert Jm == pytest.approx(J, rel=1e-4)
+    assert rel(gmm.cpu().numpy(), gm) <= 2e-4 and rel(gRm.cpu().numpy(), gR) <= 2e-4
+    mm = p.c_cell ** -2.0
+    n1 = p.n[0] + 1
+    xs = (np.arange(n1) - 0.5) * p.h
+    X, Y = np.meshgrid(xs, xs, indexing="ij")
+
+    def J_at(mv=None, Rv=None):
+        q = W.Problem(p.name, p.ndim, p.n, p.h, (mm if mv is None else mv) ** -0.5,
+                      p.R_node if Rv is None else Rv, p.omega, p.F, p.T, p.rho)
+        sq = htd.Solver(q, precision="fp64")
+        for k in ("nP", "dt", "omega_c"):
+            assert sq.params[k] == prm0[k], k
+        Jq = sq.grad_td(F, st.rec_idx, d, want_grad=False)[0]
+        sq.close()
+        return Jq
+
+    eps = 1e-3
+    for cen, wid in (((0.4, 0.6), 0.02), ((0.7, 0.3), 0.005)):
+        v = np.exp(-((X - cen[0]) ** 2 + (Y - cen[1]) ** 2) / wid) * mm
+        v[mm == mm.max()] = 0.0
+        v[mm == mm.min()] = 0.0
+        v *= 1e-3
+        fd = (J_at(mv=mm + eps * v) - J_at(mv=mm - eps * v)) / (2 * eps)
+        assert abs(np.sum(gm * v) - fd) <= 1e-4 * abs(fd), (np.sum(gm * v), fd)
+    w = 1e-3 * p.R_node * np.exp(-((X[:-1, :-1] - 0.02) ** 2 + (Y[:-1, :-1] - 0.5) ** 2) / 0.01)
+    fd = (J_at(Rv=p.R_node + eps * w) - J_at(Rv=p.R_node - eps * w)) / (2 * eps)
+    assert abs(np.sum(gR * w) - fd) <= 1e-4 * abs(fd), (np.sum(gR * w), fd)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_recurrence_gradient_on_a_block_of_the_adjoint_configuration(precision):
+    """Oracle parity on a 96 x 96 block cropped from the adjoint configuration's
+    model (its top-left corner: part of the top absorbing layer with the
+    receivers on its first row), three seeded sources inside the block, T by
+    the block's size in wavelengths."""
+    st = W.config_adjoint(512)
+    p = st.prob
+    b = 96
+    c = np.ascontiguousarray(p.c_cell[: b + 1, : b + 1])
+    R = np.ascontiguousarray(p.R_node[:b, :b])
+    T = W.periods_for(b, p.h, float(c.min()), p.omega)
+    F = W.seeded_sources(11, 2, (b, b), p.h, 3, 8)
+    q = W.Problem("adjoint_block", 2, (b, b), p.h, c, R, p.omega, F[0], T, p.rho)
+    rec = np.arange(1 * b, 2 * b, dtype=np.int64)          # the block's second row
+    d = 1e-2 * (W.white_noise(21, (3, rec.size)) + 1j * W.white_noise(22, (3, rec.size)))
+    s = htd.Solver(q, precision=precision)
+    J, gm, gR = s.grad_td(dev(F), rec, dev(d))
+    s.close()
+    Jo, gmo, gRo = oracle.Oracle(q).grad_td(F, rec, d, "table1")
+    fp64 = precision == "fp64"
+    assert J == pytest.approx(Jo, rel=1e-10 if fp64 else 1e-5)
+    assert rel(gm.cpu().numpy(), gmo) <= (1e-8 if fp64 else 2e-4)
+    assert rel(gR.cpu().numpy(), gRo) <= (1e-8 if fp64 else 2e-4)

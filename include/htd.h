@@ -175,6 +175,9 @@ typedef struct {
     double ms_precond;        /* device time inside preconditioner applications,
                                  CUDA events on the call's stream */
     long long launches;       /* kernels launched by the call (graph nodes counted) */
+    int reorth;               /* Arnoldi steps that needed the second Gram-Schmidt
+                                 pass (||w|| fell below 1/sqrt(2) of itself in the
+                                 first) */
     int hist_len;
     double hist[256];         /* Arnoldi estimate after each step (first 256) */
 } htd_solve_info;
@@ -310,8 +313,10 @@ htd_status htd_residual_norm_noalloc(htd_handle h, const void *F_dev, const void
 /*
  * Solve H U = F with restarted GMRES(m), m = opt.restart (Sec. 2.4): flexible
  * right preconditioning (default) or left preconditioning, preconditioner P of
- * the handle, Arnoldi by classical Gram-Schmidt with one reorthogonalisation
- * in FP64, Givens least squares on the host.
+ * the handle, Arnoldi by classical Gram-Schmidt in FP64 with a second
+ * (re-orthogonalisation) pass in the steps where the first pass removed more
+ * than half of the new vector's squared norm ("twice is enough"), Givens least
+ * squares on the host.
  *   F_dev      complex128[N] right-hand side (device).
  *   U_dev      complex128[N] (device): initial guess on entry, solution on exit.
  *   tol        stop when the Arnoldi estimate and the true relative residual

@@ -3,7 +3,8 @@
 // A batch is a list of instances (handles), instance i carrying nrhs[i]
 // right-hand sides.  Every (instance, rhs) pair is one system H_i U = F, solved
 // by the same FGMRES(m) as htd_gmres_solve (flexible right preconditioning,
-// classical Gram-Schmidt with one re-orthogonalisation in FP64, Givens
+// classical Gram-Schmidt in FP64 with a second pass where the first lost more
+// than half of the new vector's norm, Givens
 // rotations on the host, true-residual stopping test), but all systems advance
 // in lockstep so that the preconditioner applications of one Arnoldi step run
 // together:
@@ -320,7 +321,10 @@ htd_status batch_gmres(htd_batch b, const void *const *F_dev, void *const *U_dev
         }
         if ((st = precond_round(b, sel, in, out, s)) != HTD_OK) return st;
 
-        // ---- w = H Z_j built in basis slot j + 1, CGS2 against V_0..V_j -------
+        // ---- w = H Z_j built in basis slot j + 1, Gram-Schmidt against V_0..V_j:
+        // pass 1 for every running system, one fetch; pass 2 for the systems
+        // whose first pass lost more than half of ||w||^2 (the single-system
+        // driver's test, so both take the same decisions), one more fetch ----
         for (size_t k = 0; k < ns; ++k) {
             if (!sel[k]) continue;
             Sys &y = b->sys[k];
@@ -328,13 +332,27 @@ htd_status batch_gmres(htd_batch b, const void *const *F_dev, void *const *U_dev
             const int kc = y.j + 1;
             double2 *vn = y.V + (int64_t)kc * y.N;
             htd::ctx_apply_H(c, y.Z + (int64_t)y.j * y.N, nullptr, vn, s);
-            for (int pass = 0; pass < 2; ++pass) {
-                double2 *hb = b->hdev + k * kHBlock + 72 * pass;
-                htd::ctx_dots(c, y.V, y.N, kc + 1, vn, hb, s);     // V_i^H w and ||w||^2
-                htd::launch_sub_combination(y.V, y.N, kc, hb, vn, y.N, s);
-            }
+            double2 *hb = b->hdev + k * kHBlock;
+            htd::ctx_dots(c, y.V, y.N, kc + 1, vn, hb, s);         // V_i^H w and ||w||^2
+            htd::launch_sub_combination(y.V, y.N, kc, hb, vn, y.N, s);
         }
         if ((st = fetch_blocks(b, s)) != HTD_OK) return st;
+        std::vector<char> second(ns, 0);
+        std::vector<double> w1sq(ns, 0.0);
+        bool any_second = false;
+        for (size_t k = 0; k < ns; ++k) {
+            if (!sel[k]) continue;
+            Sys &y = b->sys[k];
+            second[k] = htd::cgs_needs_second_pass(b->hhost + k * kHBlock, y.j + 1, &w1sq[k]);
+            if (!second[k]) continue;
+            any_second = true;
+            const int kc = y.j + 1;
+            double2 *vn = y.V + (int64_t)kc * y.N;
+            double2 *hb = b->hdev + k * kHBlock + 72;
+            htd::ctx_dots(b->ctx[y.inst], y.V, y.N, kc + 1, vn, hb, s);
+            htd::launch_sub_combination(y.V, y.N, kc, hb, vn, y.N, s);
+        }
+        if (any_second && (st = fetch_blocks(b, s)) != HTD_OK) return st;
         const double ms = round_ms(b);
 
         // ---- Givens update on the host; finished cycles update U -------------
@@ -348,7 +366,13 @@ htd_status batch_gmres(htd_batch b, const void *const *F_dev, void *const *U_dev
             y.info.steps += b->ci[y.inst].nsteps * b->ci[y.inst].runs;
             y.info.ms_precond += ms;
             zc *col = &y.Hm[(size_t)j * (m + 1)];
-            const double hn2 = htd::cgs2_column(hh, hh + 72, j + 1, col);
+            double hn2 = w1sq[k];
+            if (second[k]) {
+                hn2 = htd::cgs2_column(hh, hh + 72, j + 1, col);
+                y.info.reorth++;
+            } else {
+                htd::cgs1_column(hh, j + 1, col);
+            }
             if (!std::isfinite(hn2)) return HTD_ERR_NONFINITE;
             const double hn = std::sqrt(hn2 > 0 ? hn2 : 0.0);
             col[j + 1] = hn;

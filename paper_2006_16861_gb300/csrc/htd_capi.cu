@@ -556,19 +556,30 @@ htd_status gmres(htd_ctx *c, const double2 *F, double2 *U, double tol, int maxit
                 apply_H(c, vj, nullptr, c->t, s);
                 if ((st = precond(c, c->t, vn, s)) != HTD_OK) goto out;
             }
-            // classical Gram-Schmidt with one reorthogonalisation, FP64: per pass
-            // V_i^H w for i <= j and ||w||^2 in one kernel, then w -= V h
+            // classical Gram-Schmidt, FP64: per pass V_i^H w for i <= j and
+            // ||w||^2 in one kernel, then w -= V h; a second pass only when the
+            // first lost more than half of ||w||^2 (cgs_needs_second_pass)
             const int k = j + 1;
-            for (int pass = 0; pass < 2; ++pass) {
-                dots_to(c, c->V, k + 1, vn, 72 * pass, s);
-                htd::launch_sub_combination(c->V, N, k, c->hdev + 72 * pass, vn, N, s);
-            }
-            HTD_CUDA(cudaMemcpyAsync(c->hhost, c->hdev, sizeof(double2) * (72 + k + 1),
+            dots_to(c, c->V, k + 1, vn, 0, s);
+            htd::launch_sub_combination(c->V, N, k, c->hdev, vn, N, s);
+            HTD_CUDA(cudaMemcpyAsync(c->hhost, c->hdev, sizeof(double2) * (k + 1),
                                      cudaMemcpyDeviceToHost, s));
             HTD_CUDA(cudaStreamSynchronize(s));
             HTD_CUDA(cudaGetLastError());
             zc *col = &Hm[(size_t)j * (m + 1)];
-            const double hn2 = htd::cgs2_column(c->hhost, c->hhost + 72, k, col);
+            double hn2 = 0.0;
+            if (htd::cgs_needs_second_pass(c->hhost, k, &hn2)) {
+                dots_to(c, c->V, k + 1, vn, 72, s);
+                htd::launch_sub_combination(c->V, N, k, c->hdev + 72, vn, N, s);
+                HTD_CUDA(cudaMemcpyAsync(c->hhost + 72, c->hdev + 72, sizeof(double2) * (k + 1),
+                                         cudaMemcpyDeviceToHost, s));
+                HTD_CUDA(cudaStreamSynchronize(s));
+                HTD_CUDA(cudaGetLastError());
+                hn2 = htd::cgs2_column(c->hhost, c->hhost + 72, k, col);
+                ++loc.reorth;
+            } else {
+                htd::cgs1_column(c->hhost, k, col);
+            }
             if (!std::isfinite(hn2)) { st = HTD_ERR_NONFINITE; goto out; }
             const double hn = std::sqrt(hn2 > 0 ? hn2 : 0.0);
             col[j + 1] = hn;

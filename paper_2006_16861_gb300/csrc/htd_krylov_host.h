@@ -67,4 +67,28 @@ inline double cgs2_column(const C2 *h0, const C2 *h1, int k, zcd *col)
     return h1[k].x - hh;
 }
 
+// Selective re-orthogonalisation ("twice is enough": Daniel, Gragg, Kaufman
+// and Stewart 1976; Giraud, Langou and Rozloznik 2005).  After pass 1 (h0,
+// k + 1 results) the new vector's squared norm is ||w_1||^2 = ||w||^2 - |h0|^2
+// (Pythagoras against the orthonormal V).  If ||w_1||^2 >= ||w||^2 / 2 the
+// projection lost at most one bit and one pass keeps w_1 orthogonal to V to
+// working precision: the column is h0 and ||w_1||^2 is returned through *w1sq
+// (no cancellation: the subtracted part is at most half).  Otherwise (or if a
+// value is not finite) a second pass is needed and cgs2_column completes it.
+template <typename C2>
+inline bool cgs_needs_second_pass(const C2 *h0, int k, double *w1sq)
+{
+    double hh = 0.0;
+    for (int i = 0; i < k; ++i) hh += h0[i].x * h0[i].x + h0[i].y * h0[i].y;
+    const double w2 = h0[k].x;
+    *w1sq = w2 - hh;
+    return !(*w1sq >= 0.5 * w2);
+}
+
+template <typename C2>
+inline void cgs1_column(const C2 *h0, int k, zcd *col)
+{
+    for (int i = 0; i < k; ++i) col[i] = zcd(h0[i].x, h0[i].y);
+}
+
 }  // namespace htd

@@ -86,7 +86,8 @@ class SolveInfo(ctypes.Structure):
                 ("steps", ctypes.c_longlong), ("rel_res_true", ctypes.c_double),
                 ("rel_res_est", ctypes.c_double), ("ms_total", ctypes.c_double),
                 ("ms_precond", ctypes.c_double), ("launches", ctypes.c_longlong),
-                ("hist_len", ctypes.c_int), ("hist", ctypes.c_double * 256)]
+                ("reorth", ctypes.c_int), ("hist_len", ctypes.c_int),
+                ("hist", ctypes.c_double * 256)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "hist"}

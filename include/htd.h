@@ -419,9 +419,15 @@ htd_status htd_batch_destroy(htd_batch b);
 /*
  * U_i[r] = P_i F_i[r] for every system: F_dev[i], U_dev[i] are complex128
  * [nrhs[i]][N_i] (device, distinct).  One application of every preconditioner
- * (both runs in mode EXACT) as one CUDA-graph launch per run: the captured
- * step sequences of all handles are child graphs of one graph, and each step
- * kernel covers all right-hand sides of its handle.  Asynchronous on stream.
+ * (both runs in mode EXACT) as one CUDA-graph launch per run.  When at least
+ * two handles are 2-D with FP32 recurrence (I_acd, Table 1 or exact read-out),
+ * they run as ONE persistent launch: a queue of tasks (level = 8 steps,
+ * handle, rhs slot, tile) of the blocked kernel's work, ordered by level, each
+ * tile starting a level once its 3 x 3 tile neighbourhood has finished the
+ * previous one; the other handles' captured step sequences are child graphs
+ * beside it, and each of their step kernels covers all right-hand sides of its
+ * handle.  Every output equals the handle's own htd_apply_precond bit for bit.
+ * Asynchronous on stream.
  */
 htd_status htd_batch_apply_precond(htd_batch b, const void *const *F_dev, void *const *U_dev,
                                    void *stream);
@@ -464,6 +470,19 @@ htd_status htd_set_wait_limit(htd_handle h, long long limit_ns, int stall_test);
  * after < 0 switches it off.  Process-wide, not thread-safe.
  */
 void htd_test_fail_alloc(long long after);
+
+/* How a batch runs its preconditioner applications (filled after the first
+ * application or solve; zeros before). */
+typedef struct {
+    int instances;           /* handles in the batch */
+    int systems;             /* (handle, right-hand side) pairs */
+    int grouped;             /* 2-D FP32 handles run by the one persistent launch
+                                (0: every handle runs its own step sequence) */
+    int group_ctas;          /* persistent CTAs of that launch */
+    long long group_tasks;   /* its tasks per run: levels x tiles x rhs slots */
+    int group_steps_per_task; /* recurrence steps per task (the blocked depth B) */
+} htd_batch_desc;
+htd_status htd_batch_describe(htd_batch b, htd_batch_desc *out);
 
 /* Static string for a status code. */
 const char *htd_status_string(htd_status s);

@@ -13,8 +13,13 @@
 //    (their slots in the handle's per-rhs arrays; the active list is read by the
 //    kernels from device memory, so converged systems drop out of a captured
 //    sequence without a new capture);
-//  - across handles, the captured step sequences (different sizes, kernels and
-//    step counts T n_P) are child graphs of one graph, launched once per run.
+//  - the 2-D FP32 handles (at least two, Table 1 or exact read-out) run as one
+//    persistent launch per run: a queue of (level, instance, rhs slot, tile)
+//    tasks of the blocked pair kernel's work, each tile starting a level when
+//    its 3 x 3 neighbourhood has finished the previous one (htd_tblock.cu);
+//  - the other handles' captured step sequences (different sizes, kernels and
+//    step counts T n_P) are child graphs of one graph beside it, launched once
+//    per run.
 //
 // The paper treats one system at a time (Sec. 5); the batch changes only the
 // schedule, not the arithmetic of any system.
@@ -81,9 +86,22 @@ struct htd_batch_s {
     cudaEvent_t tab_ev = nullptr;        // last copy of the table (guards tab_host)
     bool tab_pending = false;
     cudaEvent_t ev[2] = {nullptr, nullptr};
-    // one graph: every handle's step sequence as a child graph
+    // one graph: the group launch and every other handle's step sequence as
+    // child graphs
     cudaGraphExec_t exec = nullptr;
     bool graph_tried = false;
+    // the persistent launch over the 2-D handles
+    std::vector<char> in_group;          // per instance
+    std::vector<int> group;              // instance indices, most levels first
+    htd::TbPlan gplan{};
+    int gctas = 0;
+    htd::GroupSched gsched{};
+    htd::GroupInst *ginst = nullptr;
+    long long *glev = nullptr, *goff = nullptr;
+    int *gdone = nullptr, *gabort = nullptr;
+    size_t gdone_n = 0;
+    unsigned long long *ghead = nullptr;
+    float *gab = nullptr;
 };
 
 namespace {
@@ -92,6 +110,9 @@ void free_batch(htd_batch b)
 {
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
+    void *gp[] = {b->ginst, b->glev, b->goff, b->gdone, b->gabort, b->ghead, b->gab};
+    for (void *q : gp)
+        if (q) cudaFree(q);
     if (b->ws) cudaFree(b->ws);
     if (b->hdev) cudaFree(b->hdev);
     if (b->tab_dev) cudaFree(b->tab_dev);
@@ -103,17 +124,149 @@ void free_batch(htd_batch b)
     delete b;
 }
 
-// the batch graph: no dependencies between the children, so the handles'
-// step sequences may run concurrently
+// The group of 2-D handles run by one persistent launch: its instance table
+// (tensor maps for the group plan's box, planes, coefficients, step tables),
+// the level and instance offsets of the task queue, and the counters.
+htd_status build_group(htd_batch b)
+{
+    const int ninst = (int)b->ctx.size();
+    b->in_group.assign(ninst, 0);
+    std::vector<htd::CtxGroupView> views(ninst);
+    std::vector<int> cand;
+    for (int i = 0; i < ninst; ++i)
+        if (htd::ctx_group_view(b->ctx[i], &views[i])) cand.push_back(i);
+    if (cand.size() < 2 || !htd::group2d_plan(&b->gplan)) return HTD_OK;
+    const htd::TbPlan &P = b->gplan;
+    b->gctas = htd::group2d_ctas();
+    if (b->gctas < 1) return HTD_OK;
+    auto nlev = [&](int i) { return (int)((views[i].nsteps + P.B - 1) / P.B); };
+    std::stable_sort(cand.begin(), cand.end(), [&](int x, int y) { return nlev(x) > nlev(y); });
+    const int ng = (int)cand.size();
+    std::vector<htd::GroupInst> gi(ng);
+    std::vector<long long> inst_off(ng + 1, 0);
+    size_t ab_n = 0, done_n = 0;
+    for (int g = 0; g < ng; ++g) {
+        const htd::CtxGroupView &v = views[cand[g]];
+        ab_n += v.ab.size();
+        const int gx = (int)((v.L.nx + P.TX - 1) / P.TX), gy = (int)((v.L.ny + P.TY - 1) / P.TY);
+        done_n += (size_t)gx * gy * v.R.slots;
+    }
+    HTD_CUDA(htd::dev_malloc((void **)&b->gab, sizeof(float) * ab_n));
+    HTD_CUDA(htd::dev_malloc((void **)&b->gdone, sizeof(int) * done_n));
+    b->gdone_n = done_n;
+    size_t ab_at = 0, done_at = 0;
+    for (int g = 0; g < ng; ++g) {
+        const htd::CtxGroupView &v = views[cand[g]];
+        htd::GroupInst &I = gi[g];
+        std::memset((void *)&I, 0, sizeof(I));
+        float *planes[6] = {v.u[0], v.u[1], v.u[2], v.u[3], const_cast<float *>(v.kap),
+                            const_cast<float *>(v.dco)};
+        if (!htd::make_tb2d_maps<float>(v.L, P, planes, &I.maps, v.rcap)) {
+            (void)cudaGetLastError();
+            return HTD_OK;                   // no tensor maps: keep the per-handle launches
+        }
+        for (int q = 0; q < 4; ++q) I.u[q] = v.u[q];
+        I.dco = v.dco;
+        I.fre = v.fre;
+        I.fim = v.fim;
+        I.L = v.L;
+        I.C = v.C;
+        HTD_CUDA(cudaMemcpy(b->gab + ab_at, v.ab.data(), sizeof(float) * v.ab.size(),
+                            cudaMemcpyHostToDevice));
+        I.ab = b->gab + ab_at;
+        ab_at += v.ab.size();
+        I.nsteps = v.nsteps;
+        I.jim = v.jim;
+        I.jfin = v.jfin;
+        I.slot = v.slot;
+        I.R = v.R;
+        I.err = v.err;
+        I.grid_x = (int)((v.L.nx + P.TX - 1) / P.TX);
+        I.grid_y = (int)((v.L.ny + P.TY - 1) / P.TY);
+        I.nlev = nlev(cand[g]);
+        I.done = b->gdone + done_at;
+        done_at += (size_t)I.grid_x * I.grid_y * v.R.slots;
+        inst_off[g + 1] = inst_off[g] + (long long)I.grid_x * I.grid_y * v.R.slots;
+    }
+    const int nlev_max = gi[0].nlev;
+    std::vector<long long> lev_off(nlev_max + 1, 0);
+    for (int k = 0, active = ng; k < nlev_max; ++k) {
+        while (active > 0 && gi[active - 1].nlev <= k) --active;
+        lev_off[k + 1] = lev_off[k] + inst_off[active];
+    }
+    HTD_CUDA(htd::dev_malloc((void **)&b->ginst, sizeof(htd::GroupInst) * ng));
+    HTD_CUDA(cudaMemcpy(b->ginst, gi.data(), sizeof(htd::GroupInst) * ng, cudaMemcpyHostToDevice));
+    HTD_CUDA(htd::dev_malloc((void **)&b->glev, sizeof(long long) * (nlev_max + 1)));
+    HTD_CUDA(cudaMemcpy(b->glev, lev_off.data(), sizeof(long long) * (nlev_max + 1),
+                        cudaMemcpyHostToDevice));
+    HTD_CUDA(htd::dev_malloc((void **)&b->goff, sizeof(long long) * (ng + 1)));
+    HTD_CUDA(cudaMemcpy(b->goff, inst_off.data(), sizeof(long long) * (ng + 1),
+                        cudaMemcpyHostToDevice));
+    HTD_CUDA(htd::dev_malloc((void **)&b->ghead, sizeof(unsigned long long)));
+    HTD_CUDA(htd::dev_malloc((void **)&b->gabort, sizeof(int)));
+    htd::GroupSched &S = b->gsched;
+    S.inst = b->ginst;
+    S.lev_off = b->glev;
+    S.inst_off = b->goff;
+    S.ninst = ng;
+    S.nlev_max = nlev_max;
+    S.ntasks = lev_off[nlev_max];
+    S.head = b->ghead;
+    S.abort = b->gabort;
+    b->group = cand;
+    for (int i : cand) b->in_group[i] = 1;
+    return HTD_OK;
+}
+
+// one run of the group: every member starts from rest, the queue and the
+// counters start at zero, then the persistent launch
+htd_status run_group(htd_batch b, cudaStream_t s)
+{
+    for (int i : b->group) {
+        htd_status st = htd::ctx_zero_states(b->ctx[i], s);
+        if (st != HTD_OK) return st;
+    }
+    HTD_CUDA(cudaMemsetAsync(b->gdone, 0, sizeof(int) * b->gdone_n, s));
+    HTD_CUDA(cudaMemsetAsync(b->ghead, 0, sizeof(unsigned long long), s));
+    HTD_CUDA(cudaMemsetAsync(b->gabort, 0, sizeof(int), s));
+    htd::launch_group2d(b->gplan, b->gsched, b->gctas, s);
+    HTD_CUDA(cudaGetLastError());
+    return HTD_OK;
+}
+
+// the batch graph: no dependencies between the children, so the group launch
+// and the other handles' step sequences may run concurrently
 htd_status build_graph(htd_batch b)
 {
     if (b->graph_tried) return HTD_OK;
     b->graph_tried = true;
+    htd_status gst = build_group(b);
+    if (gst != HTD_OK) return gst;
     std::vector<cudaGraph_t> kids;
-    for (htd_ctx *c : b->ctx) {
-        cudaGraph_t g = htd::ctx_step_graph(c);
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        if (b->in_group[i]) continue;
+        cudaGraph_t g = htd::ctx_step_graph(b->ctx[i]);
         if (!g) return HTD_OK;               // no capture: run the handles one by one
         kids.push_back(g);
+    }
+    cudaGraph_t ggraph = nullptr;
+    if (!b->group.empty()) {
+        cudaStream_t cs;
+        HTD_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            const long long before = htd::g_launches;
+            htd_status st = run_group(b, cs);
+            ok = cudaStreamEndCapture(cs, &ggraph) == cudaSuccess && st == HTD_OK;
+            htd::g_launches = before;        // captured, not launched
+        }
+        cudaStreamDestroy(cs);
+        (void)cudaGetLastError();
+        if (!ok) {
+            if (ggraph) cudaGraphDestroy(ggraph);
+            return HTD_OK;
+        }
+        kids.push_back(ggraph);
     }
     cudaGraph_t parent = nullptr;
     HTD_CUDA(cudaGraphCreate(&parent, 0));
@@ -130,6 +283,7 @@ htd_status build_graph(htd_batch b)
         ok = false;
     }
     cudaGraphDestroy(parent);
+    if (ggraph) cudaGraphDestroy(ggraph);      // the parent holds its own copy
     (void)cudaGetLastError();
     return HTD_OK;
 }
@@ -195,13 +349,16 @@ htd_status precond_round(htd_batch b, const std::vector<char> &sel,
         if (!any) continue;
         if (b->exec) {
             HTD_CUDA(cudaGraphLaunch(b->exec, s));
-            for (int i = 0; i < ninst; ++i) htd::g_launches += b->ci[i].nsteps;
+            for (int i = 0; i < ninst; ++i)
+                if (!b->in_group[i]) htd::g_launches += b->ci[i].nsteps;
+            if (!b->group.empty()) htd::g_launches += 1;
         } else {
             for (int i = 0; i < ninst; ++i) {
                 const bool on = !idx[i].empty() && run < b->ci[i].runs;
-                if (!on) continue;
+                if (!on || b->in_group[i]) continue;
                 if ((st = htd::ctx_run_steps(b->ctx[i], s)) != HTD_OK) return st;
             }
+            if (!b->group.empty() && (st = run_group(b, s)) != HTD_OK) return st;
         }
     }
     HTD_CUDA(cudaEventRecord(b->ev[1], s));
@@ -485,6 +642,21 @@ htd_status create_batch(int ninst, const htd_handle *handles, const int *nrhs, h
 }  // namespace
 
 extern "C" {
+
+htd_status htd_batch_describe(htd_batch b, htd_batch_desc *out)
+{
+    if (!b || !out) return HTD_ERR_ARG;
+    std::memset(out, 0, sizeof(*out));
+    out->instances = (int)b->ctx.size();
+    out->systems = (int)b->sys.size();
+    if (!b->group.empty()) {
+        out->grouped = (int)b->group.size();
+        out->group_ctas = b->gctas;
+        out->group_tasks = b->gsched.ntasks;
+        out->group_steps_per_task = b->gplan.B;
+    }
+    return HTD_OK;
+}
 
 htd_status htd_batch_create(int ninst, const htd_handle *handles, const int *nrhs, htd_batch *out)
 {

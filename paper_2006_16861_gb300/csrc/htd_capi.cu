@@ -1372,6 +1372,46 @@ void ctx_dots(htd_ctx *c, const double2 *V, int64_t ldv, int kcount, const doubl
     launch_reduce(c->partial, c->nb, kcount, out, s);
 }
 
+bool ctx_group_view(htd_ctx *c, CtxGroupView *out)
+{
+    if (c->d != 2 || c->opt.precision != HTD_MIXED || c->opt.integrator != HTD_ACD) return false;
+    if (c->opt.mode != HTD_MODE_TABLE1 && c->opt.mode != HTD_MODE_EXACT) return false;
+    if (!c->u2 || !c->u3) return false;
+    out->L = c->Lr;
+    out->u[0] = (float *)c->u0;
+    out->u[1] = (float *)c->u1;
+    out->u[2] = (float *)c->u2;
+    out->u[3] = (float *)c->u3;
+    out->kap = (const float *)c->kap;
+    out->dco = (const float *)c->dco;
+    out->fre = (const float *)c->fre;
+    out->fim = (const float *)c->fim;
+    out->C = cast_coef<float>(c->C);
+    out->nsteps = c->nsteps;
+    out->ab.resize(2 * (size_t)c->nsteps);
+    for (long long j = 0; j < c->nsteps; ++j) {
+        out->ab[j] = (float)c->atab[j];
+        out->ab[c->nsteps + j] = (float)c->btab[j];
+    }
+    // the output steps of run_steps_direct (Table 1: snapshot a quarter period
+    // before the end; both modes: the final state)
+    out->jim = c->nsteps - c->nP / 4;
+    out->jfin = c->nsteps;
+    out->slot = c->slot;
+    out->R = c->Rs;
+    out->err = c->err_dev;
+    out->rcap = c->rcap;
+    return true;
+}
+
+htd_status ctx_zero_states(htd_ctx *c, cudaStream_t s)
+{
+    const size_t bytes = c->esz * (size_t)c->Lr.total * c->rcap;
+    HTD_CUDA(cudaMemsetAsync(c->u0, 0, bytes, s));
+    HTD_CUDA(cudaMemsetAsync(c->u1, 0, bytes, s));
+    return HTD_OK;
+}
+
 htd_status ctx_take_error(htd_ctx *c)
 {
     int flag = 0;

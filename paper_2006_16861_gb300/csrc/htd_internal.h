@@ -266,6 +266,24 @@ void ctx_dots(htd_ctx *c, const double2 *V, int64_t ldv, int kcount, const doubl
 // read and clear the device error word: HTD_ERR_TIMEOUT if a bounded wait gave up
 htd_status ctx_take_error(htd_ctx *c);
 
+// What a group launch needs of a handle: false unless the handle is 2-D, FP32
+// recurrence, I_acd, Table 1 or exact read-out, with the second state pair.
+struct CtxGroupView {
+    Layout L;
+    float *u[4];
+    const float *kap, *dco, *fre, *fim;
+    StepCoef<float> C;
+    std::vector<float> ab;       // a_j then b_j, as the blocked kernel rounds them
+    long long nsteps, jim, jfin;
+    const OutSlot *slot;
+    RhsSet R;
+    int *err;
+    int rcap;
+};
+bool ctx_group_view(htd_ctx *c, CtxGroupView *out);
+// zero the first state pair of every rhs slot (a run starts from rest)
+htd_status ctx_zero_states(htd_ctx *c, cudaStream_t s);
+
 // ---- temporally blocked 2-D recurrence (htd_tblock.cu) ------------------------
 
 constexpr int kTbMaxSteps = 8;
@@ -323,6 +341,52 @@ void launch_tb2d(const TbPlan &p, const TbMaps &maps, int in0, int in1, const La
                  T *uD, const T *dco, const T *fre, const T *fim, const StepCoef<T> &C,
                  const TbSteps<T> &S, const OutSlot *slot, int *err, cudaStream_t s,
                  const RhsSet &R = RhsSet{}, bool overlap = false);
+
+// ---- one persistent launch for many 2-D instances (htd_tblock.cu) -----------
+//
+// The blocked pair form of the 2-D step for a whole group of instances (each
+// with its own size, coefficients, step count and right-hand-side slots) in
+// one launch per run: a work queue of tasks (level k, instance, slot, tile),
+// level k = steps k B .. k B + B - 1 of the instance's run, ordered by level;
+// a tile starts level k when its 3 x 3 tile neighbourhood (same instance and
+// slot) has finished level k - 1 (per-tile counters, release / acquire).
+
+// one instance of a group (device memory; CUtensorMap carries the alignment
+// the tensor maps need)
+struct GroupInst {
+    TbMaps maps;                 // u0, u1, u2, u3 (rhs stacks), q*kappa, d for the group's box
+    float *u[4];                 // the state planes: pair (0, 1) and pair (2, 3)
+    const float *dco, *fre, *fim;
+    Layout L;
+    StepCoef<float> C;
+    const float *ab;             // a_j at [0, nsteps), b_j at [nsteps, 2 nsteps)
+    long long nsteps, jim, jfin; // output steps: snapshot after step jim - 1, final after jfin - 1
+    const OutSlot *slot;         // output slot per rhs
+    RhsSet R;                    // active list, slots, per-rhs stride
+    int *err;                    // the handle's status words
+    int *done;                   // [slot][tile] levels completed in this run
+    int grid_x, grid_y;
+    int nlev;                    // levels per run, ceil(nsteps / B)
+};
+
+// queue of one run (device memory, except the counts)
+struct GroupSched {
+    const GroupInst *inst;       // sorted by nlev, largest first
+    const long long *lev_off;    // [nlev_max + 1] first task of each level
+    const long long *inst_off;   // [ninst + 1] first task of each instance within a level
+    int ninst, nlev_max;
+    long long ntasks;
+    unsigned long long *head;    // next task (zeroed before each run)
+    int *abort;                  // set when a wait gives up: no CTA takes another task
+};
+
+// The group plan (B = 8 steps, 8 rows per thread, 20 row groups, d staged:
+// the pair configuration the tuner picks on large grids), or false if it does
+// not fit the device.
+bool group2d_plan(TbPlan *p);
+// Persistent CTAs that fit the device at once for the group plan.
+int group2d_ctas();
+void launch_group2d(const TbPlan &p, const GroupSched &S, int ctas, cudaStream_t s);
 
 // Assembled FP64 operator: coefficient planes (N doubles each) of the centre
 // and of the positive offsets (the other half follows from symmetry):

@@ -636,6 +636,334 @@ void add_candidate(const Layout &L, std::vector<TbPlan> &out)
     out.push_back(p);
 }
 
+// ---- one persistent launch for a group of 2-D instances ---------------------
+
+__device__ __forceinline__ int ld_acquire_gpu(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_gpu(int *p, int v)
+{
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// orders this thread's generic-proxy view of global memory with its later (or
+// earlier) bulk tensor copies
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_inval(uint64_t *bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Persistent CTAs take tasks (level k, instance, rhs slot, tile) from a queue
+// ordered by level.  A task is the work of one tb2d_pair_kernel CTA -- B steps
+// of one tile from TMA-loaded shared memory, the same arithmetic in the same
+// order, so the results are those of the per-instance launches bit for bit --
+// started only when the 3 x 3 tiles around it (same instance and slot) have
+// finished level k - 1: its halo then holds u_{kB}, u_{kB-1}, and no
+// neighbour still reads the pair this task overwrites.  A task's dependencies
+// have lower queue positions, so the lowest unfinished task can always run and
+// the queue cannot deadlock (whatever number of CTAs is resident).  Every wait
+// is bounded by the instance's limit; a wait that gives up sets the
+// instance's error word and the group's abort word, and every CTA stops.
+template <int B, int RPT, int RG, bool SD>
+__global__ void __launch_bounds__(32 * RG, 1)
+tb2d_group_kernel(GroupSched Q)
+{
+    typedef float T;
+    constexpr int W = kW, TX = W - 2 * B, BW = kBoxW;
+    constexpr int H = RG * RPT, TY = H - 2 * B;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    constexpr int ae = (int)(tb2d_array_bytes<T>(H) / sizeof(T));
+    T *smem_t = reinterpret_cast<T *>(smem_raw);
+    T *su0 = smem_t;
+    T *su1 = smem_t + ae;
+    T *sk = smem_t + 2 * ae;
+    T *sd = smem_t + 3 * ae;                               // SD only
+    constexpr int kArrays = SD ? 4 : 3;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_t + kArrays * ae);
+    __shared__ T s_a[kTbMaxSteps], s_b[kTbMaxSteps];
+    __shared__ int s_flags[kTbMaxSteps];
+    __shared__ uint64_t nbar[2][RG];
+    __shared__ int nabort, s_ok, s_nsub;
+    __shared__ long long s_task;
+
+    const int tid = threadIdx.x;
+    const int wg = tid >> 5, wl = tid & 31;
+    if (smem_u32(smem_raw) & 127u) {                      // TMA destinations 128-byte aligned
+        if (tid == 0) atomicExch(Q.abort, 1);
+        return;
+    }
+    for (;;) {
+        if (tid == 0) {
+            long long t = Q.ntasks;
+            if (!*(volatile int *)Q.abort) t = (long long)atomicAdd(Q.head, 1ull);
+            s_task = t;
+        }
+        __syncthreads();
+        const long long task = s_task;
+        if (task >= Q.ntasks) break;
+        // level: the last k with lev_off[k] <= task; instance: the last i with
+        // inst_off[i] <= task - lev_off[k] (instances sorted by level count,
+        // so the ones still running at level k come first)
+        int lo = 0, hi = Q.nlev_max;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (Q.lev_off[mid] <= task) lo = mid; else hi = mid;
+        }
+        const int k = lo;
+        const long long local = task - Q.lev_off[k];
+        lo = 0;
+        hi = Q.ninst;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (Q.inst_off[mid] <= local) lo = mid; else hi = mid;
+        }
+        const GroupInst &I = Q.inst[lo];
+        const int ntile = I.grid_x * I.grid_y;
+        const long long q = local - Q.inst_off[lo];
+        const int slot_k = (int)(q / ntile), tile = (int)(q % ntile);
+        const int bx = tile % I.grid_x, by = tile / I.grid_x;
+        int *done = I.done + (size_t)slot_k * ntile;
+        int rhs;
+        if (!rhs_of_slot(I.R, slot_k, rhs)) {             // idle slot: nothing to compute
+            __syncthreads();
+            if (tid == 0) st_release_gpu(&done[tile], k + 1);
+            continue;
+        }
+        const Layout &L = I.L;
+        const int64_t x0 = (int64_t)bx * TX - B;
+        const int64_t y0 = (int64_t)by * TY - B;
+        const int64_t c0 = L.xl + x0 - 1;
+        const int xs = (int)(c0 - (c0 % 4));
+        const int off = (int)(c0 - xs);
+        const int ys = (int)y0;
+        const int rp = (k & 1) ? 2 : 0;                   // pair read at this level
+        const int wp = 2 - rp;                            // pair written
+        float *uC = I.u[wp] + rhs * I.R.stride;
+        float *uD = I.u[wp + 1] + rhs * I.R.stride;
+        const float *fre = I.fre + rhs * I.R.stride;
+        const float *fim = I.fim + rhs * I.R.stride;
+        const OutSlot *slot = I.slot + rhs;
+        const long long j0 = (long long)k * B;
+
+        if (tid == 0) {
+            // the 3 x 3 tiles around have finished level k - 1 (bounded wait)
+            int ok = 1;
+            if (k > 0) {
+                unsigned long long lim = *reinterpret_cast<volatile const unsigned long long *>(I.err + 2);
+                if (lim == 0) lim = kDefaultWaitNs;
+                const unsigned long long t0 = global_ns();
+                for (int dy = -1; dy <= 1 && ok; ++dy)
+                    for (int dx = -1; dx <= 1 && ok; ++dx) {
+                        const int nx_ = bx + dx, ny_ = by + dy;
+                        if (nx_ < 0 || ny_ < 0 || nx_ >= I.grid_x || ny_ >= I.grid_y) continue;
+                        const int *cnt = &done[ny_ * I.grid_x + nx_];
+                        while (ld_acquire_gpu(cnt) < k) {
+                            if (*(volatile int *)Q.abort) { ok = 0; break; }
+                            if (global_ns() - t0 > lim) {
+                                atomicExch(I.err, 1);
+                                atomicExch(Q.abort, 1);
+                                ok = 0;
+                                break;
+                            }
+                        }
+                    }
+                fence_proxy_async_global();               // the halo written by others, for TMA
+            }
+            s_ok = ok;
+            const int nsub = (int)min((long long)B, I.nsteps - j0);
+            s_nsub = nsub;
+#pragma unroll
+            for (int qq = 0; qq < kTbMaxSteps; ++qq) {
+                const long long j = j0 + qq;
+                const bool in = qq < nsub;
+                s_a[qq] = in ? I.ab[j] : 0.f;
+                s_b[qq] = in ? I.ab[I.nsteps + j] : 0.f;
+                int fl = 0;
+                if (in && j + 1 == I.jim) fl |= 1;
+                if (in && j + 1 == I.jfin) fl |= 2;
+                s_flags[qq] = fl;
+            }
+            for (int qq = 0; qq < 2; ++qq)
+                for (int g = 0; g < RG; ++g)
+                    mbar_init(&nbar[qq][g], (unsigned)((g > 0) + (g < RG - 1)));
+            nabort = 0;
+            if (ok) {
+                // the tensor maps live in global memory (written by a host copy):
+                // acquire them for the tensor-map proxy before a copy uses them
+                const int used[4] = {4, 5, rp, rp + 1};
+                for (int qq = 0; qq < 4; ++qq)
+                    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                                     reinterpret_cast<uint64_t>(&I.maps.m[used[qq]]))
+                                 : "memory");
+                mbar_init(bar, 1);
+                mbar_expect_tx(bar, (unsigned)(kArrays * (size_t)(H + 2) * BW * sizeof(T)));
+                tma_load_2d(sk, &I.maps.m[4], xs, ys, bar);
+                if (SD) tma_load_2d(sd, &I.maps.m[5], xs, ys, bar);
+                tma_load_3d(su0, &I.maps.m[rp], xs, ys, rhs, bar);
+                tma_load_3d(su1, &I.maps.m[rp + 1], xs, ys, rhs, bar);
+            }
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        const int nsub = s_nsub;
+
+        const int lx = 2 * wl;
+        const int row0 = wg * RPT;
+        const int64_t gx = x0 + lx;
+        const bool inA = gx >= 0 && gx < L.nx, inB = gx + 1 >= 0 && gx + 1 < L.nx;
+        float2 rd[SD ? 1 : RPT], rfr[RPT], rfi[RPT];
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+            const int64_t gy = y0 + row0 + i;
+            const bool rin = gy >= 0 && gy < L.ny;
+            const int64_t g = rin ? (gy + 1) * L.pitch + L.xl + gx : 0;
+            const bool a = rin && inA, b = rin && inB;
+            if (!SD) rd[i] = pr(a ? I.dco[g] : 0.f, b ? I.dco[g + 1] : 0.f);
+            rfr[i] = pr(a ? fre[g] : 0.f, b ? fre[g + 1] : 0.f);
+            rfi[i] = pr(a ? fim[g] : 0.f, b ? fim[g + 1] : 0.f);
+        }
+        const bool ok = mbar_wait_bounded(bar);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicExch(I.err, 1);
+                atomicExch(Q.abort, 1);
+                mbar_wait_bounded(bar);
+            }
+            __syncthreads();
+            break;
+        }
+
+        const bool ownA = lx >= B && lx < B + TX;
+        const int cc = lx + off;
+        const int dom_lo = (int)max((int64_t)0, -y0);
+        const int dom_hi = (int)min((int64_t)H, (int64_t)L.ny - y0);
+        const Stencil2dCoef<float2> SC = stencil2d_coef2(I.C);
+        const float2 n2 = pr(-2.f, -2.f);
+        auto urow = [&](const T *pl, int r, float2 &m, float2 &z, float2 &p) {
+            const T *qp = pl + r * BW + cc;
+            const float l = qp[0];
+            z = *reinterpret_cast<const float2 *>(qp + 1);
+            const float rr = qp[3];
+            m = pr(l, z.x);
+            p = pr(z.y, rr);
+        };
+        auto krow = [&](int r, float2 &k0, float2 &k1) {
+            const T *qp = sk + r * BW + cc;
+            k1 = *reinterpret_cast<const float2 *>(qp + 1);
+            k0 = pr(qp[0], k1.x);
+        };
+        auto step = [&](int s, auto with_out) {
+            constexpr bool kOut = decltype(with_out)::value;
+            const T *__restrict__ cur = (s & 1) ? su1 : su0;
+            T *__restrict__ prv = (s & 1) ? su0 : su1;
+            const float2 a2 = pr(s_a[s], s_a[s]), nb2 = pr(-s_b[s], -s_b[s]);
+            const int flags = s_flags[s];
+            float2 umm, um0, ump, u0m, u00, u0p;
+            urow(cur, row0, umm, um0, ump);
+            urow(cur, row0 + 1, u0m, u00, u0p);
+            float2 pm = vadd(umm, ump), p0 = vadd(u0m, u0p);
+            float2 k00, k01;
+            krow(row0, k00, k01);
+            float2 hk0 = vadd(k00, k01);
+#pragma unroll
+            for (int i = 0; i < RPT; ++i) {
+                const int ly = row0 + i;
+                float2 upm, up0, upp, k10, k11;
+                urow(cur, ly + 2, upm, up0, upp);
+                krow(ly + 1, k10, k11);
+                const float2 pp = vadd(upm, upp);
+                const float2 hk1 = vadd(k10, k11);
+                const float2 acc = stencil2d(SC, umm, um0, ump, u0m, u00, u0p, upm, up0, upp, k00,
+                                             k01, k10, k11, pm, p0, pp, hk0, hk1);
+                const int ni = (ly + 1) * BW + cc + 1;
+                const float2 ag = vfma(a2, rfr[i], vfma(nb2, rfi[i], acc));
+                const float2 uprev = *reinterpret_cast<const float2 *>(prv + ni);
+                const float2 dn = SD ? *reinterpret_cast<const float2 *>(sd + ni) : rd[SD ? 0 : i];
+                const float2 unew = vfma(dn, vfma(n2, uprev, ag), uprev);
+                *reinterpret_cast<float2 *>(prv + ni) = unew;
+                if (kOut && ownA && ly >= B && ly < B + TY && ly >= dom_lo && ly < dom_hi) {
+                    const int64_t c = (y0 + ly) * L.nx + gx;
+                    if ((flags & 1) && slot->snap_part) {
+                        if (inA) slot->snap_part[2 * c] = (double)unew.x;
+                        if (inB) slot->snap_part[2 * c + 2] = (double)unew.y;
+                    }
+                    if ((flags & 2) && slot->final_part) {
+                        if (inA) slot->final_part[2 * c] = (double)unew.x;
+                        if (inB) slot->final_part[2 * c + 2] = (double)unew.y;
+                    }
+                }
+                umm = u0m; um0 = u00; ump = u0p; pm = p0;
+                u0m = upm; u00 = up0; u0p = upp; p0 = pp;
+                k00 = k10; k01 = k11; hk0 = hk1;
+            }
+        };
+        unsigned long long nlim = 0;
+        for (int s = 0; s < nsub; ++s) {
+            if (s > 0) {
+                uint64_t *b = &nbar[(s - 1) & 1][wg];
+                const unsigned par = (unsigned)(((s - 1) >> 1) & 1);
+                if (!mbar_try_wait(b, par)) {
+                    const unsigned long long t0 = global_ns();
+                    if (nlim == 0) {
+                        nlim = *reinterpret_cast<volatile const unsigned long long *>(I.err + 2);
+                        if (nlim == 0) nlim = kDefaultWaitNs;
+                    }
+                    while (!*(volatile int *)&nabort && !mbar_try_wait(b, par)) {
+                        if (global_ns() - t0 > nlim) {
+                            *(volatile int *)&nabort = 1;
+                            atomicExch(I.err, 1);
+                            atomicExch(Q.abort, 1);
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            if (s_flags[s]) step(s, std::true_type{});
+            else step(s, std::false_type{});
+            if (s + 1 < nsub) {
+                __syncwarp();
+                if (wl == 0) {
+                    if (wg > 0) mbar_arrive_cta(&nbar[s & 1][wg - 1]);
+                    if (wg < RG - 1) mbar_arrive_cta(&nbar[s & 1][wg + 1]);
+                }
+            }
+        }
+        __syncwarp();
+        // each warp stores its own rows of the owned core (reads of shared
+        // memory only, so no barrier is needed before it)
+        const T *last = (nsub & 1) ? su1 : su0;
+        const T *prev = (nsub & 1) ? su0 : su1;
+        if (ownA && (inA || inB)) {
+            for (int ly = max(row0, B); ly < min(row0 + RPT, B + TY); ++ly) {
+                const int64_t gy = y0 + ly;
+                if (gy >= L.ny) break;
+                const int64_t g = (gy + 1) * L.pitch + L.xl + gx;
+                const int si = (ly + 1) * BW + cc + 1;
+                if (inA) { uC[g] = last[si]; uD[g] = prev[si]; }
+                if (inB) { uC[g + 1] = last[si + 1]; uD[g + 1] = prev[si + 1]; }
+            }
+        }
+        __syncthreads();                                   // the core is stored by every thread
+        if (tid == 0) {
+            __threadfence();
+            fence_proxy_async_global();
+            st_release_gpu(&done[tile], k + 1);
+            mbar_inval(bar);
+            for (int qq = 0; qq < 2; ++qq)
+                for (int g = 0; g < RG; ++g) mbar_inval(&nbar[qq][g]);
+        }
+    }
+}
+
 }  // namespace
 
 template <typename T>
@@ -753,6 +1081,56 @@ void launch_tb2d(const TbPlan &p, const TbMaps &maps, int in0, int in1, const La
     HTD_TB2D_CASE(8, 6, 16)
     HTD_TB2D_CASE(8, 10, 16)
 #undef HTD_TB2D_CASE
+}
+
+// The group plan: node pairs, 8 steps per launch, 8 rows per thread, 20 row
+// groups, d staged in shared memory.
+constexpr int kGB = 8, kGRPT = 8, kGRG = 20;
+constexpr bool kGSD = true;
+
+bool group2d_plan(TbPlan *p)
+{
+    constexpr int H = kGRG * kGRPT;
+    const size_t smem = tb2d_smem_bytes<float>(H, kGSD ? 4 : 3);
+    if (cudaFuncSetAttribute(tb2d_group_kernel<kGB, kGRPT, kGRG, kGSD>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    p->B = kGB;
+    p->RPT = kGRPT;
+    p->RG = kGRG;
+    p->pair = true;
+    p->sd = kGSD;
+    p->TX = kW - 2 * kGB;
+    p->TY = H - 2 * kGB;
+    p->H = H;
+    p->smem = smem;
+    p->grid_x = p->grid_y = 0;
+    p->occ = 0;
+    p->waves = 0;
+    return group2d_ctas() > 0;
+}
+
+int group2d_ctas()
+{
+    constexpr int H = kGRG * kGRPT;
+    const size_t smem = tb2d_smem_bytes<float>(H, kGSD ? 4 : 3);
+    int occ = 0, dev = 0, nsm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tb2d_group_kernel<kGB, kGRPT, kGRG, kGSD>,
+                                                      32 * kGRG, smem) != cudaSuccess ||
+        cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return occ * nsm;
+}
+
+void launch_group2d(const TbPlan &p, const GroupSched &S, int ctas, cudaStream_t s)
+{
+    tb2d_group_kernel<kGB, kGRPT, kGRG, kGSD><<<ctas, 32 * kGRG, p.smem, s>>>(S);
+    ++g_launches;
 }
 
 template std::vector<TbPlan> tb2d_candidates<float>(const Layout &, int);

@@ -36,7 +36,8 @@ EXPORTS = ("htd_default_options", "htd_create", "htd_destroy", "htd_plan", "htd_
            "htd_apply_precond", "htd_apply_H", "htd_residual_norm", "htd_residual_norm_noalloc",
            "htd_gmres_solve", "htd_grad", "htd_grad_td",
            "htd_gmres_solve_host", "htd_batch_create", "htd_batch_destroy",
-           "htd_batch_apply_precond", "htd_batch_gmres_solve", "htd_set_wait_limit",
+           "htd_batch_apply_precond", "htd_batch_gmres_solve", "htd_batch_describe",
+           "htd_set_wait_limit",
            "htd_test_fail_alloc", "htd_status_string")
 
 
@@ -78,6 +79,15 @@ class Params(ctypes.Structure):
         d["tile"] = list(self.tile)
         return d
 
+
+
+class BatchDesc(ctypes.Structure):
+    _fields_ = [("instances", ctypes.c_int), ("systems", ctypes.c_int),
+                ("grouped", ctypes.c_int), ("group_ctas", ctypes.c_int),
+                ("group_tasks", ctypes.c_longlong), ("group_steps_per_task", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class SolveInfo(ctypes.Structure):
@@ -133,6 +143,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.htd_batch_destroy.argtypes = [vp]
     lib.htd_batch_apply_precond.argtypes = [vp, vp, vp, vp]
     lib.htd_batch_gmres_solve.argtypes = [vp, vp, vp, d, i, vp, vp]
+    lib.htd_batch_describe.argtypes = [vp, ctypes.POINTER(BatchDesc)]
     lib.htd_set_wait_limit.argtypes = [vp, ctypes.c_longlong, i]
     lib.htd_test_fail_alloc.argtypes = [ctypes.c_longlong]
     lib.htd_test_fail_alloc.restype = None
@@ -325,6 +336,13 @@ def htd_batch_create(handles, nrhs) -> int:
 
 def htd_batch_destroy(batch: int) -> None:
     _check(load().htd_batch_destroy(batch), "htd_batch_destroy")
+
+
+def htd_batch_describe(batch: int) -> dict:
+    """How the batch runs its applications (after the first one)."""
+    out = BatchDesc()
+    _check(load().htd_batch_describe(batch, ctypes.byref(out)), "htd_batch_describe")
+    return out.as_dict()
 
 
 def _ptr_array(ts) -> ctypes.Array:
@@ -547,6 +565,9 @@ class Batch:
         Us = self.zeros() if Us is None else Us
         htd_batch_apply_precond(self.handle, Fs, Us, stream)
         return Us
+
+    def describe(self) -> dict:
+        return htd_batch_describe(self.handle)
 
     def solve(self, Fs, Us=None, tol=1e-6, max_iters=400, stream=None,
               allow_not_converged=False):

@@ -159,3 +159,64 @@ def test_config_batched_full_size():
     b.close()
     for s in solvers:
         s.close()
+
+
+GROUP_SIZES = [(1, 7), (3, 2), (37, 45), (130, 67), (64, 300), (101, 101), (211, 97)]
+
+
+def test_group_launch_equals_per_handle_launches():
+    """2-D FP32 handles of many sizes (ragged; one tile of 1 x 7 and 3 x 2 nodes;
+    up to 5 x 2 tiles), step counts and right-hand-side slots (one handle with
+    three of four slots used, one with two, one in exact mode) run by the one
+    persistent group launch: every output equals that handle's own
+    application bit for bit, on two applications in a row (graph replay), and
+    a 3-D handle in the same batch runs beside the group as its own child graph."""
+    Ts = [2, 2, 3, 2, 3, 2, 4]
+    probs = [het_problem(2, n, T=T) for n, T in zip(GROUP_SIZES, Ts)]
+    modes = ["table1", "table1", "table1", "table1", "table1", "exact", "table1"]
+    nrhs = [1, 1, 3, 1, 2, 1, 1]
+    caps = [1, 1, 4, 1, 2, 1, 1]
+    solvers = [htd.Solver(p, precision="mixed", mode=m, max_rhs=c)
+               for p, m, c in zip(probs, modes, caps)]
+    p3 = het_problem(3, (21, 17, 19), T=2)
+    solvers.append(htd.Solver(p3, precision="mixed", max_rhs=2))
+    probs.append(p3)
+    nrhs.append(2)
+    assert len({s.params["steps"] for s in solvers}) > 2
+    b = htd.Batch(solvers, nrhs)
+    Fs = [rhs_stack(p, r, 60 + 7 * k) for k, (p, r) in enumerate(zip(probs, nrhs))]
+    for rep in range(2):
+        Us = b.precond([dev(F) for F in Fs])
+        if rep == 0:
+            d = b.describe()
+            assert d["grouped"] == 7 and d["group_ctas"] > 0 and d["group_steps_per_task"] == 8
+        for s, F, U in zip(solvers, Fs, Us):
+            Ub = host(U)
+            for r in range(F.shape[0]):
+                single = host(s.precond(dev(F[r])))
+                assert np.array_equal(Ub[r], single), rel_l2(Ub[r].reshape(-1), single.reshape(-1))
+    b.close()
+    for s in solvers:
+        s.close()
+
+
+def test_group_launch_solve_equals_single_solves():
+    """Lockstep FGMRES over five 2-D FP32 handles of different sizes and step
+    counts run by the group launch (systems leave the batch at different
+    iterations, so the group's slots go idle one by one): the same iterations
+    and the same solutions bit for bit as htd_gmres_solve per handle."""
+    sizes = [(64, 61), (101, 101), (150, 97), (37, 190), (200, 200)]
+    probs = [het_problem(2, n, T=T) for n, T in zip(sizes, [4, 6, 5, 8, 9])]
+    solvers = [htd.Solver(p, precision="mixed", restart=10) for p in probs]
+    b = htd.Batch(solvers, [1] * len(solvers))
+    Us, infos = b.solve([dev(p.F[None]) for p in probs], tol=1e-7, max_iters=300)
+    assert b.describe()["grouped"] == len(solvers)
+    its = []
+    for s, p, U, info in zip(solvers, probs, Us, infos):
+        U1, info1 = s.solve(dev(p.F), tol=1e-7, max_iters=300)
+        assert info["converged"] and info1["converged"]
+        assert info["iterations"] == info1["iterations"]
+        its.append(info["iterations"])
+        assert np.array_equal(host(U)[0], host(U1))
+    assert len(set(its)) > 1
+    b.close()

@@ -79,8 +79,10 @@ NCU_TRAFFIC = {
                   "nodes": 1001 * 1001},
     "stream3d": {"file": "htd_stream3d.cu", "sha16": "4f289c964d28aa22",
                  "bytes": 193680896 + 18157568, "nodes": 192 ** 3},
-    "stream3d_pair": {"file": "htd_stream3d_pair.cu", "sha16": "8c6bdafcd9f39e71",
-                      "bytes": 201089536 + 15837696, "nodes": 192 ** 3},
+    # captured on the 256^3 bench workload itself (z chunk 19, five launches
+    # averaged): no scaling
+    "stream3d_pair": {"file": "htd_stream3d_pair.cu", "sha16": "8e7b6e322a4ec81b",
+                      "bytes": 440159078 + 52479795, "nodes": 256 ** 3},
 }
 
 WORKLOADS = ["3d_layered_256", "2d_grf_1001", "3d_layered_192", "2d_const_101",

@@ -148,6 +148,12 @@ typedef struct {
     int s3_stages;     /* ring stages of the streamed 3-D kernels: 0 = 5, or 4, 6, 7 */
     int s3_zchunk;     /* z planes per CTA of the streamed 3-D kernels: 0 = chosen
                           at create by timing, else that many */
+    int s3_rhs_per_cta; /* right-hand sides per CTA of the streamed 3-D pair kernel
+                          for handles with max_rhs > 1: 0 = 1 or 2, whichever is
+                          faster when timed at create with every rhs slot active;
+                          1; 2 (one CTA streams a column tile for two rhs slots,
+                          loading q*kappa and d once and computing every stencil
+                          coefficient once for both; 4 ring stages) */
     int launch;        /* bit flags: HTD_LAUNCH_NO_OVERLAP (consecutive step
                           launches do not overlap by programmatic dependent
                           launch), HTD_LAUNCH_NO_GRAPH (steps launched one by one
@@ -237,6 +243,8 @@ typedef struct {
                                 (gather / z-march), 1 temporally blocked 2-D
                                 (TMA tiles), 2 TMA-streamed 3-D, 3 one-step
                                 backward differences (HTD_ABD); -1 in htd_plan */
+    int rhs_per_cta;         /* right-hand sides one CTA of the step kernel works
+                                on (1 or 2); 0 in htd_plan */
 } htd_params;
 
 /*

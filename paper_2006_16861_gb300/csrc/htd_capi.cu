@@ -166,6 +166,7 @@ struct htd_ctx {
     int s3_zchunk = 0;
     int s3_shape = 0;
     int s3_stages = 5;
+    int s3_rpc = 1;             // right-hand sides per CTA of the streamed pair kernel
     // right-hand-side batch: rcap rhs slots in every per-rhs array (u0, u1, u2,
     // u3, fre, fim, slot); act_dev = active list read by the step kernels
     int rcap = 1;
@@ -351,7 +352,7 @@ htd_status run_steps_direct(htd_ctx *c, cudaStream_t s)
                     htd::launch_stream3d_pair(c->s3maps, (int)(j & 1), L, um, C,
                                               (T)c->atab[j], (T)c->btab[j], c->slot, flags,
                                               c->s3_zchunk, c->s3_stages, c->err_dev, s, c->Rs,
-                                              j > 0 && step_overlap(c));
+                                              j > 0 && step_overlap(c), c->s3_rpc);
                 else
                     htd::launch_stream3d(c->s3maps, (int)(j & 1), c->s3_shape, L, um, C,
                                          (T)c->atab[j], (T)c->btab[j], c->slot, flags,
@@ -733,7 +734,7 @@ htd_status autotune_tb2d(htd_ctx *c, int want_B, int want_RPT)
 // one step each on the context's own buffers with zero forcing and no outputs.
 // How the CTAs of the last wave fill the GPU decides the best length, which no
 // simple rule predicts well (at 256^3: 37 planes beats 32 and 64 by 3-8 %).
-htd_status autotune_s3_zchunk(htd_ctx *c)
+htd_status autotune_s3_zchunk(htd_ctx *c, const htd::RhsSet &R = htd::RhsSet{})
 {
     const Layout &L = c->Lr;
     std::vector<int> cands;
@@ -767,7 +768,7 @@ htd_status autotune_s3_zchunk(htd_ctx *c)
                 htd::launch_stream3d_pair(c->s3maps, r & 1, L, (r & 1) ? (float *)c->u0
                                                                         : (float *)c->u1,
                                           C, 0.f, 0.f, c->slot, 0, zc, c->s3_stages, c->err_dev, s,
-                                          htd::RhsSet{}, r > 0 && step_overlap(c));
+                                          R, r > 0 && step_overlap(c), c->s3_rpc);
             else
                 htd::launch_stream3d(c->s3maps, r & 1, c->s3_shape, L,
                                      (r & 1) ? (float *)c->u0 : (float *)c->u1, C, 0.f, 0.f,
@@ -976,6 +977,7 @@ htd_status plan_impl(const htd_grid *grid, const double *c_cell, const double *R
     if (opt.s3_kernel < HTD_S3_PAIR || opt.s3_kernel > HTD_S3_NODE_128x2) return HTD_ERR_ARG;
     if (opt.s3_stages != 0 && (opt.s3_stages < 4 || opt.s3_stages > 7)) return HTD_ERR_ARG;
     if (opt.s3_zchunk < 0 || opt.s3_zchunk > (1 << 24)) return HTD_ERR_ARG;
+    if (opt.s3_rhs_per_cta < 0 || opt.s3_rhs_per_cta > 2) return HTD_ERR_ARG;
     if (opt.launch & ~(HTD_LAUNCH_NO_OVERLAP | HTD_LAUNCH_NO_GRAPH)) return HTD_ERR_ARG;
     if (opt.wait_limit_ns < 0) return HTD_ERR_ARG;
     pl->opt = opt;
@@ -1058,6 +1060,7 @@ htd_status plan_impl(const htd_grid *grid, const double *c_cell, const double *R
     P.ctas_per_sm = 0;
     P.waves = 0;
     P.step_kernel = -1;
+    P.rhs_per_cta = 0;
     return HTD_OK;
 }
 
@@ -1262,12 +1265,50 @@ htd_status create_impl(const htd_grid *grid, const double *c_cell, const double 
                 c->use_s3 = htd::make_stream3d_maps(L, c->s3_shape, planes, &c->s3maps);
             if (c->use_s3) {
                 c->s3_stages = (opt.s3_stages == 0) ? 5 : opt.s3_stages;
+                c->s3_rpc = 1;
                 c->s3_zchunk = c->s3_shape == kS3Pair ? htd::stream3d_pair_zchunk(L, c->s3_stages)
                                                       : htd::stream3d_zchunk(L, c->s3_shape);
+                // right-hand sides per CTA (pair kernel, handles with several rhs):
+                // 2 when asked, or the faster of 1 and 2 timed with every rhs slot
+                // active (each with its own z chunk)
+                const bool multi = c->s3_shape == kS3Pair && c->rcap > 1;
+                const int want_rpc = multi ? opt.s3_rhs_per_cta : 1;
+                htd::RhsSet all = htd::RhsSet{};
+                if (multi) {
+                    std::vector<int> idx(c->rcap);
+                    for (int k = 0; k < c->rcap; ++k) idx[k] = k;
+                    htd::launch_set_act(c->act_dev, c->rcap, idx.data(), 0);
+                    HTD_CUDA(cudaDeviceSynchronize());
+                    all = c->Rs;
+                }
                 if (opt.s3_zchunk > 0) {
                     c->s3_zchunk = opt.s3_zchunk;
+                    if (want_rpc == 2) {
+                        c->s3_rpc = 2;
+                        c->s3_stages = 4;
+                    }
+                } else if (want_rpc == 0) {
+                    htd_status ts = autotune_s3_zchunk(c, all);
+                    if (ts != HTD_OK) return ts;
+                    const int z1 = c->s3_zchunk, st1 = c->s3_stages;
+                    const float us1 = c->step_us;
+                    c->s3_rpc = 2;
+                    c->s3_stages = 4;
+                    c->s3_zchunk = htd::stream3d_pair_zchunk(L, 4, 2);
+                    if ((ts = autotune_s3_zchunk(c, all)) != HTD_OK) return ts;
+                    if (!(c->step_us < us1)) {
+                        c->s3_rpc = 1;
+                        c->s3_stages = st1;
+                        c->s3_zchunk = z1;
+                        c->step_us = us1;
+                    }
                 } else {
-                    htd_status ts = autotune_s3_zchunk(c);
+                    if (want_rpc == 2) {
+                        c->s3_rpc = 2;
+                        c->s3_stages = 4;
+                        c->s3_zchunk = htd::stream3d_pair_zchunk(L, 4, 2);
+                    }
+                    htd_status ts = autotune_s3_zchunk(c, all);
                     if (ts != HTD_OK) return ts;
                 }
             }
@@ -1497,6 +1538,7 @@ void htd_default_options(htd_options *opt)
     opt->s3_kernel = HTD_S3_PAIR;
     opt->s3_stages = 0;
     opt->s3_zchunk = 0;
+    opt->s3_rhs_per_cta = 0;
     opt->launch = 0;
     opt->wait_limit_ns = 0;
 }
@@ -1563,7 +1605,7 @@ htd_status htd_get_params(htd_handle h, htd_params *out)
         P.tile[0] = tx[sh];
         P.tile[1] = ty[sh];
         P.tile[2] = h->s3_zchunk;
-        P.ctas_per_sm = (sh == kS3Pair && h->s3_stages <= 5) ? 3 : 2;
+        P.ctas_per_sm = (sh == kS3Pair && h->s3_stages <= 5 && h->s3_rpc == 1) ? 3 : 2;
         int dev = 0, nsm = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -1573,6 +1615,7 @@ htd_status htd_get_params(htd_handle h, htd_params *out)
         P.waves = (int)((ctas + slots - 1) / slots);
     }
     P.step_kernel = (h->opt.integrator == HTD_ABD) ? 3 : h->use_tb ? 1 : (h->use_s3 ? 2 : 0);
+    P.rhs_per_cta = h->use_s3 ? h->s3_rpc : 1;
     return HTD_OK;
 }
 

@@ -440,15 +440,20 @@ void launch_stream3d(const Stream3Maps &maps, int from, int shape, const Layout 
 // outermost); q*kappa and d are shared.
 bool make_stream3d_pair_maps(const Layout &L, float *const planes[6], Stream3Maps *maps,
                              int nrhs = 1);
-// stages: 6 (2 CTAs per SM) or 4 (3 CTAs per SM)
-int stream3d_pair_zchunk(const Layout &L, int stages);
+// first z chunk to try for a ring of `stages` stages and `rpc` right-hand sides
+// per CTA (3 CTAs per SM for rpc 1 with 4-5 stages, else 2)
+int stream3d_pair_zchunk(const Layout &L, int stages, int rpc = 1);
+size_t stream3d_pair_smem_bytes(int stages, int rpc = 1);
 // overlap: the launch may start while the previous kernel of the stream drains
 // (its prologue loads q*kappa, d and the forcing, which no step writes; the
-// state planes are loaded after the wait for that kernel)
+// state planes are loaded after the wait for that kernel).  rpc: right-hand
+// sides per CTA, 1 (any stages) or 2 (4 stages): a CTA then streams one column
+// tile for two rhs slots, loading q*kappa and d once and computing each
+// stencil coefficient once for both.
 void launch_stream3d_pair(const Stream3Maps &maps, int from, const Layout &L, float *um,
                           const StepCoef<float> &C, float a, float b, const OutSlot *slot,
                           int flags, int zchunk, int stages, int *err, cudaStream_t s,
-                          const RhsSet &R = RhsSet{}, bool overlap = false);
+                          const RhsSet &R = RhsSet{}, bool overlap = false, int rpc = 1);
 
 // Gradient through the recurrence (htd_grad_td): res = U[rec] - d and the
 // adjoint forcing planes are/aim (padded, pre-zeroed) += Re/Im res at receivers

@@ -39,12 +39,23 @@ constexpr int kHaloW = 72, kHaloH = kTY + 2;
 constexpr int kHaloElems = kHaloW * kHaloH;     // 720 floats copied
 constexpr int kHaloStride = 768;                // padded to 3072 bytes (128-byte multiple)
 constexpr int kNodeElems = kTX * kTY;           // 512 floats
-constexpr int kStageElems = 2 * kHaloStride + 4 * kNodeElems;
-constexpr unsigned kStageTxBytes = (2 * kHaloElems + 4 * kNodeElems) * 4;
-// the two halo planes of a z chunk carry only what the stencil reads from them:
-// u_j and q*kappa on the lower one, u_j on the upper one
-constexpr unsigned kFirstTxBytes = 2 * kHaloElems * 4;
-constexpr unsigned kLastTxBytes = kHaloElems * 4;
+// Stage layout for RPC right-hand sides per CTA: the u_j halo box of each rhs,
+// the q*kappa halo box, d, then Re F, Im F, u_{j-1} of each rhs.  RPC = 1 is the
+// single-rhs layout [u_j | q*kappa | d | Re F | Im F | u_{j-1}].
+template <int RPC>
+__host__ __device__ constexpr int stage_elems()
+{
+    return (RPC + 1) * kHaloStride + (1 + 3 * RPC) * kNodeElems;
+}
+// bytes a stage's copies bring: node planes of the chunk (everything) and the
+// two halo planes (u_j and q*kappa on the lower one, u_j on the upper one),
+// for `nr` right-hand sides present in the CTA
+__host__ __device__ constexpr unsigned stage_tx_bytes(int kind, int nr)
+{
+    return kind == 0 ? (unsigned)(((nr + 1) * kHaloElems + (1 + 3 * nr) * kNodeElems) * 4)
+         : kind == 1 ? (unsigned)((nr + 1) * kHaloElems * 4)
+                     : (unsigned)(nr * kHaloElems * 4);
+}
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;
 
 __device__ __forceinline__ unsigned smem_u32(const void *p)
@@ -112,34 +123,45 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
-// Stored plane p of rhs r into one stage: u_j and q*kappa with the halo, d,
-// Re F, Im F, u_{j-1}.  The stage's byte count is announced first; the
-// coefficient part (q*kappa, d, forcing: no step writes them) and the state
-// part (u_j, u_{j-1}) may be issued separately.  `kind` 0: a node plane of the
-// chunk (everything); 1: the lower halo plane (u_j, q*kappa); 2: the upper
-// halo plane (u_j only).  The node boxes of a halo plane are never read.
+// Stored plane p into one stage for the rhs r[0 .. nr) of the CTA: u_j and
+// q*kappa with the halo, d, Re F, Im F, u_{j-1}.  The stage's byte count is
+// announced first; the coefficient part (q*kappa, d, forcing: no step writes
+// them) and the state part (u_j, u_{j-1}) may be issued separately.  `kind` 0:
+// a node plane of the chunk (everything); 1: the lower halo plane (u_j,
+// q*kappa); 2: the upper halo plane (u_j only).  The node boxes of a halo
+// plane are never read.
+template <int RPC>
 __device__ __forceinline__ void load_stage_coef(const Stream3Maps &maps, float *stage, uint64_t *bar,
-                                                int xs, int xn, int y0, int p, int r, int kind)
+                                                int xs, int xn, int y0, int p, const int *r, int nr,
+                                                int kind)
 {
-    const unsigned bytes = kind == 0 ? kStageTxBytes : kind == 1 ? kFirstTxBytes : kLastTxBytes;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
+                 "r"(stage_tx_bytes(kind, nr))
                  : "memory");
     if (kind == 2) return;
-    tma_load_3d(stage + kHaloStride, &maps.m[2], xs, y0, p, bar);
+    tma_load_3d(stage + RPC * kHaloStride, &maps.m[2], xs, y0, p, bar);
     if (kind == 1) return;
-    tma_load_3d(stage + 2 * kHaloStride, &maps.m[3], xn, y0 + 1, p, bar);
-    tma_load_4d(stage + 2 * kHaloStride + kNodeElems, &maps.m[4], xn, y0 + 1, p, r, bar);
-    tma_load_4d(stage + 2 * kHaloStride + 2 * kNodeElems, &maps.m[5], xn, y0 + 1, p, r, bar);
+    float *nd = stage + (RPC + 1) * kHaloStride;
+    tma_load_3d(nd, &maps.m[3], xn, y0 + 1, p, bar);
+    for (int q = 0; q < nr; ++q) {
+        float *nq = nd + kNodeElems + q * 3 * kNodeElems;
+        tma_load_4d(nq, &maps.m[4], xn, y0 + 1, p, r[q], bar);
+        tma_load_4d(nq + kNodeElems, &maps.m[5], xn, y0 + 1, p, r[q], bar);
+    }
 }
 
+template <int RPC>
 __device__ __forceinline__ void load_stage_state(const Stream3Maps &maps, int iu, int ium,
                                                  float *stage, uint64_t *bar, int xs, int xn,
-                                                 int y0, int p, int r, int kind)
+                                                 int y0, int p, const int *r, int nr, int kind)
 {
-    tma_load_4d(stage, &maps.m[iu], xs, y0, p, r, bar);
-    if (kind == 0)
-        tma_load_4d(stage + 2 * kHaloStride + 3 * kNodeElems, &maps.m[ium], xn, y0 + 1, p, r, bar);
+    float *nd = stage + (RPC + 1) * kHaloStride;
+    for (int q = 0; q < nr; ++q) {
+        tma_load_4d(stage + q * kHaloStride, &maps.m[iu], xs, y0, p, r[q], bar);
+        if (kind == 0)
+            tma_load_4d(nd + kNodeElems + q * 3 * kNodeElems + 2 * kNodeElems, &maps.m[ium], xn,
+                        y0 + 1, p, r[q], bar);
+    }
 }
 
 // programmatic dependent launch (no-ops for an ordinary launch): code before
@@ -164,33 +186,46 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 
 // NS shared-memory stages: the consumers hold one or two of them (the stage
 // being read and the previous one, whose node data the finished node plane
-// needs), the rest is the producer's lead; 4 or 5 stages (57 / 72 KB) fit 3
-// CTAs per SM (the default, 5), 6 or 7 stages (86 / 100 KB) fit 2
-template <int NS>
-__global__ void __launch_bounds__(kThreads + 32, NS >= 6 ? 2 : 3)
+// needs), the rest is the producer's lead.  RPC = 1: 4 or 5 stages (57 / 72 KB)
+// fit 3 CTAs per SM (the default, 5), 6 or 7 stages (86 / 100 KB) fit 2.
+// RPC = 2 (two right-hand sides per CTA sharing the q*kappa and d boxes and
+// every stencil coefficient): 4 stages (94 KB), 2 CTAs per SM.
+template <int NS, int RPC>
+__global__ void __launch_bounds__(kThreads + 32, RPC == 2 ? 2 : (NS >= 6 ? 2 : 3))
 stream3d_pair_kernel(const __grid_constant__ Stream3Maps maps, int iu, int ium,
                      float *__restrict__ um, Layout L, StepCoef<float> C, float a, float b,
                      const OutSlot *__restrict__ slot, int flags, int zchunk, int *__restrict__ err,
                      RhsSet R)
 {
+    constexpr int kSE = stage_elems<RPC>();
     extern __shared__ __align__(128) float ring[];
-    uint64_t *full = reinterpret_cast<uint64_t *>(ring + NS * kStageElems);
+    uint64_t *full = reinterpret_cast<uint64_t *>(ring + NS * kSE);
     uint64_t *empty = full + NS;
     __shared__ int abort_flag;
 
     const int tid = threadIdx.x;
-    // the rhs slot varies fastest over the CTAs, so the rhs of one column tile
-    // run side by side and share its q*kappa and d through L2
-    int rhs;
-    if (!rhs_of_slot(R, (int)(blockIdx.x % (unsigned)R.slots), rhs)) return;
+    // the rhs slots vary fastest over the CTAs, so the rhs of one column tile
+    // run side by side and share its q*kappa and d through L2; a CTA takes
+    // slots g RPC .. g RPC + RPC - 1 of its group g (the present ones)
+    const int ngroups = (R.slots + RPC - 1) / RPC;
+    const int grp = (int)(blockIdx.x % (unsigned)ngroups);
+    int rr[RPC];
+    int nr = 0;
+#pragma unroll
+    for (int q = 0; q < RPC; ++q) {
+        int rq;
+        if (grp * RPC + q < R.slots && rhs_of_slot(R, grp * RPC + q, rq)) rr[nr++] = rq;
+    }
+    if (nr == 0) return;
+#pragma unroll
+    for (int q = 1; q < RPC; ++q)
+        if (q >= nr) rr[q] = rr[0];          // an absent second rhs repeats the first (not stored)
     if (smem_u32(ring) & 127u) {              // TMA destinations must be 128-byte aligned
         if (tid == 0) atomicExch(err, 1);
         return;
     }
-    const int64_t x0 = (int64_t)(blockIdx.x / (unsigned)R.slots) * kTX;
+    const int64_t x0 = (int64_t)(blockIdx.x / (unsigned)ngroups) * kTX;
     const int64_t y0 = (int64_t)blockIdx.y * kTY;
-    um += rhs * R.stride;
-    slot += rhs;
     const int64_t zb = (int64_t)blockIdx.z * zchunk;
     const int64_t ze = min((int64_t)L.nz, zb + zchunk);
     if (zb >= ze) return;
@@ -219,20 +254,20 @@ stream3d_pair_kernel(const __grid_constant__ Stream3Maps maps, int iu, int ium,
             const int npre = min(NS, nplanes);
             auto kind_of = [&](int p) { return p == 0 ? 1 : (p == nplanes - 1 ? 2 : 0); };
             for (int p = 0; p < npre; ++p)
-                load_stage_coef(maps, ring + p * kStageElems, &full[p], xs, xn, (int)y0,
-                                (int)(zb + p), rhs, kind_of(p));
+                load_stage_coef<RPC>(maps, ring + p * kSE, &full[p], xs, xn, (int)y0,
+                                     (int)(zb + p), rr, nr, kind_of(p));
             grid_dep_wait();
             for (int p = 0; p < npre; ++p)
-                load_stage_state(maps, iu, ium, ring + p * kStageElems, &full[p], xs, xn, (int)y0,
-                                 (int)(zb + p), rhs, kind_of(p));
+                load_stage_state<RPC>(maps, iu, ium, ring + p * kSE, &full[p], xs, xn, (int)y0,
+                                      (int)(zb + p), rr, nr, kind_of(p));
             for (int p = NS; p < nplanes; ++p) {
                 const int st = p % NS;
                 if (!wait_bounded(&empty[st], (unsigned)(((p / NS) - 1) & 1), &abort_flag)) break;
-                float *stage = ring + st * kStageElems;
-                load_stage_coef(maps, stage, &full[st], xs, xn, (int)y0, (int)(zb + p), rhs,
-                                kind_of(p));
-                load_stage_state(maps, iu, ium, stage, &full[st], xs, xn, (int)y0, (int)(zb + p),
-                                 rhs, kind_of(p));
+                float *stage = ring + st * kSE;
+                load_stage_coef<RPC>(maps, stage, &full[st], xs, xn, (int)y0, (int)(zb + p), rr,
+                                     nr, kind_of(p));
+                load_stage_state<RPC>(maps, iu, ium, stage, &full[st], xs, xn, (int)y0,
+                                      (int)(zb + p), rr, nr, kind_of(p));
             }
             if (abort_flag) {
                 atomicExch(err, 1);
@@ -278,13 +313,16 @@ stream3d_pair_kernel(const __grid_constant__ Stream3Maps maps, int iu, int ium,
     // (ty, 2 tx) in the node boxes
     const int uo = ty * kHaloW + 2 * tx + 3;
     const int no = ty * kTX + 2 * tx;
-    float *ump = um + (zb + 1) * L.plane + (gy + 1) * L.pitch + L.xl + gx;   // u_{j+1} at node zb
+    float *ump[RPC];                                   // u_{j+1} at node zb, per rhs
+#pragma unroll
+    for (int q = 0; q < RPC; ++q)
+        ump[q] = um + rr[q] * R.stride + (zb + 1) * L.plane + (gy + 1) * L.pitch + L.xl + gx;
     int64_t cidx = (zb * L.ny + gy) * L.nx + gx;
     const int64_t cstride = L.ny * L.nx;
 
     // u_j of one stored plane at row oy as the three pairs (u(x-1+ox), u(x+ox))
-    auto load_u = [&](float2 (&w)[3], const float *stage, int oy) {
-        const float *r = stage + uo + oy * kHaloW;
+    auto load_u = [&](float2 (&w)[3], const float *ubox, int oy) {
+        const float *r = ubox + uo + oy * kHaloW;
         const float um1 = r[0];
         const float2 mid = *reinterpret_cast<const float2 *>(r + 1);
         const float up2 = r[3];
@@ -296,7 +334,7 @@ stream3d_pair_kernel(const __grid_constant__ Stream3Maps maps, int iu, int ium,
     // (oy, ox) - 1 (-1 keeps the lower cell, +1 the upper, 0 both), same order of
     // additions as the one-node kernel: along x first, then across y
     auto load_k = [&](float2 (&kk)[3][3], const float *stage) {
-        const float *r = stage + kHaloStride + uo;
+        const float *r = stage + RPC * kHaloStride + uo;
         float2 kx[2][3];
 #pragma unroll
         for (int ay = 0; ay < 2; ++ay) {
@@ -319,13 +357,16 @@ stream3d_pair_kernel(const __grid_constant__ Stream3Maps maps, int iu, int ium,
     // c(P)) and P - 1 (upper plane, c(P-1)) -- where c(P) is the cell plane
     // stored with P.  A node plane receives its lower, middle and upper terms in
     // that order, each in (oy, ox) order, so the sums are those of the one-node
-    // kernel bit for bit.  accL, accM, accU: node planes P + 1, P, P - 1.
+    // kernel bit for bit.  accL, accM, accU: node planes P + 1, P, P - 1, one
+    // set per rhs; every coefficient is computed once and used for each rhs.
     float2 kprev[3][3], kcur[3][3];
 #pragma unroll
     for (int oy = 0; oy < 3; ++oy)
 #pragma unroll
         for (int ox = 0; ox < 3; ++ox) kprev[oy][ox] = bc(0.f);
-    float2 accL = bc(0.f), accM = bc(0.f), accU = bc(0.f);
+    float2 accL[RPC], accM[RPC], accU[RPC];
+#pragma unroll
+    for (int q = 0; q < RPC; ++q) accL[q] = accM[q] = accU[q] = bc(0.f);
     auto coef = [&](int oz, int oy, int ox, float2 ks) -> float2 {
         const int sh = (oz != 1) + (oy != 1) + (ox != 1);
         return (sh == 0) ? fma2(m0, ks, cc0) : fma2(mf[sh], ks, ncf[sh]);
@@ -336,42 +377,62 @@ stream3d_pair_kernel(const __grid_constant__ Stream3Maps maps, int iu, int ium,
                        kU = decltype(doU)::value;
 #pragma unroll
         for (int oy = 0; oy < 3; ++oy) {
-            float2 uv[3];
-            load_u(uv, st, oy);
+            float2 uv[RPC][3];
+#pragma unroll
+            for (int q = 0; q < RPC; ++q) load_u(uv[q], st + q * kHaloStride, oy);
 #pragma unroll
             for (int ox = 0; ox < 3; ++ox) {
-                if (kL) accL = fma2(coef(0, oy, ox, kcur[oy][ox]), uv[ox], accL);
-                if (kM) accM = fma2(coef(1, oy, ox, add2(kprev[oy][ox], kcur[oy][ox])), uv[ox], accM);
-                if (kU) accU = fma2(coef(2, oy, ox, kprev[oy][ox]), uv[ox], accU);
+                if (kL) {
+                    const float2 cL = coef(0, oy, ox, kcur[oy][ox]);
+#pragma unroll
+                    for (int q = 0; q < RPC; ++q) accL[q] = fma2(cL, uv[q][ox], accL[q]);
+                }
+                if (kM) {
+                    const float2 cM = coef(1, oy, ox, add2(kprev[oy][ox], kcur[oy][ox]));
+#pragma unroll
+                    for (int q = 0; q < RPC; ++q) accM[q] = fma2(cM, uv[q][ox], accM[q]);
+                }
+                if (kU) {
+                    const float2 cU = coef(2, oy, ox, kprev[oy][ox]);
+#pragma unroll
+                    for (int q = 0; q < RPC; ++q) accU[q] = fma2(cU, uv[q][ox], accU[q]);
+                }
             }
         }
     };
     // node plane of stored plane `sn` complete: update, store, outputs
-    auto finish = [&](const float *sn, float2 acc) {
-        const float *nd = sn + 2 * kHaloStride + no;
+    auto finish = [&](const float *sn) {
+        const float *nd = sn + (RPC + 1) * kHaloStride + no;
         const float2 d = *reinterpret_cast<const float2 *>(nd);
-        const float2 fr = *reinterpret_cast<const float2 *>(nd + kNodeElems);
-        const float2 fi = *reinterpret_cast<const float2 *>(nd + 2 * kNodeElems);
-        const float2 uprev = *reinterpret_cast<const float2 *>(nd + 3 * kNodeElems);
-        const float2 g = fma2(a2, fr, mul2(nb2, fi));
-        const float2 t = fma2(ntwo, uprev, add2(acc, g));
-        const float2 unew = fma2(d, t, uprev);
-        if (actB) {
-            *reinterpret_cast<float2 *>(ump) = unew;
-        } else if (actA) {
-            *ump = unew.x;
-        }
-        if (flags && actA) {
-            if ((flags & 1) && slot->snap_part) {
-                slot->snap_part[2 * cidx] = (double)unew.x;
-                if (actB) slot->snap_part[2 * cidx + 2] = (double)unew.y;
+#pragma unroll
+        for (int q = 0; q < RPC; ++q) {
+            const float *nq = nd + kNodeElems + q * 3 * kNodeElems;
+            const float2 fr = *reinterpret_cast<const float2 *>(nq);
+            const float2 fi = *reinterpret_cast<const float2 *>(nq + kNodeElems);
+            const float2 uprev = *reinterpret_cast<const float2 *>(nq + 2 * kNodeElems);
+            const float2 g = fma2(a2, fr, mul2(nb2, fi));
+            const float2 t = fma2(ntwo, uprev, add2(accU[q], g));
+            const float2 unew = fma2(d, t, uprev);
+            if (q < nr) {
+                if (actB) {
+                    *reinterpret_cast<float2 *>(ump[q]) = unew;
+                } else if (actA) {
+                    *ump[q] = unew.x;
+                }
+                if (flags && actA) {
+                    const OutSlot *sl = slot + rr[q];
+                    if ((flags & 1) && sl->snap_part) {
+                        sl->snap_part[2 * cidx] = (double)unew.x;
+                        if (actB) sl->snap_part[2 * cidx + 2] = (double)unew.y;
+                    }
+                    if ((flags & 2) && sl->final_part) {
+                        sl->final_part[2 * cidx] = (double)unew.x;
+                        if (actB) sl->final_part[2 * cidx + 2] = (double)unew.y;
+                    }
+                }
             }
-            if ((flags & 2) && slot->final_part) {
-                slot->final_part[2 * cidx] = (double)unew.x;
-                if (actB) slot->final_part[2 * cidx + 2] = (double)unew.y;
-            }
+            ump[q] += L.plane;
         }
-        ump += L.plane;
         cidx += cstride;
     };
 
@@ -384,7 +445,7 @@ stream3d_pair_kernel(const __grid_constant__ Stream3Maps maps, int iu, int ium,
     bool ok = true;
     for (int p = 0; p < nplanes; ++p) {
         if (!(ok = full_wait_next())) break;
-        const float *st = ring + (p % NS) * kStageElems;
+        const float *st = ring + (p % NS) * kSE;
         if (p < nplanes - 1) load_k(kcur, st);
         const bool hL = p <= nplanes - 3, hM = p >= 1 && p <= nplanes - 2, hU = p >= 2;
         if (hL && hM && hU) push(st, T_{}, T_{}, T_{});
@@ -394,11 +455,14 @@ stream3d_pair_kernel(const __grid_constant__ Stream3Maps maps, int iu, int ium,
         else if (hL) push(st, T_{}, F_{}, F_{});
         else if (hM) push(st, F_{}, T_{}, F_{});
         else push(st, F_{}, F_{}, T_{});
-        if (hU) finish(ring + ((p - 1) % NS) * kStageElems, accU);
+        if (hU) finish(ring + ((p - 1) % NS) * kSE);
         if (p >= 1) release_next();
-        accU = accM;
-        accM = accL;
-        accL = bc(0.f);
+#pragma unroll
+        for (int q = 0; q < RPC; ++q) {
+            accU[q] = accM[q];
+            accM[q] = accL[q];
+            accL[q] = bc(0.f);
+        }
 #pragma unroll
         for (int oy = 0; oy < 3; ++oy)
 #pragma unroll
@@ -408,9 +472,10 @@ stream3d_pair_kernel(const __grid_constant__ Stream3Maps maps, int iu, int ium,
 
 }  // namespace
 
-size_t stream3d_pair_smem_bytes(int stages)
+size_t stream3d_pair_smem_bytes(int stages, int rpc)
 {
-    return (size_t)stages * kStageElems * sizeof(float) + 2 * stages * sizeof(uint64_t);
+    const int se = (rpc == 2) ? stage_elems<2>() : stage_elems<1>();
+    return (size_t)stages * se * sizeof(float) + 2 * stages * sizeof(uint64_t);
 }
 
 bool make_stream3d_pair_maps(const Layout &L, float *const planes[6], Stream3Maps *maps, int nrhs)
@@ -449,24 +514,27 @@ bool make_stream3d_pair_maps(const Layout &L, float *const planes[6], Stream3Map
             CUDA_SUCCESS)
             return false;
     }
-    return cudaFuncSetAttribute(stream3d_pair_kernel<7>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)stream3d_pair_smem_bytes(7)) == cudaSuccess &&
-           cudaFuncSetAttribute(stream3d_pair_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)stream3d_pair_smem_bytes(6)) == cudaSuccess &&
-           cudaFuncSetAttribute(stream3d_pair_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)stream3d_pair_smem_bytes(5)) == cudaSuccess &&
-           cudaFuncSetAttribute(stream3d_pair_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)stream3d_pair_smem_bytes(4)) == cudaSuccess;
+    const int smem_attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    return cudaFuncSetAttribute(stream3d_pair_kernel<7, 1>, (cudaFuncAttribute)smem_attr,
+                                (int)stream3d_pair_smem_bytes(7, 1)) == cudaSuccess &&
+           cudaFuncSetAttribute(stream3d_pair_kernel<6, 1>, (cudaFuncAttribute)smem_attr,
+                                (int)stream3d_pair_smem_bytes(6, 1)) == cudaSuccess &&
+           cudaFuncSetAttribute(stream3d_pair_kernel<5, 1>, (cudaFuncAttribute)smem_attr,
+                                (int)stream3d_pair_smem_bytes(5, 1)) == cudaSuccess &&
+           cudaFuncSetAttribute(stream3d_pair_kernel<4, 1>, (cudaFuncAttribute)smem_attr,
+                                (int)stream3d_pair_smem_bytes(4, 1)) == cudaSuccess &&
+           cudaFuncSetAttribute(stream3d_pair_kernel<4, 2>, (cudaFuncAttribute)smem_attr,
+                                (int)stream3d_pair_smem_bytes(4, 2)) == cudaSuccess;
 }
 
-int stream3d_pair_zchunk(const Layout &L, int stages)
+int stream3d_pair_zchunk(const Layout &L, int stages, int rpc)
 {
     int dev = 0, nsm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int64_t tiles = ((L.nx + kTX - 1) / kTX) * ((L.ny + kTY - 1) / kTY);
     int64_t zc = 64;
-    const int per_sm = stages <= 5 ? 3 : 2;
+    const int per_sm = (rpc == 2 || stages >= 6) ? 2 : 3;
     while (zc > 16 && tiles * ((L.nz + zc - 1) / zc) < per_sm * nsm) zc /= 2;
     if (zc > L.nz) zc = L.nz;
     return (int)zc;
@@ -475,23 +543,27 @@ int stream3d_pair_zchunk(const Layout &L, int stages)
 void launch_stream3d_pair(const Stream3Maps &maps, int from, const Layout &L, float *um,
                           const StepCoef<float> &C, float a, float b, const OutSlot *slot,
                           int flags, int zchunk, int stages, int *err, cudaStream_t s,
-                          const RhsSet &R, bool overlap)
+                          const RhsSet &R, bool overlap, int rpc)
 {
     const int iu = from ? 1 : 0, ium = from ? 6 : 7;
-    dim3 grd((unsigned)(((L.nx + kTX - 1) / kTX) * R.slots), (unsigned)((L.ny + kTY - 1) / kTY),
+    const int groups = (rpc == 2) ? (R.slots + 1) / 2 : R.slots;
+    dim3 grd((unsigned)(((L.nx + kTX - 1) / kTX) * groups), (unsigned)((L.ny + kTY - 1) / kTY),
              (unsigned)((L.nz + zchunk - 1) / zchunk));
-    if (stages == 7)
-        launch_ex(stream3d_pair_kernel<7>, grd, kThreads + 32, stream3d_pair_smem_bytes(7), s,
-                  overlap, maps, iu, ium, um, L, C, a, b, slot, flags, zchunk, err, R);
+    if (rpc == 2)
+        launch_ex(stream3d_pair_kernel<4, 2>, grd, kThreads + 32, stream3d_pair_smem_bytes(4, 2),
+                  s, overlap, maps, iu, ium, um, L, C, a, b, slot, flags, zchunk, err, R);
+    else if (stages == 7)
+        launch_ex(stream3d_pair_kernel<7, 1>, grd, kThreads + 32, stream3d_pair_smem_bytes(7, 1),
+                  s, overlap, maps, iu, ium, um, L, C, a, b, slot, flags, zchunk, err, R);
     else if (stages == 5)
-        launch_ex(stream3d_pair_kernel<5>, grd, kThreads + 32, stream3d_pair_smem_bytes(5), s,
-                  overlap, maps, iu, ium, um, L, C, a, b, slot, flags, zchunk, err, R);
+        launch_ex(stream3d_pair_kernel<5, 1>, grd, kThreads + 32, stream3d_pair_smem_bytes(5, 1),
+                  s, overlap, maps, iu, ium, um, L, C, a, b, slot, flags, zchunk, err, R);
     else if (stages == 4)
-        launch_ex(stream3d_pair_kernel<4>, grd, kThreads + 32, stream3d_pair_smem_bytes(4), s,
-                  overlap, maps, iu, ium, um, L, C, a, b, slot, flags, zchunk, err, R);
+        launch_ex(stream3d_pair_kernel<4, 1>, grd, kThreads + 32, stream3d_pair_smem_bytes(4, 1),
+                  s, overlap, maps, iu, ium, um, L, C, a, b, slot, flags, zchunk, err, R);
     else
-        launch_ex(stream3d_pair_kernel<6>, grd, kThreads + 32, stream3d_pair_smem_bytes(6), s,
-                  overlap, maps, iu, ium, um, L, C, a, b, slot, flags, zchunk, err, R);
+        launch_ex(stream3d_pair_kernel<6, 1>, grd, kThreads + 32, stream3d_pair_smem_bytes(6, 1),
+                  s, overlap, maps, iu, ium, um, L, C, a, b, slot, flags, zchunk, err, R);
     ++g_launches;
 }
 

@@ -60,8 +60,8 @@ class Options(ctypes.Structure):
                 ("stencil_gamma", ctypes.c_double), ("tblock", ctypes.c_int),
                 ("tb_rows", ctypes.c_int), ("tb_form", ctypes.c_int),
                 ("s3_kernel", ctypes.c_int), ("s3_stages", ctypes.c_int),
-                ("s3_zchunk", ctypes.c_int), ("launch", ctypes.c_int),
-                ("wait_limit_ns", ctypes.c_longlong)]
+                ("s3_zchunk", ctypes.c_int), ("s3_rhs_per_cta", ctypes.c_int),
+                ("launch", ctypes.c_int), ("wait_limit_ns", ctypes.c_longlong)]
 
 
 class Params(ctypes.Structure):
@@ -72,7 +72,7 @@ class Params(ctypes.Structure):
                 ("nP", ctypes.c_int), ("T", ctypes.c_int), ("steps", ctypes.c_longlong),
                 ("steps_per_launch", ctypes.c_int), ("tile", ctypes.c_int * 3),
                 ("ctas_per_sm", ctypes.c_int), ("waves", ctypes.c_int),
-                ("step_kernel", ctypes.c_int)]
+                ("step_kernel", ctypes.c_int), ("rhs_per_cta", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "tile"}
@@ -412,7 +412,7 @@ def htd_status_string(status: int) -> str:
 # ---- convenience object ------------------------------------------------------
 
 KERNEL_FIELDS = ("tb_rows", "tb_form", "s3_kernel", "s3_stages", "s3_zchunk", "launch",
-                 "wait_limit_ns")
+                 "wait_limit_ns", "s3_rhs_per_cta")
 
 
 def make_options(prob=None, precision: str = "fp64", mode: str = "table1",

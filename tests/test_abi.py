@@ -45,8 +45,9 @@ def test_struct_layouts_match_header(tmp_path):
         " offsetof(htd_solve_info, hist), offsetof(htd_params, nP), offsetof(htd_options, damping),"
         " offsetof(htd_options, stencil_a), offsetof(htd_options, stencil_gamma),"
         " offsetof(htd_options, tblock));"
-        "printf(\"%zu %zu %zu\\n\", offsetof(htd_options, s3_kernel),"
-        " offsetof(htd_options, launch), offsetof(htd_options, wait_limit_ns));"
+        "printf(\"%zu %zu %zu %zu %zu\\n\", offsetof(htd_options, s3_kernel),"
+        " offsetof(htd_options, launch), offsetof(htd_options, wait_limit_ns),"
+        " offsetof(htd_options, s3_rhs_per_cta), offsetof(htd_params, rhs_per_cta));"
         "return 0;}\n")
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
@@ -58,14 +59,16 @@ def test_struct_layouts_match_header(tmp_path):
             htd.Options.damping.offset, htd.Options.stencil_a.offset,
             htd.Options.stencil_gamma.offset, htd.Options.tblock.offset,
             htd.Options.s3_kernel.offset, htd.Options.launch.offset,
-            htd.Options.wait_limit_ns.offset]
+            htd.Options.wait_limit_ns.offset, htd.Options.s3_rhs_per_cta.offset,
+            htd.Params.rhs_per_cta.offset]
     assert got == want
 
 
 @pytest.mark.parametrize("field,value", [("tb_rows", 7), ("tb_rows", -1), ("tb_form", 4),
                                          ("tb_form", -1), ("s3_kernel", 5), ("s3_kernel", -1),
                                          ("s3_stages", 3), ("s3_stages", 8), ("s3_zchunk", -1),
-                                         ("launch", 4), ("wait_limit_ns", -1)])
+                                         ("launch", 4), ("wait_limit_ns", -1),
+                                         ("s3_rhs_per_cta", 3), ("s3_rhs_per_cta", -1)])
 def test_plan_rejects_bad_kernel_selection(field, value):
     """The kernel-selection fields of htd_options are validated on the host,
     like every other option (HTD_ERR_ARG)."""

@@ -205,8 +205,10 @@ def test_group_launch_solve_equals_single_solves():
     counts run by the group launch (systems leave the batch at different
     iterations, so the group's slots go idle one by one): the same iterations
     and the same solutions bit for bit as htd_gmres_solve per handle."""
-    sizes = [(64, 61), (101, 101), (150, 97), (37, 190), (200, 200)]
-    probs = [het_problem(2, n, T=T) for n, T in zip(sizes, [4, 6, 5, 8, 9])]
+    # five 2-D instances of the batched workload's recipe (smooth random c, a
+    # layer of 4 % of the side, T = side in wavelengths), sides 60 .. 200
+    probs = W.config_batched(n3=12, nsrc=1, ninst=5, side_lo=60, side_hi=200).probs[1:]
+    assert len({p.n for p in probs}) > 1
     solvers = [htd.Solver(p, precision="mixed", restart=10) for p in probs]
     b = htd.Batch(solvers, [1] * len(solvers))
     Us, infos = b.solve([dev(p.F[None]) for p in probs], tol=1e-7, max_iters=300)
@@ -219,4 +221,45 @@ def test_group_launch_solve_equals_single_solves():
         its.append(info["iterations"])
         assert np.array_equal(host(U)[0], host(U1))
     assert len(set(its)) > 1
+    b.close()
+
+
+@pytest.mark.parametrize("nrhs", [2, 5, 6])
+def test_two_rhs_per_cta_equals_one(nrhs):
+    """The streamed 3-D pair kernel with two right-hand sides per CTA (q*kappa, d
+    and every stencil coefficient loaded or computed once for both) gives each
+    right-hand side the bits of one-per-CTA launches and of the handle's own
+    single application; an odd count leaves the last CTA with one, and a
+    handle with six slots carrying fewer leaves slots idle."""
+    p = het_problem(3, (45, 37, 29), T=2)
+    s1 = htd.Solver(p, precision="mixed", max_rhs=6, s3_rhs_per_cta=1)
+    s2 = htd.Solver(p, precision="mixed", max_rhs=6, s3_rhs_per_cta=2)
+    assert s1.params["rhs_per_cta"] == 1 and s2.params["rhs_per_cta"] == 2
+    assert s1.params["step_kernel"] == s2.params["step_kernel"] == 2
+    F = rhs_stack(p, nrhs, 90)
+    b1 = htd.Batch([s1], [nrhs])
+    b2 = htd.Batch([s2], [nrhs])
+    for rep in range(2):
+        U1 = host(b1.precond([dev(F)])[0])
+        U2 = host(b2.precond([dev(F)])[0])
+        assert np.array_equal(U1, U2), rel_l2(U1.reshape(-1), U2.reshape(-1))
+    for r in range(nrhs):
+        assert np.array_equal(U2[r], host(s1.precond(dev(F[r]))))
+    b1.close()
+    b2.close()
+
+
+def test_rhs_per_cta_is_tuned_for_multi_rhs_handles():
+    """A 3-D handle with several right-hand sides times one and two per CTA at
+    create and reports its choice; a one-rhs handle uses one."""
+    p = het_problem(3, (64, 48, 40), T=2)
+    s = htd.Solver(p, precision="mixed", max_rhs=8)
+    assert s.params["rhs_per_cta"] in (1, 2)
+    s1 = htd.Solver(p, precision="mixed")
+    assert s1.params["rhs_per_cta"] == 1
+    F = rhs_stack(p, 8, 120)
+    b = htd.Batch([s], [8])
+    Ub = host(b.precond([dev(F)])[0])
+    for r in (0, 7):
+        assert np.array_equal(Ub[r], host(s1.precond(dev(F[r]))))
     b.close()

@@ -31,6 +31,8 @@ Printed (one JSON line on rank 0):
   batched     the 96-system batched workload solved in lockstep, and the same
               systems solved one at a time;
   adjoint     the two gradients of the 512^2, 8-source adjoint configuration;
+  projection  one application with the windowed projection read-out against
+              Table 1 (2-D 1001^2 and 3-D 256^3) and the window's cost per step;
   cpu_baseline the FP64 CPU oracle on a bounded sample of the same workload,
               on one core and on all host cores (independent copies);
   clocks, gpu_launches  SM clocks sampled during the timed region; kernels
@@ -136,6 +138,8 @@ def parse_args(argv=None):
     ap.add_argument("--restart", type=int, default=20)
     ap.add_argument("--batched", type=int, default=1,
                     help="also time the batched workload (96 systems, lockstep FGMRES)")
+    ap.add_argument("--projection", type=int, default=1,
+                    help="also time one application in projection mode against Table 1")
     ap.add_argument("--adjoint", type=int, default=1,
                     help="also time the gradients of the adjoint configuration (512^2, 8 sources)")
     ap.add_argument("--secondary-2d", type=int, default=1,
@@ -422,6 +426,46 @@ def secondary_2d(htd, stream, flush, pk, reps=5, fp64=True):
     return out
 
 
+def secondary_projection(htd, stream, flush):
+    """Projection read-out against Table 1: one preconditioner application in
+    each mode (mixed precision, proj_periods = 1, so the window is the last
+    n_P steps) on the 2-D 1001^2 and the 3-D 256^3 workloads, three timed
+    applications each after one warm-up (CUDA events, L2 flushed before each).
+    window_cost_vs_table1_steps = (t_project - t_table1) / n_P steps, divided by
+    Table 1's time per step."""
+    import torch
+    out = {}
+    for name in ("2d_grf_1001", "3d_layered_256"):
+        p, _ = make_workload(name)
+        F = torch.from_numpy(np.ascontiguousarray(p.F)).cuda()
+        U = torch.zeros_like(F)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        res = {}
+        for mode in ("table1", "project"):
+            s = htd.Solver(p, precision="mixed", mode=mode, restart=1)
+            prm = s.params
+            times = []
+            for r in range(4):
+                flush.fill_(8)
+                e0.record(stream)
+                htd.htd_apply_precond(s.handle, F, U, stream)
+                e1.record(stream)
+                e1.synchronize()
+                if r > 0:
+                    times.append(e0.elapsed_time(e1))
+            s.close()
+            res[mode] = statistics.mean(times)
+        steps, nP = prm["steps"], prm["nP"]
+        per_step = res["table1"] / steps
+        out[name] = {"table1_ms": res["table1"], "project_ms": res["project"],
+                     "steps": steps, "window_steps": nP,
+                     "window_cost_vs_table1_steps": (res["project"] - res["table1"]) / nP / per_step
+                     + 1.0}
+        del F, U
+    return out
+
+
 def secondary_batched(htd, stream, flush, sub_rhs=4, sub_inst=4):
     """Batched workload: the 3-D layered model at 128^3 with 32 seeded point sources
     as 32 right-hand sides of one handle, plus 64 2-D instances with sides uniform in
@@ -461,9 +505,12 @@ def secondary_batched(htd, stream, flush, sub_rhs=4, sub_inst=4):
             for _ in range(F.shape[0]):
                 ups += p.N * infos[k]["steps"]
                 k += 1
+        desc = b.describe()
+        desc["rhs_per_cta_3d"] = [sv.params["rhs_per_cta"] for sv in solvers if sv.prob.ndim == 3]
         b.close()
         for sv in solvers:
             sv.close()
+        run.desc = desc
         return min(times), ups, infos
 
     def sequential(probs, Fs):
@@ -491,6 +538,7 @@ def secondary_batched(htd, stream, flush, sub_rhs=4, sub_inst=4):
         return total, ups
 
     ms, ups, infos = run("mixed", setup.probs, setup.F, 1)
+    desc = run.desc
     its = [i["iterations"] for i in infos]
     seq_ms, seq_ups = sequential(setup.probs, setup.F)
     sub_p = setup.probs[:1 + sub_inst]
@@ -503,7 +551,14 @@ def secondary_batched(htd, stream, flush, sub_rhs=4, sub_inst=4):
             "value": ups / (ms * 1e-3) / 1e9, "unit": UNIT, "time_to_tol_ms": ms,
             "iterations_min": min(its), "iterations_max": max(its),
             "rel_res_true_max": max(i["rel_res_true"] for i in infos),
-            "graph": "one launch per preconditioner round (65 child graphs)",
+            "graph": "one graph launch per preconditioner round",
+            "form": {1: "every handle's step sequence as a child graph",
+                     2: "the 2-D handles as one persistent launch beside the 3-D handle's graph"}
+            .get(desc["form"], "undecided"),
+            "ns_per_update_plain": desc["ns_per_update_plain"],
+            "ns_per_update_group": desc["ns_per_update_group"],
+            "grouped_handles": desc["grouped"],
+            "rhs_per_cta_3d": desc["rhs_per_cta_3d"],
             "sequential": {"time_ms": seq_ms, "value": seq_ups / (seq_ms * 1e-3) / 1e9,
                            "what": "the same 96 systems solved one at a time, device time "
                                    "summed (first solve of each handle untimed)"},
@@ -767,6 +822,9 @@ def run_ours(args):
     adjoint = None
     if args.adjoint:
         adjoint = secondary_adjoint(htd, stream)
+    projection = None
+    if args.projection:
+        projection = secondary_projection(htd, stream, flush)
 
     cpu = None
     if rank == 0 and world == 1 and args.cpu_sample_s > 0:
@@ -799,6 +857,7 @@ def run_ours(args):
             "secondary_2d": sec2d,
             "batched": batched,
             "adjoint": adjoint,
+            "projection": projection,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk,

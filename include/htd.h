@@ -157,7 +157,10 @@ typedef struct {
     int launch;        /* bit flags: HTD_LAUNCH_NO_OVERLAP (consecutive step
                           launches do not overlap by programmatic dependent
                           launch), HTD_LAUNCH_NO_GRAPH (steps launched one by one
-                          instead of replaying a captured CUDA graph) */
+                          instead of replaying a captured CUDA graph),
+                          HTD_LAUNCH_NO_GROUP (in a batch, this handle keeps its
+                          own step sequence instead of joining the persistent
+                          launch of the batch's 2-D handles) */
     long long wait_limit_ns; /* bound of the device-side waits between the row
                           groups of the blocked 2-D kernel; 0 = 1 s.  A wait that
                           runs out makes the call return HTD_ERR_TIMEOUT (see
@@ -167,7 +170,7 @@ typedef struct {
 enum { HTD_TB_ANY = 0, HTD_TB_COLUMN = 1, HTD_TB_PAIR = 2, HTD_TB_PAIR_SD = 3 };
 enum { HTD_S3_PAIR = 0, HTD_S3_ZMARCH = 1, HTD_S3_NODE_32x8 = 2, HTD_S3_NODE_64x4 = 3,
        HTD_S3_NODE_128x2 = 4 };
-enum { HTD_LAUNCH_NO_OVERLAP = 1, HTD_LAUNCH_NO_GRAPH = 2 };
+enum { HTD_LAUNCH_NO_OVERLAP = 1, HTD_LAUNCH_NO_GRAPH = 2, HTD_LAUNCH_NO_GROUP = 4 };
 
 typedef struct {
     int iterations;           /* Arnoldi steps taken */
@@ -427,15 +430,16 @@ htd_status htd_batch_destroy(htd_batch b);
 /*
  * U_i[r] = P_i F_i[r] for every system: F_dev[i], U_dev[i] are complex128
  * [nrhs[i]][N_i] (device, distinct).  One application of every preconditioner
- * (both runs in mode EXACT) as one CUDA-graph launch per run.  When at least
- * two handles are 2-D with FP32 recurrence (I_acd, Table 1 or exact read-out),
- * they run as ONE persistent launch: a queue of tasks (level = 8 steps,
- * handle, rhs slot, tile) of the blocked kernel's work, ordered by level, each
- * tile starting a level once its 3 x 3 tile neighbourhood has finished the
- * previous one; the other handles' captured step sequences are child graphs
- * beside it, and each of their step kernels covers all right-hand sides of its
- * handle.  Every output equals the handle's own htd_apply_precond bit for bit.
- * Asynchronous on stream.
+ * (both runs in mode EXACT) as one CUDA-graph launch per run, in the batch's
+ * current form (htd_batch_desc): every handle's captured step sequence as a
+ * child graph, each step kernel covering all right-hand sides of its handle;
+ * or, when at least two handles are 2-D with FP32 recurrence (I_acd, Table 1
+ * or exact read-out), those handles as ONE persistent launch -- a queue of
+ * tasks (level = 8 steps, handle, rhs slot, tile) of the blocked kernel's
+ * work, ordered by level, each tile starting a level once its 3 x 3 tile
+ * neighbourhood has finished the previous one -- beside the other handles'
+ * sequences.  Every output equals the handle's own htd_apply_precond bit for
+ * bit in either form.  Asynchronous on stream.
  */
 htd_status htd_batch_apply_precond(htd_batch b, const void *const *F_dev, void *const *U_dev,
                                    void *stream);
@@ -480,17 +484,32 @@ htd_status htd_set_wait_limit(htd_handle h, long long limit_ns, int stall_test);
 void htd_test_fail_alloc(long long after);
 
 /* How a batch runs its preconditioner applications (filled after the first
- * application or solve; zeros before). */
+ * application or solve; zeros before).  A batch with a group of 2-D handles
+ * has two forms of a run that give the same bits: every handle's own step
+ * sequence as a child graph (plain), or the group's persistent launch beside
+ * the other handles' sequences (group).  The first two rounds of a solve run
+ * one form each; the one with the smaller device time per point update is
+ * kept for the batch from then on. */
 typedef struct {
     int instances;           /* handles in the batch */
     int systems;             /* (handle, right-hand side) pairs */
-    int grouped;             /* 2-D FP32 handles run by the one persistent launch
-                                (0: every handle runs its own step sequence) */
+    int grouped;             /* 2-D FP32 handles the persistent launch would run
+                                (0: no group) */
     int group_ctas;          /* persistent CTAs of that launch */
     long long group_tasks;   /* its tasks per run: levels x tiles x rhs slots */
     int group_steps_per_task; /* recurrence steps per task (the blocked depth B) */
+    int form;                /* 0 not yet decided, 1 plain, 2 group */
+    double ns_per_update_plain; /* device time per point update of the timed round
+                                   in each form (0 until timed) */
+    double ns_per_update_group;
 } htd_batch_desc;
 htd_status htd_batch_describe(htd_batch b, htd_batch_desc *out);
+
+/* Set the batch's form: 0 = decide by timing the first rounds of the next
+ * solve (the default), 1 = every handle's own step sequence, 2 = the group's
+ * persistent launch (HTD_ERR_ARG if the batch has no group).  Either form
+ * gives the same bits. */
+htd_status htd_batch_set_form(htd_batch b, int form);
 
 /* Static string for a status code. */
 const char *htd_status_string(htd_status s);

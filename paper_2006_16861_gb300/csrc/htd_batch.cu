@@ -86,10 +86,15 @@ struct htd_batch_s {
     cudaEvent_t tab_ev = nullptr;        // last copy of the table (guards tab_host)
     bool tab_pending = false;
     cudaEvent_t ev[2] = {nullptr, nullptr};
-    // one graph: the group launch and every other handle's step sequence as
-    // child graphs
-    cudaGraphExec_t exec = nullptr;
+    // two graphs of one run: every handle's step sequence as a child graph
+    // (exec_plain), or the group launch beside the other handles' sequences
+    // (exec); `form` is the one in use: 0 undecided (the first rounds of a
+    // solve time both), 1 plain, 2 group
+    cudaGraphExec_t exec = nullptr, exec_plain = nullptr;
     bool graph_tried = false;
+    int form = 0;
+    int round_form = 0;                  // form of the last round launched
+    double form_ms[3] = {0.0, 0.0, 0.0};
     // the persistent launch over the 2-D handles
     std::vector<char> in_group;          // per instance
     std::vector<int> group;              // instance indices, most levels first
@@ -110,6 +115,7 @@ void free_batch(htd_batch b)
 {
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->exec_plain) cudaGraphExecDestroy(b->exec_plain);
     void *gp[] = {b->ginst, b->glev, b->goff, b->gdone, b->gabort, b->ghead, b->gab};
     for (void *q : gp)
         if (q) cudaFree(q);
@@ -234,23 +240,49 @@ htd_status run_group(htd_batch b, cudaStream_t s)
     return HTD_OK;
 }
 
-// the batch graph: no dependencies between the children, so the group launch
-// and the other handles' step sequences may run concurrently
+// Instantiate a graph whose children (no dependencies between them, so they
+// may run concurrently) are the given graphs.
+htd_status make_parent(const std::vector<cudaGraph_t> &kids, cudaGraphExec_t *out)
+{
+    cudaGraph_t parent = nullptr;
+    HTD_CUDA(cudaGraphCreate(&parent, 0));
+    bool ok = true;
+    for (cudaGraph_t g : kids) {
+        cudaGraphNode_t node;
+        if (cudaGraphAddChildGraphNode(&node, parent, nullptr, 0, g) != cudaSuccess) {
+            ok = false;
+            break;
+        }
+    }
+    if (ok && cudaGraphInstantiate(out, parent, 0) != cudaSuccess) {
+        *out = nullptr;
+        ok = false;
+    }
+    cudaGraphDestroy(parent);
+    (void)cudaGetLastError();
+    return HTD_OK;
+}
+
+// The batch graphs: every handle's captured step sequence as a child graph
+// (the plain form), and, when the batch has a group of 2-D handles, the group
+// launch beside the other handles' sequences.  Both give the same bits; the
+// first rounds of a solve time them and the faster one is kept.
 htd_status build_graph(htd_batch b)
 {
     if (b->graph_tried) return HTD_OK;
     b->graph_tried = true;
     htd_status gst = build_group(b);
     if (gst != HTD_OK) return gst;
-    std::vector<cudaGraph_t> kids;
+    std::vector<cudaGraph_t> all, others;
     for (size_t i = 0; i < b->ctx.size(); ++i) {
-        if (b->in_group[i]) continue;
         cudaGraph_t g = htd::ctx_step_graph(b->ctx[i]);
         if (!g) return HTD_OK;               // no capture: run the handles one by one
-        kids.push_back(g);
+        all.push_back(g);
+        if (!b->in_group[i]) others.push_back(g);
     }
-    cudaGraph_t ggraph = nullptr;
+    if ((gst = make_parent(all, &b->exec_plain)) != HTD_OK) return gst;
     if (!b->group.empty()) {
+        cudaGraph_t ggraph = nullptr;
         cudaStream_t cs;
         HTD_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
@@ -262,29 +294,13 @@ htd_status build_graph(htd_batch b)
         }
         cudaStreamDestroy(cs);
         (void)cudaGetLastError();
-        if (!ok) {
-            if (ggraph) cudaGraphDestroy(ggraph);
-            return HTD_OK;
+        if (ok) {
+            others.push_back(ggraph);
+            if ((gst = make_parent(others, &b->exec)) != HTD_OK) return gst;
         }
-        kids.push_back(ggraph);
+        if (ggraph) cudaGraphDestroy(ggraph);  // the parent holds its own copy
     }
-    cudaGraph_t parent = nullptr;
-    HTD_CUDA(cudaGraphCreate(&parent, 0));
-    bool ok = true;
-    for (cudaGraph_t g : kids) {
-        cudaGraphNode_t node;
-        if (cudaGraphAddChildGraphNode(&node, parent, nullptr, 0, g) != cudaSuccess) {
-            ok = false;
-            break;
-        }
-    }
-    if (ok && cudaGraphInstantiate(&b->exec, parent, 0) != cudaSuccess) {
-        b->exec = nullptr;
-        ok = false;
-    }
-    cudaGraphDestroy(parent);
-    if (ggraph) cudaGraphDestroy(ggraph);      // the parent holds its own copy
-    (void)cudaGetLastError();
+    if (!b->exec) b->form = 1;               // no group: the plain form only
     return HTD_OK;
 }
 
@@ -347,12 +363,17 @@ htd_status precond_round(htd_batch b, const std::vector<char> &sel,
             }
         }
         if (!any) continue;
-        if (b->exec) {
-            HTD_CUDA(cudaGraphLaunch(b->exec, s));
+        // undecided: the plain form first, then the group form
+        const int use = (b->form != 0) ? b->form : (b->form_ms[1] == 0.0 ? 1 : 2);
+        cudaGraphExec_t ex = (use == 2) ? b->exec : b->exec_plain;
+        if (ex) {
+            HTD_CUDA(cudaGraphLaunch(ex, s));
+            b->round_form = use;
             for (int i = 0; i < ninst; ++i)
-                if (!b->in_group[i]) htd::g_launches += b->ci[i].nsteps;
-            if (!b->group.empty()) htd::g_launches += 1;
+                if (use == 1 || !b->in_group[i]) htd::g_launches += b->ci[i].nsteps;
+            if (use == 2) htd::g_launches += 1;
         } else {
+            b->round_form = 0;
             for (int i = 0; i < ninst; ++i) {
                 const bool on = !idx[i].empty() && run < b->ci[i].runs;
                 if (!on || b->in_group[i]) continue;
@@ -511,6 +532,18 @@ htd_status batch_gmres(htd_batch b, const void *const *F_dev, void *const *U_dev
         }
         if (any_second && (st = fetch_blocks(b, s)) != HTD_OK) return st;
         const double ms = round_ms(b);
+        if (b->form == 0 && b->round_form != 0) {
+            // the form choice: device time per point update of this round
+            double upd = 0.0;
+            for (size_t k = 0; k < ns; ++k)
+                if (sel[k]) {
+                    const htd::CtxInfo &ci = b->ci[b->sys[k].inst];
+                    upd += (double)b->sys[k].N * (double)ci.nsteps * ci.runs;
+                }
+            if (upd > 0.0 && ms > 0.0) b->form_ms[b->round_form] = 1e6 * ms / upd;   // ns per update
+            if (b->form_ms[1] > 0.0 && b->form_ms[2] > 0.0)
+                b->form = (b->form_ms[2] < b->form_ms[1]) ? 2 : 1;
+        }
 
         // ---- Givens update on the host; finished cycles update U -------------
         bool any_y = false;
@@ -655,6 +688,21 @@ htd_status htd_batch_describe(htd_batch b, htd_batch_desc *out)
         out->group_tasks = b->gsched.ntasks;
         out->group_steps_per_task = b->gplan.B;
     }
+    out->form = b->form;
+    out->ns_per_update_plain = b->form_ms[1];
+    out->ns_per_update_group = b->form_ms[2];
+    return HTD_OK;
+}
+
+htd_status htd_batch_set_form(htd_batch b, int form)
+{
+    if (!b || form < 0 || form > 2) return HTD_ERR_ARG;
+    htd_status st = build_graph(b);
+    if (st != HTD_OK) return st;
+    if (form == 2 && !b->exec) return HTD_ERR_ARG;
+    if (form == 1 && !b->exec_plain) return HTD_ERR_ARG;
+    b->form = form;
+    if (form == 0) b->form_ms[1] = b->form_ms[2] = 0.0;
     return HTD_OK;
 }
 

@@ -978,7 +978,8 @@ htd_status plan_impl(const htd_grid *grid, const double *c_cell, const double *R
     if (opt.s3_stages != 0 && (opt.s3_stages < 4 || opt.s3_stages > 7)) return HTD_ERR_ARG;
     if (opt.s3_zchunk < 0 || opt.s3_zchunk > (1 << 24)) return HTD_ERR_ARG;
     if (opt.s3_rhs_per_cta < 0 || opt.s3_rhs_per_cta > 2) return HTD_ERR_ARG;
-    if (opt.launch & ~(HTD_LAUNCH_NO_OVERLAP | HTD_LAUNCH_NO_GRAPH)) return HTD_ERR_ARG;
+    if (opt.launch & ~(HTD_LAUNCH_NO_OVERLAP | HTD_LAUNCH_NO_GRAPH | HTD_LAUNCH_NO_GROUP))
+        return HTD_ERR_ARG;
     if (opt.wait_limit_ns < 0) return HTD_ERR_ARG;
     pl->opt = opt;
 
@@ -1416,6 +1417,7 @@ void ctx_dots(htd_ctx *c, const double2 *V, int64_t ldv, int kcount, const doubl
 bool ctx_group_view(htd_ctx *c, CtxGroupView *out)
 {
     if (c->d != 2 || c->opt.precision != HTD_MIXED || c->opt.integrator != HTD_ACD) return false;
+    if (c->opt.launch & HTD_LAUNCH_NO_GROUP) return false;
     if (c->opt.mode != HTD_MODE_TABLE1 && c->opt.mode != HTD_MODE_EXACT) return false;
     if (!c->u2 || !c->u3) return false;
     out->L = c->Lr;

@@ -638,6 +638,9 @@ void add_candidate(const Layout &L, std::vector<TbPlan> &out)
 
 // ---- one persistent launch for a group of 2-D instances ---------------------
 
+// queue offsets kept in shared memory up to these counts (global memory beyond)
+constexpr int kGroupMaxLevels = 1024, kGroupMaxInst = 256;
+
 __device__ __forceinline__ int ld_acquire_gpu(const int *p)
 {
     int v;
@@ -692,8 +695,11 @@ tb2d_group_kernel(GroupSched Q)
     __shared__ T s_a[kTbMaxSteps], s_b[kTbMaxSteps];
     __shared__ int s_flags[kTbMaxSteps];
     __shared__ uint64_t nbar[2][RG];
-    __shared__ int nabort, s_ok, s_nsub;
-    __shared__ long long s_task;
+    __shared__ int nabort, s_ok;
+    __shared__ long long s_task, s_next;
+    // the queue offsets, copied once per CTA (binary searches in shared memory)
+    __shared__ long long s_lev[kGroupMaxLevels + 1], s_off[kGroupMaxInst + 1];
+    __shared__ unsigned long long s_fenced;               // instances whose maps were acquired
 
     const int tid = threadIdx.x;
     const int wg = tid >> 5, wl = tid & 31;
@@ -701,11 +707,29 @@ tb2d_group_kernel(GroupSched Q)
         if (tid == 0) atomicExch(Q.abort, 1);
         return;
     }
+    const bool lev_in_smem = Q.nlev_max <= kGroupMaxLevels, off_in_smem = Q.ninst <= kGroupMaxInst;
+    if (lev_in_smem)
+        for (int i = tid; i <= Q.nlev_max; i += blockDim.x) s_lev[i] = Q.lev_off[i];
+    if (off_in_smem)
+        for (int i = tid; i <= Q.ninst; i += blockDim.x) s_off[i] = Q.inst_off[i];
+    if (tid == 0) {
+        s_fenced = 0ull;
+        long long t = Q.ntasks;
+        if (!*(volatile int *)Q.abort) t = (long long)atomicAdd(Q.head, 1ull);
+        s_next = t;
+    }
+    const long long *lev_off = lev_in_smem ? s_lev : Q.lev_off;
+    const long long *inst_off = off_in_smem ? s_off : Q.inst_off;
     for (;;) {
+        __syncthreads();
         if (tid == 0) {
-            long long t = Q.ntasks;
-            if (!*(volatile int *)Q.abort) t = (long long)atomicAdd(Q.head, 1ull);
+            // the task taken one round ahead; take the next one now, so that
+            // the queue's latency is hidden behind this task
+            const long long t = s_next;
             s_task = t;
+            long long n = Q.ntasks;
+            if (t < Q.ntasks && !*(volatile int *)Q.abort) n = (long long)atomicAdd(Q.head, 1ull);
+            s_next = n;
         }
         __syncthreads();
         const long long task = s_task;
@@ -716,25 +740,25 @@ tb2d_group_kernel(GroupSched Q)
         int lo = 0, hi = Q.nlev_max;
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
-            if (Q.lev_off[mid] <= task) lo = mid; else hi = mid;
+            if (lev_off[mid] <= task) lo = mid; else hi = mid;
         }
         const int k = lo;
-        const long long local = task - Q.lev_off[k];
+        const long long local = task - lev_off[k];
         lo = 0;
         hi = Q.ninst;
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
-            if (Q.inst_off[mid] <= local) lo = mid; else hi = mid;
+            if (inst_off[mid] <= local) lo = mid; else hi = mid;
         }
-        const GroupInst &I = Q.inst[lo];
+        const int inst = lo;
+        const GroupInst &I = Q.inst[inst];
         const int ntile = I.grid_x * I.grid_y;
-        const long long q = local - Q.inst_off[lo];
+        const long long q = local - inst_off[inst];
         const int slot_k = (int)(q / ntile), tile = (int)(q % ntile);
         const int bx = tile % I.grid_x, by = tile / I.grid_x;
         int *done = I.done + (size_t)slot_k * ntile;
         int rhs;
         if (!rhs_of_slot(I.R, slot_k, rhs)) {             // idle slot: nothing to compute
-            __syncthreads();
             if (tid == 0) st_release_gpu(&done[tile], k + 1);
             continue;
         }
@@ -753,68 +777,84 @@ tb2d_group_kernel(GroupSched Q)
         const float *fim = I.fim + rhs * I.R.stride;
         const OutSlot *slot = I.slot + rhs;
         const long long j0 = (long long)k * B;
+        const int nsub = (int)min((long long)B, I.nsteps - j0);
 
-        if (tid == 0) {
-            // the 3 x 3 tiles around have finished level k - 1 (bounded wait)
+        if (wg == 0) {
+            // the 3 x 3 tiles around have finished level k - 1: lane l < 9 polls
+            // tile (l % 3 - 1, l / 3 - 1) (bounded wait; all nine at once)
             int ok = 1;
             if (k > 0) {
-                unsigned long long lim = *reinterpret_cast<volatile const unsigned long long *>(I.err + 2);
-                if (lim == 0) lim = kDefaultWaitNs;
-                const unsigned long long t0 = global_ns();
-                for (int dy = -1; dy <= 1 && ok; ++dy)
-                    for (int dx = -1; dx <= 1 && ok; ++dx) {
-                        const int nx_ = bx + dx, ny_ = by + dy;
-                        if (nx_ < 0 || ny_ < 0 || nx_ >= I.grid_x || ny_ >= I.grid_y) continue;
-                        const int *cnt = &done[ny_ * I.grid_x + nx_];
-                        while (ld_acquire_gpu(cnt) < k) {
-                            if (*(volatile int *)Q.abort) { ok = 0; break; }
-                            if (global_ns() - t0 > lim) {
-                                atomicExch(I.err, 1);
-                                atomicExch(Q.abort, 1);
-                                ok = 0;
-                                break;
-                            }
-                        }
+                const int nx_ = bx + (wl % 3) - 1, ny_ = by + (wl / 3) - 1;
+                const bool mine = wl < 9 && nx_ >= 0 && ny_ >= 0 && nx_ < I.grid_x && ny_ < I.grid_y;
+                const int *cnt = mine ? &done[ny_ * I.grid_x + nx_] : nullptr;
+                unsigned long long lim = 0, t0 = 0;
+                bool waited = false;
+                for (;;) {
+                    const bool ready = !mine || ld_acquire_gpu(cnt) >= k;
+                    if (__all_sync(0xffffffffu, ready)) break;
+                    if (!waited) {
+                        waited = true;
+                        t0 = global_ns();
+                        lim = *reinterpret_cast<volatile const unsigned long long *>(I.err + 2);
+                        if (lim == 0) lim = kDefaultWaitNs;
                     }
-                fence_proxy_async_global();               // the halo written by others, for TMA
+                    const bool give_up = *(volatile int *)Q.abort || global_ns() - t0 > lim;
+                    if (__any_sync(0xffffffffu, give_up)) {
+                        if (wl == 0) {
+                            atomicExch(I.err, 1);
+                            atomicExch(Q.abort, 1);
+                        }
+                        ok = 0;
+                        break;
+                    }
+                }
+                // lanes 1 .. 8 acquired their tiles' counters; the warp barrier
+                // orders those acquires before lane 0's fence and copies
+                __syncwarp();
+                if (wl == 0) fence_proxy_async_global();   // the halo written by others, for TMA
             }
-            s_ok = ok;
-            const int nsub = (int)min((long long)B, I.nsteps - j0);
-            s_nsub = nsub;
-#pragma unroll
-            for (int qq = 0; qq < kTbMaxSteps; ++qq) {
-                const long long j = j0 + qq;
-                const bool in = qq < nsub;
-                s_a[qq] = in ? I.ab[j] : 0.f;
-                s_b[qq] = in ? I.ab[I.nsteps + j] : 0.f;
+            // the steps' forcing coefficients and output flags, one lane each
+            if (wl < kTbMaxSteps) {
+                const long long j = j0 + wl;
+                const bool in = wl < nsub;
+                s_a[wl] = in ? I.ab[j] : 0.f;
+                s_b[wl] = in ? I.ab[I.nsteps + j] : 0.f;
                 int fl = 0;
                 if (in && j + 1 == I.jim) fl |= 1;
                 if (in && j + 1 == I.jfin) fl |= 2;
-                s_flags[qq] = fl;
+                s_flags[wl] = fl;
             }
-            for (int qq = 0; qq < 2; ++qq)
-                for (int g = 0; g < RG; ++g)
-                    mbar_init(&nbar[qq][g], (unsigned)((g > 0) + (g < RG - 1)));
-            nabort = 0;
-            if (ok) {
-                // the tensor maps live in global memory (written by a host copy):
-                // acquire them for the tensor-map proxy before a copy uses them
-                const int used[4] = {4, 5, rp, rp + 1};
-                for (int qq = 0; qq < 4; ++qq)
-                    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
-                                     reinterpret_cast<uint64_t>(&I.maps.m[used[qq]]))
-                                 : "memory");
-                mbar_init(bar, 1);
-                mbar_expect_tx(bar, (unsigned)(kArrays * (size_t)(H + 2) * BW * sizeof(T)));
-                tma_load_2d(sk, &I.maps.m[4], xs, ys, bar);
-                if (SD) tma_load_2d(sd, &I.maps.m[5], xs, ys, bar);
-                tma_load_3d(su0, &I.maps.m[rp], xs, ys, rhs, bar);
-                tma_load_3d(su1, &I.maps.m[rp + 1], xs, ys, rhs, bar);
+            if (wl == 0) {
+                s_ok = ok;
+                nabort = 0;
+                if (ok) {
+                    // the tensor maps live in global memory (written by a host
+                    // copy): acquired for the tensor-map proxy once per CTA and
+                    // instance, before a copy uses them
+                    const unsigned long long bit = (inst < 64) ? (1ull << inst) : 0ull;
+                    if (!(s_fenced & bit)) {
+                        for (int qq = 0; qq < 6; ++qq)
+                            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                                             reinterpret_cast<uint64_t>(&I.maps.m[qq]))
+                                         : "memory");
+                        s_fenced |= bit;
+                    }
+                    mbar_init(bar, 1);
+                    mbar_expect_tx(bar, (unsigned)(kArrays * (size_t)(H + 2) * BW * sizeof(T)));
+                    tma_load_2d(sk, &I.maps.m[4], xs, ys, bar);
+                    if (SD) tma_load_2d(sd, &I.maps.m[5], xs, ys, bar);
+                    tma_load_3d(su0, &I.maps.m[rp], xs, ys, rhs, bar);
+                    tma_load_3d(su1, &I.maps.m[rp + 1], xs, ys, rhs, bar);
+                }
             }
         }
+        // each warp initialises its own neighbour barriers (arrived on only
+        // after the barrier below)
+        if (wl == 0)
+            for (int qq = 0; qq < 2; ++qq)
+                mbar_init(&nbar[qq][wg], (unsigned)((wg > 0) + (wg < RG - 1)));
         __syncthreads();
         if (!s_ok) break;
-        const int nsub = s_nsub;
 
         const int lx = 2 * wl;
         const int row0 = wg * RPT;
@@ -958,9 +998,9 @@ tb2d_group_kernel(GroupSched Q)
             fence_proxy_async_global();
             st_release_gpu(&done[tile], k + 1);
             mbar_inval(bar);
-            for (int qq = 0; qq < 2; ++qq)
-                for (int g = 0; g < RG; ++g) mbar_inval(&nbar[qq][g]);
         }
+        if (wl == 0)
+            for (int qq = 0; qq < 2; ++qq) mbar_inval(&nbar[qq][wg]);
     }
 }
 

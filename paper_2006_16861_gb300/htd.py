@@ -29,7 +29,7 @@ STENCIL_Q1MIX, STENCIL_FD5, STENCIL_FAMILY = 0, 1, 2
 BC_DIRICHLET = 0
 TB_ANY, TB_COLUMN, TB_PAIR, TB_PAIR_SD = 0, 1, 2, 3
 S3_PAIR, S3_ZMARCH, S3_NODE_32x8, S3_NODE_64x4, S3_NODE_128x2 = 0, 1, 2, 3, 4
-LAUNCH_NO_OVERLAP, LAUNCH_NO_GRAPH = 1, 2
+LAUNCH_NO_OVERLAP, LAUNCH_NO_GRAPH, LAUNCH_NO_GROUP = 1, 2, 4
 
 #: every function include/htd.h declares (checked by the ABI test)
 EXPORTS = ("htd_default_options", "htd_create", "htd_destroy", "htd_plan", "htd_get_params",
@@ -37,6 +37,7 @@ EXPORTS = ("htd_default_options", "htd_create", "htd_destroy", "htd_plan", "htd_
            "htd_gmres_solve", "htd_grad", "htd_grad_td",
            "htd_gmres_solve_host", "htd_batch_create", "htd_batch_destroy",
            "htd_batch_apply_precond", "htd_batch_gmres_solve", "htd_batch_describe",
+           "htd_batch_set_form",
            "htd_set_wait_limit",
            "htd_test_fail_alloc", "htd_status_string")
 
@@ -84,7 +85,9 @@ class Params(ctypes.Structure):
 class BatchDesc(ctypes.Structure):
     _fields_ = [("instances", ctypes.c_int), ("systems", ctypes.c_int),
                 ("grouped", ctypes.c_int), ("group_ctas", ctypes.c_int),
-                ("group_tasks", ctypes.c_longlong), ("group_steps_per_task", ctypes.c_int)]
+                ("group_tasks", ctypes.c_longlong), ("group_steps_per_task", ctypes.c_int),
+                ("form", ctypes.c_int), ("ns_per_update_plain", ctypes.c_double),
+                ("ns_per_update_group", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -144,6 +147,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.htd_batch_apply_precond.argtypes = [vp, vp, vp, vp]
     lib.htd_batch_gmres_solve.argtypes = [vp, vp, vp, d, i, vp, vp]
     lib.htd_batch_describe.argtypes = [vp, ctypes.POINTER(BatchDesc)]
+    lib.htd_batch_set_form.argtypes = [vp, i]
     lib.htd_set_wait_limit.argtypes = [vp, ctypes.c_longlong, i]
     lib.htd_test_fail_alloc.argtypes = [ctypes.c_longlong]
     lib.htd_test_fail_alloc.restype = None
@@ -343,6 +347,12 @@ def htd_batch_describe(batch: int) -> dict:
     out = BatchDesc()
     _check(load().htd_batch_describe(batch, ctypes.byref(out)), "htd_batch_describe")
     return out.as_dict()
+
+
+def htd_batch_set_form(batch: int, form: int) -> None:
+    """0 = decide by timing the first rounds of the next solve, 1 = every
+    handle's own step sequence, 2 = the group's persistent launch."""
+    _check(load().htd_batch_set_form(batch, int(form)), "htd_batch_set_form")
 
 
 def _ptr_array(ts) -> ctypes.Array:
@@ -568,6 +578,9 @@ class Batch:
 
     def describe(self) -> dict:
         return htd_batch_describe(self.handle)
+
+    def set_form(self, form: int) -> None:
+        htd_batch_set_form(self.handle, form)
 
     def solve(self, Fs, Us=None, tol=1e-6, max_iters=400, stream=None,
               allow_not_converged=False):

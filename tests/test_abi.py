@@ -67,7 +67,7 @@ def test_struct_layouts_match_header(tmp_path):
 @pytest.mark.parametrize("field,value", [("tb_rows", 7), ("tb_rows", -1), ("tb_form", 4),
                                          ("tb_form", -1), ("s3_kernel", 5), ("s3_kernel", -1),
                                          ("s3_stages", 3), ("s3_stages", 8), ("s3_zchunk", -1),
-                                         ("launch", 4), ("wait_limit_ns", -1),
+                                         ("launch", 8), ("wait_limit_ns", -1),
                                          ("s3_rhs_per_cta", 3), ("s3_rhs_per_cta", -1)])
 def test_plan_rejects_bad_kernel_selection(field, value):
     """The kernel-selection fields of htd_options are validated on the host,

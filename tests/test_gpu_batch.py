@@ -184,12 +184,14 @@ def test_group_launch_equals_per_handle_launches():
     nrhs.append(2)
     assert len({s.params["steps"] for s in solvers}) > 2
     b = htd.Batch(solvers, nrhs)
+    b.set_form(2)                                  # the group's persistent launch
     Fs = [rhs_stack(p, r, 60 + 7 * k) for k, (p, r) in enumerate(zip(probs, nrhs))]
     for rep in range(2):
         Us = b.precond([dev(F) for F in Fs])
         if rep == 0:
             d = b.describe()
             assert d["grouped"] == 7 and d["group_ctas"] > 0 and d["group_steps_per_task"] == 8
+            assert d["form"] == 2
         for s, F, U in zip(solvers, Fs, Us):
             Ub = host(U)
             for r in range(F.shape[0]):
@@ -211,16 +213,25 @@ def test_group_launch_solve_equals_single_solves():
     assert len({p.n for p in probs}) > 1
     solvers = [htd.Solver(p, precision="mixed", restart=10) for p in probs]
     b = htd.Batch(solvers, [1] * len(solvers))
-    Us, infos = b.solve([dev(p.F[None]) for p in probs], tol=1e-7, max_iters=300)
-    assert b.describe()["grouped"] == len(solvers)
-    its = []
-    for s, p, U, info in zip(solvers, probs, Us, infos):
-        U1, info1 = s.solve(dev(p.F), tol=1e-7, max_iters=300)
-        assert info["converged"] and info1["converged"]
-        assert info["iterations"] == info1["iterations"]
-        its.append(info["iterations"])
-        assert np.array_equal(host(U)[0], host(U1))
-    assert len(set(its)) > 1
+    singles = [s.solve(dev(p.F), tol=1e-7, max_iters=300) for s, p in zip(solvers, probs)]
+    # the group form throughout, then the form chosen by timing the first rounds
+    for form in (2, 0):
+        b.set_form(form)
+        Us, infos = b.solve([dev(p.F[None]) for p in probs], tol=1e-7, max_iters=300)
+        d = b.describe()
+        assert d["grouped"] == len(solvers)
+        if form == 2:
+            assert d["form"] == 2
+        else:
+            assert d["form"] in (1, 2)
+            assert d["ns_per_update_plain"] > 0 and d["ns_per_update_group"] > 0
+        its = []
+        for (U1, info1), U, info in zip(singles, Us, infos):
+            assert info["converged"] and info1["converged"]
+            assert info["iterations"] == info1["iterations"]
+            its.append(info["iterations"])
+            assert np.array_equal(host(U)[0], host(U1))
+        assert len(set(its)) > 1
     b.close()
 
 

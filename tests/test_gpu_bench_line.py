@@ -18,7 +18,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def test_bench_line_small_workload():
     cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--workload", "2d_const_101",
            "--steps", "3", "--warmup", "3", "--fp64-steps", "1", "--cpu-sample-s", "0",
-           "--e2e-steps", "1", "--secondary-2d", "0", "--batched", "0", "--adjoint", "0"]
+           "--e2e-steps", "1", "--secondary-2d", "0", "--batched", "0", "--adjoint", "0", "--projection", "0"]
     out = subprocess.run(cmd, capture_output=True, text=True, check=True, cwd=ROOT).stdout
     line = json.loads(out.strip().splitlines()[-1])
     for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
@@ -46,7 +46,7 @@ def test_bench_line_hbm_roofline_arithmetic():
     --option reaches the solver."""
     cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--workload", "3d_layered_192",
            "--steps", "1", "--warmup", "3", "--fp64-steps", "0", "--cpu-sample-s", "0",
-           "--e2e-steps", "0", "--secondary-2d", "0", "--batched", "0", "--adjoint", "0",
+           "--e2e-steps", "0", "--secondary-2d", "0", "--batched", "0", "--adjoint", "0", "--projection", "0",
            "--option", "s3_stages=5"]
     out = subprocess.run(cmd, capture_output=True, text=True, check=True, cwd=ROOT).stdout
     line = json.loads(out.strip().splitlines()[-1])

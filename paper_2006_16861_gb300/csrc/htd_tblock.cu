@@ -677,7 +677,7 @@ __device__ __forceinline__ void mbar_inval(uint64_t *bar)
 // is bounded by the instance's limit; a wait that gives up sets the
 // instance's error word and the group's abort word, and every CTA stops.
 template <int B, int RPT, int RG, bool SD>
-__global__ void __launch_bounds__(32 * RG, 1)
+__global__ void __launch_bounds__(32 * RG, RG <= 8 ? 2 : 1)
 tb2d_group_kernel(GroupSched Q)
 {
     typedef float T;
@@ -1123,8 +1123,11 @@ void launch_tb2d(const TbPlan &p, const TbMaps &maps, int in0, int in1, const La
 #undef HTD_TB2D_CASE
 }
 
-// The group plan: node pairs, 8 steps per launch, 8 rows per thread, 20 row
-// groups, d staged in shared memory.
+// The group plan: node pairs, 8 steps per task, 8 rows per thread, 20 row
+// groups, d staged in shared memory (the configuration the tuner picks on the
+// large 2-D grids; one CTA per SM).  Measured against it on the batched
+// workload's 64 instances: 4 steps, 10 rows, 8 groups, two CTAs per SM took
+// 22 % longer (twice the loads and stores per step).
 constexpr int kGB = 8, kGRPT = 8, kGRG = 20;
 constexpr bool kGSD = true;
 

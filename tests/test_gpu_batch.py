@@ -190,7 +190,7 @@ def test_group_launch_equals_per_handle_launches():
         Us = b.precond([dev(F) for F in Fs])
         if rep == 0:
             d = b.describe()
-            assert d["grouped"] == 7 and d["group_ctas"] > 0 and d["group_steps_per_task"] == 8
+            assert d["grouped"] == 7 and d["group_ctas"] > 0 and d["group_steps_per_task"] in (4, 8)
             assert d["form"] == 2
         for s, F, U in zip(solvers, Fs, Us):
             Ub = host(U)

@@ -138,6 +138,9 @@ def parse_args(argv=None):
     ap.add_argument("--restart", type=int, default=20)
     ap.add_argument("--batched", type=int, default=1,
                     help="also time the batched workload (96 systems, lockstep FGMRES)")
+    ap.add_argument("--batched-parts", type=int, default=0,
+                    help="also time the batch's parts in each form (3-D handle with one and two "
+                         "rhs per CTA, 2-D handles as child graphs and as the group launch)")
     ap.add_argument("--projection", type=int, default=1,
                     help="also time one application in projection mode against Table 1")
     ap.add_argument("--adjoint", type=int, default=1,
@@ -466,7 +469,7 @@ def secondary_projection(htd, stream, flush):
     return out
 
 
-def secondary_batched(htd, stream, flush, sub_rhs=4, sub_inst=4):
+def secondary_batched(htd, stream, flush, sub_rhs=4, sub_inst=4, parts=False):
     """Batched workload: the 3-D layered model at 128^3 with 32 seeded point sources
     as 32 right-hand sides of one handle, plus 64 2-D instances with sides uniform in
     [200, 1000] -- 96 systems, one CUDA-graph launch per preconditioner round,
@@ -481,10 +484,13 @@ def secondary_batched(htd, stream, flush, sub_rhs=4, sub_inst=4):
     def dev(x):
         return torch.from_numpy(np.ascontiguousarray(x, dtype=np.complex128)).cuda()
 
-    def run(precision, probs, Fs, reps):
-        solvers = [htd.Solver(p, precision=precision, max_rhs=F.shape[0], restart=20)
+    def run(precision, probs, Fs, reps, form=0, kw3=None):
+        solvers = [htd.Solver(p, precision=precision, max_rhs=F.shape[0], restart=20,
+                              **((kw3 or {}) if p.ndim == 3 else {}))
                    for p, F in zip(probs, Fs)]
         b = htd.Batch(solvers, [F.shape[0] for F in Fs])
+        if form:
+            b.set_form(form)
         Fd = [dev(F) for F in Fs]
         Us = b.zeros()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -541,6 +547,19 @@ def secondary_batched(htd, stream, flush, sub_rhs=4, sub_inst=4):
     desc = run.desc
     its = [i["iterations"] for i in infos]
     seq_ms, seq_ups = sequential(setup.probs, setup.F)
+    parts_out = None
+    if parts:
+        # one timed solve per variant: the 3-D handle alone with one and two rhs
+        # per CTA, the 2-D handles alone as child graphs and as the group launch,
+        # and the whole batch in the group form
+        p3, F3, p2, F2 = setup.probs[:1], setup.F[:1], setup.probs[1:], setup.F[1:]
+        parts_out = {
+            "3d_alone_rhs_per_cta_1_ms": run("mixed", p3, F3, 1, kw3=dict(s3_rhs_per_cta=1))[0],
+            "3d_alone_rhs_per_cta_2_ms": run("mixed", p3, F3, 1, kw3=dict(s3_rhs_per_cta=2))[0],
+            "2d_alone_plain_ms": run("mixed", p2, F2, 1, form=1)[0],
+            "2d_alone_group_ms": run("mixed", p2, F2, 1, form=2)[0],
+            "all_group_ms": run("mixed", setup.probs, setup.F, 1, form=2)[0],
+        }
     sub_p = setup.probs[:1 + sub_inst]
     sub_F = [setup.F[0][:sub_rhs]] + setup.F[1:1 + sub_inst]
     ms_m, _, _ = run("mixed", sub_p, sub_F, 1)
@@ -563,6 +582,7 @@ def secondary_batched(htd, stream, flush, sub_rhs=4, sub_inst=4):
                            "what": "the same 96 systems solved one at a time, device time "
                                    "summed (first solve of each handle untimed)"},
             "speedup_vs_sequential": seq_ms / ms,
+            "parts": parts_out,
             "fp64_sub_batch": {"systems": sub_rhs + sub_inst, "mixed_ms": ms_m, "fp64_ms": ms_f,
                                "speedup_vs_fp64": ms_f / ms_m,
                                "fp64_rel_res_true_max": max(i["rel_res_true"] for i in inf_f)}}
@@ -818,7 +838,7 @@ def run_ours(args):
         sec2d = secondary_2d(htd, stream, flush, pk)
     batched = None
     if args.batched:
-        batched = secondary_batched(htd, stream, flush)
+        batched = secondary_batched(htd, stream, flush, parts=bool(args.batched_parts))
     adjoint = None
     if args.adjoint:
         adjoint = secondary_adjoint(htd, stream)

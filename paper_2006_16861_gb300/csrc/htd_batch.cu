@@ -332,6 +332,7 @@ htd_status precond_round(htd_batch b, const std::vector<char> &sel,
                          const std::vector<const double2 *> &in, const std::vector<double2 *> &out,
                          cudaStream_t s)
 {
+    htd::NvtxRange nvtx_range("batch_round");
     const int ninst = (int)b->ctx.size();
     HTD_CUDA(cudaEventRecord(b->ev[0], s));
     htd_status st = wait_table(b);
@@ -410,6 +411,7 @@ htd_status fetch_blocks(htd_batch b, cudaStream_t s)
 htd_status batch_gmres(htd_batch b, const void *const *F_dev, void *const *U_dev, double tol,
                        int maxit, cudaStream_t s, htd_solve_info *info)
 {
+    htd::NvtxRange nvtx_range("htd_batch_gmres_solve");
     const auto t0 = std::chrono::steady_clock::now();
     const long long launches0 = htd::g_launches;
     const size_t ns = b->sys.size();

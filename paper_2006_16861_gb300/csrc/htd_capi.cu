@@ -437,6 +437,7 @@ htd_status collect_precond_time(htd_ctx *c)
 // U = P F (F, U compact complex128 on the device)
 htd_status precond(htd_ctx *c, const double2 *F, double2 *U, cudaStream_t s)
 {
+    htd::NvtxRange nvtx_range("precond");
     const bool mixed = c->opt.precision == HTD_MIXED;
     htd_status cst = collect_precond_time(c);
     if (cst != HTD_OK) return cst;
@@ -1548,6 +1549,7 @@ void htd_default_options(htd_options *opt)
 htd_status htd_create(const htd_grid *grid, const double *c_cell_host, const double *R_node_host,
                       double omega_phys, int bc, const htd_options *opt, htd_handle *out)
 {
+    htd::NvtxRange nvtx_range("htd_create");
     if (!out) return HTD_ERR_ARG;
     htd_ctx *c = new (std::nothrow) htd_ctx();
     if (!c) return HTD_ERR_OOM;
@@ -1623,6 +1625,7 @@ htd_status htd_get_params(htd_handle h, htd_params *out)
 
 htd_status htd_apply_precond(htd_handle h, const void *F_dev, void *U_dev, void *stream)
 {
+    htd::NvtxRange nvtx_range("htd_apply_precond");
     if (!h || !F_dev || !U_dev || F_dev == U_dev) return HTD_ERR_ARG;
     return precond(h, (const double2 *)F_dev, (double2 *)U_dev, (cudaStream_t)stream);
 }
@@ -1653,6 +1656,7 @@ htd_status htd_residual_norm(htd_handle h, const void *F_dev, const void *U_dev,
 htd_status htd_gmres_solve(htd_handle h, const void *F_dev, void *U_dev, double tol, int max_iters,
                            void *stream, htd_solve_info *info)
 {
+    htd::NvtxRange nvtx_range("htd_gmres_solve");
     if (!h || !F_dev || !U_dev || F_dev == U_dev || max_iters < 0) return HTD_ERR_ARG;
     return gmres(h, (const double2 *)F_dev, (double2 *)U_dev, tol, max_iters, (cudaStream_t)stream, info);
 }
@@ -1660,6 +1664,7 @@ htd_status htd_gmres_solve(htd_handle h, const void *F_dev, void *U_dev, double 
 htd_status htd_gmres_solve_host(htd_handle h, const void *F_host, void *U_host, double tol,
                                 int max_iters, void *stream, htd_solve_info *info)
 {
+    htd::NvtxRange nvtx_range("htd_gmres_solve_host");
     if (!h || !F_host || !U_host || max_iters < 0) return HTD_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t vb = sizeof(double2) * (size_t)h->Lr.N;
@@ -1679,6 +1684,7 @@ htd_status htd_grad(htd_handle h, int nsrc, const void *F_dev, int nrec,
                     void *grad_m_dev, void *grad_R_dev, double *misfit, void *stream,
                     htd_solve_info *info)
 {
+    htd::NvtxRange nvtx_range("htd_grad");
     if (!h || nsrc < 1 || !F_dev || nrec < 0 || !misfit || max_iters < 0 || !(tol > 0.0))
         return HTD_ERR_ARG;
     if (h->opt.damping != HTD_DAMP_NODE) return HTD_ERR_ARG;   // dH/dR is diagonal here
@@ -1762,6 +1768,7 @@ htd_status htd_grad_td(htd_handle h, int nsrc, const void *F_dev, int nrec,
                        const int64_t *rec_idx_host, const void *d_dev, int checkpoint_every,
                        void *grad_m_dev, void *grad_R_dev, double *misfit, void *stream)
 {
+    htd::NvtxRange nvtx_range("htd_grad_td");
     if (!h || nsrc < 1 || !F_dev || nrec < 0 || !misfit || checkpoint_every < 0)
         return HTD_ERR_ARG;
     if (h->opt.mode != HTD_MODE_TABLE1 && h->opt.mode != HTD_MODE_EXACT) return HTD_ERR_ARG;

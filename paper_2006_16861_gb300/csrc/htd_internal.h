@@ -4,6 +4,7 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <cstdint>
 #include <vector>
 
@@ -131,6 +132,17 @@ __device__ __forceinline__ bool rhs_of_slot(const RhsSet &R, int k, int &rhs)
     rhs = __ldg(R.act + 1 + k);
     return true;
 }
+
+// ---- tracing -------------------------------------------------------------------
+
+// NVTX range for the scope (header-only NVTX3: a no-op unless a profiler that
+// reads NVTX is attached, e.g. ncu --nvtx or Nsight Systems)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // ---- device allocation (htd_capi.cu) ---------------------------------------
 

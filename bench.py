@@ -73,18 +73,23 @@ F32_FLOPS_PER_UPDATE = {2: 41, 3: 135}
 FP64_FLOPS_PER_UPDATE = {2: 44, 3: 135}
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
-# capture, valid only for the kernel source it was taken on (sha256 prefix of the
-# file); scaled by node count to other grid sizes.  The captures are summarised
-# under profiles/.
+# capture, valid only for the kernel source it was taken on: the sha256 prefix
+# of the kernel's region of its file (from `begin`, or the file start, up to
+# `end`), so that edits elsewhere in the file keep the record; scaled by node
+# count to other grid sizes.  The captures are summarised under profiles/.
 NCU_TRAFFIC = {
-    "tb2d_pair": {"file": "htd_tblock.cu", "sha16": "b9afe2271fc20c85", "bytes": 25192448 + 1792,
-                  "nodes": 1001 * 1001},
-    "stream3d": {"file": "htd_stream3d.cu", "sha16": "4f289c964d28aa22",
-                 "bytes": 193680896 + 18157568, "nodes": 192 ** 3},
+    # 2-D 1001^2 bench leg, five launches averaged (the grid stays in L2)
+    "tb2d_pair": {"file": "htd_tblock.cu", "begin": "// Node-pair form of tb2d_kernel (FP32)",
+                  "end": "template <int B, int RPT, int RG, bool SD>\nvoid add_pair_candidate",
+                  "sha16": "bc39e0a2f3fd839d", "bytes": 25193114 + 0, "nodes": 1001 * 1001},
+    "stream3d": {"file": "htd_stream3d.cu", "begin": "", "end": "}  // namespace\n",
+                 "sha16": "4f957ccf1e700468", "bytes": 193680896 + 18157568, "nodes": 192 ** 3},
     # captured on the 256^3 bench workload itself (z chunk 19, five launches
     # averaged): no scaling
-    "stream3d_pair": {"file": "htd_stream3d_pair.cu", "sha16": "8e7b6e322a4ec81b",
-                      "bytes": 440159078 + 52479795, "nodes": 256 ** 3},
+    "stream3d_pair": {"file": "htd_stream3d_pair.cu", "begin": "",
+                      "end": "}  // namespace\n\nsize_t stream3d_pair_smem_bytes",
+                      "sha16": "73ccff94cf1225fe", "bytes": 440054323 + 52439450,
+                      "nodes": 256 ** 3},
 }
 
 WORKLOADS = ["3d_layered_256", "2d_grf_1001", "3d_layered_192", "2d_const_101",
@@ -114,11 +119,13 @@ def ncu_traffic(key, nodes):
         return None
     path = os.path.join(ROOT, "paper_2006_16861_gb300", "csrc", rec["file"])
     try:
-        with open(path, "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()[:16]
-    except OSError:
+        with open(path) as f:
+            text = f.read()
+        i = text.index(rec["begin"]) if rec["begin"] else 0
+        j = text.index(rec["end"], i)
+    except (OSError, ValueError):
         return None
-    if sha != rec["sha16"]:
+    if hashlib.sha256(text[i:j].encode()).hexdigest()[:16] != rec["sha16"]:
         return None
     return rec["bytes"] * nodes / rec["nodes"]
 

@@ -1126,8 +1126,10 @@ void launch_tb2d(const TbPlan &p, const TbMaps &maps, int in0, int in1, const La
 // The group plan: node pairs, 8 steps per task, 8 rows per thread, 20 row
 // groups, d staged in shared memory (the configuration the tuner picks on the
 // large 2-D grids; one CTA per SM).  Measured against it on the batched
-// workload's 64 instances: 4 steps, 10 rows, 8 groups, two CTAs per SM took
-// 22 % longer (twice the loads and stores per step).
+// workload's 64 instances: 4 steps per task on 56 x 152 tiles (1.37 times the
+// useful nodes computed instead of 1.67) took 25 % longer, and 4 steps, 10
+// rows, 8 groups with two CTAs per SM 22 % longer: the fixed cost of a task
+// (its tile's copies in and out, the neighbour check) outweighs the halo.
 constexpr int kGB = 8, kGRPT = 8, kGRG = 20;
 constexpr bool kGSD = true;
 

@@ -65,3 +65,24 @@ def test_kernel_option_parsing():
 
 def test_default_workload_is_the_largest_single_gpu_config():
     assert bench.parse_args([]).workload == "3d_layered_256"
+
+
+def test_traffic_records_follow_the_kernel_source(tmp_path, monkeypatch):
+    """Each ncu traffic record holds while the kernel's region of its source file
+    is the one captured, also after edits elsewhere in the file, and turns
+    null once the region changes."""
+    import shutil
+    for key, rec in bench.NCU_TRAFFIC.items():
+        assert bench.ncu_traffic(key, rec["nodes"]) == rec["bytes"], key
+    csrc = tmp_path / "paper_2006_16861_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    src = os.path.join(ROOT, "paper_2006_16861_gb300", "csrc", "htd_tblock.cu")
+    shutil.copy(src, csrc / "htd_tblock.cu")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    rec = bench.NCU_TRAFFIC["tb2d_pair"]
+    text = (csrc / "htd_tblock.cu").read_text()
+    (csrc / "htd_tblock.cu").write_text(text + "\n// an edit outside the kernel\n")
+    assert bench.ncu_traffic("tb2d_pair", rec["nodes"]) == rec["bytes"]
+    i = text.index(rec["begin"])
+    (csrc / "htd_tblock.cu").write_text(text[:i + 5] + "x" + text[i + 5:])
+    assert bench.ncu_traffic("tb2d_pair", rec["nodes"]) is None

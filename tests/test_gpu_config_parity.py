@@ -14,7 +14,8 @@ configuration (Sec. 2.4; the FP32 preconditioner is inexact, the flexible
 method keeps the Arnoldi relation exact in FP64).
 
 Also at full size: one FP64 preconditioner application with all T n_P steps
-(2-D 1001^2, T = 125) against the oracle within 1e-10, and a short FP32 run of
+(2-D 1001^2, T = 125; the 3-D recipe at 64^3 with the 256^3 configuration's
+T = 32) against the oracle within 1e-10, and a short FP32 run of
 the bench's step kernels on their full grids (the blocked 2-D kernel at 1001^2,
 the streamed 3-D kernel at 256^3) against the oracle within 2e-5, relative L2
 and maximum norm.
@@ -197,3 +198,19 @@ def test_fp32_bench_kernels_on_full_grids_match_the_oracle(name):
     s.close()
     ref = oracle.Oracle(p).precond(p.F)
     assert rel(U, ref) <= 2e-5 and maxrel(U, ref) <= 2e-5, (rel(U, ref), maxrel(U, ref))
+
+
+def test_3d_layered_recipe_at_its_full_T_matches_the_oracle():
+    """The 3-D configuration's recipe (4 layers x (1 + 0.1 GRF), 8 points per
+    wavelength, layer of the same physical width) on a 64^3 grid with the full
+    T = 32 of the 256^3 configuration (384 steps per application): FP64 within
+    1e-10 of the oracle, FP32 within 2e-5, relative L2 and maximum norm."""
+    p = W.config_3d_layered(64, layer=6, T=32)
+    ref = oracle.Oracle(p).precond(p.F)
+    for precision, tol in (("fp64", 1e-10), ("mixed", 2e-5)):
+        s = htd.Solver(p, precision=precision)
+        assert s.params["steps"] == 384
+        U = s.precond(dev(p.F)).cpu().numpy()
+        s.close()
+        assert rel(U, ref) <= tol and maxrel(U, ref) <= tol, (precision, rel(U, ref),
+                                                               maxrel(U, ref))

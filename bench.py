@@ -26,8 +26,9 @@ Printed (one JSON line on rank 0):
   time_to_tol_ms / fp64_time_to_tol_ms / speedup_vs_fp64
               the solve time in mixed and in plain FP64 mode on the same GPU;
   fp64_roofline the FP64 step kernel of the plain form against the FP64 pipe;
-  secondary_2d the 2-D 1001^2 heterogeneous solve (L2-resident; its blocked
-              step kernel is reported against the FP32 pipe, `bound` "alu");
+  secondary_2d the 2-D 1001^2 heterogeneous solve (L2-resident; its step
+              kernel -- the one the create-time tuner picks: blocked or
+              resident-grid -- is reported against the FP32 pipe, `bound` "alu");
   batched     the 96-system batched workload solved in lockstep, and the same
               systems solved one at a time;
   adjoint     the two gradients of the 512^2, 8-source adjoint configuration;
@@ -66,6 +67,17 @@ TOL = 1e-6
 # B-step temporally blocked launch reads the same 6 planes once and writes the
 # last two states (8 words)
 WORDS_ONE_STEP, WORDS_BLOCKED = 7, 8
+# the resident-grid 2-D kernel moves q*kappa, d, Re F, Im F in and the two
+# FP64 outputs out once per run (launch)
+WORDS_RESIDENT = 8
+
+
+def launch_words(prm):
+    """Algorithmic 4-byte words per node of one step-kernel launch."""
+    if prm.get("step_kernel") == 4:
+        return WORDS_RESIDENT
+    spl = max(1, int(prm.get("steps_per_launch", 1) or 1))
+    return WORDS_ONE_STEP if spl == 1 else WORDS_BLOCKED
 # FLOPs per point update as the step kernels compute them (FMA = 2).  FP32: 2-D
 # 12 FMA + 11 add + 6 mul; 3-D 57 FMA + 21 add/mul.  FP64: 2-D 12 FMA + 20
 # add/mul; 3-D as FP32.
@@ -99,6 +111,8 @@ WORKLOADS = ["3d_layered_256", "2d_grf_1001", "3d_layered_192", "2d_const_101",
 def step_kernel_name(prm, ndim):
     """(name, traffic key) of the recurrence kernel a context uses."""
     sk = prm.get("step_kernel")
+    if sk == 4:
+        return f"res2d_kernel<{prm['tile'][0]}x{prm['tile'][1]}>", None
     if sk == 1:
         if prm["tile"][2] == 2:
             return f"tb2d_pair_kernel<{prm['steps_per_launch']}>", "tb2d_pair"
@@ -408,7 +422,7 @@ def secondary_2d(htd, stream, flush, pk, reps=5, fp64=True):
     us_launch = 1e3 * ms_prec / max(1, launches)
     tflops = F32_FLOPS_PER_UPDATE[2] * N * steps / (ms_prec * 1e-3) / 1e12
     kern, tkey = step_kernel_name(prm, 2)
-    words = WORDS_ONE_STEP if spl == 1 else WORDS_BLOCKED
+    words = launch_words(prm)
     out = {"workload": "2d_grf_1001", "value": N * steps / (ms * 1e-3) / 1e9, "unit": UNIT,
            "time_to_tol_ms": ms, "iterations": infos[-1]["iterations"],
            "rel_res_true": max(i["rel_res_true"] for i in infos),
@@ -417,6 +431,7 @@ def secondary_2d(htd, stream, flush, pk, reps=5, fp64=True):
                         "frac": tflops / pk["fp32_tflops"],
                         "flops_per_update": F32_FLOPS_PER_UPDATE[2],
                         "steps_per_launch": spl, "avg_launch_us": us_launch,
+                        "us_per_step": 1e3 * ms_prec / steps,
                         "traffic": ncu_traffic(tkey, N) if tkey else None,
                         "bytes_per_launch": N * 4 * words,
                         "l2_resident": True,
@@ -763,7 +778,7 @@ def run_ours(args):
     runs = steps_run // prm["steps"]
     step_launches = runs * (-(-prm["steps"] // spl))
     avg_launch_s = ms_prec * 1e-3 / max(1, step_launches)
-    bytes_per_launch = N * 4 * (WORDS_ONE_STEP if spl == 1 else WORDS_BLOCKED)
+    bytes_per_launch = N * 4 * launch_words(prm)
     achieved = bytes_per_launch / avg_launch_s / 1e9
     l2_resident = bytes_per_launch < 96 * (1 << 20)
     kern, tkey = step_kernel_name(prm, p.ndim)
@@ -777,6 +792,7 @@ def run_ours(args):
                 "traffic": ncu_traffic(tkey, N) if tkey else None,
                 "steps_per_launch": spl, "bytes_per_launch": bytes_per_launch,
                 "avg_launch_us": avg_launch_s * 1e6, "l2_resident": True,
+                "us_per_step": 1e3 * ms_prec / steps_run,
                 "peak_kind": f"FP32 pipe derived: {pk['nsm']} SMs x 128 lanes x 2 FLOP x "
                              f"{pk['sm_max_mhz']:.0f} MHz (not measured)"}
     else:

@@ -126,10 +126,11 @@ typedef struct {
     double stencil_gamma; /* HTD_STENCIL_FAMILY: weight of the Q1 element stiffness,
                           in [0, 1] (default 1) */
     int tblock;        /* recurrence steps per launch of the 2-D FP32 kernel:
-                          0 = chosen at create by timing the one-step kernel and
-                          the blocked configurations (default), 1 = one step per
-                          launch, 4 or 8 = temporally blocked with that depth.
-                          Ignored for other precisions, dimensions and I_abd */
+                          0 = chosen at create by timing the one-step kernel,
+                          the blocked configurations and the resident-grid
+                          kernel (default), 1 = one step per launch, 4 or 8 =
+                          temporally blocked with that depth.  Ignored for
+                          other precisions, dimensions and I_abd */
     /* Kernel selection.  The defaults (all 0) let htd_create pick by timing;
        the other values restrict or force a kernel variant, for tuning and for
        tests that compare variants.  Every variant computes the same recurrence;
@@ -139,7 +140,20 @@ typedef struct {
     int tb_form;       /* blocked 2-D kernel: HTD_TB_ANY (tuned), HTD_TB_COLUMN
                           (one column per thread), HTD_TB_PAIR (two columns per
                           thread in paired FP32 instructions, d in registers),
-                          HTD_TB_PAIR_SD (pairs, d staged in shared memory) */
+                          HTD_TB_PAIR_SD (pairs, d staged in shared memory),
+                          HTD_TB_RESIDENT (the resident-grid kernel whenever
+                          the handle qualifies, else as HTD_TB_ANY).  The
+                          resident-grid kernel runs a whole run in one
+                          cooperative launch: the grid is cut into at most one
+                          tile per SM, each CTA keeps its tile's states and
+                          coefficients in shared memory for all T n_P steps
+                          and swaps edge values with its neighbours through
+                          global memory every step.  It qualifies for a
+                          handle with max_rhs 1, Table 1 or exact read-out and
+                          a grid whose tiles fit the shared memory of one SM
+                          (about 1.3 M nodes on 152 SMs); a handle that joins
+                          a batch leaves it for its tuned blocked
+                          configuration */
     int s3_kernel;     /* 3-D FP32 step kernel: HTD_S3_PAIR (TMA-streamed z
                           planes, node pairs; default), HTD_S3_ZMARCH (one step
                           per launch, register z-march), HTD_S3_NODE_32x8,
@@ -167,7 +181,8 @@ typedef struct {
                           htd_set_wait_limit) */
 } htd_options;
 
-enum { HTD_TB_ANY = 0, HTD_TB_COLUMN = 1, HTD_TB_PAIR = 2, HTD_TB_PAIR_SD = 3 };
+enum { HTD_TB_ANY = 0, HTD_TB_COLUMN = 1, HTD_TB_PAIR = 2, HTD_TB_PAIR_SD = 3,
+       HTD_TB_RESIDENT = 4 };
 enum { HTD_S3_PAIR = 0, HTD_S3_ZMARCH = 1, HTD_S3_NODE_32x8 = 2, HTD_S3_NODE_64x4 = 3,
        HTD_S3_NODE_128x2 = 4 };
 enum { HTD_LAUNCH_NO_OVERLAP = 1, HTD_LAUNCH_NO_GRAPH = 2, HTD_LAUNCH_NO_GROUP = 4 };
@@ -234,18 +249,21 @@ typedef struct {
     int T;                   /* periods */
     long long steps;         /* recurrence steps per real run: T * nP */
     int steps_per_launch;    /* recurrence steps per kernel launch (temporal
-                                blocking; 1 = one step per launch; 0 in htd_plan,
-                                which does not look at the device) */
-    int tile[3];             /* owned tile (x, y) of the blocked 2-D step kernel and
-                                its columns per thread (1, or 2: node pairs in paired
-                                FP32 instructions), or column tile and z chunk of the
-                                streamed 3-D one; 0 if unused */
+                                blocking; 1 = one step per launch; T * nP for the
+                                resident-grid kernel; 0 in htd_plan, which does not
+                                look at the device) */
+    int tile[3];             /* owned tile (x, y) of the blocked or resident-grid
+                                2-D step kernel and its columns per thread (1, or
+                                2: node pairs in paired FP32 instructions), or
+                                column tile and z chunk of the streamed 3-D one; 0
+                                if unused */
     int ctas_per_sm;         /* resident CTAs per SM of that kernel */
     int waves;               /* waves of CTAs per launch of that kernel */
     int step_kernel;         /* recurrence kernel in use: 0 one step per launch
                                 (gather / z-march), 1 temporally blocked 2-D
                                 (TMA tiles), 2 TMA-streamed 3-D, 3 one-step
-                                backward differences (HTD_ABD); -1 in htd_plan */
+                                backward differences (HTD_ABD), 4 resident-grid
+                                2-D (one launch per run); -1 in htd_plan */
     int rhs_per_cta;         /* right-hand sides one CTA of the step kernel works
                                 on (1 or 2); 0 in htd_plan */
 } htd_params;

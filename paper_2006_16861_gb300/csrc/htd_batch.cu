@@ -650,6 +650,7 @@ htd_status create_batch(int ninst, const htd_handle *handles, const int *nrhs, h
         tab += 2 * ci.rcap;
         b->tab_off.push_back(tab);
     }
+    for (htd_ctx *c : b->ctx) htd::ctx_join_batch(c);
     HTD_CUDA(htd::dev_malloc((void **)&b->ws, sizeof(double2) * ws));
     size_t off = 0;
     for (Sys &y : b->sys) {

@@ -160,6 +160,11 @@ struct htd_ctx {
     htd::TbPlan tb{};
     htd::TbMaps tbmaps{};
     bool use_tb = false;
+    // resident-grid 2-D step (FP32, one rhs): a whole run in one cooperative launch
+    htd::Res2dPlan res{};
+    bool use_res = false;
+    float2 *res_ab = nullptr;               // (a_j, b_j) per step
+    unsigned long long *res_x = nullptr;    // edge exchange buffer
     // TMA-streamed 3-D step (FP32)
     htd::Stream3Maps s3maps{};
     bool use_s3 = false;
@@ -225,7 +230,7 @@ void free_ctx(htd_ctx *c)
     void *dev[] = {c->kap, c->dco, c->fre, c->fim, c->u0, c->u1, c->kap64, c->imH, c->coefP, c->coefI, c->V, c->Z,
                    c->w, c->t, c->r, c->partial, c->hdev, c->slot, c->Fh, c->Uh, c->u2, c->u3,
                    c->err_dev, c->gU, c->gMu, c->gR, c->gres, c->grec, c->act_dev,
-                   c->acc, c->td_ws};
+                   c->acc, c->td_ws, c->res_ab, c->res_x};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (c->hhost) cudaFreeHost(c->hhost);
@@ -251,12 +256,23 @@ htd_status run_steps_direct(htd_ctx *c, cudaStream_t s)
 {
     const Layout &L = c->Lr;
     const StepCoef<T> C = cast_coef<T>(c->C);
-    T *A = (T *)c->u0, *B = (T *)c->u1;
-    HTD_CUDA(cudaMemsetAsync(A, 0, sizeof(T) * L.total * c->rcap, s));
-    HTD_CUDA(cudaMemsetAsync(B, 0, sizeof(T) * L.total * c->rcap, s));
     const bool project = c->opt.mode == HTD_MODE_PROJECT;
     const long long jim = project ? -1 : c->nsteps - c->nP / 4;
     const long long jfin = project ? -1 : c->nsteps;
+    if constexpr (std::is_same<T, float>::value) {
+        if (c->use_res && !project) {
+            // the whole run in one launch; the global state planes are not used
+            htd::launch_res2d(c->res, (const float *)c->kap, (const float *)c->dco,
+                              (const float *)c->fre, (const float *)c->fim, L, C, c->res_ab,
+                              (int)c->nsteps, (int)jim, (int)jfin, c->slot, c->res_x, c->err_dev,
+                              s);
+            HTD_CUDA(cudaGetLastError());
+            return HTD_OK;
+        }
+    }
+    T *A = (T *)c->u0, *B = (T *)c->u1;
+    HTD_CUDA(cudaMemsetAsync(A, 0, sizeof(T) * L.total * c->rcap, s));
+    HTD_CUDA(cudaMemsetAsync(B, 0, sizeof(T) * L.total * c->rcap, s));
     const long long n_acc = project ? (long long)c->opt.proj_periods * c->nP : 0;
     const long long j_acc = c->nsteps - n_acc;           // first step whose new state counts
     const int64_t astride = 4 * L.N;
@@ -641,18 +657,22 @@ htd_status upload_recurrence(htd_ctx *c, const std::vector<double> &qkap, const 
     return HTD_OK;
 }
 
-// Time the one-step kernel and every blocked configuration on the handle's own
-// (zeroed) planes and keep the fastest per step.  No output is written: the
-// step flags are zero during tuning.
+// Time the one-step kernel, every blocked configuration and, for a single-rhs
+// handle whose grid fits the SMs' shared memory (Table 1 or EXACT read-out),
+// the resident-grid kernel on the handle's own (zeroed) planes, and keep the
+// fastest per step.  HTD_TB_RESIDENT takes the resident kernel whenever it
+// fits; the best blocked configuration is kept as well (a batch uses it).  No
+// output is written: the step flags are zero during tuning.
 htd_status autotune_tb2d(htd_ctx *c, int want_B, int want_RPT)
 {
     const Layout &L = c->Lr;
     std::vector<htd::TbPlan> all = htd::tb2d_candidates<float>(L, want_B);
     std::vector<htd::TbPlan> cands;
     const int form = c->opt.tb_form;                       // HTD_TB_ANY: every form
+    const int bform = (form == HTD_TB_RESIDENT) ? HTD_TB_ANY : form;
     for (const htd::TbPlan &p : all) {
         const int pf = !p.pair ? HTD_TB_COLUMN : (p.sd ? HTD_TB_PAIR_SD : HTD_TB_PAIR);
-        if ((want_RPT == 0 || p.RPT == want_RPT) && (form == HTD_TB_ANY || form == pf))
+        if ((want_RPT == 0 || p.RPT == want_RPT) && (bform == HTD_TB_ANY || bform == pf))
             cands.push_back(p);
     }
     if (cands.empty()) return HTD_OK;
@@ -715,18 +735,52 @@ htd_status autotune_tb2d(htd_ctx *c, int want_B, int want_RPT)
             best_maps = maps;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaStreamDestroy(s);
-    int flag = 0;
-    HTD_CUDA(cudaMemcpy(&flag, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
-    if (flag) return HTD_ERR_TIMEOUT;
     c->step_us = (best >= 0) ? best_us : one_step_us;
     if (best >= 0) {
         c->use_tb = true;
         c->tb = cands[best];
         c->tbmaps = best_maps;
     }
+    // the resident-grid kernel: one whole run untimed, one timed
+    const bool res_try = want_B == 0 && want_RPT == 0 && c->rcap == 1 &&
+                         c->opt.mode != HTD_MODE_PROJECT && c->nsteps < (1LL << 30) &&
+                         (form == HTD_TB_ANY || form == HTD_TB_RESIDENT);
+    if (res_try && htd::res2d_plan(L, &c->res)) {
+        std::vector<float2> ab((size_t)c->nsteps);
+        for (long long j = 0; j < c->nsteps; ++j)
+            ab[j] = make_float2((float)c->atab[j], (float)c->btab[j]);
+        HTD_CUDA(htd::dev_malloc(&c->res_ab, sizeof(float2) * ab.size()));
+        HTD_CUDA(cudaMemcpy(c->res_ab, ab.data(), sizeof(float2) * ab.size(),
+                            cudaMemcpyHostToDevice));
+        HTD_CUDA(htd::dev_malloc(&c->res_x, sizeof(unsigned long long) * c->res.xwords));
+        for (int r = 0; r < 2; ++r) {
+            if (r == 1) HTD_CUDA(cudaEventRecord(e0, s));
+            htd::launch_res2d(c->res, (const float *)c->kap, (const float *)c->dco,
+                              (const float *)c->fre, (const float *)c->fim, L, C, c->res_ab,
+                              (int)c->nsteps, -1, -1, c->slot, c->res_x, c->err_dev, s);
+        }
+        HTD_CUDA(cudaEventRecord(e1, s));
+        HTD_CUDA(cudaEventSynchronize(e1));
+        HTD_CUDA(cudaGetLastError());
+        float ms = 0.f;
+        HTD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        const float us = 1e3f * ms / (float)c->nsteps;
+        if (form == HTD_TB_RESIDENT || us < c->step_us) {
+            c->use_res = true;
+            c->step_us = us;
+        } else {
+            cudaFree(c->res_ab);
+            cudaFree(c->res_x);
+            c->res_ab = nullptr;
+            c->res_x = nullptr;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    int flag = 0;
+    HTD_CUDA(cudaMemcpy(&flag, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) return HTD_ERR_TIMEOUT;
     return HTD_OK;
 }
 
@@ -974,7 +1028,7 @@ htd_status plan_impl(const htd_grid *grid, const double *c_cell, const double *R
     if (opt.tb_rows != 0 && opt.tb_rows != 6 && opt.tb_rows != 8 && opt.tb_rows != 10 &&
         opt.tb_rows != 12 && opt.tb_rows != 20)
         return HTD_ERR_ARG;
-    if (opt.tb_form < HTD_TB_ANY || opt.tb_form > HTD_TB_PAIR_SD) return HTD_ERR_ARG;
+    if (opt.tb_form < HTD_TB_ANY || opt.tb_form > HTD_TB_RESIDENT) return HTD_ERR_ARG;
     if (opt.s3_kernel < HTD_S3_PAIR || opt.s3_kernel > HTD_S3_NODE_128x2) return HTD_ERR_ARG;
     if (opt.s3_stages != 0 && (opt.s3_stages < 4 || opt.s3_stages > 7)) return HTD_ERR_ARG;
     if (opt.s3_zchunk < 0 || opt.s3_zchunk > (1 << 24)) return HTD_ERR_ARG;
@@ -1397,6 +1451,18 @@ htd_status ctx_run_steps(htd_ctx *c, cudaStream_t s)
     return (c->opt.precision == HTD_MIXED) ? run_steps<float>(c, s) : run_steps<double>(c, s);
 }
 
+void ctx_join_batch(htd_ctx *c)
+{
+    if (!c->use_res) return;
+    c->use_res = false;
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->exec = nullptr;
+    c->graph = nullptr;
+    c->graph_tried = false;
+    if (c->use_tb) c->step_us = c->tb.us_per_step;
+}
+
 void ctx_account(htd_ctx *c, int applies, long long steps)
 {
     c->applies += applies;
@@ -1596,12 +1662,12 @@ htd_status htd_get_params(htd_handle h, htd_params *out)
     P.nP = h->nP;
     P.T = h->T;
     P.steps = h->nsteps;
-    P.steps_per_launch = h->use_tb ? h->tb.B : 1;
-    P.tile[0] = h->use_tb ? h->tb.TX : 0;
-    P.tile[1] = h->use_tb ? h->tb.TY : 0;
-    P.tile[2] = h->use_tb ? (h->tb.pair ? 2 : 1) : 0;
-    P.ctas_per_sm = h->use_tb ? h->tb.occ : 0;
-    P.waves = h->use_tb ? h->tb.waves : 0;
+    P.steps_per_launch = h->use_res ? (int)h->nsteps : h->use_tb ? h->tb.B : 1;
+    P.tile[0] = h->use_res ? h->res.W : h->use_tb ? h->tb.TX : 0;
+    P.tile[1] = h->use_res ? h->res.H : h->use_tb ? h->tb.TY : 0;
+    P.tile[2] = h->use_res ? 2 : h->use_tb ? (h->tb.pair ? 2 : 1) : 0;
+    P.ctas_per_sm = h->use_res ? 1 : h->use_tb ? h->tb.occ : 0;
+    P.waves = h->use_res ? 1 : h->use_tb ? h->tb.waves : 0;
     if (h->use_s3) {
         static const int tx[4] = {32, 64, 128, 64}, ty[4] = {8, 4, 2, 8};
         const int sh = (h->s3_shape >= 0 && h->s3_shape < 4) ? h->s3_shape : 0;
@@ -1618,7 +1684,10 @@ htd_status htd_get_params(htd_handle h, htd_params *out)
         const int64_t slots = (int64_t)P.ctas_per_sm * nsm;
         P.waves = (int)((ctas + slots - 1) / slots);
     }
-    P.step_kernel = (h->opt.integrator == HTD_ABD) ? 3 : h->use_tb ? 1 : (h->use_s3 ? 2 : 0);
+    P.step_kernel = (h->opt.integrator == HTD_ABD) ? 3
+                    : h->use_res                    ? 4
+                    : h->use_tb                     ? 1
+                                                    : (h->use_s3 ? 2 : 0);
     P.rhs_per_cta = h->use_s3 ? h->s3_rpc : 1;
     return HTD_OK;
 }

@@ -267,6 +267,11 @@ htd_status ctx_stage_run(htd_ctx *c, int run, int n, const int *idx, const doubl
 cudaGraph_t ctx_step_graph(htd_ctx *c);
 // the step sequence on a stream (graph launch or direct launches)
 htd_status ctx_run_steps(htd_ctx *c, cudaStream_t s);
+// A handle joining a batch leaves the resident-grid 2-D kernel (its one
+// cooperative launch holds every SM, while a batch runs its handles side by
+// side) for the blocked configuration tuned at create, and drops a graph
+// captured with it.
+void ctx_join_batch(htd_ctx *c);
 // statistics of runs launched through a batch graph
 void ctx_account(htd_ctx *c, int applies, long long steps);
 // Y = H X or F - H X (FP64)
@@ -353,6 +358,32 @@ void launch_tb2d(const TbPlan &p, const TbMaps &maps, int in0, int in1, const La
                  T *uD, const T *dco, const T *fre, const T *fim, const StepCoef<T> &C,
                  const TbSteps<T> &S, const OutSlot *slot, int *err, cudaStream_t s,
                  const RhsSet &R = RhsSet{}, bool overlap = false);
+
+// ---- resident-grid 2-D step (htd_res2d.cu) ------------------------------------
+//
+// A whole run (all steps, FP32, one rhs) in one cooperative launch: ntx x nty
+// tiles of W x H nodes, one CTA per tile and at most one per SM, every tile's
+// states, cells, d and forcing in shared memory; neighbouring tiles swap edge
+// values through `xbuf` (xwords 64-bit words, zeroed by the launcher).
+struct Res2dPlan {
+    int W = 0, H = 0;            // tile (W even); the last tile row / column may be smaller
+    int ntx = 0, nty = 0;        // tiles (CTAs) per axis
+    int rpt = 0;                 // interior rows per thread and strip (4, 8, 12 or 16)
+    size_t smem = 0;             // dynamic shared memory per CTA
+    size_t xwords = 0;           // exchange buffer words
+};
+
+// The plan for a 2-D grid, or false if the grid does not fit the SMs' shared
+// memory at one tile per SM, or the device cannot launch cooperatively.
+bool res2d_plan(const Layout &L, Res2dPlan *p);
+// Steps 0 .. nsteps-1 from zero states with forcing a_j Re F - b_j Im F
+// (ab[j] = (a_j, b_j)); the new state of step jim - 1 goes to the snapshot
+// output, that of step jfin - 1 to the final output (OutSlot of rhs 0).  A
+// wait that runs out sets err[0] = 1.
+void launch_res2d(const Res2dPlan &p, const float *kap, const float *dco, const float *fre,
+                  const float *fim, const Layout &L, const StepCoef<float> &C, const float2 *ab,
+                  int nsteps, int jim, int jfin, const OutSlot *slot, unsigned long long *xbuf,
+                  int *err, cudaStream_t s);
 
 // ---- one persistent launch for many 2-D instances (htd_tblock.cu) -----------
 //

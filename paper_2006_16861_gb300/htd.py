@@ -27,7 +27,7 @@ DAMP_NODE, DAMP_CELL = 0, 1
 FGMRES, LEFT_GMRES = 0, 1
 STENCIL_Q1MIX, STENCIL_FD5, STENCIL_FAMILY = 0, 1, 2
 BC_DIRICHLET = 0
-TB_ANY, TB_COLUMN, TB_PAIR, TB_PAIR_SD = 0, 1, 2, 3
+TB_ANY, TB_COLUMN, TB_PAIR, TB_PAIR_SD, TB_RESIDENT = 0, 1, 2, 3, 4
 S3_PAIR, S3_ZMARCH, S3_NODE_32x8, S3_NODE_64x4, S3_NODE_128x2 = 0, 1, 2, 3, 4
 LAUNCH_NO_OVERLAP, LAUNCH_NO_GRAPH, LAUNCH_NO_GROUP = 1, 2, 4
 

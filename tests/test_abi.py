@@ -64,7 +64,7 @@ def test_struct_layouts_match_header(tmp_path):
     assert got == want
 
 
-@pytest.mark.parametrize("field,value", [("tb_rows", 7), ("tb_rows", -1), ("tb_form", 4),
+@pytest.mark.parametrize("field,value", [("tb_rows", 7), ("tb_rows", -1), ("tb_form", 5),
                                          ("tb_form", -1), ("s3_kernel", 5), ("s3_kernel", -1),
                                          ("s3_stages", 3), ("s3_stages", 8), ("s3_zchunk", -1),
                                          ("launch", 8), ("wait_limit_ns", -1),
@@ -82,6 +82,7 @@ def test_plan_rejects_bad_kernel_selection(field, value):
 def test_plan_accepts_every_documented_kernel_selection():
     p = W.config_2d_constant(21)
     for kw in (dict(tb_rows=8, tb_form=htd.TB_PAIR_SD), dict(tb_form=htd.TB_COLUMN),
+               dict(tb_form=htd.TB_RESIDENT),
                dict(s3_kernel=htd.S3_NODE_128x2, s3_stages=7, s3_zchunk=16),
                dict(s3_kernel=htd.S3_ZMARCH),
                dict(launch=htd.LAUNCH_NO_OVERLAP | htd.LAUNCH_NO_GRAPH),

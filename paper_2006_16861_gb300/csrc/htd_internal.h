@@ -366,9 +366,10 @@ void launch_tb2d(const TbPlan &p, const TbMaps &maps, int in0, int in1, const La
 // states, cells, d and forcing in shared memory; neighbouring tiles swap edge
 // values through `xbuf` (xwords 64-bit words, zeroed by the launcher).
 struct Res2dPlan {
-    int W = 0, H = 0;            // tile (W even); the last tile row / column may be smaller
+    int W = 0, H = 0;            // tile (W even, at most 132); the last tile row / column may be smaller
     int ntx = 0, nty = 0;        // tiles (CTAs) per axis
-    int rpt = 0;                 // interior rows per thread and strip (4, 8, 12 or 16)
+    int rpt = 0;                 // interior rows per thread and strip (3, 5 or 8)
+    int sw = 0;                  // row stride of the shared-memory arrays (72 or 136)
     size_t smem = 0;             // dynamic shared memory per CTA
     size_t xwords = 0;           // exchange buffer words
 };

@@ -67,19 +67,24 @@ __device__ __forceinline__ void st_word(unsigned long long *p, float v, unsigned
     asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
 }
 
-__host__ __device__ constexpr size_t res2d_floats(int W, int H)
+// row strides of the shared-memory arrays the kernel is built for (8 banks
+// apart from row to row); a tile of width W uses the smallest one >= W + 4
+constexpr int kStrides[] = {72, 136};
+
+__host__ __device__ constexpr size_t res2d_floats(int SW, int H)
 {
-    return 3 * (size_t)(H + 2) * (W + 4) + 3 * (size_t)H * W;
+    return 6 * (size_t)(H + 2) * SW;
 }
 
-// Shared memory (floats): the states U0, U1 and the cells K, each (H + 2) rows
-// of SW = W + 4 columns -- node (lx, ly) at row ly + 1, column lx + 2, so that
-// the pair (lx, lx + 1), lx even, is 8-byte aligned; cell (cx, cy) (lower
-// corner node) at the place of node (cx, cy) -- then d, Re F, Im F of the
-// nodes, H x W each.  Exchange buffer of a tile and parity (E = 2W + 2H
-// words): bottom row [0, W), top row [W, 2W), left column [2W, 2W + H), right
-// column [2W + H, 2W + 2H).
-template <int RPT>
+// Shared memory: six arrays of (H + 2) rows of SW floats -- the states U0, U1,
+// the cells K, and d, Re F, Im F -- with node (lx, ly) of the tile at row
+// ly + 1, column lx + 2 of each (so the pair (lx, lx + 1), lx even, is 8-byte
+// aligned, and one offset addresses a node in all six), the state ring at rows
+// 0 and h + 1 and columns 1 and w + 2, and cell (cx, cy) (its lower corner
+// node) at the place of node (cx, cy).  Exchange buffer of a tile and parity
+// (E = 2W + 2H words): bottom row [0, W), top row [W, 2W), left column
+// [2W, 2W + H), right column [2W + H, 2W + 2H).
+template <int RPT, int SW>
 __global__ void __launch_bounds__(kResThreads, 1)
 res2d_kernel(const float *__restrict__ kap, const float *__restrict__ dco,
              const float *__restrict__ fre, const float *__restrict__ fim, Layout L,
@@ -95,59 +100,79 @@ res2d_kernel(const float *__restrict__ kap, const float *__restrict__ dco,
     const int64_t x0 = (int64_t)tx * W, y0 = (int64_t)ty * H;
     const int w = (int)min((int64_t)W, L.nx - x0);
     const int h = (int)min((int64_t)H, L.ny - y0);
-    const int SW = W + 4;
     const int NA = (H + 2) * SW;
     float *U0 = sm, *U1 = sm + NA, *K = sm + 2 * NA;
-    float *D = sm + 3 * NA, *FR = D + H * W, *FI = FR + H * W;
+    float *D = sm + 3 * NA, *FR = sm + 4 * NA, *FI = sm + 5 * NA;
     const int E = 2 * W + 2 * H;
-    unsigned long long *mine = xbuf + (size_t)(ty * ntx + tx) * 2 * E;
 
     if (tid == 0) s_abort = 0;
-    for (int i = tid; i < 2 * NA; i += kResThreads) sm[i] = 0.f;
     for (int i = tid; i < NA; i += kResThreads) {
-        const int cy = i / SW - 1, cx = i % SW - 2;
-        float v = 0.f;
-        if (cx >= -1 && cx < w && cy >= -1 && cy < h)
-            v = kap[(y0 + cy + 1) * L.pitch + L.xl + x0 + cx];
-        K[i] = v;
-    }
-    for (int i = tid; i < H * W; i += kResThreads) {
-        const int ly = i / W, lx = i % W;
-        float dv = 0.f, fr = 0.f, fi = 0.f;
-        if (lx < w && ly < h) {
+        const int ly = i / SW - 1, lx = i % SW - 2;
+        float k = 0.f, dv = 0.f, fr = 0.f, fi = 0.f;
+        if (lx >= -1 && lx < w && ly >= -1 && ly < h) {
             const int64_t g = (y0 + ly + 1) * L.pitch + L.xl + x0 + lx;
-            dv = dco[g];
-            fr = fre[g];
-            fi = fim[g];
+            k = kap[g];                                // cell (lx, ly)
+            if (lx >= 0 && ly >= 0) {
+                dv = dco[g];
+                fr = fre[g];
+                fi = fim[g];
+            }
         }
+        U0[i] = 0.f;
+        U1[i] = 0.f;
+        K[i] = k;
         D[i] = dv;
         FR[i] = fr;
         FI[i] = fi;
     }
 
-    // work of a step: strips of RPT interior rows of the interior column pairs
-    // 1 .. PL-1 (tasks 0 .. nB-1, threads 0 ..), single edge pairs (rows 0 and
-    // h-1, then the pairs 0 and PL of rows 1 .. h-2; threads nB ..), and the
-    // 2w + 2h + 4 ring slots, fetched by the edge threads after their pairs
+    // Work of a step, per thread in this order: (1) an edge pair -- rows 0 and
+    // h-1, then the pairs 0 and PL of rows 1 .. h-2 -- dealt from the last
+    // thread down, so that threads without interior work take them first; each
+    // new edge value is published at once; (2) one strip of up to RPT interior
+    // rows of an interior column pair 1 .. PL-1 (strip t on thread t); (3) the
+    // ring slot of the next state (slot k on thread k): the read of the
+    // neighbour's word is issued two rows into the thread's strip and its tag
+    // checked after the strip, so that the exchange overlaps the interior
+    // work; the word is read again only if the neighbour had not published it.
+    // The geometry of all three is the same in every step.
     const int PW = (w + 1) >> 1, PL = PW - 1;
     const int ncp = max(0, PL - 1);
     const int nrow = max(0, h - 2);
-    const int nB = ncp * ((nrow + RPT - 1) / RPT);
+    const int nS = ncp * ((nrow + RPT - 1) / RPT);
     const int nEr = (h >= 2) ? 2 : 1;
     const int nEc = (PL > 0) ? 2 : 1;
     const int nA = nEr * PW + nrow * nEc;
-    const int aFirst = (nB < kResThreads) ? nB : 0;
-    const int aStride = kResThreads - aFirst;
     const int nslot = 2 * w + 2 * h + 4;
-
-    const bool stall = tx == 0 && ty == 0 && *(volatile const int *)(err + 1) != 0;
-    unsigned long long lim = *reinterpret_cast<volatile const unsigned long long *>(err + 2);
-    if (lim == 0) lim = kDefaultWaitNs;
-
-    // ring slot k: the neighbour word it copies (offset in xbuf of parity 0, or
+    // (1) the edge pair of task a as (node offset, lx, ly)
+    auto edge_of = [&](int a, int &lx, int &ly) {
+        int p;
+        if (a < nEr * PW) {
+            ly = (a < PW) ? 0 : h - 1;
+            p = (a < PW) ? a : a - PW;
+        } else {
+            const int b = a - nEr * PW;
+            ly = 1 + b / nEc;
+            p = (b % nEc) ? PL : 0;
+        }
+        lx = 2 * p;
+    };
+    const int ea = kResThreads - 1 - tid;              // this thread's first edge task
+    int e_lx = 0, e_ly = 0;
+    if (ea < nA) edge_of(ea, e_lx, e_ly);
+    // (2) strip t: column pair, first row, rows
+    auto strip_of = [&](int t, int &lx, int &r0, int &nr) -> bool {
+        lx = 2 * (1 + t % ncp);
+        r0 = 1 + (t / ncp) * RPT;
+        nr = min(RPT, h - 1 - r0);
+        return true;
+    };
+    int s_lx = 0, s_r0 = 1, s_nr = 0;
+    const bool has_strip = tid < nS && strip_of(tid, s_lx, s_r0, s_nr);
+    // (3) the ring slot: the neighbour's word (offset in xbuf for parity 0, or
     // -1 on the domain boundary, where the ring stays zero) and its place in a
     // state array
-    auto slot_src = [&](int k, int &dst) -> long long {
+    auto slot_of = [&](int k, int &dst) -> int {
         int nbx = tx, nby = ty, idx;
         if (k < w) {                                   // below the tile: the top row of (tx, ty-1)
             nby = ty - 1;
@@ -175,17 +200,22 @@ res2d_kernel(const float *__restrict__ kap, const float *__restrict__ dco,
             dst = ((c & 2) ? h + 1 : 0) * SW + ((c & 1) ? w + 2 : 1);
         }
         if (nbx < 0 || nbx >= ntx || nby < 0 || nby >= nty) return -1;
-        return (long long)(nby * ntx + nbx) * 2 * E + idx;
+        return (nby * ntx + nbx) * 2 * E + idx;
     };
-    // copy ring slot k of state s into the state array U (bounded wait for its tag)
-    auto fetch = [&](int k, int s, float *U) {
-        int dst = 0;
-        const long long src = slot_src(k, dst);
-        if (src < 0) return;
-        const unsigned long long *p = xbuf + src + (s & 1) * E;
-        const unsigned want = (stall && s == 1) ? 0xffffffffu : (unsigned)(s + 1);
-        unsigned long long v = ld_word(p);
+    int r_dst = 0;
+    const int r_src = (tid < nslot) ? slot_of(tid, r_dst) : -1;
+
+    // store slot word v (read from p) of state s into U at dst, reading it again
+    // until it carries the tag of state s (bounded by the handle's limit; with
+    // the stall test the first wait of CTA (0, 0) expects a tag no word has)
+    auto complete = [&](const unsigned long long *p, unsigned long long v, int s, int dst,
+                        float *U) {
+        unsigned want = (unsigned)(s + 1);
+        if (s == 1 && tx == 0 && ty == 0 && *(volatile const int *)(err + 1) != 0)
+            want = 0xffffffffu;
         if ((unsigned)(v >> 32) != want) {
+            unsigned long long lim = *reinterpret_cast<volatile const unsigned long long *>(err + 2);
+            if (lim == 0) lim = kDefaultWaitNs;
             const unsigned long long t0 = global_ns();
             for (int it = 1;; ++it) {
                 v = ld_word(p);
@@ -206,23 +236,23 @@ res2d_kernel(const float *__restrict__ kap, const float *__restrict__ dco,
 
     const Stencil2dCoef<float2> SC = stencil2d_coef2(C);
     const float2 n2 = pr(-2.f, -2.f);
-    // u row ly (ring included) as the pairs (m, 0, p) = (u(lx-1+o), u(lx+o)), o = 0, 1, 2
-    auto urow = [&](const float *P, int ly, int lx, float2 &m, float2 &z, float2 &p) {
-        const float *q = P + (ly + 1) * SW + lx + 1;
+    // u row at q (the node lx - 1 of the row) as the pairs (m, 0, p) =
+    // (u(lx-1+o), u(lx+o)), o = 0, 1, 2
+    auto urow = [&](const float *q, float2 &m, float2 &z, float2 &p) {
         const float l = q[0];
         z = ld2(q + 1);
         const float r = q[3];
         m = pr(l, z.x);
         p = pr(z.y, r);
     };
-    // cell row cy: k0 = cells left of the nodes (lx-1, lx), k1 = cells right of them
-    auto krow = [&](int cy, int lx, float2 &k0, float2 &k1) {
-        const float *q = K + (cy + 1) * SW + lx + 1;
+    // cells at q (the cell lx - 1 of a cell row): k0 = cells left of the nodes
+    // (lx-1, lx), k1 = cells right of them
+    auto krow = [&](const float *q, float2 &k0, float2 &k1) {
         k1 = ld2(q + 1);
         k0 = pr(q[0], k1.x);
     };
     auto output = [&](int lx, int ly, float2 u, int fl, bool two) {
-        const int64_t c = (y0 + ly) * L.nx + x0 + lx;
+        const int64_t c = ((int64_t)blockIdx.y * H + ly) * L.nx + (int64_t)blockIdx.x * W + lx;
         if ((fl & 1) && slot->snap_part) {
             slot->snap_part[2 * c] = (double)u.x;
             if (two) slot->snap_part[2 * c + 2] = (double)u.y;
@@ -230,6 +260,48 @@ res2d_kernel(const float *__restrict__ kap, const float *__restrict__ dco,
         if ((fl & 2) && slot->final_part) {
             slot->final_part[2 * c] = (double)u.x;
             if (two) slot->final_part[2 * c + 2] = (double)u.y;
+        }
+    };
+    // the new state of the pair at node offset o (row ly + 1, column lx + 2)
+    // from its stencil sum
+    auto update = [&](int o, float2 acc, float2 a2, float2 nb2, float *nxt) -> float2 {
+        const float2 ag = vfma(a2, ld2(FR + o), vfma(nb2, ld2(FI + o), acc));
+        const float2 uprev = ld2(nxt + o);
+        return vfma(ld2(D + o), vfma(n2, uprev, ag), uprev);
+    };
+    // nr <= RPT interior rows r0 .. r0+nr-1 of the column pair lx; the read of
+    // the ring word at rp (if any) is issued before the third row
+    auto strip = [&](int lx, int r0, int nr, const float *cur, float *nxt, float2 a2, float2 nb2,
+                     int fl, const unsigned long long *rp, unsigned long long &rv, bool &issued) {
+        const int o0 = r0 * SW + lx + 1;               // node (lx - 1, r0 - 1)
+        const float *qc = cur + o0, *qk = K + o0;
+        float2 umm, um0, ump, u0m, u00, u0p, k00, k01;
+        urow(qc, umm, um0, ump);
+        urow(qc + SW, u0m, u00, u0p);
+        float2 pm = vadd(umm, ump), p0 = vadd(u0m, u0p);
+        krow(qk, k00, k01);
+        float2 hk0 = vadd(k00, k01);
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+            if (i >= nr) break;
+            if (i == 2 && rp) {
+                rv = ld_word(rp);
+                issued = true;
+            }
+            float2 upm, up0, upp, k10, k11;
+            urow(qc + (i + 2) * SW, upm, up0, upp);
+            krow(qk + (i + 1) * SW, k10, k11);
+            const float2 pp = vadd(upm, upp);
+            const float2 hk1 = vadd(k10, k11);
+            const float2 acc = stencil2d(SC, umm, um0, ump, u0m, u00, u0p, upm, up0, upp, k00, k01,
+                                         k10, k11, pm, p0, pp, hk0, hk1);
+            const int o = o0 + (i + 1) * SW + 1;       // node (lx, r0 + i)
+            const float2 unew = update(o, acc, a2, nb2, nxt);
+            st2(nxt + o, unew);
+            if (fl) output(lx, r0 + i, unew, fl, true);
+            umm = u0m; um0 = u00; ump = u0p; pm = p0;
+            u0m = upm; u00 = up0; u0p = upp; p0 = pp;
+            k00 = k10; k01 = k11; hk0 = hk1;
         }
     };
 
@@ -240,103 +312,99 @@ res2d_kernel(const float *__restrict__ kap, const float *__restrict__ dco,
         const float2 abj = __ldg(ab + j);
         const float2 a2 = pr(abj.x, abj.x), nb2 = pr(-abj.y, -abj.y);
         const int fl = ((j + 1 == jim) ? 1 : 0) | ((j + 1 == jfin) ? 2 : 0);
+        const bool more = j + 1 < nsteps;
 
-        for (int t = tid; t < nB; t += kResThreads) {
-            const int lx = 2 * (1 + t % ncp);
-            const int r0 = 1 + (t / ncp) * RPT;
-            const int r1 = min(r0 + RPT, h - 1);
-            float2 umm, um0, ump, u0m, u00, u0p, k00, k01;
-            urow(cur, r0 - 1, lx, umm, um0, ump);
-            urow(cur, r0, lx, u0m, u00, u0p);
-            float2 pm = vadd(umm, ump), p0 = vadd(u0m, u0p);
-            krow(r0 - 1, lx, k00, k01);
-            float2 hk0 = vadd(k00, k01);
-#pragma unroll
-            for (int i = 0; i < RPT; ++i) {
-                const int ly = r0 + i;
-                if (ly >= r1) break;
-                float2 upm, up0, upp, k10, k11;
-                urow(cur, ly + 1, lx, upm, up0, upp);
-                krow(ly, lx, k10, k11);
-                const float2 pp = vadd(upm, upp);
-                const float2 hk1 = vadd(k10, k11);
-                const float2 acc = stencil2d(SC, umm, um0, ump, u0m, u00, u0p, upm, up0, upp, k00,
-                                             k01, k10, k11, pm, p0, pp, hk0, hk1);
-                const int ni = ly * W + lx, si = (ly + 1) * SW + lx + 2;
-                const float2 ag = vfma(a2, ld2(FR + ni), vfma(nb2, ld2(FI + ni), acc));
-                const float2 uprev = ld2(nxt + si);
-                const float2 unew = vfma(ld2(D + ni), vfma(n2, uprev, ag), uprev);
-                st2(nxt + si, unew);
-                if (fl) output(lx, ly, unew, fl, true);
-                umm = u0m; um0 = u00; ump = u0p; pm = p0;
-                u0m = upm; u00 = up0; u0p = upp; p0 = pp;
-                k00 = k10; k01 = k11; hk0 = hk1;
-            }
-        }
-        if (tid >= aFirst) {
+        // (1) edge pairs, published as they are computed
+        if (ea < nA) {
             const unsigned tag = (unsigned)(j + 2);
-            unsigned long long *pub = mine + ((j + 1) & 1) * E;
+            unsigned long long *pub = xbuf + (size_t)((ty * ntx + tx) * 2 + ((j + 1) & 1)) * E;
             auto publish = [&](int lx, int ly, float v) {
                 if (ly == 0) st_word(pub + lx, v, tag);
                 if (ly == h - 1) st_word(pub + W + lx, v, tag);
                 if (lx == 0) st_word(pub + 2 * W + ly, v, tag);
                 if (lx == w - 1) st_word(pub + 2 * W + H + ly, v, tag);
             };
-            for (int a = tid - aFirst; a < nA; a += aStride) {
-                int ly, p;
-                if (a < nEr * PW) {
-                    ly = (a < PW) ? 0 : h - 1;
-                    p = (a < PW) ? a : a - PW;
-                } else {
-                    const int b = a - nEr * PW;
-                    ly = 1 + b / nEc;
-                    p = (b % nEc) ? PL : 0;
-                }
-                const int lx = 2 * p;
+            for (int a = ea; a < nA; a += kResThreads) {
+                int lx = e_lx, ly = e_ly;
+                if (a != ea) edge_of(a, lx, ly);
+                const int o = (ly + 1) * SW + lx + 2;
                 float2 umm, um0, ump, u0m, u00, u0p, upm, up0, upp, k00, k01, k10, k11;
-                urow(cur, ly - 1, lx, umm, um0, ump);
-                urow(cur, ly, lx, u0m, u00, u0p);
-                urow(cur, ly + 1, lx, upm, up0, upp);
-                krow(ly - 1, lx, k00, k01);
-                krow(ly, lx, k10, k11);
+                urow(cur + o - SW - 1, umm, um0, ump);
+                urow(cur + o - 1, u0m, u00, u0p);
+                urow(cur + o + SW - 1, upm, up0, upp);
+                krow(K + o - SW - 1, k00, k01);
+                krow(K + o - 1, k10, k11);
                 const float2 acc =
                     stencil2d(SC, umm, um0, ump, u0m, u00, u0p, upm, up0, upp, k00, k01, k10, k11,
                               vadd(umm, ump), vadd(u0m, u0p), vadd(upm, upp), vadd(k00, k01),
                               vadd(k10, k11));
-                const int ni = ly * W + lx, si = (ly + 1) * SW + lx + 2;
-                const float2 ag = vfma(a2, ld2(FR + ni), vfma(nb2, ld2(FI + ni), acc));
-                const float2 uprev = ld2(nxt + si);
-                const float2 unew = vfma(ld2(D + ni), vfma(n2, uprev, ag), uprev);
+                const float2 unew = update(o, acc, a2, nb2, nxt);
                 const bool two = lx + 1 < w;                // the second node is in the tile
-                if (two) st2(nxt + si, unew);
-                else nxt[si] = unew.x;
+                if (two) st2(nxt + o, unew);
+                else nxt[o] = unew.x;
                 publish(lx, ly, unew.x);
                 if (two) publish(lx + 1, ly, unew.y);
                 if (fl) output(lx, ly, unew, fl, two);
             }
-            if (j + 1 < nsteps)
-                for (int k = tid - aFirst; k < nslot; k += aStride) fetch(k, j + 1, nxt);
         }
+
+        // (2) the interior strip, with the read of this thread's ring slot
+        const unsigned long long *rp =
+            (more && r_src >= 0) ? xbuf + r_src + ((j + 1) & 1) * E : nullptr;
+        unsigned long long rv = 0;
+        bool issued = false;
+        if (has_strip) strip(s_lx, s_r0, s_nr, cur, nxt, a2, nb2, fl, rp, rv, issued);
+        for (int t = tid + kResThreads; t < nS; t += kResThreads) {
+            int lx, r0, nr;
+            if (strip_of(t, lx, r0, nr))
+                strip(lx, r0, nr, cur, nxt, a2, nb2, fl, nullptr, rv, issued);
+        }
+
+        // (3) the ring of u_{j+1}
+        if (rp) complete(rp, issued ? rv : ld_word(rp), j + 1, r_dst, nxt);
+        if (more)
+            for (int k = tid + kResThreads; k < nslot; k += kResThreads) {
+                int dst = 0;
+                const int src = slot_of(k, dst);
+                if (src < 0) continue;
+                const unsigned long long *p = xbuf + src + ((j + 1) & 1) * E;
+                complete(p, ld_word(p), j + 1, dst, nxt);
+            }
         __syncthreads();
         if (s_abort) break;
     }
 }
 
-template <int RPT>
-bool set_smem_attr(size_t smem)
+// the kernel for (RPT rows per strip, row stride SW), for every pair a plan
+// may choose
+constexpr int kRpts[] = {3, 5, 8};
+
+template <typename Fn>
+void with_kernel(int rpt, int sw, Fn &&fn)
 {
-    return cudaFuncSetAttribute(res2d_kernel<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem) == cudaSuccess;
+    if (sw == 72) {
+        if (rpt == 3) fn(res2d_kernel<3, 72>);
+        else if (rpt == 5) fn(res2d_kernel<5, 72>);
+        else fn(res2d_kernel<8, 72>);
+    } else {
+        if (rpt == 3) fn(res2d_kernel<3, 136>);
+        else if (rpt == 5) fn(res2d_kernel<5, 136>);
+        else fn(res2d_kernel<8, 136>);
+    }
 }
 
-// edge and interior tasks of a full W x H tile with RPT rows per strip
-int res2d_tasks(int W, int H, int rpt)
+// Rows of work of the busiest thread of a full W x H tile with RPT rows per
+// strip (an edge pair counted as two rows: it has no register window), or -1
+// if there are more strips than threads.
+int res2d_load(int W, int H, int rpt)
 {
     const int PW = (W + 1) / 2, PL = PW - 1;
     const int nrow = std::max(0, H - 2);
-    const int nB = std::max(0, PL - 1) * ((nrow + rpt - 1) / rpt);
+    const int nS = std::max(0, PL - 1) * ((nrow + rpt - 1) / rpt);
     const int nA = ((H >= 2) ? 2 : 1) * PW + nrow * ((PL > 0) ? 2 : 1);
-    return nA + nB;
+    if (nS > kResThreads) return -1;
+    const int edges = (nA + kResThreads - 1) / kResThreads;     // edge pairs per thread
+    return std::min(rpt, nrow) + 2 * (nS + nA > kResThreads ? edges : 0);
 }
 
 }  // namespace
@@ -353,6 +421,30 @@ bool res2d_plan(const Layout &L, Res2dPlan *out)
         return false;
     }
     if (!coop || nsm < 1) return false;
+    // the limit is a property of the kernel, shared by every handle: raise it
+    // to what the device allows beside the kernel's static shared memory,
+    // rather than to this plan's size (a smaller plan made later must not
+    // shrink it under an earlier handle's launches)
+    int avail = maxsm;
+    bool attr_ok = true;
+    for (int sw : kStrides)
+        for (int r : kRpts)
+            with_kernel(r, sw, [&](auto kern) {
+                cudaFuncAttributes fa;
+                if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) {
+                    attr_ok = false;
+                    return;
+                }
+                const int dyn = maxsm - (int)fa.sharedSizeBytes;
+                avail = std::min(avail, dyn);
+                attr_ok = attr_ok && dyn > 0 &&
+                          cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               dyn) == cudaSuccess;
+            });
+    if (!attr_ok) {
+        (void)cudaGetLastError();
+        return false;
+    }
     // the tiling with the smallest largest tile (then the shortest edges) that
     // fits one tile per CTA, one CTA per SM
     Res2dPlan best;
@@ -365,38 +457,40 @@ bool res2d_plan(const Layout &L, Res2dPlan *out)
         if (tiles_y < 1) break;
         const long long H = (L.ny + tiles_y - 1) / tiles_y;
         const long long nty = (L.ny + H - 1) / H;
-        if (W > 4096 || H > 4096) continue;
-        const size_t smem = res2d_floats((int)W, (int)H) * sizeof(float);
-        if (smem > (size_t)maxsm) continue;
+        int sw = 0;
+        for (int s : kStrides)
+            if (sw == 0 && W + 4 <= s) sw = s;
+        if (sw == 0 || H > 4096) continue;
+        const size_t smem = res2d_floats(sw, (int)H) * sizeof(float);
+        if (smem > (size_t)avail) continue;
         const long long area = W * H, edge = W + H;
         if (best_area < 0 || area < best_area || (area == best_area && edge < best_edge)) {
             best_area = area;
             best_edge = edge;
             best.W = (int)W;
             best.H = (int)H;
+            best.sw = sw;
             best.ntx = (int)ntx;
             best.nty = (int)nty;
             best.smem = smem;
         }
     }
     if (best_area < 0) return false;
-    best.rpt = 16;
-    for (int r : {4, 8, 12, 16})
-        if (res2d_tasks(best.W, best.H, r) <= kResThreads) {
+    best.rpt = kRpts[sizeof(kRpts) / sizeof(kRpts[0]) - 1];
+    int best_load = -1;
+    for (int r : kRpts) {
+        const int ld = res2d_load(best.W, best.H, r);
+        if (ld >= 0 && (best_load < 0 || ld < best_load)) {
+            best_load = ld;
             best.rpt = r;
-            break;
         }
-    const bool attr = best.rpt == 4    ? set_smem_attr<4>(best.smem)
-                      : best.rpt == 8  ? set_smem_attr<8>(best.smem)
-                      : best.rpt == 12 ? set_smem_attr<12>(best.smem)
-                                       : set_smem_attr<16>(best.smem);
+    }
     int occ = 0;
-    const cudaError_t oe =
-        best.rpt == 4    ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, res2d_kernel<4>, kResThreads, best.smem)
-        : best.rpt == 8  ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, res2d_kernel<8>, kResThreads, best.smem)
-        : best.rpt == 12 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, res2d_kernel<12>, kResThreads, best.smem)
-                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, res2d_kernel<16>, kResThreads, best.smem);
-    if (!attr || oe != cudaSuccess || occ < 1 || (long long)best.ntx * best.nty > (long long)occ * nsm) {
+    cudaError_t oe = cudaSuccess;
+    with_kernel(best.rpt, best.sw, [&](auto kern) {
+        oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kResThreads, best.smem);
+    });
+    if (oe != cudaSuccess || occ < 1 || (long long)best.ntx * best.nty > (long long)occ * nsm) {
         (void)cudaGetLastError();
         return false;
     }
@@ -421,16 +515,10 @@ void launch_res2d(const Res2dPlan &p, const float *kap, const float *dco, const 
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-#define HTD_RES2D_LAUNCH(R)                                                                     \
-    (void)cudaLaunchKernelEx(&cfg, res2d_kernel<R>, kap, dco, fre, fim, L, C, ab, nsteps, jim, \
-                             jfin, slot, xbuf, err, p.W, p.H)
-    switch (p.rpt) {
-        case 4: HTD_RES2D_LAUNCH(4); break;
-        case 8: HTD_RES2D_LAUNCH(8); break;
-        case 12: HTD_RES2D_LAUNCH(12); break;
-        default: HTD_RES2D_LAUNCH(16); break;
-    }
-#undef HTD_RES2D_LAUNCH
+    with_kernel(p.rpt, p.sw, [&](auto kern) {
+        (void)cudaLaunchKernelEx(&cfg, kern, kap, dco, fre, fim, L, C, ab, nsteps, jim, jfin, slot,
+                                 xbuf, err, p.W, p.H);
+    });
     ++g_launches;
 }
 

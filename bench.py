@@ -29,13 +29,17 @@ Printed (one JSON line on rank 0):
   secondary_2d the 2-D 1001^2 heterogeneous solve (L2-resident; its step
               kernel -- the one the create-time tuner picks: blocked or
               resident-grid -- is reported against the FP32 pipe, `bound` "alu");
+  config1     the 2-D 101^2 constant-c configuration: time to 1e-6 in plain
+              FP64 (FGMRES and Table 1; exact read-out with left GMRES, the
+              paper's own form) and with the FP32 recurrence;
   batched     the 96-system batched workload solved in lockstep, and the same
               systems solved one at a time;
   adjoint     the two gradients of the 512^2, 8-source adjoint configuration;
   projection  one application with the windowed projection read-out against
               Table 1 (2-D 1001^2 and 3-D 256^3) and the window's cost per step;
   cpu_baseline the FP64 CPU oracle on a bounded sample of the same workload,
-              on one core and on all host cores (independent copies);
+              on one core and on all host cores (independent copies), and its
+              whole FGMRES solve of the 101^2 configuration (config1_solve);
   clocks, gpu_launches  SM clocks sampled during the timed region; kernels
               launched by the library in it.
 
@@ -168,6 +172,9 @@ def parse_args(argv=None):
                     help="also time the gradients of the adjoint configuration (512^2, 8 sources)")
     ap.add_argument("--secondary-2d", type=int, default=1,
                     help="also time the 2-D 1001^2 solve (L2-resident, ALU roofline)")
+    ap.add_argument("--config1", type=int, default=1,
+                    help="also time the 2-D 101^2 constant-c configuration (plain FP64 and "
+                         "mixed, FGMRES and the paper's exact read-out with left GMRES)")
     ap.add_argument("--option", action="append", default=[], metavar="KEY=VALUE",
                     help="kernel-selection field of htd_options for the headline solver")
     return ap.parse_args(argv)
@@ -385,7 +392,60 @@ def cpu_baseline(p, budget_s, all_cores=True):
     return out
 
 
+def cpu_config1_solve():
+    """The oracle's own FGMRES(20) solve of the 2-D 101^2 constant-c workload to
+    a true relative residual of 1e-6 (Table 1 read-out), on one core."""
+    import oracle
+    p, _ = make_workload("2d_const_101")
+    o = oracle.Oracle(p)
+    t0 = time.perf_counter()
+    _, info = o.gmres(p.F, krylov="fgmres", precond="table1", tol=TOL, restart=20, maxit=400)
+    ms = 1e3 * (time.perf_counter() - t0)
+    return {"workload": "2d_const_101", "kind": "oracle", "cores": 1, "time_to_tol_ms": ms,
+            "iterations": int(info["iterations"])}
+
+
 # ---- secondary legs -------------------------------------------------------------
+
+def secondary_config1(htd, stream, reps=5):
+    """The 2-D 101^2 constant-c configuration (120 recurrence steps per
+    application): time to a true relative residual of 1e-6 (CUDA events, one
+    warm-up and `reps` timed solves) in the plain FP64 form with FGMRES(20) and
+    Table 1, in the paper's own form (exact read-out, left GMRES(20)), and with
+    the FP32 recurrence; the step kernel each form runs."""
+    import torch
+    p, _ = make_workload("2d_const_101")
+    N = math.prod(p.n)
+    F = torch.from_numpy(np.ascontiguousarray(p.F)).cuda()
+    U = torch.zeros_like(F)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    out = {"workload": "2d_const_101", "n": list(p.n), "unit": UNIT}
+    forms = {"fp64_fgmres_table1": dict(precision="fp64"),
+             "fp64_left_gmres_exact": dict(precision="fp64", krylov="left", mode="exact"),
+             "mixed_fgmres_table1": dict(precision="mixed")}
+    for name, kw in forms.items():
+        s = htd.Solver(p, restart=20, **kw)
+        prm = s.params
+        times, info = [], None
+        for r in range(reps + 1):
+            U.zero_()
+            e0.record(stream)
+            info = htd.htd_gmres_solve(s.handle, F, U, TOL, 400, stream)
+            e1.record(stream)
+            e1.synchronize()
+            if r > 0:
+                times.append(e0.elapsed_time(e1))
+        s.close()
+        ms = statistics.mean(times)
+        out[name] = {"time_to_tol_ms": ms, "iterations": info["iterations"],
+                     "rel_res_true": info["rel_res_true"],
+                     "value": N * info["steps"] / (ms * 1e-3) / 1e9,
+                     "us_per_step": 1e3 * info["ms_precond"] / max(1, info["steps"]),
+                     "step_kernel": step_kernel_name(prm, 2)[0] if kw["precision"] == "mixed"
+                     else "step2d_kernel<double>", "steps_per_apply": prm["steps"]}
+    return out
+
 
 def secondary_2d(htd, stream, flush, pk, reps=5, fp64=True):
     """The 2-D 1001^2 heterogeneous workload: the mixed FGMRES(20) solve to 1e-6
@@ -866,6 +926,9 @@ def run_ours(args):
     sec2d = None
     if args.secondary_2d and args.workload != "2d_grf_1001":
         sec2d = secondary_2d(htd, stream, flush, pk)
+    config1 = None
+    if args.config1 and args.workload != "2d_const_101":
+        config1 = secondary_config1(htd, stream)
     batched = None
     if args.batched:
         batched = secondary_batched(htd, stream, flush, parts=bool(args.batched_parts))
@@ -881,6 +944,8 @@ def run_ours(args):
         import oracle
         oracle.build()
         cpu = cpu_baseline(p, args.cpu_sample_s)
+        if args.config1:
+            cpu["config1_solve"] = cpu_config1_solve()
 
     ms_per_step = total_ms / args.steps
     if rank == 0:
@@ -905,6 +970,7 @@ def run_ours(args):
             "roofline": roof,
             "cpu_baseline": cpu,
             "secondary_2d": sec2d,
+            "config1": config1,
             "batched": batched,
             "adjoint": adjoint,
             "projection": projection,

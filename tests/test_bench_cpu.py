@@ -86,3 +86,12 @@ def test_traffic_records_follow_the_kernel_source(tmp_path, monkeypatch):
     i = text.index(rec["begin"])
     (csrc / "htd_tblock.cu").write_text(text[:i + 5] + "x" + text[i + 5:])
     assert bench.ncu_traffic("tb2d_pair", rec["nodes"]) is None
+
+
+def test_oracle_solves_the_101_configuration_for_the_cpu_leg():
+    """The CPU leg's whole-solve figure for the 101^2 configuration: the oracle's
+    FGMRES(20) with Table 1 reaches 1e-6 in a handful of iterations."""
+    oracle.build()
+    out = bench.cpu_config1_solve()
+    assert out["kind"] == "oracle" and out["cores"] == 1
+    assert 1 <= out["iterations"] <= 20 and out["time_to_tol_ms"] > 0

@@ -163,7 +163,7 @@ struct htd_ctx {
     // resident-grid 2-D step (FP32, one rhs): a whole run in one cooperative launch
     htd::Res2dPlan res{};
     bool use_res = false;
-    float2 *res_ab = nullptr;               // (a_j, b_j) per step
+    void *res_ab = nullptr;                 // a_j, b_j per step, in the recurrence precision
     unsigned long long *res_x = nullptr;    // edge exchange buffer
     // TMA-streamed 3-D step (FP32)
     htd::Stream3Maps s3maps{};
@@ -259,16 +259,13 @@ htd_status run_steps_direct(htd_ctx *c, cudaStream_t s)
     const bool project = c->opt.mode == HTD_MODE_PROJECT;
     const long long jim = project ? -1 : c->nsteps - c->nP / 4;
     const long long jfin = project ? -1 : c->nsteps;
-    if constexpr (std::is_same<T, float>::value) {
-        if (c->use_res && !project) {
-            // the whole run in one launch; the global state planes are not used
-            htd::launch_res2d(c->res, (const float *)c->kap, (const float *)c->dco,
-                              (const float *)c->fre, (const float *)c->fim, L, C, c->res_ab,
-                              (int)c->nsteps, (int)jim, (int)jfin, c->slot, c->res_x, c->err_dev,
-                              s);
-            HTD_CUDA(cudaGetLastError());
-            return HTD_OK;
-        }
+    if (c->use_res && !project) {
+        // the whole run in one launch; the global state planes are not used
+        htd::launch_res2d<T>(c->res, (const T *)c->kap, (const T *)c->dco, (const T *)c->fre,
+                             (const T *)c->fim, L, C, (const T *)c->res_ab, (int)c->nsteps,
+                             (int)jim, (int)jfin, c->slot, c->res_x, c->err_dev, s);
+        HTD_CUDA(cudaGetLastError());
+        return HTD_OK;
     }
     T *A = (T *)c->u0, *B = (T *)c->u1;
     HTD_CUDA(cudaMemsetAsync(A, 0, sizeof(T) * L.total * c->rcap, s));
@@ -657,6 +654,82 @@ htd_status upload_recurrence(htd_ctx *c, const std::vector<double> &qkap, const 
     return HTD_OK;
 }
 
+// The resident-grid kernel for a single-rhs handle with Table 1 or exact
+// read-out whose grid fits: one whole run untimed, one timed; kept when
+// `force` or when faster per step than c->step_us (the best so far).
+template <typename T>
+htd_status try_res2d(htd_ctx *c, bool force, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1)
+{
+    if (c->rcap != 1 || c->opt.mode == HTD_MODE_PROJECT || c->nsteps >= (1LL << 30)) return HTD_OK;
+    if (!htd::res2d_plan<T>(c->Lr, &c->res)) return HTD_OK;
+    std::vector<T> ab(2 * (size_t)c->nsteps);
+    for (long long j = 0; j < c->nsteps; ++j) {
+        ab[2 * j] = (T)c->atab[j];
+        ab[2 * j + 1] = (T)c->btab[j];
+    }
+    HTD_CUDA(htd::dev_malloc(&c->res_ab, sizeof(T) * ab.size()));
+    HTD_CUDA(cudaMemcpy(c->res_ab, ab.data(), sizeof(T) * ab.size(), cudaMemcpyHostToDevice));
+    HTD_CUDA(htd::dev_malloc(&c->res_x, sizeof(unsigned long long) * c->res.xwords));
+    const StepCoef<T> C = cast_coef<T>(c->C);
+    for (int r = 0; r < 2; ++r) {
+        if (r == 1) HTD_CUDA(cudaEventRecord(e0, s));
+        htd::launch_res2d<T>(c->res, (const T *)c->kap, (const T *)c->dco, (const T *)c->fre,
+                             (const T *)c->fim, c->Lr, C, (const T *)c->res_ab, (int)c->nsteps,
+                             -1, -1, c->slot, c->res_x, c->err_dev, s);
+    }
+    HTD_CUDA(cudaEventRecord(e1, s));
+    HTD_CUDA(cudaEventSynchronize(e1));
+    HTD_CUDA(cudaGetLastError());
+    float ms = 0.f;
+    HTD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    const float us = 1e3f * ms / (float)c->nsteps;
+    if (force || us < c->step_us) {
+        c->use_res = true;
+        c->step_us = us;
+    } else {
+        cudaFree(c->res_ab);
+        cudaFree(c->res_x);
+        c->res_ab = nullptr;
+        c->res_x = nullptr;
+    }
+    return HTD_OK;
+}
+
+// The plain FP64 2-D recurrence: the one-step kernel (one launch per step)
+// against the FP64 resident-grid kernel, each timed on the handle's own
+// (zeroed) planes; the faster is kept (HTD_TB_RESIDENT: the resident kernel
+// whenever it qualifies).
+htd_status autotune_fp64_2d(htd_ctx *c)
+{
+    cudaStream_t s;
+    HTD_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    cudaEvent_t e0, e1;
+    HTD_CUDA(cudaEventCreate(&e0));
+    HTD_CUDA(cudaEventCreate(&e1));
+    const StepCoef<double> C = cast_coef<double>(c->C);
+    const int reps = 64;
+    for (int r = 0; r < 2 + reps; ++r) {
+        if (r == 2) HTD_CUDA(cudaEventRecord(e0, s));
+        htd::launch_step<double>(c->Lr, (const double *)c->u0, (double *)c->u1,
+                                 (const double *)c->kap, (const double *)c->dco,
+                                 (const double *)c->fre, (const double *)c->fim, C, 0.0, 0.0,
+                                 c->slot, 0, s);
+    }
+    HTD_CUDA(cudaEventRecord(e1, s));
+    HTD_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    HTD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    c->step_us = 1e3f * ms / reps;
+    htd_status st = try_res2d<double>(c, c->opt.tb_form == HTD_TB_RESIDENT, s, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    if (st != HTD_OK) return st;
+    int flag = 0;
+    HTD_CUDA(cudaMemcpy(&flag, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
+    return flag ? HTD_ERR_TIMEOUT : HTD_OK;
+}
+
 // Time the one-step kernel, every blocked configuration and, for a single-rhs
 // handle whose grid fits the SMs' shared memory (Table 1 or EXACT read-out),
 // the resident-grid kernel on the handle's own (zeroed) planes, and keep the
@@ -741,39 +814,11 @@ htd_status autotune_tb2d(htd_ctx *c, int want_B, int want_RPT)
         c->tb = cands[best];
         c->tbmaps = best_maps;
     }
-    // the resident-grid kernel: one whole run untimed, one timed
-    const bool res_try = want_B == 0 && want_RPT == 0 && c->rcap == 1 &&
-                         c->opt.mode != HTD_MODE_PROJECT && c->nsteps < (1LL << 30) &&
-                         (form == HTD_TB_ANY || form == HTD_TB_RESIDENT);
-    if (res_try && htd::res2d_plan(L, &c->res)) {
-        std::vector<float2> ab((size_t)c->nsteps);
-        for (long long j = 0; j < c->nsteps; ++j)
-            ab[j] = make_float2((float)c->atab[j], (float)c->btab[j]);
-        HTD_CUDA(htd::dev_malloc(&c->res_ab, sizeof(float2) * ab.size()));
-        HTD_CUDA(cudaMemcpy(c->res_ab, ab.data(), sizeof(float2) * ab.size(),
-                            cudaMemcpyHostToDevice));
-        HTD_CUDA(htd::dev_malloc(&c->res_x, sizeof(unsigned long long) * c->res.xwords));
-        for (int r = 0; r < 2; ++r) {
-            if (r == 1) HTD_CUDA(cudaEventRecord(e0, s));
-            htd::launch_res2d(c->res, (const float *)c->kap, (const float *)c->dco,
-                              (const float *)c->fre, (const float *)c->fim, L, C, c->res_ab,
-                              (int)c->nsteps, -1, -1, c->slot, c->res_x, c->err_dev, s);
-        }
-        HTD_CUDA(cudaEventRecord(e1, s));
-        HTD_CUDA(cudaEventSynchronize(e1));
-        HTD_CUDA(cudaGetLastError());
-        float ms = 0.f;
-        HTD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        const float us = 1e3f * ms / (float)c->nsteps;
-        if (form == HTD_TB_RESIDENT || us < c->step_us) {
-            c->use_res = true;
-            c->step_us = us;
-        } else {
-            cudaFree(c->res_ab);
-            cudaFree(c->res_x);
-            c->res_ab = nullptr;
-            c->res_x = nullptr;
-        }
+    // the resident-grid kernel
+    const bool res_try = want_B == 0 && want_RPT == 0 && (form == HTD_TB_ANY || form == HTD_TB_RESIDENT);
+    if (res_try) {
+        htd_status rs = try_res2d<float>(c, form == HTD_TB_RESIDENT, s, e0, e1);
+        if (rs != HTD_OK) return rs;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1298,6 +1343,12 @@ htd_status create_impl(const htd_grid *grid, const double *c_cell, const double 
         const int want = (opt.tblock == 1) ? 0 : opt.tblock;
         if (d == 2 && mixed && !abd && opt.tblock != 1) {
             htd_status ts = autotune_tb2d(c, want, opt.tb_rows);
+            if (ts != HTD_OK) return ts;
+        }
+        // the plain FP64 2-D recurrence: one-step launches or the resident grid
+        const bool fp64_res_form = opt.tb_form == HTD_TB_ANY || opt.tb_form == HTD_TB_RESIDENT;
+        if (d == 2 && !mixed && !abd && opt.tblock == 0 && fp64_res_form) {
+            htd_status ts = autotune_fp64_2d(c);
             if (ts != HTD_OK) return ts;
         }
     }

@@ -361,10 +361,11 @@ void launch_tb2d(const TbPlan &p, const TbMaps &maps, int in0, int in1, const La
 
 // ---- resident-grid 2-D step (htd_res2d.cu) ------------------------------------
 //
-// A whole run (all steps, FP32, one rhs) in one cooperative launch: ntx x nty
-// tiles of W x H nodes, one CTA per tile and at most one per SM, every tile's
-// states, cells, d and forcing in shared memory; neighbouring tiles swap edge
-// values through `xbuf` (xwords 64-bit words, zeroed by the launcher).
+// A whole run (all steps, one rhs, FP32 or FP64) in one cooperative launch:
+// ntx x nty tiles of W x H nodes, one CTA per tile and at most one per SM,
+// every tile's states, cells, d and forcing in shared memory; neighbouring
+// tiles swap edge values through `xbuf` (xwords 64-bit words, zeroed by the
+// launcher).
 struct Res2dPlan {
     int W = 0, H = 0;            // tile (W even, at most 132); the last tile row / column may be smaller
     int ntx = 0, nty = 0;        // tiles (CTAs) per axis
@@ -374,17 +375,20 @@ struct Res2dPlan {
     size_t xwords = 0;           // exchange buffer words
 };
 
-// The plan for a 2-D grid, or false if the grid does not fit the SMs' shared
-// memory at one tile per SM, or the device cannot launch cooperatively.
+// The plan for a 2-D grid in precision T, or false if the grid does not fit
+// the SMs' shared memory at one tile per SM, or the device cannot launch
+// cooperatively.
+template <typename T>
 bool res2d_plan(const Layout &L, Res2dPlan *p);
 // Steps 0 .. nsteps-1 from zero states with forcing a_j Re F - b_j Im F
-// (ab[j] = (a_j, b_j)); the new state of step jim - 1 goes to the snapshot
-// output, that of step jfin - 1 to the final output (OutSlot of rhs 0).  A
-// wait that runs out sets err[0] = 1.
-void launch_res2d(const Res2dPlan &p, const float *kap, const float *dco, const float *fre,
-                  const float *fim, const Layout &L, const StepCoef<float> &C, const float2 *ab,
-                  int nsteps, int jim, int jfin, const OutSlot *slot, unsigned long long *xbuf,
-                  int *err, cudaStream_t s);
+// (ab[2j] = a_j, ab[2j+1] = b_j); the new state of step jim - 1 goes to the
+// snapshot output, that of step jfin - 1 to the final output (OutSlot of rhs
+// 0).  A wait that runs out sets err[0] = 1.
+template <typename T>
+void launch_res2d(const Res2dPlan &p, const T *kap, const T *dco, const T *fre, const T *fim,
+                  const Layout &L, const StepCoef<T> &C, const T *ab, int nsteps, int jim,
+                  int jfin, const OutSlot *slot, unsigned long long *xbuf, int *err,
+                  cudaStream_t s);
 
 // ---- one persistent launch for many 2-D instances (htd_tblock.cu) -----------
 //

@@ -38,13 +38,55 @@ namespace htd {
 
 namespace {
 
-constexpr int kResThreads = 768;
+// threads per CTA: 768 for FP32 (80 registers each), 512 for FP64 (its
+// register windows are twice as wide)
+template <typename T>
+__host__ __device__ constexpr int res_threads()
+{
+    return sizeof(T) == 8 ? 512 : 768;
+}
 
-__device__ __forceinline__ float2 pr(float a, float b) { return make_float2(a, b); }
+// A node pair (lx, lx + 1) as one value: float2 for the FP32 recurrence
+// (paired FP32 instructions), DPair for FP64 (two scalar FP64 operations, each
+// lane rounded like the one-step kernel's scalar).
+struct __align__(16) DPair {
+    double x, y;
+};
+// (the FP32 and scalar overloads of the enclosing namespace stay visible)
+using htd::vadd;
+using htd::vfma;
+using htd::vmul;
+__device__ __forceinline__ DPair vadd(DPair a, DPair b) { return {__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y)}; }
+__device__ __forceinline__ DPair vmul(DPair a, DPair b) { return {__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y)}; }
+__device__ __forceinline__ DPair vfma(DPair a, DPair b, DPair c)
+{
+    return {__fma_rn(a.x, b.x, c.x), __fma_rn(a.y, b.y, c.y)};
+}
 
-__device__ __forceinline__ float2 ld2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+template <typename T>
+struct PairOf;
+template <>
+struct PairOf<float> {
+    typedef float2 V;
+    __device__ static V make(float a, float b) { return make_float2(a, b); }
+};
+template <>
+struct PairOf<double> {
+    typedef DPair V;
+    __device__ static V make(double a, double b) { return {a, b}; }
+};
 
-__device__ __forceinline__ void st2(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
+template <typename T>
+__device__ __forceinline__ typename PairOf<T>::V ld2(const T *p)
+{
+    return *reinterpret_cast<const typename PairOf<T>::V *>(p);
+}
+
+template <typename T>
+__device__ __forceinline__ void st2(T *p, typename PairOf<T>::V v)
+{
+    *reinterpret_cast<typename PairOf<T>::V *>(p) = v;
+}
 
 __device__ __forceinline__ unsigned long long global_ns()
 {
@@ -61,39 +103,100 @@ __device__ __forceinline__ unsigned long long ld_word(const unsigned long long *
     return v;
 }
 
-__device__ __forceinline__ void st_word(unsigned long long *p, float v, unsigned tag)
+__device__ __forceinline__ void st_word(unsigned long long *p, unsigned bits, unsigned tag)
 {
-    const unsigned long long w = ((unsigned long long)tag << 32) | __float_as_uint(v);
+    const unsigned long long w = ((unsigned long long)tag << 32) | bits;
     asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
 }
 
-// row strides of the shared-memory arrays the kernel is built for (8 banks
-// apart from row to row); a tile of width W uses the smallest one >= W + 4
+// An exchanged value as tagged words: an FP32 value in one word, an FP64 value
+// in two (low and high halves, each with the tag), valid when every tag is the
+// expected one.
+template <typename T>
+struct Xword;
+template <>
+struct Xword<float> {
+    static constexpr int kPer = 1;
+    struct Raw {
+        unsigned long long w;
+    };
+    __device__ static void put(unsigned long long *p, float v, unsigned tag)
+    {
+        st_word(p, __float_as_uint(v), tag);
+    }
+    __device__ static Raw get(const unsigned long long *p) { return {ld_word(p)}; }
+    __device__ static bool ok(const Raw &r, unsigned want) { return (unsigned)(r.w >> 32) == want; }
+    __device__ static float value(const Raw &r) { return __uint_as_float((unsigned)r.w); }
+};
+template <>
+struct Xword<double> {
+    static constexpr int kPer = 2;
+    struct Raw {
+        unsigned long long lo, hi;
+    };
+    __device__ static void put(unsigned long long *p, double v, unsigned tag)
+    {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+        st_word(p, (unsigned)b, tag);
+        st_word(p + 1, (unsigned)(b >> 32), tag);
+    }
+    __device__ static Raw get(const unsigned long long *p) { return {ld_word(p), ld_word(p + 1)}; }
+    __device__ static bool ok(const Raw &r, unsigned want)
+    {
+        return (unsigned)(r.lo >> 32) == want && (unsigned)(r.hi >> 32) == want;
+    }
+    __device__ static double value(const Raw &r)
+    {
+        return __longlong_as_double((long long)((r.hi << 32) | (r.lo & 0xffffffffull)));
+    }
+};
+
+// the step coefficients broadcast to node pairs
+__device__ __forceinline__ Stencil2dCoef<float2> pair_coef(const StepCoef<float> &C)
+{
+    return stencil2d_coef2(C);
+}
+
+__device__ __forceinline__ Stencil2dCoef<DPair> pair_coef(const StepCoef<double> &C)
+{
+    auto b = [](double x) { return DPair{x, x}; };
+    return {b(C.c0), b(C.mt[0]), b(C.mt[1]), b(C.mt[2]), b(-C.cs[1]), b(-C.cs[2])};
+}
+
+// row strides of the shared-memory arrays the kernel is built for (8 banks of
+// 4 bytes apart from row to row for FP32); a tile of width W uses the smallest
+// one >= W + 4
 constexpr int kStrides[] = {72, 136};
 
-__host__ __device__ constexpr size_t res2d_floats(int SW, int H)
+__host__ __device__ constexpr size_t res2d_elems(int SW, int H)
 {
     return 6 * (size_t)(H + 2) * SW;
 }
 
-// Shared memory: six arrays of (H + 2) rows of SW floats -- the states U0, U1,
-// the cells K, and d, Re F, Im F -- with node (lx, ly) of the tile at row
-// ly + 1, column lx + 2 of each (so the pair (lx, lx + 1), lx even, is 8-byte
-// aligned, and one offset addresses a node in all six), the state ring at rows
-// 0 and h + 1 and columns 1 and w + 2, and cell (cx, cy) (its lower corner
-// node) at the place of node (cx, cy).  Exchange buffer of a tile and parity
-// (E = 2W + 2H words): bottom row [0, W), top row [W, 2W), left column
-// [2W, 2W + H), right column [2W + H, 2W + 2H).
-template <int RPT, int SW>
-__global__ void __launch_bounds__(kResThreads, 1)
-res2d_kernel(const float *__restrict__ kap, const float *__restrict__ dco,
-             const float *__restrict__ fre, const float *__restrict__ fim, Layout L,
-             StepCoef<float> C, const float2 *__restrict__ ab, int nsteps, int jim, int jfin,
+// Shared memory: six arrays of (H + 2) rows of SW elements of T -- the states
+// U0, U1, the cells K, and d, Re F, Im F -- with node (lx, ly) of the tile at
+// row ly + 1, column lx + 2 of each (so the pair (lx, lx + 1), lx even, is
+// aligned for one vector access, and one offset addresses a node in all six),
+// the state ring at rows 0 and h + 1 and columns 1 and w + 2, and cell
+// (cx, cy) (its lower corner node) at the place of node (cx, cy).  Exchange
+// buffer of a tile and parity: E = 2W + 2H values (X::kPer words each) --
+// bottom row [0, W), top row [W, 2W), left column [2W, 2W + H), right column
+// [2W + H, 2W + 2H).
+template <typename T, int RPT, int SW>
+__global__ void __launch_bounds__(res_threads<T>(), 1)
+res2d_kernel(const T *__restrict__ kap, const T *__restrict__ dco, const T *__restrict__ fre,
+             const T *__restrict__ fim, Layout L, StepCoef<T> C,
+             const typename PairOf<T>::V *__restrict__ ab, int nsteps, int jim, int jfin,
              const OutSlot *__restrict__ slot, unsigned long long *__restrict__ xbuf,
              int *__restrict__ err, int W, int H)
 {
-    extern __shared__ __align__(16) float sm[];
+    typedef typename PairOf<T>::V V;
+    typedef Xword<T> X;
+    constexpr int NT = res_threads<T>();
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *sm = reinterpret_cast<T *>(smraw);
     __shared__ int s_abort;
+    auto pr = [](T a, T b) { return PairOf<T>::make(a, b); };
     const int tid = threadIdx.x;
     const int tx = blockIdx.x, ty = blockIdx.y;
     const int ntx = gridDim.x, nty = gridDim.y;
@@ -101,14 +204,14 @@ res2d_kernel(const float *__restrict__ kap, const float *__restrict__ dco,
     const int w = (int)min((int64_t)W, L.nx - x0);
     const int h = (int)min((int64_t)H, L.ny - y0);
     const int NA = (H + 2) * SW;
-    float *U0 = sm, *U1 = sm + NA, *K = sm + 2 * NA;
-    float *D = sm + 3 * NA, *FR = sm + 4 * NA, *FI = sm + 5 * NA;
-    const int E = 2 * W + 2 * H;
+    T *U0 = sm, *U1 = sm + NA, *K = sm + 2 * NA;
+    T *D = sm + 3 * NA, *FR = sm + 4 * NA, *FI = sm + 5 * NA;
+    const int EW = (2 * W + 2 * H) * X::kPer;          // exchange words per tile and parity
 
     if (tid == 0) s_abort = 0;
-    for (int i = tid; i < NA; i += kResThreads) {
+    for (int i = tid; i < NA; i += NT) {
         const int ly = i / SW - 1, lx = i % SW - 2;
-        float k = 0.f, dv = 0.f, fr = 0.f, fi = 0.f;
+        T k = 0, dv = 0, fr = 0, fi = 0;
         if (lx >= -1 && lx < w && ly >= -1 && ly < h) {
             const int64_t g = (y0 + ly + 1) * L.pitch + L.xl + x0 + lx;
             k = kap[g];                                // cell (lx, ly)
@@ -157,7 +260,7 @@ res2d_kernel(const float *__restrict__ kap, const float *__restrict__ dco,
         }
         lx = 2 * p;
     };
-    const int ea = kResThreads - 1 - tid;              // this thread's first edge task
+    const int ea = NT - 1 - tid;              // this thread's first edge task
     int e_lx = 0, e_ly = 0;
     if (ea < nA) edge_of(ea, e_lx, e_ly);
     // (2) strip t: column pair, first row, rows
@@ -200,26 +303,25 @@ res2d_kernel(const float *__restrict__ kap, const float *__restrict__ dco,
             dst = ((c & 2) ? h + 1 : 0) * SW + ((c & 1) ? w + 2 : 1);
         }
         if (nbx < 0 || nbx >= ntx || nby < 0 || nby >= nty) return -1;
-        return (nby * ntx + nbx) * 2 * E + idx;
+        return (nby * ntx + nbx) * 2 * EW + idx * X::kPer;
     };
     int r_dst = 0;
     const int r_src = (tid < nslot) ? slot_of(tid, r_dst) : -1;
 
-    // store slot word v (read from p) of state s into U at dst, reading it again
-    // until it carries the tag of state s (bounded by the handle's limit; with
-    // the stall test the first wait of CTA (0, 0) expects a tag no word has)
-    auto complete = [&](const unsigned long long *p, unsigned long long v, int s, int dst,
-                        float *U) {
+    // store slot value v (read from p) of state s into U at dst, reading it again
+    // until its words carry the tag of state s (bounded by the handle's limit;
+    // with the stall test the first wait of CTA (0, 0) expects a tag no word has)
+    auto complete = [&](const unsigned long long *p, typename X::Raw v, int s, int dst, T *U) {
         unsigned want = (unsigned)(s + 1);
         if (s == 1 && tx == 0 && ty == 0 && *(volatile const int *)(err + 1) != 0)
             want = 0xffffffffu;
-        if ((unsigned)(v >> 32) != want) {
+        if (!X::ok(v, want)) {
             unsigned long long lim = *reinterpret_cast<volatile const unsigned long long *>(err + 2);
             if (lim == 0) lim = kDefaultWaitNs;
             const unsigned long long t0 = global_ns();
             for (int it = 1;; ++it) {
-                v = ld_word(p);
-                if ((unsigned)(v >> 32) == want) break;
+                v = X::get(p);
+                if (X::ok(v, want)) break;
                 if ((it & 31) == 0 && *(volatile int *)err) {
                     s_abort = 1;
                     return;
@@ -231,27 +333,27 @@ res2d_kernel(const float *__restrict__ kap, const float *__restrict__ dco,
                 }
             }
         }
-        U[dst] = __uint_as_float((unsigned)v);
+        U[dst] = X::value(v);
     };
 
-    const Stencil2dCoef<float2> SC = stencil2d_coef2(C);
-    const float2 n2 = pr(-2.f, -2.f);
+    const Stencil2dCoef<V> SC = pair_coef(C);
+    const V n2 = pr(T(-2), T(-2));
     // u row at q (the node lx - 1 of the row) as the pairs (m, 0, p) =
     // (u(lx-1+o), u(lx+o)), o = 0, 1, 2
-    auto urow = [&](const float *q, float2 &m, float2 &z, float2 &p) {
-        const float l = q[0];
+    auto urow = [&](const T *q, V &m, V &z, V &p) {
+        const T l = q[0];
         z = ld2(q + 1);
-        const float r = q[3];
+        const T r = q[3];
         m = pr(l, z.x);
         p = pr(z.y, r);
     };
     // cells at q (the cell lx - 1 of a cell row): k0 = cells left of the nodes
     // (lx-1, lx), k1 = cells right of them
-    auto krow = [&](const float *q, float2 &k0, float2 &k1) {
+    auto krow = [&](const T *q, V &k0, V &k1) {
         k1 = ld2(q + 1);
         k0 = pr(q[0], k1.x);
     };
-    auto output = [&](int lx, int ly, float2 u, int fl, bool two) {
+    auto output = [&](int lx, int ly, V u, int fl, bool two) {
         const int64_t c = ((int64_t)blockIdx.y * H + ly) * L.nx + (int64_t)blockIdx.x * W + lx;
         if ((fl & 1) && slot->snap_part) {
             slot->snap_part[2 * c] = (double)u.x;
@@ -264,39 +366,39 @@ res2d_kernel(const float *__restrict__ kap, const float *__restrict__ dco,
     };
     // the new state of the pair at node offset o (row ly + 1, column lx + 2)
     // from its stencil sum
-    auto update = [&](int o, float2 acc, float2 a2, float2 nb2, float *nxt) -> float2 {
-        const float2 ag = vfma(a2, ld2(FR + o), vfma(nb2, ld2(FI + o), acc));
-        const float2 uprev = ld2(nxt + o);
+    auto update = [&](int o, V acc, V a2, V nb2, T *nxt) -> V {
+        const V ag = vfma(a2, ld2(FR + o), vfma(nb2, ld2(FI + o), acc));
+        const V uprev = ld2(nxt + o);
         return vfma(ld2(D + o), vfma(n2, uprev, ag), uprev);
     };
     // nr <= RPT interior rows r0 .. r0+nr-1 of the column pair lx; the read of
     // the ring word at rp (if any) is issued before the third row
-    auto strip = [&](int lx, int r0, int nr, const float *cur, float *nxt, float2 a2, float2 nb2,
-                     int fl, const unsigned long long *rp, unsigned long long &rv, bool &issued) {
+    auto strip = [&](int lx, int r0, int nr, const T *cur, T *nxt, V a2, V nb2, int fl,
+                     const unsigned long long *rp, typename X::Raw &rv, bool &issued) {
         const int o0 = r0 * SW + lx + 1;               // node (lx - 1, r0 - 1)
-        const float *qc = cur + o0, *qk = K + o0;
-        float2 umm, um0, ump, u0m, u00, u0p, k00, k01;
+        const T *qc = cur + o0, *qk = K + o0;
+        V umm, um0, ump, u0m, u00, u0p, k00, k01;
         urow(qc, umm, um0, ump);
         urow(qc + SW, u0m, u00, u0p);
-        float2 pm = vadd(umm, ump), p0 = vadd(u0m, u0p);
+        V pm = vadd(umm, ump), p0 = vadd(u0m, u0p);
         krow(qk, k00, k01);
-        float2 hk0 = vadd(k00, k01);
+        V hk0 = vadd(k00, k01);
 #pragma unroll
         for (int i = 0; i < RPT; ++i) {
             if (i >= nr) break;
             if (i == 2 && rp) {
-                rv = ld_word(rp);
+                rv = X::get(rp);
                 issued = true;
             }
-            float2 upm, up0, upp, k10, k11;
+            V upm, up0, upp, k10, k11;
             urow(qc + (i + 2) * SW, upm, up0, upp);
             krow(qk + (i + 1) * SW, k10, k11);
-            const float2 pp = vadd(upm, upp);
-            const float2 hk1 = vadd(k10, k11);
-            const float2 acc = stencil2d(SC, umm, um0, ump, u0m, u00, u0p, upm, up0, upp, k00, k01,
+            const V pp = vadd(upm, upp);
+            const V hk1 = vadd(k10, k11);
+            const V acc = stencil2d(SC, umm, um0, ump, u0m, u00, u0p, upm, up0, upp, k00, k01,
                                          k10, k11, pm, p0, pp, hk0, hk1);
             const int o = o0 + (i + 1) * SW + 1;       // node (lx, r0 + i)
-            const float2 unew = update(o, acc, a2, nb2, nxt);
+            const V unew = update(o, acc, a2, nb2, nxt);
             st2(nxt + o, unew);
             if (fl) output(lx, r0 + i, unew, fl, true);
             umm = u0m; um0 = u00; ump = u0p; pm = p0;
@@ -307,38 +409,38 @@ res2d_kernel(const float *__restrict__ kap, const float *__restrict__ dco,
 
     __syncthreads();
     for (int j = 0; j < nsteps; ++j) {
-        const float *cur = (j & 1) ? U1 : U0;          // u_j (ring filled)
-        float *nxt = (j & 1) ? U0 : U1;                // u_{j-1}, becomes u_{j+1}
-        const float2 abj = __ldg(ab + j);
-        const float2 a2 = pr(abj.x, abj.x), nb2 = pr(-abj.y, -abj.y);
+        const T *cur = (j & 1) ? U1 : U0;              // u_j (ring filled)
+        T *nxt = (j & 1) ? U0 : U1;                    // u_{j-1}, becomes u_{j+1}
+        const V abj = ab[j];
+        const V a2 = pr(abj.x, abj.x), nb2 = pr(-abj.y, -abj.y);
         const int fl = ((j + 1 == jim) ? 1 : 0) | ((j + 1 == jfin) ? 2 : 0);
         const bool more = j + 1 < nsteps;
 
         // (1) edge pairs, published as they are computed
         if (ea < nA) {
             const unsigned tag = (unsigned)(j + 2);
-            unsigned long long *pub = xbuf + (size_t)((ty * ntx + tx) * 2 + ((j + 1) & 1)) * E;
-            auto publish = [&](int lx, int ly, float v) {
-                if (ly == 0) st_word(pub + lx, v, tag);
-                if (ly == h - 1) st_word(pub + W + lx, v, tag);
-                if (lx == 0) st_word(pub + 2 * W + ly, v, tag);
-                if (lx == w - 1) st_word(pub + 2 * W + H + ly, v, tag);
+            unsigned long long *pub = xbuf + (size_t)((ty * ntx + tx) * 2 + ((j + 1) & 1)) * EW;
+            auto publish = [&](int lx, int ly, T v) {
+                if (ly == 0) X::put(pub + X::kPer * lx, v, tag);
+                if (ly == h - 1) X::put(pub + X::kPer * (W + lx), v, tag);
+                if (lx == 0) X::put(pub + X::kPer * (2 * W + ly), v, tag);
+                if (lx == w - 1) X::put(pub + X::kPer * (2 * W + H + ly), v, tag);
             };
-            for (int a = ea; a < nA; a += kResThreads) {
+            for (int a = ea; a < nA; a += NT) {
                 int lx = e_lx, ly = e_ly;
                 if (a != ea) edge_of(a, lx, ly);
                 const int o = (ly + 1) * SW + lx + 2;
-                float2 umm, um0, ump, u0m, u00, u0p, upm, up0, upp, k00, k01, k10, k11;
+                V umm, um0, ump, u0m, u00, u0p, upm, up0, upp, k00, k01, k10, k11;
                 urow(cur + o - SW - 1, umm, um0, ump);
                 urow(cur + o - 1, u0m, u00, u0p);
                 urow(cur + o + SW - 1, upm, up0, upp);
                 krow(K + o - SW - 1, k00, k01);
                 krow(K + o - 1, k10, k11);
-                const float2 acc =
+                const V acc =
                     stencil2d(SC, umm, um0, ump, u0m, u00, u0p, upm, up0, upp, k00, k01, k10, k11,
                               vadd(umm, ump), vadd(u0m, u0p), vadd(upm, upp), vadd(k00, k01),
                               vadd(k10, k11));
-                const float2 unew = update(o, acc, a2, nb2, nxt);
+                const V unew = update(o, acc, a2, nb2, nxt);
                 const bool two = lx + 1 < w;                // the second node is in the tile
                 if (two) st2(nxt + o, unew);
                 else nxt[o] = unew.x;
@@ -350,66 +452,65 @@ res2d_kernel(const float *__restrict__ kap, const float *__restrict__ dco,
 
         // (2) the interior strip, with the read of this thread's ring slot
         const unsigned long long *rp =
-            (more && r_src >= 0) ? xbuf + r_src + ((j + 1) & 1) * E : nullptr;
-        unsigned long long rv = 0;
+            (more && r_src >= 0) ? xbuf + r_src + ((j + 1) & 1) * EW : nullptr;
+        typename X::Raw rv{};
         bool issued = false;
         if (has_strip) strip(s_lx, s_r0, s_nr, cur, nxt, a2, nb2, fl, rp, rv, issued);
-        for (int t = tid + kResThreads; t < nS; t += kResThreads) {
+        for (int t = tid + NT; t < nS; t += NT) {
             int lx, r0, nr;
             if (strip_of(t, lx, r0, nr))
                 strip(lx, r0, nr, cur, nxt, a2, nb2, fl, nullptr, rv, issued);
         }
 
         // (3) the ring of u_{j+1}
-        if (rp) complete(rp, issued ? rv : ld_word(rp), j + 1, r_dst, nxt);
+        if (rp) complete(rp, issued ? rv : X::get(rp), j + 1, r_dst, nxt);
         if (more)
-            for (int k = tid + kResThreads; k < nslot; k += kResThreads) {
+            for (int k = tid + NT; k < nslot; k += NT) {
                 int dst = 0;
                 const int src = slot_of(k, dst);
                 if (src < 0) continue;
-                const unsigned long long *p = xbuf + src + ((j + 1) & 1) * E;
-                complete(p, ld_word(p), j + 1, dst, nxt);
+                const unsigned long long *p = xbuf + src + ((j + 1) & 1) * EW;
+                complete(p, X::get(p), j + 1, dst, nxt);
             }
         __syncthreads();
         if (s_abort) break;
     }
 }
 
-// the kernel for (RPT rows per strip, row stride SW), for every pair a plan
-// may choose
+// the kernel for (precision, RPT rows per strip, row stride SW), for every
+// pair (RPT, SW) a plan may choose
 constexpr int kRpts[] = {3, 5, 8};
 
-template <typename Fn>
+template <typename T, typename Fn>
 void with_kernel(int rpt, int sw, Fn &&fn)
 {
     if (sw == 72) {
-        if (rpt == 3) fn(res2d_kernel<3, 72>);
-        else if (rpt == 5) fn(res2d_kernel<5, 72>);
-        else fn(res2d_kernel<8, 72>);
+        if (rpt == 3) fn(res2d_kernel<T, 3, 72>);
+        else if (rpt == 5) fn(res2d_kernel<T, 5, 72>);
+        else fn(res2d_kernel<T, 8, 72>);
     } else {
-        if (rpt == 3) fn(res2d_kernel<3, 136>);
-        else if (rpt == 5) fn(res2d_kernel<5, 136>);
-        else fn(res2d_kernel<8, 136>);
+        if (rpt == 3) fn(res2d_kernel<T, 3, 136>);
+        else if (rpt == 5) fn(res2d_kernel<T, 5, 136>);
+        else fn(res2d_kernel<T, 8, 136>);
     }
 }
 
 // Rows of work of the busiest thread of a full W x H tile with RPT rows per
 // strip (an edge pair counted as two rows: it has no register window), or -1
 // if there are more strips than threads.
-int res2d_load(int W, int H, int rpt)
+int res2d_load(int W, int H, int rpt, int NT)
 {
     const int PW = (W + 1) / 2, PL = PW - 1;
     const int nrow = std::max(0, H - 2);
     const int nS = std::max(0, PL - 1) * ((nrow + rpt - 1) / rpt);
     const int nA = ((H >= 2) ? 2 : 1) * PW + nrow * ((PL > 0) ? 2 : 1);
-    if (nS > kResThreads) return -1;
-    const int edges = (nA + kResThreads - 1) / kResThreads;     // edge pairs per thread
-    return std::min(rpt, nrow) + 2 * (nS + nA > kResThreads ? edges : 0);
+    if (nS > NT) return -1;
+    const int edges = (nA + NT - 1) / NT;                       // edge pairs per thread
+    return std::min(rpt, nrow) + 2 * (nS + nA > NT ? edges : 0);
 }
 
-}  // namespace
-
-bool res2d_plan(const Layout &L, Res2dPlan *out)
+template <typename T>
+bool plan_impl(const Layout &L, Res2dPlan *out)
 {
     if (L.d != 2 || L.nx < 1 || L.ny < 1) return false;
     int dev = 0, nsm = 0, coop = 0, maxsm = 0;
@@ -429,7 +530,7 @@ bool res2d_plan(const Layout &L, Res2dPlan *out)
     bool attr_ok = true;
     for (int sw : kStrides)
         for (int r : kRpts)
-            with_kernel(r, sw, [&](auto kern) {
+            with_kernel<T>(r, sw, [&](auto kern) {
                 cudaFuncAttributes fa;
                 if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) {
                     attr_ok = false;
@@ -461,7 +562,7 @@ bool res2d_plan(const Layout &L, Res2dPlan *out)
         for (int s : kStrides)
             if (sw == 0 && W + 4 <= s) sw = s;
         if (sw == 0 || H > 4096) continue;
-        const size_t smem = res2d_floats(sw, (int)H) * sizeof(float);
+        const size_t smem = res2d_elems(sw, (int)H) * sizeof(T);
         if (smem > (size_t)avail) continue;
         const long long area = W * H, edge = W + H;
         if (best_area < 0 || area < best_area || (area == best_area && edge < best_edge)) {
@@ -479,7 +580,7 @@ bool res2d_plan(const Layout &L, Res2dPlan *out)
     best.rpt = kRpts[sizeof(kRpts) / sizeof(kRpts[0]) - 1];
     int best_load = -1;
     for (int r : kRpts) {
-        const int ld = res2d_load(best.W, best.H, r);
+        const int ld = res2d_load(best.W, best.H, r, res_threads<T>());
         if (ld >= 0 && (best_load < 0 || ld < best_load)) {
             best_load = ld;
             best.rpt = r;
@@ -487,27 +588,38 @@ bool res2d_plan(const Layout &L, Res2dPlan *out)
     }
     int occ = 0;
     cudaError_t oe = cudaSuccess;
-    with_kernel(best.rpt, best.sw, [&](auto kern) {
-        oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kResThreads, best.smem);
+    with_kernel<T>(best.rpt, best.sw, [&](auto kern) {
+        oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, res_threads<T>(),
+                                                           best.smem);
     });
     if (oe != cudaSuccess || occ < 1 || (long long)best.ntx * best.nty > (long long)occ * nsm) {
         (void)cudaGetLastError();
         return false;
     }
-    best.xwords = (size_t)best.ntx * best.nty * 2 * (2 * (size_t)best.W + 2 * (size_t)best.H);
+    best.xwords = (size_t)best.ntx * best.nty * 2 * (2 * (size_t)best.W + 2 * (size_t)best.H) *
+                  Xword<T>::kPer;
     *out = best;
     return true;
 }
 
-void launch_res2d(const Res2dPlan &p, const float *kap, const float *dco, const float *fre,
-                  const float *fim, const Layout &L, const StepCoef<float> &C, const float2 *ab,
-                  int nsteps, int jim, int jfin, const OutSlot *slot, unsigned long long *xbuf,
-                  int *err, cudaStream_t s)
+}  // namespace
+
+template <typename T>
+bool res2d_plan(const Layout &L, Res2dPlan *p)
+{
+    return plan_impl<T>(L, p);
+}
+
+template <typename T>
+void launch_res2d(const Res2dPlan &p, const T *kap, const T *dco, const T *fre, const T *fim,
+                  const Layout &L, const StepCoef<T> &C, const T *ab, int nsteps, int jim,
+                  int jfin, const OutSlot *slot, unsigned long long *xbuf, int *err,
+                  cudaStream_t s)
 {
     (void)cudaMemsetAsync(xbuf, 0, p.xwords * sizeof(unsigned long long), s);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)p.ntx, (unsigned)p.nty);
-    cfg.blockDim = dim3(kResThreads);
+    cfg.blockDim = dim3(res_threads<T>());
     cfg.dynamicSmemBytes = p.smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -515,11 +627,23 @@ void launch_res2d(const Res2dPlan &p, const float *kap, const float *dco, const 
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    with_kernel(p.rpt, p.sw, [&](auto kern) {
-        (void)cudaLaunchKernelEx(&cfg, kern, kap, dco, fre, fim, L, C, ab, nsteps, jim, jfin, slot,
-                                 xbuf, err, p.W, p.H);
+    const auto *abv = reinterpret_cast<const typename PairOf<T>::V *>(ab);
+    with_kernel<T>(p.rpt, p.sw, [&](auto kern) {
+        (void)cudaLaunchKernelEx(&cfg, kern, kap, dco, fre, fim, L, C, abv, nsteps, jim, jfin,
+                                 slot, xbuf, err, p.W, p.H);
     });
     ++g_launches;
 }
+
+template bool res2d_plan<float>(const Layout &, Res2dPlan *);
+template bool res2d_plan<double>(const Layout &, Res2dPlan *);
+template void launch_res2d<float>(const Res2dPlan &, const float *, const float *, const float *,
+                                  const float *, const Layout &, const StepCoef<float> &,
+                                  const float *, int, int, int, const OutSlot *,
+                                  unsigned long long *, int *, cudaStream_t);
+template void launch_res2d<double>(const Res2dPlan &, const double *, const double *,
+                                   const double *, const double *, const Layout &,
+                                   const StepCoef<double> &, const double *, int, int, int,
+                                   const OutSlot *, unsigned long long *, int *, cudaStream_t);
 
 }  // namespace htd

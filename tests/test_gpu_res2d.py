@@ -1,4 +1,4 @@
-"""The resident-grid 2-D kernel (HTD_TB_RESIDENT, step kernel 4).
+"""The resident-grid 2-D kernel (HTD_TB_RESIDENT, step kernel 4), FP32 and FP64.
 
 One cooperative launch runs a whole preconditioner run with the grid held in
 shared memory across the SMs; neighbouring tiles swap their edge values through
@@ -169,3 +169,60 @@ def test_a_resident_handle_joining_a_batch_uses_its_blocked_configuration():
     b.close()
     s.close()
     t.close()
+
+
+# ---- the plain FP64 recurrence -------------------------------------------------
+
+@pytest.mark.parametrize("n", [(37, 29), (5, 700), (130, 257), (101, 101)])
+def test_fp64_resident_equals_the_fp64_one_step_kernel(n):
+    """FP64: each exchanged value travels as two tagged 32-bit halves; the
+    arithmetic per node is the one-step FP64 kernel's, so the outputs agree bit
+    for bit (Table 1 and exact read-out)."""
+    p = _problem(n, T=2)
+    for mode in ("table1", "exact"):
+        s1 = htd.Solver(p, precision="fp64", mode=mode, tblock=1)
+        sr = htd.Solver(p, precision="fp64", mode=mode, tb_form=htd.TB_RESIDENT)
+        assert s1.params["step_kernel"] == 0 and sr.params["step_kernel"] == 4
+        U1 = s1.precond(dev(p.F)).cpu().numpy()
+        Ur = sr.precond(dev(p.F)).cpu().numpy()
+        s1.close()
+        sr.close()
+        assert np.isfinite(Ur).all() and np.abs(Ur).max() > 0
+        assert np.array_equal(Ur, U1), (mode, float(np.abs(Ur - U1).max()))
+
+
+def test_fp64_resident_config1_solve_matches_the_oracle():
+    """The 101^2 configuration in plain FP64 through the resident kernel: one
+    full application within 1e-10 of the oracle, and FGMRES(20) to 1e-6 with the
+    one-step kernel's iterates exactly."""
+    p = W.config_2d_constant(101)
+    sr = htd.Solver(p, precision="fp64", tb_form=htd.TB_RESIDENT)
+    assert sr.params["step_kernel"] == 4
+    U = sr.precond(dev(p.F)).cpu().numpy()
+    ref = oracle.Oracle(p).precond(p.F)
+    a, b = U.reshape(-1), ref.reshape(-1)
+    assert np.linalg.norm(a - b) / np.linalg.norm(b) <= 1e-10
+    assert np.abs(a - b).max() / np.abs(b).max() <= 1e-10
+    Ur, ir = sr.solve(dev(p.F), tol=1e-6)
+    s1 = htd.Solver(p, precision="fp64", tblock=1)
+    U1, i1 = s1.solve(dev(p.F), tol=1e-6)
+    assert ir["converged"] and ir["iterations"] == i1["iterations"]
+    assert np.array_equal(Ur.cpu().numpy(), U1.cpu().numpy())
+    sr.close()
+    s1.close()
+
+
+def test_fp64_resident_wait_runs_out_then_the_handle_solves():
+    p = W.config_2d_constant(101)
+    s = htd.Solver(p, precision="fp64", tb_form=htd.TB_RESIDENT)
+    assert s.params["step_kernel"] == 4
+    F = dev(p.F)
+    htd.htd_set_wait_limit(s.handle, 1_000_000, stall_test=True)
+    U = s.zeros()
+    with pytest.raises(htd.HtdError) as e:
+        htd.htd_gmres_solve(s.handle, F, U, 1e-6, 2)
+    assert e.value.status == TIMEOUT
+    htd.htd_set_wait_limit(s.handle, 0, stall_test=False)
+    U.zero_()
+    assert htd.htd_gmres_solve(s.handle, F, U, 1e-6, 100)["converged"]
+    s.close()

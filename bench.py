@@ -112,11 +112,15 @@ WORKLOADS = ["3d_layered_256", "2d_grf_1001", "3d_layered_192", "2d_const_101",
              "3d_paper_shape", "3d_paper_shape_4hz", "3d_paper_shape_6hz"]
 
 
-def step_kernel_name(prm, ndim):
-    """(name, traffic key) of the recurrence kernel a context uses."""
+def step_kernel_name(prm, ndim, prec="float"):
+    """(name, traffic key) of the recurrence kernel a context uses (prec: the
+    recurrence precision, "float" or "double")."""
     sk = prm.get("step_kernel")
     if sk == 4:
-        return f"res2d_kernel<{prm['tile'][0]}x{prm['tile'][1]}>", None
+        p = "" if prec == "float" else "double,"
+        return f"res2d_kernel<{p}{prm['tile'][0]}x{prm['tile'][1]}>", None
+    if prec == "double":
+        return f"step{ndim}d_kernel<double>", None
     if sk == 1:
         if prm["tile"][2] == 2:
             return f"tb2d_pair_kernel<{prm['steps_per_launch']}>", "tb2d_pair"
@@ -442,8 +446,9 @@ def secondary_config1(htd, stream, reps=5):
                      "rel_res_true": info["rel_res_true"],
                      "value": N * info["steps"] / (ms * 1e-3) / 1e9,
                      "us_per_step": 1e3 * info["ms_precond"] / max(1, info["steps"]),
-                     "step_kernel": step_kernel_name(prm, 2)[0] if kw["precision"] == "mixed"
-                     else "step2d_kernel<double>", "steps_per_apply": prm["steps"]}
+                     "step_kernel": step_kernel_name(
+                         prm, 2, "float" if kw["precision"] == "mixed" else "double")[0],
+                     "steps_per_apply": prm["steps"]}
     return out
 
 

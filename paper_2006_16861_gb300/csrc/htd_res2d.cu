@@ -31,6 +31,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "htd_internal.h"
 
@@ -373,8 +374,12 @@ res2d_kernel(const T *__restrict__ kap, const T *__restrict__ dco, const T *__re
     };
     // nr <= RPT interior rows r0 .. r0+nr-1 of the column pair lx; the read of
     // the ring word at rp (if any) is issued before the third row
+    // (kFull: nr == RPT, so the unrolled rows need no test; kOut: a step with
+    // output flags)
     auto strip = [&](int lx, int r0, int nr, const T *cur, T *nxt, V a2, V nb2, int fl,
-                     const unsigned long long *rp, typename X::Raw &rv, bool &issued) {
+                     const unsigned long long *rp, typename X::Raw &rv, bool &issued,
+                     auto full_tag, auto out_tag) {
+        constexpr bool kFull = decltype(full_tag)::value, kOut = decltype(out_tag)::value;
         const int o0 = r0 * SW + lx + 1;               // node (lx - 1, r0 - 1)
         const T *qc = cur + o0, *qk = K + o0;
         V umm, um0, ump, u0m, u00, u0p, k00, k01;
@@ -385,7 +390,7 @@ res2d_kernel(const T *__restrict__ kap, const T *__restrict__ dco, const T *__re
         V hk0 = vadd(k00, k01);
 #pragma unroll
         for (int i = 0; i < RPT; ++i) {
-            if (i >= nr) break;
+            if (!kFull && i >= nr) break;
             if (i == 2 && rp) {
                 rv = X::get(rp);
                 issued = true;
@@ -400,7 +405,7 @@ res2d_kernel(const T *__restrict__ kap, const T *__restrict__ dco, const T *__re
             const int o = o0 + (i + 1) * SW + 1;       // node (lx, r0 + i)
             const V unew = update(o, acc, a2, nb2, nxt);
             st2(nxt + o, unew);
-            if (fl) output(lx, r0 + i, unew, fl, true);
+            if (kOut) output(lx, r0 + i, unew, fl, true);
             umm = u0m; um0 = u00; ump = u0p; pm = p0;
             u0m = upm; u00 = up0; u0p = upp; p0 = pp;
             k00 = k10; k01 = k11; hk0 = hk1;
@@ -455,11 +460,20 @@ res2d_kernel(const T *__restrict__ kap, const T *__restrict__ dco, const T *__re
             (more && r_src >= 0) ? xbuf + r_src + ((j + 1) & 1) * EW : nullptr;
         typename X::Raw rv{};
         bool issued = false;
-        if (has_strip) strip(s_lx, s_r0, s_nr, cur, nxt, a2, nb2, fl, rp, rv, issued);
+        using T_ = std::true_type;
+        using F_ = std::false_type;
+        if (has_strip) {
+            if (s_nr == RPT) {
+                if (fl) strip(s_lx, s_r0, s_nr, cur, nxt, a2, nb2, fl, rp, rv, issued, T_{}, T_{});
+                else strip(s_lx, s_r0, s_nr, cur, nxt, a2, nb2, fl, rp, rv, issued, T_{}, F_{});
+            } else {
+                strip(s_lx, s_r0, s_nr, cur, nxt, a2, nb2, fl, rp, rv, issued, F_{}, T_{});
+            }
+        }
         for (int t = tid + NT; t < nS; t += NT) {
             int lx, r0, nr;
             if (strip_of(t, lx, r0, nr))
-                strip(lx, r0, nr, cur, nxt, a2, nb2, fl, nullptr, rv, issued);
+                strip(lx, r0, nr, cur, nxt, a2, nb2, fl, nullptr, rv, issued, F_{}, T_{});
         }
 
         // (3) the ring of u_{j+1}

@@ -13,9 +13,11 @@ required to be <= 1e-6 after FGMRES run to the tolerance stated per
 configuration (Sec. 2.4; the FP32 preconditioner is inexact, the flexible
 method keeps the Arnoldi relation exact in FP64).
 
-Also at full size: one FP64 preconditioner application with all T n_P steps
-(2-D 1001^2, T = 125; the 3-D recipe at 64^3 with the 256^3 configuration's
-T = 32) against the oracle within 1e-10, and a short FP32 run of
+Also at full size: one preconditioner application with all T n_P steps
+(2-D 1001^2, T = 125, in FP64 within 1e-10 and with the tuned FP32 kernel
+within fp32_tol(T), which grows with T -- see fp32_tol; the 3-D recipe at
+64^3 with the 256^3 configuration's T = 32) against the oracle, and a short
+FP32 run of
 the bench's step kernels on their full grids (the blocked 2-D kernel at 1001^2,
 the streamed 3-D kernel at 256^3) against the oracle within 2e-5, relative L2
 and maximum norm.
@@ -164,16 +166,37 @@ def test_config_adjoint_forward_solve_against_fp64():
     assert e_tight <= 1e-6
 
 
-def test_fp64_full_application_at_1001_matches_the_oracle():
-    """All 1500 steps of one Table 1 application on the 1001^2 configuration in
-    FP64 against the oracle: relative L2 and maximum norm within 1e-10."""
+EPS32 = 2.0 ** -24
+
+
+def fp32_tol(T):
+    """Tolerance of one FP32 application of T periods against the FP64 oracle.
+    Rounding the recurrence's coefficients (q*kappa, d, the step scalars) to
+    FP32 perturbs each discrete frequency by a relative O(EPS32), so after T
+    periods the response drifts in phase by about 2 pi T EPS32; the per-step
+    rounding adds a random walk of about sqrt(T n_P) EPS32, far below it for
+    the configurations' T.  Twice the drift, and never below the 2e-5 used
+    for short runs."""
+    return max(2e-5, 2.0 * 2.0 * math.pi * T * EPS32)
+
+
+def test_full_application_at_1001_matches_the_oracle():
+    """All 1500 steps of one Table 1 application on the 1001^2 configuration
+    against the oracle: FP64 within 1e-10, and the FP32 recurrence the tuner
+    picks (the kernel the bench times) within fp32_tol(125) = 9.4e-5, relative
+    L2 and maximum norm."""
     p = W.config_2d_heterogeneous(1001)
-    s = htd.Solver(p, precision="fp64")
-    assert s.params["steps"] == 1500
-    U = s.precond(dev(p.F)).cpu().numpy()
-    s.close()
     ref = oracle.Oracle(p).precond(p.F)
-    assert rel(U, ref) <= 1e-10 and maxrel(U, ref) <= 1e-10, (rel(U, ref), maxrel(U, ref))
+    for precision, tol in (("fp64", 1e-10), ("mixed", fp32_tol(p.T))):
+        s = htd.Solver(p, precision=precision)
+        assert s.params["steps"] == 1500
+        U = s.precond(dev(p.F)).cpu().numpy()
+        kernel = s.params["step_kernel"]
+        s.close()
+        print(f"\nfull-T 1001 {precision} kernel {kernel}: rel {rel(U, ref):.2e} "
+              f"max {maxrel(U, ref):.2e}")
+        assert rel(U, ref) <= tol and maxrel(U, ref) <= tol, (precision, kernel, rel(U, ref),
+                                                               maxrel(U, ref))
 
 
 @pytest.mark.parametrize("name", ["2d_grf_1001", "3d_layered_256"])
@@ -204,10 +227,11 @@ def test_3d_layered_recipe_at_its_full_T_matches_the_oracle():
     """The 3-D configuration's recipe (4 layers x (1 + 0.1 GRF), 8 points per
     wavelength, layer of the same physical width) on a 64^3 grid with the full
     T = 32 of the 256^3 configuration (384 steps per application): FP64 within
-    1e-10 of the oracle, FP32 within 2e-5, relative L2 and maximum norm."""
+    1e-10 of the oracle, FP32 within fp32_tol(32) = 2.4e-5, relative L2 and
+    maximum norm."""
     p = W.config_3d_layered(64, layer=6, T=32)
     ref = oracle.Oracle(p).precond(p.F)
-    for precision, tol in (("fp64", 1e-10), ("mixed", 2e-5)):
+    for precision, tol in (("fp64", 1e-10), ("mixed", fp32_tol(p.T))):
         s = htd.Solver(p, precision=precision)
         assert s.params["steps"] == 384
         U = s.precond(dev(p.F)).cpu().numpy()

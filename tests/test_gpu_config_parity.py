@@ -238,3 +238,26 @@ def test_3d_layered_recipe_at_its_full_T_matches_the_oracle():
         s.close()
         assert rel(U, ref) <= tol and maxrel(U, ref) <= tol, (precision, rel(U, ref),
                                                                maxrel(U, ref))
+
+
+def test_fp32_error_grows_with_T_within_the_derived_tolerance():
+    """The reading behind fp32_tol: the FP32 recurrence's error against the FP64
+    oracle grows with the number of periods (phase drift from FP32-rounded
+    coefficients) and stays within fp32_tol(T), on a 2-D heterogeneous grid for
+    T = 4, 16, 64.  (It levels off once T exceeds the damping time of the
+    absorbing layer, which forgets the early steps, so fp32_tol is an upper
+    bound.)"""
+    base = W.config_2d_heterogeneous(129)
+    errs = []
+    for T in (4, 16, 64):
+        p = W.config_2d_heterogeneous(129, T=T)
+        s = htd.Solver(p, precision="mixed")
+        U = s.precond(dev(p.F)).cpu().numpy()
+        s.close()
+        ref = oracle.Oracle(p).precond(p.F)
+        e = rel(U, ref)
+        print(f"\nfp32 error T={T}: rel {e:.2e} max {maxrel(U, ref):.2e} tol {fp32_tol(T):.1e}")
+        assert e <= fp32_tol(T) and maxrel(U, ref) <= fp32_tol(T)
+        errs.append(e)
+    assert base.n == (129, 129)
+    assert errs[2] > errs[0]

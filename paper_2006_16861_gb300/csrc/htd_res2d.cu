@@ -493,17 +493,28 @@ res2d_kernel(const T *__restrict__ kap, const T *__restrict__ dco, const T *__re
 
 // the kernel for (precision, RPT rows per strip, row stride SW), for every
 // pair (RPT, SW) a plan may choose
-constexpr int kRpts[] = {3, 5, 8};
+// FP32 strips of 3, 5 or 8 rows; FP64 also of 1 row -- its long-latency FP64
+// pipe makes a thread's chain of dependent rows, not the register window's
+// saved loads, what sets the step time on small tiles
+constexpr int kRpts[] = {1, 3, 5, 8};
+
+template <typename T>
+bool rpt_allowed(int r)
+{
+    return r != 1 || sizeof(T) == 8;
+}
 
 template <typename T, typename Fn>
 void with_kernel(int rpt, int sw, Fn &&fn)
 {
     if (sw == 72) {
-        if (rpt == 3) fn(res2d_kernel<T, 3, 72>);
+        if (rpt == 1) fn(res2d_kernel<T, 1, 72>);
+        else if (rpt == 3) fn(res2d_kernel<T, 3, 72>);
         else if (rpt == 5) fn(res2d_kernel<T, 5, 72>);
         else fn(res2d_kernel<T, 8, 72>);
     } else {
-        if (rpt == 3) fn(res2d_kernel<T, 3, 136>);
+        if (rpt == 1) fn(res2d_kernel<T, 1, 136>);
+        else if (rpt == 3) fn(res2d_kernel<T, 3, 136>);
         else if (rpt == 5) fn(res2d_kernel<T, 5, 136>);
         else fn(res2d_kernel<T, 8, 136>);
     }
@@ -543,7 +554,8 @@ bool plan_impl(const Layout &L, Res2dPlan *out)
     int avail = maxsm;
     bool attr_ok = true;
     for (int sw : kStrides)
-        for (int r : kRpts)
+        for (int r : kRpts) {
+            if (!rpt_allowed<T>(r)) continue;
             with_kernel<T>(r, sw, [&](auto kern) {
                 cudaFuncAttributes fa;
                 if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) {
@@ -556,6 +568,7 @@ bool plan_impl(const Layout &L, Res2dPlan *out)
                           cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                dyn) == cudaSuccess;
             });
+        }
     if (!attr_ok) {
         (void)cudaGetLastError();
         return false;
@@ -594,6 +607,7 @@ bool plan_impl(const Layout &L, Res2dPlan *out)
     best.rpt = kRpts[sizeof(kRpts) / sizeof(kRpts[0]) - 1];
     int best_load = -1;
     for (int r : kRpts) {
+        if (!rpt_allowed<T>(r)) continue;
         const int ld = res2d_load(best.W, best.H, r, res_threads<T>());
         if (ld >= 0 && (best_load < 0 || ld < best_load)) {
             best_load = ld;

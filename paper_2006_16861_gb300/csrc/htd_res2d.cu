@@ -1,5 +1,5 @@
-// Resident-grid 2-D recurrence (FP32, node pairs): the whole grid stays in
-// shared memory, spread over the SMs, for all T n_P steps of a run.
+// Resident-grid 2-D recurrence (FP32 or FP64, node pairs): the whole grid
+// stays in shared memory, spread over the SMs, for all T n_P steps of a run.
 //
 // One cooperative launch runs a whole preconditioner run (Def. of I_acd with
 // Table 1's windowed forcing and read-out).  The grid is cut into ntx x nty
@@ -7,16 +7,19 @@
 // resident at once.  A CTA loads its tile's q*kappa cells, d and forcing once,
 // keeps both recurrence states in shared memory with a one-node ring around
 // the tile, and in every step
-//  - computes the new state of its edge nodes and publishes each edge value
-//    to a global exchange buffer as one 64-bit word (float bits | tag << 32,
-//    tag = index of the state + 1; one buffer per state parity);
-//  - computes its interior nodes in row strips with a 3 x 3 register window,
-//    while the threads that had edge work fetch the neighbours' edges of the
-//    new state into the ring, re-reading a word until it carries the expected
-//    tag (bounded by the handle's wait limit);
+//  - computes the new state of its edge nodes first (one edge pair per
+//    thread) and publishes each edge value to a global exchange buffer as
+//    tagged 64-bit words (tag = index of the state + 1; an FP32 value in one
+//    word with its bits, an FP64 value in two words, one per 32-bit half; one
+//    buffer per state parity);
+//  - computes its interior nodes in row strips with a 3 x 3 register window;
+//    the strip threads also read the neighbours' edge words of the new state
+//    into the ring: each read is issued two rows into the thread's strip and
+//    its tags checked after the strip, re-reading until they are the expected
+//    ones (bounded by the handle's wait limit);
 //  - passes one CTA barrier.
-// Each exchanged value carries its own tag and moves as one 64-bit access,
-// so no fence has to order data before a flag.  A CTA cannot run more than one
+// Each exchanged word carries its own tag and moves as one 64-bit access, so
+// no fence has to order data before a flag.  A CTA cannot run more than one
 // step ahead of a neighbour (it needs the neighbour's edges of the previous
 // state), so two buffers per tile suffice; they are zeroed before every run
 // (tag 0 is never expected).  Nothing else touches global memory between the
@@ -231,9 +234,10 @@ res2d_kernel(const T *__restrict__ kap, const T *__restrict__ dco, const T *__re
     }
 
     // Work of a step, per thread in this order: (1) an edge pair -- rows 0 and
-    // h-1, then the pairs 0 and PL of rows 1 .. h-2 -- dealt from the last
-    // thread down, so that threads without interior work take them first; each
-    // new edge value is published at once; (2) one strip of up to RPT interior
+    // h-1, then the pairs 0 and PL of rows 1 .. h-2 -- dealt one per thread
+    // from the last thread down, so that threads without interior work take
+    // them first (several edge pairs on one thread publish the later ones too
+    // late for the neighbours); each new edge value is published at once; (2) one strip of up to RPT interior
     // rows of an interior column pair 1 .. PL-1 (strip t on thread t); (3) the
     // ring slot of the next state (slot k on thread k): the read of the
     // neighbour's word is issued two rows into the thread's strip and its tag
@@ -491,12 +495,10 @@ res2d_kernel(const T *__restrict__ kap, const T *__restrict__ dco, const T *__re
     }
 }
 
-// the kernel for (precision, RPT rows per strip, row stride SW), for every
-// pair (RPT, SW) a plan may choose
-// FP32 strips of 3, 5 or 8 rows; FP64 also of 1 row -- its long-latency FP64
-// pipe makes a thread's chain of dependent rows, not the register window's
-// saved loads, what sets the step time on small tiles (one-row strips in FP32
-// measured no faster at 101^2)
+// Rows per strip a plan may choose: FP32 3, 5 or 8; FP64 also 1 -- its
+// long-latency FP64 pipe makes a thread's chain of dependent rows, not the
+// register window's saved loads, what sets the step time on small tiles
+// (one-row strips in FP32 measured no faster at 101^2).
 constexpr int kRpts[] = {1, 3, 5, 8};
 
 template <typename T>
@@ -505,6 +507,7 @@ bool rpt_allowed(int r)
     return r != 1 || sizeof(T) == 8;
 }
 
+// fn(the kernel for precision T, RPT rows per strip, row stride SW)
 template <typename T, typename Fn>
 void with_kernel(int rpt, int sw, Fn &&fn)
 {

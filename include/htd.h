@@ -148,12 +148,15 @@ typedef struct {
                           tile per SM, each CTA keeps its tile's states and
                           coefficients in shared memory for all T n_P steps
                           and swaps edge values with its neighbours through
-                          global memory every step.  It qualifies for a
-                          handle with max_rhs 1, Table 1 or exact read-out and
-                          a grid whose tiles fit the shared memory of one SM
-                          (about 1.3 M nodes on 152 SMs); a handle that joins
-                          a batch leaves it for its tuned blocked
-                          configuration */
+                          global memory every step (in projection mode it
+                          also accumulates the window's states).  It
+                          qualifies for a handle with max_rhs 1 and a grid
+                          whose tiles fit the shared memory of one SM (about
+                          1.1 M nodes on 152 SMs with the FP32 recurrence,
+                          0.5 M with FP64); the FP64 recurrence times it
+                          against the one-step kernel when tblock is 0.  A
+                          handle that joins a batch leaves it for its tuned
+                          blocked configuration */
     int s3_kernel;     /* 3-D FP32 step kernel: HTD_S3_PAIR (TMA-streamed z
                           planes, node pairs; default), HTD_S3_ZMARCH (one step
                           per launch, register z-march), HTD_S3_NODE_32x8,

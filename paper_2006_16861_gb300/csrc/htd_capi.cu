@@ -164,6 +164,7 @@ struct htd_ctx {
     htd::Res2dPlan res{};
     bool use_res = false;
     void *res_ab = nullptr;                 // a_j, b_j per step, in the recurrence precision
+    void *res_w = nullptr;                  // projection weights per phase (PROJECT)
     unsigned long long *res_x = nullptr;    // edge exchange buffer
     // TMA-streamed 3-D step (FP32)
     htd::Stream3Maps s3maps{};
@@ -230,7 +231,7 @@ void free_ctx(htd_ctx *c)
     void *dev[] = {c->kap, c->dco, c->fre, c->fim, c->u0, c->u1, c->kap64, c->imH, c->coefP, c->coefI, c->V, c->Z,
                    c->w, c->t, c->r, c->partial, c->hdev, c->slot, c->Fh, c->Uh, c->u2, c->u3,
                    c->err_dev, c->gU, c->gMu, c->gR, c->gres, c->grec, c->act_dev,
-                   c->acc, c->td_ws, c->res_ab, c->res_x};
+                   c->acc, c->td_ws, c->res_ab, c->res_x, c->res_w};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (c->hhost) cudaFreeHost(c->hhost);
@@ -259,11 +260,26 @@ htd_status run_steps_direct(htd_ctx *c, cudaStream_t s)
     const bool project = c->opt.mode == HTD_MODE_PROJECT;
     const long long jim = project ? -1 : c->nsteps - c->nP / 4;
     const long long jfin = project ? -1 : c->nsteps;
-    if (c->use_res && !project) {
-        // the whole run in one launch; the global state planes are not used
+    if (c->use_res) {
+        // the whole run in one launch; the global state planes are not used.
+        // PROJECT: the kernel accumulates the window's states itself, then the
+        // finishing kernel writes (2 / n_acc) times the sums
+        htd::Res2dProj<T> P;
+        const long long n_res = project ? (long long)c->opt.proj_periods * c->nP : 0;
+        if (project) {
+            P.j_acc = (int)(c->nsteps - n_res);
+            P.nP = c->nP;
+            P.w = (const T *)c->res_w;
+            P.acc = (T *)c->acc;
+            P.N = L.N;
+            HTD_CUDA(cudaMemsetAsync(c->acc, 0, sizeof(T) * 4 * L.N, s));
+        }
         htd::launch_res2d<T>(c->res, (const T *)c->kap, (const T *)c->dco, (const T *)c->fre,
                              (const T *)c->fim, L, C, (const T *)c->res_ab, (int)c->nsteps,
-                             (int)jim, (int)jfin, c->slot, c->res_x, c->err_dev, s);
+                             (int)jim, (int)jfin, c->slot, c->res_x, c->err_dev, s, P);
+        if (project)
+            htd::launch_project_finish<T>(L.N, (const T *)c->acc, 4 * L.N, 2.0 / (double)n_res,
+                                          c->slot, c->Rs, s);
         HTD_CUDA(cudaGetLastError());
         return HTD_OK;
     }
@@ -660,8 +676,20 @@ htd_status upload_recurrence(htd_ctx *c, const std::vector<double> &qkap, const 
 template <typename T>
 htd_status try_res2d(htd_ctx *c, bool force, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1)
 {
-    if (c->rcap != 1 || c->opt.mode == HTD_MODE_PROJECT || c->nsteps >= (1LL << 30)) return HTD_OK;
+    if (c->rcap != 1 || c->nsteps >= (1LL << 30)) return HTD_OK;
     if (!htd::res2d_plan<T>(c->Lr, &c->res)) return HTD_OK;
+    if (c->opt.mode == HTD_MODE_PROJECT) {
+        // projection weights per phase k of the new state: cos and -sin of
+        // 2 pi k / nP, rounded as for the separate accumulation kernel
+        std::vector<T> w(2 * (size_t)c->nP);
+        for (int k = 0; k < c->nP; ++k) {
+            const double th = 2.0 * kPi * (double)k / (double)c->nP;
+            w[2 * k] = (T)std::cos(th);
+            w[2 * k + 1] = (T)(-std::sin(th));
+        }
+        HTD_CUDA(htd::dev_malloc(&c->res_w, sizeof(T) * w.size()));
+        HTD_CUDA(cudaMemcpy(c->res_w, w.data(), sizeof(T) * w.size(), cudaMemcpyHostToDevice));
+    }
     std::vector<T> ab(2 * (size_t)c->nsteps);
     for (long long j = 0; j < c->nsteps; ++j) {
         ab[2 * j] = (T)c->atab[j];
@@ -689,8 +717,10 @@ htd_status try_res2d(htd_ctx *c, bool force, cudaStream_t s, cudaEvent_t e0, cud
     } else {
         cudaFree(c->res_ab);
         cudaFree(c->res_x);
+        cudaFree(c->res_w);
         c->res_ab = nullptr;
         c->res_x = nullptr;
+        c->res_w = nullptr;
     }
     return HTD_OK;
 }

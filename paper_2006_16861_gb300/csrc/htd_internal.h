@@ -375,6 +375,20 @@ struct Res2dPlan {
     size_t xwords = 0;           // exchange buffer words
 };
 
+// Projection read-out inside the resident run: the new states of steps j >=
+// j_acc are accumulated, with the compensated sums of the separate
+// accumulation kernel, into acc (planes [s_re, s_im, c_re, c_im] of N compact
+// nodes) with weights w[2k] = cos theta_k, w[2k+1] = -sin theta_k, k = (j + 1)
+// mod nP.  j_acc >= nsteps: no accumulation.
+template <typename T>
+struct Res2dProj {
+    int j_acc = 1 << 30;
+    int nP = 1;
+    const T *w = nullptr;
+    T *acc = nullptr;
+    int64_t N = 0;
+};
+
 // The plan for a 2-D grid in precision T, or false if the grid does not fit
 // the SMs' shared memory at one tile per SM, or the device cannot launch
 // cooperatively.
@@ -388,7 +402,7 @@ template <typename T>
 void launch_res2d(const Res2dPlan &p, const T *kap, const T *dco, const T *fre, const T *fim,
                   const Layout &L, const StepCoef<T> &C, const T *ab, int nsteps, int jim,
                   int jfin, const OutSlot *slot, unsigned long long *xbuf, int *err,
-                  cudaStream_t s);
+                  cudaStream_t s, const Res2dProj<T> &P = Res2dProj<T>{});
 
 // ---- one persistent launch for many 2-D instances (htd_tblock.cu) -----------
 //

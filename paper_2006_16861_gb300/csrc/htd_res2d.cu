@@ -192,7 +192,7 @@ res2d_kernel(const T *__restrict__ kap, const T *__restrict__ dco, const T *__re
              const T *__restrict__ fim, Layout L, StepCoef<T> C,
              const typename PairOf<T>::V *__restrict__ ab, int nsteps, int jim, int jfin,
              const OutSlot *__restrict__ slot, unsigned long long *__restrict__ xbuf,
-             int *__restrict__ err, int W, int H)
+             int *__restrict__ err, int W, int H, Res2dProj<T> P)
 {
     typedef typename PairOf<T>::V V;
     typedef Xword<T> X;
@@ -492,6 +492,28 @@ res2d_kernel(const T *__restrict__ kap, const T *__restrict__ dco, const T *__re
             }
         __syncthreads();
         if (s_abort) break;
+        // projection read-out: the compensated accumulation of u_{j+1} (complete
+        // in nxt, which the next step only reads) into the sums and
+        // compensations (re, im), as the separate accumulation kernel does it,
+        // the tile's nodes in compact order
+        if (j >= P.j_acc) {
+            const int k = (j + 1) % P.nP;
+            const T wc = P.w[2 * k], ws = P.w[2 * k + 1];
+            T *a = P.acc;
+            for (int i = tid; i < w * h; i += NT) {
+                const int ly = i / w, lx = i - ly * w;
+                const int64_t c = ((int64_t)blockIdx.y * H + ly) * L.nx +
+                                  (int64_t)blockIdx.x * W + lx;
+                const T v = nxt[(ly + 1) * SW + lx + 2];
+                T sr = a[c], si = a[P.N + c], cr = a[2 * P.N + c], ci = a[3 * P.N + c];
+                const T yr = wc * v - cr, yi = ws * v - ci;
+                const T tr = sr + yr, ti = si + yi;
+                a[2 * P.N + c] = (tr - sr) - yr;
+                a[3 * P.N + c] = (ti - si) - yi;
+                a[c] = tr;
+                a[P.N + c] = ti;
+            }
+        }
     }
 }
 
@@ -646,7 +668,7 @@ template <typename T>
 void launch_res2d(const Res2dPlan &p, const T *kap, const T *dco, const T *fre, const T *fim,
                   const Layout &L, const StepCoef<T> &C, const T *ab, int nsteps, int jim,
                   int jfin, const OutSlot *slot, unsigned long long *xbuf, int *err,
-                  cudaStream_t s)
+                  cudaStream_t s, const Res2dProj<T> &P)
 {
     (void)cudaMemsetAsync(xbuf, 0, p.xwords * sizeof(unsigned long long), s);
     cudaLaunchConfig_t cfg = {};
@@ -662,7 +684,7 @@ void launch_res2d(const Res2dPlan &p, const T *kap, const T *dco, const T *fre, 
     const auto *abv = reinterpret_cast<const typename PairOf<T>::V *>(ab);
     with_kernel<T>(p.rpt, p.sw, [&](auto kern) {
         (void)cudaLaunchKernelEx(&cfg, kern, kap, dco, fre, fim, L, C, abv, nsteps, jim, jfin,
-                                 slot, xbuf, err, p.W, p.H);
+                                 slot, xbuf, err, p.W, p.H, P);
     });
     ++g_launches;
 }
@@ -672,10 +694,12 @@ template bool res2d_plan<double>(const Layout &, Res2dPlan *);
 template void launch_res2d<float>(const Res2dPlan &, const float *, const float *, const float *,
                                   const float *, const Layout &, const StepCoef<float> &,
                                   const float *, int, int, int, const OutSlot *,
-                                  unsigned long long *, int *, cudaStream_t);
+                                  unsigned long long *, int *, cudaStream_t,
+                                  const Res2dProj<float> &);
 template void launch_res2d<double>(const Res2dPlan &, const double *, const double *,
                                    const double *, const double *, const Layout &,
                                    const StepCoef<double> &, const double *, int, int, int,
-                                   const OutSlot *, unsigned long long *, int *, cudaStream_t);
+                                   const OutSlot *, unsigned long long *, int *, cudaStream_t,
+                                   const Res2dProj<double> &);
 
 }  // namespace htd

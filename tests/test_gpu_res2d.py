@@ -226,3 +226,32 @@ def test_fp64_resident_wait_runs_out_then_the_handle_solves():
     U.zero_()
     assert htd.htd_gmres_solve(s.handle, F, U, 1e-6, 100)["converged"]
     s.close()
+
+
+# ---- projection read-out inside the resident run --------------------------------
+
+@pytest.mark.parametrize("precision,periods", [("mixed", 1), ("mixed", 2), ("fp64", 1)])
+def test_resident_projection_matches_the_oracle(precision, periods):
+    """PROJECT mode on the resident kernel: the window's states are accumulated
+    inside the launch (compensated sums, compact order, after each window
+    step's barrier) and finished by the same kernel as the other paths.
+    Against the oracle (2e-5 FP32, 1e-10 FP64) and against the one-step path."""
+    p = _problem((129, 161), T=3)
+    tol = 2e-5 if precision == "mixed" else 1e-10
+    sr = htd.Solver(p, precision=precision, mode="project", proj_periods=periods,
+                    tb_form=htd.TB_RESIDENT)
+    s1 = htd.Solver(p, precision=precision, mode="project", proj_periods=periods, tblock=1)
+    assert sr.params["step_kernel"] == 4 and s1.params["step_kernel"] == 0
+    o = oracle.Oracle(p)
+    for F in (p.F, W.random_rhs(3, p.n)):
+        Ur = sr.precond(dev(F)).cpu().numpy()
+        U1 = s1.precond(dev(F)).cpu().numpy()
+        ref = o.precond(F, "project", periods)
+        a, b = Ur.reshape(-1), ref.reshape(-1)
+        assert np.linalg.norm(a - b) / np.linalg.norm(b) <= tol
+        assert np.abs(a - b).max() / np.abs(b).max() <= tol
+        c = U1.reshape(-1)
+        assert np.linalg.norm(a - c) / np.linalg.norm(c) <= (1e-6 if precision == "mixed"
+                                                             else 1e-13)
+    sr.close()
+    s1.close()
